@@ -1,0 +1,346 @@
+#!/usr/bin/env python3
+"""Throughput of the phase-space lattice step on GB300, in phase-space cell updates per second.
+
+Default workload: the 1D ensemble -- 4096 independent seeded flow realisations with N_x drawn
+uniformly from {1024, 2048, 4096, 8192}, N_v = 65, St cycling {0.1, 1, 10}, FP32 storage,
+advanced by one persistent launch per step captured in one CUDA graph.  A "step" advances every
+instance by one lattice time step (stream, drag, diffusion).  The inputs (two 4.1 GB ping-pong
+buffers) are larger than L2, so no flush is needed between steps.
+
+--impl reference times the FP64 CPU oracle on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "phase-space cell updates/s (GCUPS) and % HBM roofline, plain vs FP16/learned"
+UNIT = "GCUPS"
+NV = 65
+N_INST = 4096
+SEED = 1234
+WORKLOAD = ("1D ensemble FP32: 4096 seeded OU flow realisations, N_x uniform over "
+            "{1024,2048,4096,8192}, N_v=65, St in {0.1,1,10}, kappa=1e-3")
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=200)
+    p.add_argument("--warmup", type=int, default=5)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--cpu-seconds", type=float, default=10.0)
+    p.add_argument("--instances", type=int, default=N_INST,
+                   help="ensemble size (smaller cases are for profiling only)")
+    p.add_argument("--no-autotune", action="store_true")
+    p.add_argument("--no-per-instance", action="store_true")
+    return p.parse_args()
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            pk = json.load(fh)
+        return float(pk["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def profile_traffic(kernel_file: str, src: str):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken on this source."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", kernel_file)
+    try:
+        txt = open(path).read()
+    except OSError:
+        return None
+    h = hashlib.sha256(open(os.path.join(ROOT, src), "rb").read()).hexdigest()[:16]
+    vals = {}
+    for line in txt.splitlines():
+        if ":" in line and line.strip().startswith(("traffic_bytes_per_launch", "source_sha256",
+                                                    "units_per_launch")):
+            k, v = line.split(":", 1)
+            vals[k.strip().lstrip("- ")] = v.strip().strip("`")
+    if vals.get("source_sha256") != h or "traffic_bytes_per_launch" not in vals:
+        return None
+    return float(vals["traffic_bytes_per_launch"]), float(vals.get("units_per_launch", "nan"))
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "100", "-f", self.path],
+                stdout=subprocess.DEVNULL, stderr=subprocess.DEVNULL)
+            time.sleep(0.3)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.15)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        try:
+            for line in open(self.path):
+                p = [x.strip() for x in line.split(",")]
+                if len(p) >= 9:
+                    rows.append(p)
+            os.unlink(self.path)
+        except Exception:
+            return None
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i] == "Active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+                "samples": len(rows)}
+
+
+# ---------------------------------------------------------------------------------------------
+# CPU oracle timing (the reference arm and the cpu_baseline leg)
+# ---------------------------------------------------------------------------------------------
+class OracleSample:
+    """The FP64 oracle, as it stands, on the first instances of the benchmark ensemble
+    (about `sample_cells` phase-space cells per step)."""
+
+    def __init__(self, sample_cells: int = 2_000_000):
+        from oracle import lattice as O
+        from paper_1508_02899_gb300 import inputs as I
+        self.O = O
+        self.tab = I.ensemble_table(N_INST, SEED, nv=NV)
+        self.idx, self.cells = [], 0
+        while self.cells < sample_cells:
+            self.idx.append(len(self.idx))
+            self.cells += int(self.tab.nx[self.idx[-1]]) * NV
+        f0 = I.ensemble_initial(self.tab, NV, None, None, instances=self.idx)
+        self.fl = I.flow1d_inputs(SEED, 1, n_inst=len(self.idx))
+        self.state = {i: (f0[i], self.fl.amp0[j].copy()) for j, i in enumerate(self.idx)}
+
+    def step(self):
+        O, tab, fl = self.O, self.tab, self.fl
+        for j, i in enumerate(self.idx):
+            f, amp = self.state[i]
+            nx = int(tab.nx[i])
+            dv = (tab.L[i] / nx) / tab.dt[i]
+            u = O.flow1d_u(amp, fl.k, nx)
+            f = O.step_1d(f, u, tab.tau_p[i], tab.kappa[i], tab.dt[i], dv)
+            amp = O.ou_advance(amp, fl.noise[0, j], tab.dt[i], fl.tau_f, fl.sigma)
+            self.state[i] = (f, amp)
+
+    def describe(self, steps):
+        return (f"first {len(self.idx)} of 4096 instances ({self.cells} cells per step), "
+                f"{steps} steps")
+
+    def time_for(self, budget_s: float):
+        steps, t0 = 0, time.perf_counter()
+        while True:
+            self.step()
+            steps += 1
+            el = time.perf_counter() - t0
+            if el >= budget_s:
+                return steps, el
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    smp = OracleSample()
+    for _ in range(args.warmup):
+        smp.step()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        smp.step()
+    el = time.perf_counter() - t0
+    value = smp.cells * args.steps / el / 1e9
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1000 * el / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "reference": "FP64 CPU oracle (numpy, one core)",
+                   "sample": smp.describe(args.steps)},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": smp.describe(args.steps)},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "gpu_launches": 0,
+    }
+    print(json.dumps(line))
+    return 0
+
+
+# ---------------------------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------------------------
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    import torch
+    import torch.distributed as dist
+
+    from paper_1508_02899_gb300 import inputs as I
+    from paper_1508_02899_gb300 import lat
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=dev)
+
+    K, W = args.steps, args.warmup
+    n_inst = args.instances
+    tab = I.ensemble_table(n_inst, SEED + rank, nv=NV)
+    total_steps = W + K + 1
+    fl = I.flow1d_inputs(SEED + 7 + rank, total_steps, n_inst=n_inst)
+    f0 = I.ensemble_initial(tab, NV, torch.float32, dev)
+    ens = lat.Ensemble(f0, nv=NV, nx=tab.nx, L=tab.L, tau_p=tab.tau_p, kappa=tab.kappa,
+                       dt=tab.dt)
+    ens.set_flow_modes(fl.k, fl.amp0, fl.tau_f, fl.sigma)
+    ens.set_noise(fl.noise)
+    cells = int(tab.nx.sum()) * NV
+    best = None if args.no_autotune else ens.autotune(reps=3)
+
+    # unbatched baseline: one launch per instance per step (context, not the headline)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    per_inst_ms = None
+    if not args.no_per_instance:
+        ens.set_launch(mode=1)
+        torch.cuda.synchronize()
+        ev0.record()
+        ens.step(1)
+        ev1.record()
+        torch.cuda.synchronize()
+        per_inst_ms = ev0.elapsed_time(ev1)
+        ens.set_launch(mode=0)
+
+    ens.prepare(W)
+    ens.prepare(K)
+    ens.step(W)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    clocks.start()
+    ev0.record()
+    ens.step(K)
+    ev1.record()
+    torch.cuda.synchronize()
+    ck = clocks.stop()
+    if world > 1:
+        dist.barrier()
+    ms = ev0.elapsed_time(ev1)
+    t = torch.tensor([ms], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms_max = float(t.item())
+    status = ens.status()
+
+    value = world * cells * K / (ms_max / 1e3) / 1e9
+
+    # end to end through the C ABI with host buffers: per step, the step's noise row from
+    # pinned host memory, one step, and the per-instance moments back to host memory
+    noise_rows = torch.from_numpy(np.ascontiguousarray(fl.noise[:1])).pin_memory()
+    glob = np.zeros((n_inst, 3))
+    K_e2e = max(3, min(K, 50))
+    ens.prepare(1)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(K_e2e):
+        ens.set_noise_pinned(noise_rows)
+        ens.step(1)
+        ens.moments(per_cell=False, globals_out=glob)
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    e2e_value = world * cells * K_e2e / e2e_s / 1e9
+
+    peak, peak_src = measured_peaks()
+    bytes_per_launch = cells * 8  # one FP32 read and one FP32 write of every cell
+    ms_launch = ms_max / K
+    achieved = bytes_per_launch / (ms_launch / 1e3) / 1e9
+    tr = profile_traffic("step1d_ensemble_fp32_nv65.md", "paper_1508_02899_gb300/csrc/step1d.cu")
+    traffic = None
+    if tr is not None:
+        tb, units = tr
+        traffic = tb * (cells / units) if units == units and units > 0 else tb
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        smp = OracleSample()
+        c_steps, c_el = smp.time_for(args.cpu_seconds)
+        cpu = {"value": smp.cells * c_steps / c_el / 1e9, "unit": UNIT, "cores": 1,
+               "kind": "oracle", "sample": smp.describe(c_steps)}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K,
+            "warmup": W, "ms_per_step": ms_max / K, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD if n_inst == N_INST else
+                       f"{WORKLOAD} (profiling case: {n_inst} instances)",
+                       "instances": n_inst, "nv": NV,
+                       "cells_per_step_per_gpu": cells,
+                       "l2": "inputs larger than L2 (two 4.1 GB FP32 buffers); no flush",
+                       "launch": best, "status": status},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": traffic,
+                         "peak_source": peak_src, "kernel": "k_step1d_reg<float,65>",
+                         "bytes_per_launch": bytes_per_launch},
+            "cpu_baseline": cpu,
+            "e2e": {"value": e2e_value, "unit": UNIT, "steps": K_e2e,
+                    "h2d_bytes_per_step": int(noise_rows.numel() * 8),
+                    "d2h_bytes_per_step": int(glob.size * 8)},
+            "gpu_launches": K + 1,
+            "clocks": ck,
+            "batching": {"persistent_graph_gcups": value / world,
+                         "per_instance_launch_gcups":
+                             None if per_inst_ms is None else cells / (per_inst_ms / 1e3) / 1e9},
+        }
+        print(json.dumps(line))
+    ens.close()
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,180 @@
+/*
+ * lat.h - C ABI of the GB300 phase-space lattice library.
+ *
+ * The library advances the discretised phase-space density f(x, v, t) of heavy inertial
+ * particles (Laenen, Krstulovic & Bec, arXiv:1508.02899) by the lattice method of Section 2:
+ * an exact streaming shift in x by the lattice velocity index (dx = dv dt), a first-order
+ * upwind finite-volume step of the Stokes drag a = -(v - u(x,t))/tau_p of Eq. (stokes_drag),
+ * and a finite-volume velocity diffusion with coefficient kappa (Eq. conslaw), with zero flux
+ * through the walls of the velocity box.  Every step runs in this library's CUDA kernels on
+ * one GPU; there is no CPU fallback.
+ *
+ * Conventions shared by every call:
+ *  - Every call returns an int status (LAT_OK = 0 or one of the LAT_E* codes below) except
+ *    lat_strerror, lat_free and the small getters.  A failed call leaves the context as it
+ *    was unless the code is LAT_ECUDA (the CUDA context may then be unusable).
+ *  - Velocity lattice: N_v odd, J = (N_v - 1)/2, v_j = j dv for j = -J..J, dv = dx / dt,
+ *    dx = L / N_x (Section 2; the cell centres span [-V_max, V_max] with V_max = J dv).
+ *  - Layout of f in device memory, element type given by dtype, densely packed:
+ *        d = 1: f[j][x]          (x fastest), N_v * N_x elements per instance;
+ *               ensemble instances are concatenated in instance order.
+ *        d = 2: f[jy][jx][y][x]  (x fastest), N_v^2 * N_y * N_x elements.
+ *    f is a density: the mass of a cell is f dx^d dv^d (Section 3.2 normalisation).
+ *  - Ownership: the caller owns the two device buffers f_a and f_b passed to lat_init /
+ *    lat_ensemble_init and any device field passed to lat_set_flow; they must outlive the
+ *    context.  Each step reads the current buffer and writes the other one; lat_current
+ *    tells which one holds the state.  The context owns only its own scratch (flow state,
+ *    noise table, reduction partials, CUDA graphs) and frees it in lat_free.
+ *  - All work is enqueued on the stream given at init (NULL = legacy default stream);
+ *    lat_step is asynchronous, lat_moments and lat_status synchronise that stream.
+ *  - Device-side conditions (CFL exceeded by the evolving flow, exhausted noise table,
+ *    non-finite values, FP16 scale overflow) are recorded in a device status word and
+ *    reported by the next synchronising call (lat_moments, lat_status).
+ */
+#ifndef LAT_H
+#define LAT_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ---- */
+#define LAT_OK 0
+#define LAT_EINVAL 1     /* bad argument (null pointer, size, layout, unsupported N_v) */
+#define LAT_ECFL 2       /* Eq. (cfl) or Eq. (stabLapl) violated (host check or device flag) */
+#define LAT_ENOMEM 3     /* device allocation of context scratch failed */
+#define LAT_ECUDA 4      /* a CUDA runtime call failed */
+#define LAT_ENUMERIC 5   /* non-finite value met in f (found by lat_moments) */
+#define LAT_ETIMEOUT 6   /* a bounded device wait gave up */
+#define LAT_EOVERFLOW 7  /* a reduced-precision value exceeded its line scale */
+#define LAT_ENOISE 8     /* a step ran past the end of the noise table (flow frozen then) */
+
+/* ---- storage types of f ---- */
+#define LAT_F64 0
+#define LAT_F32 1
+#define LAT_F16 2
+#define LAT_BF16 3
+
+/* ---- flow kinds (lat_flow.kind) ---- */
+#define LAT_FLOW_NONE 0   /* u = 0 */
+#define LAT_FLOW_FIELD 1  /* caller's device field, frozen until the next lat_set_flow */
+#define LAT_FLOW_MODES 2  /* synthetic random flow evolved on the device every step */
+
+typedef struct lat_ctx lat_ctx;
+
+/* One lattice (Section 2).  d = 1: ny must be 1.  d = 2: the domain is nx*dx by ny*dx. */
+typedef struct {
+    int d;          /* spatial dimension, 1 or 2 */
+    int nx, ny;     /* spatial cells */
+    int nv;         /* velocity cells per component, odd, 1..129 */
+    int dtype;      /* LAT_F64, LAT_F32 (d = 1, 2); LAT_F16, LAT_BF16 (d = 2) */
+    double L;       /* period along x: dx = L / nx */
+    double tau_p;   /* Stokes time of Eq. (stokes_drag); +inf switches the drag off */
+    double kappa;   /* velocity diffusion coefficient of Eq. (conslaw), >= 0 */
+    double dt;      /* time step; dv = dx / dt */
+} lat_grid;
+
+/* One member of a 1D ensemble (independent realisation, own size and parameters). */
+typedef struct {
+    int nx;
+    double L, tau_p, kappa, dt;
+} lat_instance;
+
+/*
+ * Carrier flow u(x, t).
+ *  FIELD: `field` is a device array of d * ny * nx values (component-major: all u_x, then
+ *    all u_y), double for LAT_F64 contexts and float otherwise.  For an ensemble it holds the
+ *    instances' fields concatenated.  Not copied: it must stay valid while steps run.
+ *  MODES, d = 1 (Sec. 3.1 Eq. u1d/A1d with M modes):
+ *    u(x_i) = sum_m A_m cos(2 pi k_m i / N_x) + B_m sin(2 pi k_m i / N_x), with amplitudes
+ *    that are Ornstein-Uhlenbeck processes of correlation time tau_f and stationary standard
+ *    deviation sigma, updated exactly after every step:
+ *        A <- A e^{-dt/tau_f} + sigma sqrt(1 - e^{-2 dt/tau_f}) xi,  xi ~ N(0,1) from the
+ *    noise table (lat_set_noise).  k: host [M] wavenumbers; amp0: host [n_inst][2M] initial
+ *    (A_0..A_{M-1}, B_0..B_{M-1}).  M <= 16.
+ *  MODES, d = 2 (incompressible random-phase flow): psi = sum_m a_m cos(theta_m),
+ *    theta_m = 2 pi (kx_m i / N_x + ky_m l / N_y) + phi_m, u = (d_y psi, -d_x psi); phases
+ *    walk as phi <- phi + sqrt(2 dt / tau_f) xi.  k: host [M][2]; amp0: host [M] amplitudes
+ *    a_m; phase0: host [M] initial phases.  M <= 512.
+ *  tau_f <= 0 or infinite freezes the flow (no noise is consumed).
+ * Step n uses the flow at t_n, then the flow state advances to t_{n+1}.
+ */
+typedef struct {
+    int kind;
+    const void* field;
+    int nmodes;
+    const int* k;
+    const double* amp0;
+    const double* phase0;
+    double tau_f;
+    double sigma;
+} lat_flow;
+
+/* Create a context for one lattice.  f_a holds the initial state; f_b is the other ping-pong
+ * buffer (same size).  stream: a cudaStream_t or NULL.  Returns LAT_ECFL if the lattice is
+ * unstable at rest: (dt/dv) J dv / tau_p > 1 (Eq. cfl with u = 0) or 2 d kappa dt/dv^2 > 1
+ * (Eq. stabLapl generalised to d dimensions). */
+int lat_init(lat_ctx** out, const lat_grid* g, void* f_a, void* f_b, void* stream);
+
+/* Create a context for n_inst independent 1D lattices sharing N_v and dtype (F64 or F32),
+ * advanced together by one persistent launch per step (captured in a CUDA graph). */
+int lat_ensemble_init(lat_ctx** out, int n_inst, const lat_instance* inst, int nv, int dtype,
+                      void* f_a, void* f_b, void* stream);
+
+/* Set the carrier flow (see lat_flow).  Resets the noise table. */
+int lat_set_flow(lat_ctx* c, const lat_flow* flow);
+
+/* Copy `rows` steps of standard normal draws from host memory into the context's noise table;
+ * row r feeds the flow update after the r-th following step.  Layout: d = 1 [rows][n_inst][2M],
+ * d = 2 [rows][M].  Pinned host memory makes the copy asynchronous. */
+int lat_set_noise(lat_ctx* c, const double* noise, long long rows);
+
+/* Enqueue n time steps (Section 2: stream, drag, diffuse) on the context's stream.  In the
+ * default launch mode the n steps are one CUDA-graph launch; the graph is captured on first use
+ * of that n and cached (see lat_prepare). */
+int lat_step(lat_ctx* c, int n);
+
+/* Capture and instantiate the graph for n steps now, without running it, so that a later
+ * lat_step(c, n) does no capture work. */
+int lat_prepare(lat_ctx* c, int n);
+
+/* Velocity moments of the current state (Sec. 3.2 normalisation; Sec. 4.2 density by summing
+ * over v).  Per-cell outputs are DEVICE arrays of doubles (any may be NULL):
+ *   rho = sum_j f dv^d;  mean_v = sum_j v_j f / sum_j f (d arrays of cells, component-major);
+ *   mean_v2 = sum_j |v_j|^2 f / sum_j f; mean values are 0 where rho = 0.
+ * `globals` is a HOST array (may be NULL): per instance [M, P_1..P_d, E] = sum f dx^d dv^d
+ * times [1, v_1..v_d, |v|^2], formed with compensated (Neumaier) FP64 sums in a fixed order.
+ * Synchronises; returns the pending device status (LAT_ECFL, LAT_ENUMERIC, ...) if any. */
+int lat_moments(lat_ctx* c, double* rho, double* mean_v, double* mean_v2, double* globals);
+
+/* Synchronise, return and clear the pending device status. */
+int lat_status(lat_ctx* c);
+
+/* 0 if f_a holds the current state, 1 if f_b does. */
+int lat_current(const lat_ctx* c);
+
+/* Steps taken since init. */
+long long lat_steps_done(const lat_ctx* c);
+
+/* Launch shape of the step kernel: threads per block, x columns per thread, resident blocks
+ * per SM for the persistent grid, and mode 0 = one persistent launch over all instances,
+ * 1 = one launch per instance (the unbatched baseline).  Zeros keep the current values. */
+int lat_set_launch(lat_ctx* c, int block, int xpt, int blocks_per_sm, int mode);
+
+/* Time candidate launch shapes on the current state without advancing it (reads the current
+ * buffer, writes the other) and keep the fastest.  best[4] (host, may be NULL) receives
+ * {block, xpt, blocks_per_sm, microseconds per step}. */
+int lat_autotune(lat_ctx* c, int reps, double* best);
+
+/* Human-readable text of a status code. */
+const char* lat_strerror(int status);
+
+/* Release the context's scratch.  Does not touch f_a, f_b or a caller's field. */
+void lat_free(lat_ctx* c);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LAT_H */

@@ -1,0 +1,22 @@
+// Internal interface of the 2D lattice context (step2d.cu), used by lat_api.cu.
+#pragma once
+
+#include "lat_internal.h"
+
+namespace lat {
+
+struct Ctx2D;
+
+int ctx2d_create(Ctx2D** out, const lat_grid* g, DevState* st, int sm_count, cudaStream_t s);
+int ctx2d_set_flow(Ctx2D* c, const lat_flow* fl, bool frozen, cudaStream_t s);
+int ctx2d_set_noise(Ctx2D* c, const double* noise, long long rows, long long step,
+                    cudaStream_t s);
+int ctx2d_step(Ctx2D* c, void* const f[2], int n, cudaStream_t s);
+int ctx2d_prepare(Ctx2D* c, void* const f[2], int n);
+int ctx2d_moments(Ctx2D* c, const void* f, double* rho, double* mean_v, double* mean_v2,
+                  double* globals, cudaStream_t s);
+int ctx2d_set_launch(Ctx2D* c, int block, int xpt, int bps, int mode);
+int ctx2d_autotune(Ctx2D* c, void* const f[2], int reps, double* best, cudaStream_t s);
+void ctx2d_destroy(Ctx2D* c);
+
+}  // namespace lat

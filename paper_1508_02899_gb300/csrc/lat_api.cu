@@ -1,0 +1,603 @@
+// Host side of the C ABI declared in include/lat.h: argument validation, the stability checks
+// of Eq. (cfl) and Eq. (stabLapl), context scratch, CUDA-graph capture of multi-step runs,
+// the launch-shape autotuner and the moment reductions.
+#include <math.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <map>
+#include <tuple>
+#include <vector>
+
+#include "lat_internal.h"
+#include "lat2d.h"
+
+using namespace lat;
+
+namespace {
+
+__global__ void k_set_noise_window(DevState* st, long long base, long long rows) {
+    st->noise_base = base;
+    st->noise_rows = rows;
+}
+__global__ void k_clear_status(DevState* st) { st->status = 0u; }
+
+}  // namespace
+
+struct lat_ctx {
+    int d = 1;
+    int dtype = LAT_F32;
+    int nv = 0;
+    int n_inst = 0;
+    cudaStream_t stream = nullptr;
+    cudaStream_t cap = nullptr;      // capture stream (graphs are launched on `stream`)
+    void* f[2] = {nullptr, nullptr};
+    int cur = 0;
+    long long h_step = 0;
+    int sm_count = 0;
+
+    // 1D instances and work items
+    std::vector<Inst1D> h_inst;
+    Inst1D* d_inst = nullptr;
+    long long total_x = 0;
+    int2* d_items = nullptr;
+    int* d_inst_begin = nullptr;
+    std::vector<int> h_inst_begin;
+    int nitems = 0;
+    double* d_partials = nullptr;
+    double* d_glob = nullptr;
+    double* h_glob = nullptr;       // pinned
+
+    // flow
+    int flow_kind = LAT_FLOW_NONE;
+    int nmodes = 0;
+    int k1d[kMaxModes1D] = {0};
+    bool frozen = true;
+    const void* field = nullptr;
+    double* d_amp = nullptr;        // [2][n_inst][2M]
+    long long amp_stride = 0;
+    double* d_noise = nullptr;
+    long long noise_cap = 0;        // doubles
+    long long noise_row_len = 0;    // doubles per row
+
+    DevState* d_state = nullptr;
+    DevState* h_state = nullptr;    // pinned
+
+    // launch shape
+    int block = 256, xpt = 1, bps = 4, mode = 0;
+
+    // cached graphs keyed by the number of steps (buffers are picked by the device step parity)
+    std::map<int, cudaGraphExec_t> graphs;
+
+    // 2D
+    Ctx2D* c2 = nullptr;
+};
+
+namespace {
+
+int cuda_fail(cudaError_t e, const char* what) {
+    fprintf(stderr, "lat: %s failed: %s\n", what, cudaGetErrorString(e));
+    return LAT_ECUDA;
+}
+#define CK(call)                                                    \
+    do {                                                            \
+        cudaError_t e_ = (call);                                    \
+        if (e_ != cudaSuccess) return cuda_fail(e_, #call);         \
+    } while (0)
+
+void drop_graphs(lat_ctx* c) {
+    for (auto& kv : c->graphs) cudaGraphExecDestroy(kv.second);
+    c->graphs.clear();
+}
+
+int status_code(unsigned st) {
+    if (st & ST_NUMERIC) return LAT_ENUMERIC;
+    if (st & ST_CFL) return LAT_ECFL;
+    if (st & ST_OVERFLOW) return LAT_EOVERFLOW;
+    if (st & ST_TIMEOUT) return LAT_ETIMEOUT;
+    if (st & ST_NOISE) return LAT_ENOISE;
+    return LAT_OK;
+}
+
+int tile_of(const lat_ctx* c) { return c->block * c->xpt; }
+
+// Rebuild the (instance, x-tile) work list for the current tile width.
+int build_items(lat_ctx* c) {
+    const int tile = tile_of(c);
+    std::vector<int2> items;
+    c->h_inst_begin.assign(c->n_inst + 1, 0);
+    for (int i = 0; i < c->n_inst; ++i) {
+        c->h_inst_begin[i] = (int)items.size();
+        for (int x0 = 0; x0 < c->h_inst[i].nx; x0 += tile) items.push_back(make_int2(i, x0));
+    }
+    c->h_inst_begin[c->n_inst] = (int)items.size();
+    if (c->d_items) cudaFree(c->d_items);
+    if (c->d_inst_begin) cudaFree(c->d_inst_begin);
+    if (c->d_partials) cudaFree(c->d_partials);
+    c->d_items = nullptr;
+    c->d_inst_begin = nullptr;
+    c->d_partials = nullptr;
+    c->nitems = (int)items.size();
+    if (cudaMalloc(&c->d_items, sizeof(int2) * items.size()) != cudaSuccess ||
+        cudaMalloc(&c->d_inst_begin, sizeof(int) * (c->n_inst + 1)) != cudaSuccess ||
+        cudaMalloc(&c->d_partials, sizeof(double) * 6 * items.size()) != cudaSuccess)
+        return LAT_ENOMEM;
+    CK(cudaMemcpy(c->d_items, items.data(), sizeof(int2) * items.size(), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(c->d_inst_begin, c->h_inst_begin.data(), sizeof(int) * (c->n_inst + 1),
+                  cudaMemcpyHostToDevice));
+    drop_graphs(c);
+    return LAT_OK;
+}
+
+int persistent_grid(const lat_ctx* c) {
+    return std::max(1, std::min(c->nitems, c->bps * c->sm_count));
+}
+
+Step1DArgs step_args(const lat_ctx* c, int k, int dry) {
+    Step1DArgs a;
+    memset(&a, 0, sizeof(a));
+    a.f[0] = c->f[0];
+    a.f[1] = c->f[1];
+    (void)k;
+    a.inst = c->d_inst;
+    a.items = c->d_items;
+    a.item_begin = 0;
+    a.item_end = c->nitems;
+    a.flow_kind = c->flow_kind;
+    a.nmodes = c->nmodes;
+    for (int m = 0; m < kMaxModes1D; ++m) a.k[m] = c->k1d[m];
+    a.amp = c->d_amp;
+    a.amp_w = c->d_amp;
+    a.amp_stride = c->amp_stride;
+    a.noise = c->d_noise;
+    a.field = c->field;
+    a.st = c->d_state;
+    a.dry = dry;
+    a.frozen = c->frozen ? 1 : 0;
+    return a;
+}
+
+// Enqueue n steps of a 1D context on stream s (used directly and under capture).
+int enqueue_steps_1d(lat_ctx* c, int n, cudaStream_t s) {
+    for (int k = 0; k < n; ++k) {
+        Step1DArgs a = step_args(c, k, 0);
+        if (c->mode == 1) {
+            for (int i = 0; i < c->n_inst; ++i) {
+                a.item_begin = c->h_inst_begin[i];
+                a.item_end = c->h_inst_begin[i + 1];
+                CK(launch_step1d(c->dtype, c->nv, c->block, c->xpt, a.item_end - a.item_begin, a,
+                                 k, s));
+            }
+        } else {
+            CK(launch_step1d(c->dtype, c->nv, c->block, c->xpt, persistent_grid(c), a, k, s));
+        }
+    }
+    CK(launch_advance_step(c->d_state, n, s));
+    return LAT_OK;
+}
+
+int validate_common(double L, int nx, double tau_p, double kappa, double dt, int nv, int d) {
+    if (!(L > 0) || nx < 1 || !(dt > 0) || !(kappa >= 0) || !(tau_p > 0) || isnan(tau_p))
+        return LAT_EINVAL;
+    if (nv < 1 || nv % 2 == 0 || nv > 129) return LAT_EINVAL;
+    const double dx = L / nx, dv = dx / dt;
+    const int J = (nv - 1) / 2;
+    const double g = isinf(tau_p) ? 0.0 : dt / tau_p;
+    // Eq. (cfl) at rest (u = 0): largest |a| dt / dv = g J; unsplit 2D adds both components.
+    if (g * J * d > 1.0) return LAT_ECFL;
+    // Eq. (stabLapl) for the d-dimensional five-point (d = 2) or three-point (d = 1) Laplacian.
+    if (2.0 * d * kappa * dt / (dv * dv) > 1.0) return LAT_ECFL;
+    return LAT_OK;
+}
+
+int alloc_common(lat_ctx* c) {
+    int dev = 0;
+    CK(cudaGetDevice(&dev));
+    CK(cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, dev));
+    CK(cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking));
+    if (cudaMalloc(&c->d_state, sizeof(DevState)) != cudaSuccess) return LAT_ENOMEM;
+    if (cudaMallocHost(&c->h_state, sizeof(DevState)) != cudaSuccess) return LAT_ENOMEM;
+    CK(cudaMemsetAsync(c->d_state, 0, sizeof(DevState), c->stream));
+    return LAT_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* lat_strerror(int s) {
+    switch (s) {
+        case LAT_OK: return "ok";
+        case LAT_EINVAL: return "invalid argument";
+        case LAT_ECFL: return "stability condition violated (Eq. cfl or Eq. stabLapl)";
+        case LAT_ENOMEM: return "device allocation failed";
+        case LAT_ECUDA: return "CUDA runtime error";
+        case LAT_ENUMERIC: return "non-finite value in f";
+        case LAT_ETIMEOUT: return "bounded device wait gave up";
+        case LAT_EOVERFLOW: return "reduced-precision value exceeded its line scale";
+        case LAT_ENOISE: return "noise table exhausted (flow frozen for the remaining steps)";
+        default: return "unknown status";
+    }
+}
+
+int lat_ensemble_init(lat_ctx** out, int n_inst, const lat_instance* inst, int nv, int dtype,
+                      void* f_a, void* f_b, void* stream) {
+    if (!out || !inst || n_inst < 1 || !f_a || !f_b || f_a == f_b) return LAT_EINVAL;
+    if (dtype != LAT_F32 && dtype != LAT_F64) return LAT_EINVAL;
+    *out = nullptr;
+    for (int i = 0; i < n_inst; ++i) {
+        int v = validate_common(inst[i].L, inst[i].nx, inst[i].tau_p, inst[i].kappa, inst[i].dt,
+                                nv, 1);
+        if (v != LAT_OK) return v;
+    }
+    lat_ctx* c = new lat_ctx();
+    c->d = 1;
+    c->dtype = dtype;
+    c->nv = nv;
+    c->n_inst = n_inst;
+    c->stream = (cudaStream_t)stream;
+    c->f[0] = f_a;
+    c->f[1] = f_b;
+    c->h_inst.resize(n_inst);
+    long long off = 0, xoff = 0;
+    for (int i = 0; i < n_inst; ++i) {
+        Inst1D& q = c->h_inst[i];
+        memset(&q, 0, sizeof(q));
+        q.off = off;
+        q.xoff = xoff;
+        q.nx = inst[i].nx;
+        q.dx = inst[i].L / inst[i].nx;
+        q.dv = q.dx / inst[i].dt;
+        q.inv_dv = 1.0 / q.dv;
+        q.g = isinf(inst[i].tau_p) ? 0.0 : inst[i].dt / inst[i].tau_p;
+        q.r = inst[i].kappa * inst[i].dt / (q.dv * q.dv);
+        q.ou_e = 1.0;
+        q.ou_s = 0.0;
+        off += (long long)nv * inst[i].nx;
+        xoff += inst[i].nx;
+    }
+    c->total_x = xoff;
+    int rc = alloc_common(c);
+    if (rc == LAT_OK && cudaMalloc(&c->d_inst, sizeof(Inst1D) * n_inst) != cudaSuccess)
+        rc = LAT_ENOMEM;
+    if (rc == LAT_OK && cudaMalloc(&c->d_glob, sizeof(double) * 3 * n_inst) != cudaSuccess)
+        rc = LAT_ENOMEM;
+    if (rc == LAT_OK && cudaMallocHost(&c->h_glob, sizeof(double) * 4 * n_inst) != cudaSuccess)
+        rc = LAT_ENOMEM;
+    if (rc == LAT_OK &&
+        cudaMemcpy(c->d_inst, c->h_inst.data(), sizeof(Inst1D) * n_inst, cudaMemcpyHostToDevice) !=
+            cudaSuccess)
+        rc = LAT_ECUDA;
+    if (rc == LAT_OK) {
+        // default launch shape: one x column per thread, 256 threads, 4 resident blocks per SM
+        c->block = 256;
+        c->xpt = 1;
+        c->bps = 4;
+        if (nv > 65) c->bps = 2;
+        rc = build_items(c);
+    }
+    if (rc != LAT_OK) {
+        lat_free(c);
+        return rc;
+    }
+    *out = c;
+    return LAT_OK;
+}
+
+int lat_init(lat_ctx** out, const lat_grid* g, void* f_a, void* f_b, void* stream) {
+    if (!out || !g) return LAT_EINVAL;
+    if (g->d == 1) {
+        if (g->ny != 1) return LAT_EINVAL;
+        lat_instance in;
+        in.nx = g->nx;
+        in.L = g->L;
+        in.tau_p = g->tau_p;
+        in.kappa = g->kappa;
+        in.dt = g->dt;
+        return lat_ensemble_init(out, 1, &in, g->nv, g->dtype, f_a, f_b, stream);
+    }
+    if (g->d != 2) return LAT_EINVAL;
+    if (!f_a || !f_b || f_a == f_b || g->ny < 1) return LAT_EINVAL;
+    int v = validate_common(g->L, g->nx, g->tau_p, g->kappa, g->dt, g->nv, 2);
+    if (v != LAT_OK) return v;
+    *out = nullptr;
+    lat_ctx* c = new lat_ctx();
+    c->d = 2;
+    c->dtype = g->dtype;
+    c->nv = g->nv;
+    c->n_inst = 1;
+    c->stream = (cudaStream_t)stream;
+    c->f[0] = f_a;
+    c->f[1] = f_b;
+    int rc = alloc_common(c);
+    if (rc == LAT_OK) rc = ctx2d_create(&c->c2, g, c->d_state, c->sm_count, c->stream);
+    if (rc != LAT_OK) {
+        lat_free(c);
+        return rc;
+    }
+    *out = c;
+    return LAT_OK;
+}
+
+int lat_set_flow(lat_ctx* c, const lat_flow* fl) {
+    if (!c || !fl) return LAT_EINVAL;
+    const bool frozen = !(fl->tau_f > 0) || isinf(fl->tau_f);
+    if (c->d == 2) {
+        drop_graphs(c);
+        return ctx2d_set_flow(c->c2, fl, frozen, c->stream);
+    }
+    if (fl->kind == LAT_FLOW_NONE) {
+        c->flow_kind = LAT_FLOW_NONE;
+        c->nmodes = 0;
+    } else if (fl->kind == LAT_FLOW_FIELD) {
+        if (!fl->field) return LAT_EINVAL;
+        c->flow_kind = LAT_FLOW_FIELD;
+        c->field = fl->field;
+        c->nmodes = 0;
+    } else if (fl->kind == LAT_FLOW_MODES) {
+        if (fl->nmodes < 1 || fl->nmodes > kMaxModes1D || !fl->k || !fl->amp0) return LAT_EINVAL;
+        if (!frozen && !(fl->sigma >= 0)) return LAT_EINVAL;
+        const int M2 = 2 * fl->nmodes;
+        const long long stride = (long long)c->n_inst * M2;
+        double* amp = nullptr;
+        if (cudaMalloc(&amp, sizeof(double) * 2 * stride) != cudaSuccess) return LAT_ENOMEM;
+        // both parities start from amp0 so that a frozen flow reads the same values every step
+        CK(cudaMemcpy(amp, fl->amp0, sizeof(double) * stride, cudaMemcpyHostToDevice));
+        CK(cudaMemcpy(amp + stride, fl->amp0, sizeof(double) * stride, cudaMemcpyHostToDevice));
+        if (c->d_amp) cudaFree(c->d_amp);
+        c->d_amp = amp;
+        c->amp_stride = stride;
+        c->flow_kind = LAT_FLOW_MODES;
+        c->nmodes = fl->nmodes;
+        for (int m = 0; m < kMaxModes1D; ++m) c->k1d[m] = m < fl->nmodes ? fl->k[m] : 0;
+        c->noise_row_len = stride;
+        for (int i = 0; i < c->n_inst; ++i) {
+            Inst1D& q = c->h_inst[i];
+            const double dt = q.dx / q.dv;
+            if (frozen) {
+                q.ou_e = 1.0;
+                q.ou_s = 0.0;
+            } else {
+                q.ou_e = exp(-dt / fl->tau_f);
+                q.ou_s = fl->sigma * sqrt(1.0 - q.ou_e * q.ou_e);
+            }
+        }
+        CK(cudaMemcpy(c->d_inst, c->h_inst.data(), sizeof(Inst1D) * c->n_inst,
+                      cudaMemcpyHostToDevice));
+    } else {
+        return LAT_EINVAL;
+    }
+    c->frozen = frozen || fl->kind != LAT_FLOW_MODES;
+    k_set_noise_window<<<1, 1, 0, c->stream>>>(c->d_state, c->h_step, 0);
+    CK(cudaGetLastError());
+    drop_graphs(c);
+    return LAT_OK;
+}
+
+int lat_set_noise(lat_ctx* c, const double* noise, long long rows) {
+    if (!c || rows < 0 || (rows > 0 && !noise)) return LAT_EINVAL;
+    if (c->d == 2) {
+        int rc = ctx2d_set_noise(c->c2, noise, rows, c->h_step, c->stream);
+        if (rc == LAT_OK) drop_graphs(c);
+        return rc;
+    }
+    if (c->flow_kind != LAT_FLOW_MODES) return LAT_EINVAL;
+    const long long need = rows * c->noise_row_len;
+    if (need > c->noise_cap) {
+        CK(cudaStreamSynchronize(c->stream));
+        double* p = nullptr;
+        if (cudaMalloc(&p, sizeof(double) * need) != cudaSuccess) return LAT_ENOMEM;
+        if (c->d_noise) cudaFree(c->d_noise);
+        c->d_noise = p;
+        c->noise_cap = need;
+        drop_graphs(c);
+    }
+    if (need > 0)
+        CK(cudaMemcpyAsync(c->d_noise, noise, sizeof(double) * need, cudaMemcpyHostToDevice,
+                           c->stream));
+    k_set_noise_window<<<1, 1, 0, c->stream>>>(c->d_state, c->h_step, rows);
+    CK(cudaGetLastError());
+    return LAT_OK;
+}
+
+}  // extern "C"
+
+namespace {
+
+// Capture (once) the graph of n steps of a 1D context.
+int graph_for(lat_ctx* c, int n, cudaGraphExec_t* out) {
+    auto it = c->graphs.find(n);
+    if (it == c->graphs.end()) {
+        cudaGraph_t g = nullptr;
+        cudaGraphExec_t ge = nullptr;
+        CK(cudaStreamBeginCapture(c->cap, cudaStreamCaptureModeThreadLocal));
+        int rc = enqueue_steps_1d(c, n, c->cap);
+        cudaError_t e = cudaStreamEndCapture(c->cap, &g);
+        if (rc != LAT_OK) {
+            if (g) cudaGraphDestroy(g);
+            return rc;
+        }
+        if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
+        e = cudaGraphInstantiate(&ge, g, 0);
+        cudaGraphDestroy(g);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate");
+        if (c->graphs.size() >= 8) drop_graphs(c);
+        it = c->graphs.emplace(n, ge).first;
+    }
+    *out = it->second;
+    return LAT_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int lat_prepare(lat_ctx* c, int n) {
+    if (!c || n < 1) return LAT_EINVAL;
+    if (c->d == 2) return ctx2d_prepare(c->c2, c->f, n);
+    if (c->mode != 0) return LAT_OK;
+    cudaGraphExec_t ge;
+    return graph_for(c, n, &ge);
+}
+
+int lat_step(lat_ctx* c, int n) {
+    if (!c || n < 0) return LAT_EINVAL;
+    if (n == 0) return LAT_OK;
+    if (c->d == 2) {
+        int rc = ctx2d_step(c->c2, c->f, n, c->stream);
+        if (rc != LAT_OK) return rc;
+    } else if (c->mode != 0) {
+        int rc = enqueue_steps_1d(c, n, c->stream);
+        if (rc != LAT_OK) return rc;
+    } else {
+        cudaGraphExec_t ge;
+        int rc = graph_for(c, n, &ge);
+        if (rc != LAT_OK) return rc;
+        CK(cudaGraphLaunch(ge, c->stream));
+    }
+    c->h_step += n;
+    c->cur = (int)(c->h_step & 1);
+    return LAT_OK;
+}
+
+int lat_status(lat_ctx* c) {
+    if (!c) return LAT_EINVAL;
+    CK(cudaMemcpyAsync(c->h_state, c->d_state, sizeof(DevState), cudaMemcpyDeviceToHost,
+                       c->stream));
+    k_clear_status<<<1, 1, 0, c->stream>>>(c->d_state);
+    CK(cudaGetLastError());
+    CK(cudaStreamSynchronize(c->stream));
+    return status_code(c->h_state->status);
+}
+
+int lat_moments(lat_ctx* c, double* rho, double* mean_v, double* mean_v2, double* globals) {
+    if (!c) return LAT_EINVAL;
+    if (c->d == 2) {
+        int rc = ctx2d_moments(c->c2, c->f[c->cur], rho, mean_v, mean_v2, globals, c->stream);
+        if (rc != LAT_OK) return rc;
+        return lat_status(c);
+    }
+    Mom1DArgs a;
+    a.f = c->f[c->cur];
+    a.inst = c->d_inst;
+    a.items = c->d_items;
+    a.nitems = c->nitems;
+    a.nv = c->nv;
+    a.rho = rho;
+    a.mean_v = mean_v;
+    a.mean_v2 = mean_v2;
+    a.partials = c->d_partials;
+    a.st = c->d_state;
+    const int grid = std::max(1, std::min(c->nitems, 8 * c->sm_count));
+    CK(launch_moments1d(c->dtype, c->block, c->xpt, grid, a, c->stream));
+    CK(launch_finalize1d(c->d_partials, c->d_inst_begin, c->d_inst, c->n_inst, c->d_glob,
+                         c->stream));
+    if (globals)
+        CK(cudaMemcpyAsync(c->h_glob, c->d_glob, sizeof(double) * 3 * c->n_inst,
+                           cudaMemcpyDeviceToHost, c->stream));
+    int rc = lat_status(c);  // synchronises
+    if (globals) memcpy(globals, c->h_glob, sizeof(double) * 3 * c->n_inst);
+    return rc;
+}
+
+int lat_current(const lat_ctx* c) { return c ? c->cur : -1; }
+
+long long lat_steps_done(const lat_ctx* c) { return c ? c->h_step : -1; }
+
+int lat_set_launch(lat_ctx* c, int block, int xpt, int blocks_per_sm, int mode) {
+    if (!c) return LAT_EINVAL;
+    if (c->d == 2) {
+        int rc = ctx2d_set_launch(c->c2, block, xpt, blocks_per_sm, mode);
+        if (rc == LAT_OK) drop_graphs(c);
+        return rc;
+    }
+    const int nb = block ? block : c->block;
+    const int nxp = xpt ? xpt : c->xpt;
+    const int nbps = blocks_per_sm ? blocks_per_sm : c->bps;
+    const int nmode = mode >= 0 ? mode : c->mode;
+    if (nb < 32 || nb > 1024 || nb % 32 != 0 || nbps < 1 || nbps > 64 || nmode < 0 || nmode > 2)
+        return LAT_EINVAL;
+    if (!step1d_supported(c->dtype, c->nv, nxp)) return LAT_EINVAL;
+    if (nb > step1d_max_block(c->dtype, c->nv, nxp)) return LAT_EINVAL;
+    const bool retile = nb * nxp != tile_of(c);
+    c->block = nb;
+    c->xpt = nxp;
+    c->bps = nbps;
+    c->mode = nmode;
+    drop_graphs(c);
+    return retile ? build_items(c) : LAT_OK;
+}
+
+int lat_autotune(lat_ctx* c, int reps, double* best) {
+    if (!c || reps < 1) return LAT_EINVAL;
+    if (c->d == 2) return ctx2d_autotune(c->c2, c->f, reps, best, c->stream);
+    const int blocks[] = {128, 256, 512};
+    const int xpts[] = {1, 2};
+    const int bpss[] = {1, 2, 3, 4, 6, 8};
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    const int mode_save = c->mode;
+    double best_us = 1e300;
+    int bb = c->block, bx = c->xpt, bp = c->bps;
+    for (int b : blocks)
+        for (int x : xpts) {
+            if (!step1d_supported(c->dtype, c->nv, x)) continue;
+            for (int p : bpss) {
+                if (b * p > 2048) continue;
+                if (lat_set_launch(c, b, x, p, 0) != LAT_OK) continue;
+                Step1DArgs a = step_args(c, 0, 1);
+                const int grid = persistent_grid(c);
+                CK(launch_step1d(c->dtype, c->nv, b, x, grid, a, 0, c->stream));
+                CK(cudaEventRecord(e0, c->stream));
+                for (int r = 0; r < reps; ++r)
+                    CK(launch_step1d(c->dtype, c->nv, b, x, grid, a, 0, c->stream));
+                CK(cudaEventRecord(e1, c->stream));
+                CK(cudaEventSynchronize(e1));
+                float ms = 0.f;
+                CK(cudaEventElapsedTime(&ms, e0, e1));
+                const double us = 1000.0 * ms / reps;
+                if (us < best_us) {
+                    best_us = us;
+                    bb = b;
+                    bx = x;
+                    bp = p;
+                }
+            }
+        }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    // the dry runs may have flagged CFL on a stale buffer; clear the status they set
+    k_clear_status<<<1, 1, 0, c->stream>>>(c->d_state);
+    int rc = lat_set_launch(c, bb, bx, bp, mode_save);
+    if (best) {
+        best[0] = bb;
+        best[1] = bx;
+        best[2] = bp;
+        best[3] = best_us;
+    }
+    return rc;
+}
+
+void lat_free(lat_ctx* c) {
+    if (!c) return;
+    if (c->stream) cudaStreamSynchronize(c->stream);
+    else cudaDeviceSynchronize();
+    drop_graphs(c);
+    if (c->c2) ctx2d_destroy(c->c2);
+    cudaFree(c->d_inst);
+    cudaFree(c->d_items);
+    cudaFree(c->d_inst_begin);
+    cudaFree(c->d_partials);
+    cudaFree(c->d_glob);
+    cudaFree(c->d_amp);
+    cudaFree(c->d_noise);
+    cudaFree(c->d_state);
+    if (c->h_glob) cudaFreeHost(c->h_glob);
+    if (c->h_state) cudaFreeHost(c->h_state);
+    if (c->cap) cudaStreamDestroy(c->cap);
+    delete c;
+}
+
+}  // extern "C"

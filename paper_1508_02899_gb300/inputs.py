@@ -28,12 +28,46 @@ import numpy as np
 # --------------------------------------------------------------------------------------------
 # Initial densities
 # --------------------------------------------------------------------------------------------
-def gaussian_initial_1d(nx: int, nv: int, dx: float, dv: float, sigma_v: float) -> np.ndarray:
+def gaussian_column(nx: int, nv: int, dx: float, dv: float, sigma_v: float) -> np.ndarray:
+    """Velocity column of the uniform-in-x Gaussian initial density, normalised so that N_x
+    copies of it carry unit mass (sum f dx dv = 1)."""
     J = (nv - 1) // 2
     v = np.arange(-J, J + 1, dtype=np.float64) * dv
     g = np.exp(-0.5 * (v / sigma_v) ** 2)
-    f = np.repeat(g[:, None], nx, axis=1)
-    return f / (f.sum() * dx * dv)
+    return g / (nx * g.sum() * dx * dv)
+
+
+def gaussian_initial_1d(nx: int, nv: int, dx: float, dv: float, sigma_v: float) -> np.ndarray:
+    return np.repeat(gaussian_column(nx, nv, dx, dv, sigma_v)[:, None], nx, axis=1)
+
+
+def ensemble_initial(tab: "EnsembleTable", nv: int, dtype, device, instances=None):
+    """Concatenated 1D initial densities (sigma_v = 0.2 V_max per instance) as one torch
+    tensor built on ``device``; with ``instances`` given, only those (numpy, float64)."""
+    J = (nv - 1) // 2
+
+    def col(i):
+        nx = int(tab.nx[i])
+        dx = tab.L[i] / nx
+        dv = dx / tab.dt[i]
+        return gaussian_column(nx, nv, dx, dv, 0.2 * max(J, 1) * dv)
+
+    if instances is not None:
+        return {int(i): np.repeat(col(i)[:, None], int(tab.nx[i]), axis=1) for i in instances}
+    import torch
+    total = int((tab.nx * nv).sum())
+    out = torch.empty(total, dtype=dtype, device=device)
+    off = 0
+    cache = {}
+    for i in range(len(tab.nx)):
+        nx = int(tab.nx[i])
+        key = (nx, float(tab.dt[i]), float(tab.L[i]))
+        if key not in cache:
+            c = torch.tensor(col(i), dtype=dtype, device=device)
+            cache[key] = c[:, None].expand(nv, nx).contiguous().view(-1)
+        out[off:off + nv * nx].copy_(cache[key])
+        off += nv * nx
+    return out
 
 
 def gaussian_initial_2d(nx: int, ny: int, nv: int, dx: float, dv: float,

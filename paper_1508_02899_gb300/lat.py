@@ -1,0 +1,272 @@
+"""Thin Python binding of the C ABI in include/lat.h (argument marshalling only).
+
+Every step of the lattice method runs in the CUDA library ``liblat.so``; this module only
+passes pointers, sizes and the current CUDA stream.  PyTorch provides device memory and
+streams.  There is no CPU fallback: importing this module fails if the library is missing.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from ctypes import POINTER, byref, c_double, c_int, c_longlong, c_void_p
+
+import numpy as np
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "liblat.so")
+
+LAT_OK, LAT_EINVAL, LAT_ECFL, LAT_ENOMEM, LAT_ECUDA = 0, 1, 2, 3, 4
+LAT_ENUMERIC, LAT_ETIMEOUT, LAT_EOVERFLOW, LAT_ENOISE = 5, 6, 7, 8
+LAT_F64, LAT_F32, LAT_F16, LAT_BF16 = 0, 1, 2, 3
+FLOW_NONE, FLOW_FIELD, FLOW_MODES = 0, 1, 2
+
+_DTYPES = {torch.float64: LAT_F64, torch.float32: LAT_F32, torch.float16: LAT_F16,
+           torch.bfloat16: LAT_BF16}
+
+
+class LatGrid(ctypes.Structure):
+    _fields_ = [("d", c_int), ("nx", c_int), ("ny", c_int), ("nv", c_int), ("dtype", c_int),
+                ("L", c_double), ("tau_p", c_double), ("kappa", c_double), ("dt", c_double)]
+
+
+class LatInstance(ctypes.Structure):
+    _fields_ = [("nx", c_int), ("L", c_double), ("tau_p", c_double), ("kappa", c_double),
+                ("dt", c_double)]
+
+
+class LatFlow(ctypes.Structure):
+    _fields_ = [("kind", c_int), ("field", c_void_p), ("nmodes", c_int), ("k", POINTER(c_int)),
+                ("amp0", POINTER(c_double)), ("phase0", POINTER(c_double)),
+                ("tau_f", c_double), ("sigma", c_double)]
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"{LIB_PATH} is not built; run __graft_entry__.build() first")
+    lib = ctypes.CDLL(LIB_PATH)
+    P = c_void_p
+    sig = {
+        "lat_init": (c_int, [POINTER(P), POINTER(LatGrid), P, P, P]),
+        "lat_ensemble_init": (c_int, [POINTER(P), c_int, POINTER(LatInstance), c_int, c_int,
+                                      P, P, P]),
+        "lat_set_flow": (c_int, [P, POINTER(LatFlow)]),
+        "lat_set_noise": (c_int, [P, POINTER(c_double), c_longlong]),
+        "lat_step": (c_int, [P, c_int]),
+        "lat_prepare": (c_int, [P, c_int]),
+        "lat_moments": (c_int, [P, P, P, P, POINTER(c_double)]),
+        "lat_status": (c_int, [P]),
+        "lat_current": (c_int, [P]),
+        "lat_steps_done": (c_longlong, [P]),
+        "lat_set_launch": (c_int, [P, c_int, c_int, c_int, c_int]),
+        "lat_autotune": (c_int, [P, c_int, POINTER(c_double)]),
+        "lat_strerror": (ctypes.c_char_p, [c_int]),
+        "lat_free": (None, [P]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    return lib
+
+
+_lib = _load()
+
+
+class LatError(RuntimeError):
+    def __init__(self, code: int, what: str):
+        self.code = code
+        super().__init__(f"{what}: {_lib.lat_strerror(code).decode()} (code {code})")
+
+
+def _check(code: int, what: str):
+    if code != LAT_OK:
+        raise LatError(code, what)
+
+
+def _ptr(t: torch.Tensor | None):
+    return None if t is None else c_void_p(t.data_ptr())
+
+
+def _stream(stream):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return c_void_p(s.cuda_stream)
+
+
+def _dptr(a: np.ndarray):
+    return a.ctypes.data_as(POINTER(c_double))
+
+
+class _Ctx:
+    """Common part of single-lattice and ensemble contexts."""
+
+    def __init__(self):
+        self._h = c_void_p()
+        self._keep = []
+
+    @property
+    def handle(self):
+        return self._h
+
+    def _set_flow(self, kind, field=None, k=None, amp0=None, phase0=None, tau_f=0.0, sigma=0.0):
+        fl = LatFlow()
+        fl.kind = kind
+        fl.field = None if field is None else field.data_ptr()
+        if k is not None:
+            k = np.ascontiguousarray(k, dtype=np.int32)
+            fl.k = k.ctypes.data_as(POINTER(c_int))
+            fl.nmodes = k.shape[0]
+        if amp0 is not None:
+            amp0 = np.ascontiguousarray(amp0, dtype=np.float64)
+            fl.amp0 = _dptr(amp0)
+        if phase0 is not None:
+            phase0 = np.ascontiguousarray(phase0, dtype=np.float64)
+            fl.phase0 = _dptr(phase0)
+        fl.tau_f = float(tau_f)
+        fl.sigma = float(sigma)
+        self._field = field
+        _check(_lib.lat_set_flow(self._h, byref(fl)), "lat_set_flow")
+
+    def set_flow_none(self):
+        self._set_flow(FLOW_NONE)
+
+    def set_flow_field(self, u: torch.Tensor):
+        self._set_flow(FLOW_FIELD, field=u)
+
+    def set_noise(self, noise: np.ndarray):
+        noise = np.ascontiguousarray(noise, dtype=np.float64)
+        self._keep = [noise]
+        _check(_lib.lat_set_noise(self._h, _dptr(noise), noise.shape[0] if noise.size else 0),
+               "lat_set_noise")
+
+    def set_noise_pinned(self, noise: torch.Tensor):
+        """noise: pinned host float64 tensor (asynchronous copy)."""
+        self._keep = [noise]
+        _check(_lib.lat_set_noise(self._h, ctypes.cast(noise.data_ptr(), POINTER(c_double)),
+                                  noise.shape[0]), "lat_set_noise")
+
+    def step(self, n: int = 1):
+        _check(_lib.lat_step(self._h, int(n)), "lat_step")
+
+    def prepare(self, n: int):
+        _check(_lib.lat_prepare(self._h, int(n)), "lat_prepare")
+
+    def status(self) -> int:
+        return _lib.lat_status(self._h)
+
+    @property
+    def current_index(self) -> int:
+        return _lib.lat_current(self._h)
+
+    @property
+    def steps_done(self) -> int:
+        return _lib.lat_steps_done(self._h)
+
+    def set_launch(self, block=0, xpt=0, blocks_per_sm=0, mode=-1):
+        _check(_lib.lat_set_launch(self._h, block, xpt, blocks_per_sm, mode), "lat_set_launch")
+
+    def autotune(self, reps: int = 5):
+        best = np.zeros(4)
+        _check(_lib.lat_autotune(self._h, reps, _dptr(best)), "lat_autotune")
+        return {"block": int(best[0]), "xpt": int(best[1]), "blocks_per_sm": int(best[2]),
+                "us_per_step": float(best[3])}
+
+    def close(self):
+        if self._h:
+            _lib.lat_free(self._h)
+            self._h = c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Lattice(_Ctx):
+    """One 1D or 2D lattice.  f0 (device tensor) holds the initial state in the layout of
+    include/lat.h; a second buffer of the same shape is allocated here (torch)."""
+
+    def __init__(self, f0: torch.Tensor, *, d: int, nx: int, ny: int = 1, nv: int, L: float,
+                 tau_p: float, kappa: float, dt: float, stream=None):
+        super().__init__()
+        if f0.dtype not in _DTYPES or not f0.is_cuda or not f0.is_contiguous():
+            raise ValueError("f0 must be a contiguous CUDA tensor of float64/32/16 or bfloat16")
+        self.d, self.nx, self.ny, self.nv = d, nx, ny, nv
+        self.L, self.dt = L, dt
+        self.dx = L / nx
+        self.dv = self.dx / dt
+        self.f = [f0, torch.empty_like(f0)]
+        g = LatGrid(d, nx, ny, nv, _DTYPES[f0.dtype], L, tau_p, kappa, dt)
+        _check(_lib.lat_init(byref(self._h), byref(g), _ptr(self.f[0]), _ptr(self.f[1]),
+                             _stream(stream)), "lat_init")
+
+    @property
+    def state(self) -> torch.Tensor:
+        return self.f[self.current_index]
+
+    def set_flow_modes_1d(self, k, amp0, tau_f: float, sigma: float):
+        self._set_flow(FLOW_MODES, k=k, amp0=np.asarray(amp0).reshape(-1), tau_f=tau_f,
+                       sigma=sigma)
+
+    def set_flow_modes_2d(self, kvec, a, phi0, tau_f: float):
+        self._set_flow(FLOW_MODES, k=np.asarray(kvec, dtype=np.int32).reshape(-1, 2), amp0=a,
+                       phase0=phi0, tau_f=tau_f)
+
+    def moments(self, per_cell: bool = True):
+        ncell = self.nx * self.ny
+        dev = self.f[0].device
+        rho = torch.empty(ncell, dtype=torch.float64, device=dev) if per_cell else None
+        mv = torch.empty(self.d * ncell, dtype=torch.float64, device=dev) if per_cell else None
+        mv2 = torch.empty(ncell, dtype=torch.float64, device=dev) if per_cell else None
+        glob = np.zeros(self.d + 2)
+        code = _lib.lat_moments(self._h, _ptr(rho), _ptr(mv), _ptr(mv2), _dptr(glob))
+        return code, rho, mv, mv2, glob
+
+
+class Ensemble(_Ctx):
+    """Independent 1D lattices advanced together (one persistent launch per step)."""
+
+    def __init__(self, f0: torch.Tensor, *, nv: int, nx, L, tau_p, kappa, dt, stream=None):
+        super().__init__()
+        n = len(nx)
+        if f0.dtype not in (torch.float32, torch.float64) or not f0.is_cuda:
+            raise ValueError("f0 must be a CUDA float32/float64 tensor")
+        self.n, self.nv = n, nv
+        self.nx = np.asarray(nx, dtype=np.int64)
+        self.offsets = np.concatenate([[0], np.cumsum(self.nx * nv)])
+        self.xoff = np.concatenate([[0], np.cumsum(self.nx)])
+        self.f = [f0, torch.empty_like(f0)]
+        arr = (LatInstance * n)()
+        for i in range(n):
+            arr[i] = LatInstance(int(nx[i]), float(L[i]), float(tau_p[i]), float(kappa[i]),
+                                 float(dt[i]))
+        _check(_lib.lat_ensemble_init(byref(self._h), n, arr, nv, _DTYPES[f0.dtype],
+                                      _ptr(self.f[0]), _ptr(self.f[1]), _stream(stream)),
+               "lat_ensemble_init")
+
+    @property
+    def state(self) -> torch.Tensor:
+        return self.f[self.current_index]
+
+    def instance_view(self, i: int, t: torch.Tensor | None = None) -> torch.Tensor:
+        t = self.state if t is None else t
+        return t[self.offsets[i]:self.offsets[i + 1]].view(self.nv, int(self.nx[i]))
+
+    def set_flow_modes(self, k, amp0, tau_f: float, sigma: float):
+        self._set_flow(FLOW_MODES, k=k, amp0=np.asarray(amp0).reshape(-1), tau_f=tau_f,
+                       sigma=sigma)
+
+    def moments(self, per_cell: bool = False, globals_out: np.ndarray | None = None):
+        ncell = int(self.xoff[-1])
+        dev = self.f[0].device
+        rho = torch.empty(ncell, dtype=torch.float64, device=dev) if per_cell else None
+        mv = torch.empty(ncell, dtype=torch.float64, device=dev) if per_cell else None
+        mv2 = torch.empty(ncell, dtype=torch.float64, device=dev) if per_cell else None
+        glob = globals_out if globals_out is not None else np.zeros((self.n, 3))
+        code = _lib.lat_moments(self._h, _ptr(rho), _ptr(mv), _ptr(mv2), _dptr(glob))
+        return code, rho, mv, mv2, glob
+
+
+def exported_symbols():
+    return [n for n in dir(_lib) if n.startswith("lat_")]

@@ -1,0 +1,56 @@
+"""Host-side checks of the CUDA library that need no GPU: it builds, loads, and exports every
+entry point that include/lat.h declares (no compute calls are made here)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    names = []
+    for hdr in sorted(os.listdir(os.path.join(ROOT, "include"))):
+        if hdr.endswith(".h"):
+            src = open(os.path.join(ROOT, "include", hdr)).read()
+            src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+            names += re.findall(r"\b(lat_\w+)\s*\(", src)
+    return sorted(set(names))
+
+
+@pytest.fixture(scope="module")
+def libpath():
+    from paper_1508_02899_gb300 import build
+    if not os.path.exists(build.LIB):
+        build.build()
+    return build.LIB
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for need in ("lat_init", "lat_set_flow", "lat_step", "lat_moments", "lat_free"):
+        assert need in names
+
+
+def test_library_exports_every_declared_symbol(libpath):
+    lib = ctypes.CDLL(libpath)
+    missing = [n for n in declared_functions() if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_strerror_without_gpu(libpath):
+    lib = ctypes.CDLL(libpath)
+    lib.lat_strerror.restype = ctypes.c_char_p
+    assert lib.lat_strerror(0) == b"ok"
+    assert b"stability" in lib.lat_strerror(2)
+
+
+def test_binding_marshals_structs_like_the_header():
+    from paper_1508_02899_gb300 import lat
+    # lat_grid: 5 ints then 4 doubles (8-byte aligned); lat_flow: pointers at 8-byte offsets
+    assert ctypes.sizeof(lat.LatGrid) == 56
+    assert lat.LatGrid.L.offset == 24
+    assert ctypes.sizeof(lat.LatInstance) == 40
+    assert lat.LatFlow.field.offset == 8 and lat.LatFlow.k.offset == 24
+    assert ctypes.sizeof(lat.LatFlow) == 64
