@@ -251,7 +251,7 @@ class Ensemble(_Ctx):
 
     def instance_view(self, i: int, t: torch.Tensor | None = None) -> torch.Tensor:
         t = self.state if t is None else t
-        return t[self.offsets[i]:self.offsets[i + 1]].view(self.nv, int(self.nx[i]))
+        return t[int(self.offsets[i]):int(self.offsets[i + 1])].view(self.nv, int(self.nx[i]))
 
     def set_flow_modes(self, k, amp0, tau_f: float, sigma: float):
         self._set_flow(FLOW_MODES, k=k, amp0=np.asarray(amp0).reshape(-1), tau_f=tau_f,
