@@ -47,6 +47,10 @@ def parse():
                    help="ensemble size (smaller cases are for profiling only)")
     p.add_argument("--no-autotune", action="store_true")
     p.add_argument("--no-per-instance", action="store_true")
+    p.add_argument("--no-forms", action="store_true")
+    p.add_argument("--workload", default="ensemble", choices=["ensemble", "2d"])
+    p.add_argument("--launch", default=None,
+                   help="kernel,block,blocks_per_sm instead of autotuning (profiling runs)")
     return p.parse_args()
 
 
@@ -208,6 +212,91 @@ def run_reference(args):
 # ---------------------------------------------------------------------------------------------
 # GPU arm
 # ---------------------------------------------------------------------------------------------
+WORKLOAD_2D = ("2D FP32: periodic 512x512 grid, 33x33 velocity lattice (2.85e8 cells), St=1, "
+               "kappa=1e-3, incompressible random-phase flow |k|<=8, k^-3 spectrum, OU phases")
+
+
+def build_ensemble(args, I, lat, torch, dev, rank, nsteps):
+    n_inst = args.instances
+    tab = I.ensemble_table(n_inst, SEED + rank, nv=NV)
+    fl = I.flow1d_inputs(SEED + 7 + rank, nsteps, n_inst=n_inst)
+    f0 = I.ensemble_initial(tab, NV, torch.float32, dev)
+    ens = lat.Ensemble(f0, nv=NV, nx=tab.nx, L=tab.L, tau_p=tab.tau_p, kappa=tab.kappa,
+                       dt=tab.dt)
+    ens.set_flow_modes(fl.k, fl.amp0, fl.tau_f, fl.sigma)
+    ens.set_noise(fl.noise)
+    cells = int(tab.nx.sum()) * NV
+    desc = WORKLOAD if n_inst == N_INST else f"{WORKLOAD} (profiling case: {n_inst} instances)"
+    return ens, cells, fl.noise[:1], np.zeros((n_inst, 3)), desc
+
+
+def build_2d(args, I, lat, torch, dev, rank, nsteps, n=512, nv=33):
+    L = 2 * math.pi
+    tau_p, kappa = L, 1e-3
+    dt = I.choose_dt(2, n, L, nv, tau_p, kappa)
+    dx = L / n
+    dv = dx / dt
+    col = I.gaussian_column(1, nv, dx, dv, 0.2 * ((nv - 1) // 2) * dv)
+    col2 = torch.tensor(np.outer(col, col) / (n * n), dtype=torch.float32, device=dev)
+    f0 = col2[:, :, None, None].expand(nv, nv, n, n).contiguous()
+    fl = I.flow2d_inputs(SEED + 11 + rank, nsteps, n, n, dx)
+    lt = lat.Lattice(f0, d=2, nx=n, ny=n, nv=nv, L=L, tau_p=tau_p, kappa=kappa, dt=dt)
+    lt.set_flow_modes_2d(fl.kvec, fl.a, fl.phi0, fl.tau_f)
+    lt.set_noise(fl.noise)
+    return lt, n * n * nv * nv, fl.noise[:1], np.zeros(4), WORKLOAD_2D
+
+
+def timed(ctx, K, W, torch, dist, world, local, dev):
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ctx.prepare(W)
+    ctx.prepare(K)
+    ctx.step(W)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    clocks.start()
+    ev0.record()
+    ctx.step(K)
+    ev1.record()
+    torch.cuda.synchronize()
+    ck = clocks.stop()
+    if world > 1:
+        dist.barrier()
+    t = torch.tensor([ev0.elapsed_time(ev1)], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item()), ck
+
+
+def end_to_end(ctx, noise_row, glob, steps, torch):
+    """Per step, through the C ABI with host buffers: the step's noise row from pinned host
+    memory, one step, and the moments (globals) back to host memory."""
+    pinned = torch.from_numpy(np.ascontiguousarray(noise_row)).pin_memory()
+    ctx.prepare(1)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        ctx.set_noise_pinned(pinned)
+        ctx.step(1)
+        if glob.ndim == 2:
+            ctx.moments(per_cell=False, globals_out=glob)
+        else:
+            code, *_ , g = ctx.moments(per_cell=False)
+            glob[:] = g
+    torch.cuda.synchronize()
+    return time.perf_counter() - t0, int(pinned.numel() * 8), int(glob.size * 8)
+
+
+def kernel_label(workload, best, nv):
+    if workload == "2d":
+        return f"k_step2d_{'ring' if best and best['kernel'] == 2 else 'plain'}<{nv}>"
+    if best and best["kernel"] >= 2:
+        return f"k_step1d_ring<{nv},{best['kernel']}>"
+    return f"k_step1d_reg<float,{nv}>"
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -227,81 +316,67 @@ def main():
         dist.init_process_group("nccl", device_id=dev)
 
     K, W = args.steps, args.warmup
-    n_inst = args.instances
-    tab = I.ensemble_table(n_inst, SEED + rank, nv=NV)
-    total_steps = W + K + 1
-    fl = I.flow1d_inputs(SEED + 7 + rank, total_steps, n_inst=n_inst)
-    f0 = I.ensemble_initial(tab, NV, torch.float32, dev)
-    ens = lat.Ensemble(f0, nv=NV, nx=tab.nx, L=tab.L, tau_p=tab.tau_p, kappa=tab.kappa,
-                       dt=tab.dt)
-    ens.set_flow_modes(fl.k, fl.amp0, fl.tau_f, fl.sigma)
-    ens.set_noise(fl.noise)
-    cells = int(tab.nx.sum()) * NV
-    best = None if args.no_autotune else ens.autotune(reps=3)
+    K_e2e = max(3, min(K, 50))
+    nsteps = W + K + K_e2e + 2
+    if args.workload == "2d":
+        ctx, cells, noise_row, glob, desc = build_2d(args, I, lat, torch, dev, rank, nsteps)
+        nv, prof, src = 33, "step2d_512_fp32_nv33.md", "paper_1508_02899_gb300/csrc/step2d.cu"
+        launches_per_step = 2  # flow evaluation + fused step
+    else:
+        ctx, cells, noise_row, glob, desc = build_ensemble(args, I, lat, torch, dev, rank, nsteps)
+        nv, prof, src = NV, "step1d_ensemble_fp32_nv65.md", "paper_1508_02899_gb300/csrc/step1d.cu"
+        launches_per_step = 1
+    best = None
+    if args.launch:
+        kern, blk, bps = (int(v) for v in args.launch.split(","))
+        ctx.set_launch(kernel=kern, block=blk, blocks_per_sm=bps)
+        best = {"kernel": kern, "block": blk, "blocks_per_sm": bps, "us_per_step": None}
+    elif not args.no_autotune:
+        best = ctx.autotune(reps=3)
 
-    # unbatched baseline: one launch per instance per step (context, not the headline)
-    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     per_inst_ms = None
-    if not args.no_per_instance:
-        ens.set_launch(mode=1)
+    if args.workload == "ensemble" and not args.no_per_instance:
+        # unbatched baseline: one launch per instance per step (context, not the headline)
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ctx.set_launch(mode=1)
         torch.cuda.synchronize()
         ev0.record()
-        ens.step(1)
+        ctx.step(1)
         ev1.record()
         torch.cuda.synchronize()
         per_inst_ms = ev0.elapsed_time(ev1)
-        ens.set_launch(mode=0)
+        ctx.set_launch(mode=0)
 
-    ens.prepare(W)
-    ens.prepare(K)
-    ens.step(W)
-    torch.cuda.synchronize()
-    if world > 1:
-        dist.barrier()
-    torch.cuda.synchronize()
-    clocks = ClockSampler(local)
-    clocks.start()
-    ev0.record()
-    ens.step(K)
-    ev1.record()
-    torch.cuda.synchronize()
-    ck = clocks.stop()
-    if world > 1:
-        dist.barrier()
-    ms = ev0.elapsed_time(ev1)
-    t = torch.tensor([ms], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    ms_max = float(t.item())
-    status = ens.status()
-
+    ms_max, ck = timed(ctx, K, W, torch, dist, world, local, dev)
+    status = ctx.status()
     value = world * cells * K / (ms_max / 1e3) / 1e9
-
-    # end to end through the C ABI with host buffers: per step, the step's noise row from
-    # pinned host memory, one step, and the per-instance moments back to host memory
-    noise_rows = torch.from_numpy(np.ascontiguousarray(fl.noise[:1])).pin_memory()
-    glob = np.zeros((n_inst, 3))
-    K_e2e = max(3, min(K, 50))
-    ens.prepare(1)
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    for _ in range(K_e2e):
-        ens.set_noise_pinned(noise_rows)
-        ens.step(1)
-        ens.moments(per_cell=False, globals_out=glob)
-    torch.cuda.synchronize()
-    e2e_s = time.perf_counter() - t0
+    e2e_s, h2d, d2h = end_to_end(ctx, noise_row, glob, K_e2e, torch)
     e2e_value = world * cells * K_e2e / e2e_s / 1e9
 
     peak, peak_src = measured_peaks()
     bytes_per_launch = cells * 8  # one FP32 read and one FP32 write of every cell
-    ms_launch = ms_max / K
-    achieved = bytes_per_launch / (ms_launch / 1e3) / 1e9
-    tr = profile_traffic("step1d_ensemble_fp32_nv65.md", "paper_1508_02899_gb300/csrc/step1d.cu")
+    achieved = bytes_per_launch / (ms_max / K / 1e3) / 1e9
+    tr = profile_traffic(prof, src)
     traffic = None
     if tr is not None:
         tb, units = tr
         traffic = tb * (cells / units) if units == units and units > 0 else tb
+    ctx.close()
+    del ctx
+    torch.cuda.empty_cache()
+
+    forms = None
+    if args.workload == "ensemble" and not args.no_forms and args.instances == N_INST:
+        lt, c2, *_ = build_2d(args, I, lat, torch, dev, rank, 2 * 40 + 4)
+        b2 = lt.autotune(reps=3)
+        ms2, _ = timed(lt, 40, 3, torch, dist, world, local, dev)
+        g2 = c2 * 40 / (ms2 / 1e3) / 1e9
+        forms = {"2d_fp32_512x512_33x33": {
+            "gcups": g2, "ms_per_step": ms2 / 40, "hbm_frac": g2 * 8 / peak,
+            "kernel": kernel_label("2d", b2, 33), "steps": 40}}
+        lt.close()
+        del lt
+        torch.cuda.empty_cache()
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -315,28 +390,25 @@ def main():
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K,
             "warmup": W, "ms_per_step": ms_max / K, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": WORKLOAD if n_inst == N_INST else
-                       f"{WORKLOAD} (profiling case: {n_inst} instances)",
-                       "instances": n_inst, "nv": NV,
-                       "cells_per_step_per_gpu": cells,
-                       "l2": "inputs larger than L2 (two 4.1 GB FP32 buffers); no flush",
+            "config": {"workload": desc, "nv": nv, "cells_per_step_per_gpu": cells,
+                       "l2": "inputs larger than L2 (FP32 ping-pong buffers of GBs); no flush",
                        "launch": best, "status": status},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic,
-                         "peak_source": peak_src, "kernel": "k_step1d_reg<float,65>",
+                         "peak_source": peak_src, "kernel": kernel_label(args.workload, best, nv),
                          "bytes_per_launch": bytes_per_launch},
             "cpu_baseline": cpu,
             "e2e": {"value": e2e_value, "unit": UNIT, "steps": K_e2e,
-                    "h2d_bytes_per_step": int(noise_rows.numel() * 8),
-                    "d2h_bytes_per_step": int(glob.size * 8)},
-            "gpu_launches": K + 1,
+                    "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+            "gpu_launches": launches_per_step * K + 1,
             "clocks": ck,
-            "batching": {"persistent_graph_gcups": value / world,
-                         "per_instance_launch_gcups":
-                             None if per_inst_ms is None else cells / (per_inst_ms / 1e3) / 1e9},
         }
+        if per_inst_ms is not None:
+            line["batching"] = {"persistent_graph_gcups": value / world,
+                                "per_instance_launch_gcups": cells / (per_inst_ms / 1e3) / 1e9}
+        if forms:
+            line["forms"] = forms
         print(json.dumps(line))
-    ens.close()
     if world > 1:
         dist.destroy_process_group()
     return 0

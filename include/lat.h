@@ -158,14 +158,22 @@ int lat_current(const lat_ctx* c);
 /* Steps taken since init. */
 long long lat_steps_done(const lat_ctx* c);
 
-/* Launch shape of the step kernel: threads per block, x columns per thread, resident blocks
- * per SM for the persistent grid, and mode 0 = one persistent launch over all instances,
- * 1 = one launch per instance (the unbatched baseline).  Zeros keep the current values. */
-int lat_set_launch(lat_ctx* c, int block, int xpt, int blocks_per_sm, int mode);
+/* Launch shape of the step kernel.
+ *  kernel: 0 keep; 1 plain coalesced loads; 2..4 bulk asynchronous copies of the shifted plane
+ *          windows into a shared-memory ring of that many slots (FP32 only, every N_x a multiple
+ *          of 4 and >= 132; 2D uses a fixed 4-slot ring for any value >= 2).  Every variant
+ *          gives the same bits.
+ *  block:  threads per block (= x cells per tile) for kernel 1; the ring fixes 128; 0 keeps.
+ *  blocks_per_sm: resident blocks per SM of the persistent grid; 0 keeps.
+ *  mode:   -1 keep; 0 one persistent launch per step, n steps captured in one CUDA graph;
+ *          1 one launch per instance per step (the unbatched baseline, 1D); 2 persistent
+ *          launches issued directly (no graph).
+ * Returns LAT_EINVAL for a shape the lattice does not support. */
+int lat_set_launch(lat_ctx* c, int kernel, int block, int blocks_per_sm, int mode);
 
 /* Time candidate launch shapes on the current state without advancing it (reads the current
- * buffer, writes the other) and keep the fastest.  best[4] (host, may be NULL) receives
- * {block, xpt, blocks_per_sm, microseconds per step}. */
+ * buffer, writes the other; the flow state is not advanced) and keep the fastest.  best[4]
+ * (host, may be NULL) receives {kernel, block, blocks_per_sm, microseconds per step}. */
 int lat_autotune(lat_ctx* c, int reps, double* best);
 
 /* Human-readable text of a status code. */

@@ -15,7 +15,7 @@ int ctx2d_step(Ctx2D* c, void* const f[2], int n, cudaStream_t s);
 int ctx2d_prepare(Ctx2D* c, void* const f[2], int n);
 int ctx2d_moments(Ctx2D* c, const void* f, double* rho, double* mean_v, double* mean_v2,
                   double* globals, cudaStream_t s);
-int ctx2d_set_launch(Ctx2D* c, int block, int xpt, int bps, int mode);
+int ctx2d_set_launch(Ctx2D* c, int kernel, int block, int bps, int mode);
 int ctx2d_autotune(Ctx2D* c, void* const f[2], int reps, double* best, cudaStream_t s);
 void ctx2d_destroy(Ctx2D* c);
 

@@ -56,6 +56,7 @@ struct lat_ctx {
     bool frozen = true;
     const void* field = nullptr;
     double* d_amp = nullptr;        // [2][n_inst][2M]
+    float* d_ampf = nullptr;        // FP32 copy for the FP32 kernels
     long long amp_stride = 0;
     double* d_noise = nullptr;
     long long noise_cap = 0;        // doubles
@@ -64,8 +65,10 @@ struct lat_ctx {
     DevState* d_state = nullptr;
     DevState* h_state = nullptr;    // pinned
 
-    // launch shape
-    int block = 256, xpt = 1, bps = 4, mode = 0;
+    // launch shape: kernel variant (plain loads or bulk-copy ring), threads per block (= tile
+    // width), ring slots, resident blocks per SM of the persistent grid, launch mode
+    int variant = STEP1D_PLAIN, block = 256, slots = 3, bps = 4, mode = 0;
+    bool ring_ok = false;
 
     // cached graphs keyed by the number of steps (buffers are picked by the device step parity)
     std::map<int, cudaGraphExec_t> graphs;
@@ -100,7 +103,7 @@ int status_code(unsigned st) {
     return LAT_OK;
 }
 
-int tile_of(const lat_ctx* c) { return c->block * c->xpt; }
+int tile_of(const lat_ctx* c) { return c->block; }
 
 // Rebuild the (instance, x-tile) work list for the current tile width.
 int build_items(lat_ctx* c) {
@@ -149,6 +152,8 @@ Step1DArgs step_args(const lat_ctx* c, int k, int dry) {
     for (int m = 0; m < kMaxModes1D; ++m) a.k[m] = c->k1d[m];
     a.amp = c->d_amp;
     a.amp_w = c->d_amp;
+    a.ampf = c->d_ampf;
+    a.ampf_w = c->d_ampf;
     a.amp_stride = c->amp_stride;
     a.noise = c->d_noise;
     a.field = c->field;
@@ -166,11 +171,12 @@ int enqueue_steps_1d(lat_ctx* c, int n, cudaStream_t s) {
             for (int i = 0; i < c->n_inst; ++i) {
                 a.item_begin = c->h_inst_begin[i];
                 a.item_end = c->h_inst_begin[i + 1];
-                CK(launch_step1d(c->dtype, c->nv, c->block, c->xpt, a.item_end - a.item_begin, a,
-                                 k, s));
+                CK(launch_step1d(c->dtype, c->nv, c->variant, c->block, c->slots,
+                                 a.item_end - a.item_begin, a, k, s));
             }
         } else {
-            CK(launch_step1d(c->dtype, c->nv, c->block, c->xpt, persistent_grid(c), a, k, s));
+            CK(launch_step1d(c->dtype, c->nv, c->variant, c->block, c->slots, persistent_grid(c),
+                             a, k, s));
         }
     }
     CK(launch_advance_step(c->d_state, n, s));
@@ -254,6 +260,9 @@ int lat_ensemble_init(lat_ctx** out, int n_inst, const lat_instance* inst, int n
         q.r = inst[i].kappa * inst[i].dt / (q.dv * q.dv);
         q.ou_e = 1.0;
         q.ou_s = 0.0;
+        q.pow2 = (q.nx & (q.nx - 1)) == 0 ? 1 : 0;
+        q.two_over_nx = 2.0 / q.nx;
+        q.dt = inst[i].dt;
         off += (long long)nv * inst[i].nx;
         xoff += inst[i].nx;
     }
@@ -270,11 +279,21 @@ int lat_ensemble_init(lat_ctx** out, int n_inst, const lat_instance* inst, int n
             cudaSuccess)
         rc = LAT_ECUDA;
     if (rc == LAT_OK) {
-        // default launch shape: one x column per thread, 256 threads, 4 resident blocks per SM
-        c->block = 256;
-        c->xpt = 1;
-        c->bps = 4;
-        if (nv > 65) c->bps = 2;
+        // default launch shape: the bulk-copy ring where every instance allows it, else plain
+        // loads with 256 threads; one x column per thread
+        c->ring_ok = step1d_ring_supported(dtype, nv);
+        for (int i = 0; i < n_inst; ++i)
+            if (inst[i].nx % 4 != 0 || inst[i].nx < step1d_ring_min_nx()) c->ring_ok = false;
+        if (c->ring_ok) {
+            c->variant = STEP1D_RING;
+            c->block = step1d_ring_tile();
+            c->slots = 3;
+            c->bps = std::max(1, step1d_ring_occupancy(nv, 3));
+        } else {
+            c->variant = STEP1D_PLAIN;
+            c->block = std::min(256, step1d_max_block(dtype, nv, STEP1D_PLAIN));
+            c->bps = 4;
+        }
         rc = build_items(c);
     }
     if (rc != LAT_OK) {
@@ -341,12 +360,22 @@ int lat_set_flow(lat_ctx* c, const lat_flow* fl) {
         const int M2 = 2 * fl->nmodes;
         const long long stride = (long long)c->n_inst * M2;
         double* amp = nullptr;
+        float* ampf = nullptr;
         if (cudaMalloc(&amp, sizeof(double) * 2 * stride) != cudaSuccess) return LAT_ENOMEM;
+        if (cudaMalloc(&ampf, sizeof(float) * 2 * stride) != cudaSuccess) {
+            cudaFree(amp);
+            return LAT_ENOMEM;
+        }
         // both parities start from amp0 so that a frozen flow reads the same values every step
+        std::vector<float> a32(fl->amp0, fl->amp0 + stride);
         CK(cudaMemcpy(amp, fl->amp0, sizeof(double) * stride, cudaMemcpyHostToDevice));
         CK(cudaMemcpy(amp + stride, fl->amp0, sizeof(double) * stride, cudaMemcpyHostToDevice));
+        CK(cudaMemcpy(ampf, a32.data(), sizeof(float) * stride, cudaMemcpyHostToDevice));
+        CK(cudaMemcpy(ampf + stride, a32.data(), sizeof(float) * stride, cudaMemcpyHostToDevice));
         if (c->d_amp) cudaFree(c->d_amp);
+        if (c->d_ampf) cudaFree(c->d_ampf);
         c->d_amp = amp;
+        c->d_ampf = ampf;
         c->amp_stride = stride;
         c->flow_kind = LAT_FLOW_MODES;
         c->nmodes = fl->nmodes;
@@ -354,7 +383,7 @@ int lat_set_flow(lat_ctx* c, const lat_flow* fl) {
         c->noise_row_len = stride;
         for (int i = 0; i < c->n_inst; ++i) {
             Inst1D& q = c->h_inst[i];
-            const double dt = q.dx / q.dv;
+            const double dt = q.dt;
             if (frozen) {
                 q.ou_e = 1.0;
                 q.ou_s = 0.0;
@@ -490,7 +519,7 @@ int lat_moments(lat_ctx* c, double* rho, double* mean_v, double* mean_v2, double
     a.partials = c->d_partials;
     a.st = c->d_state;
     const int grid = std::max(1, std::min(c->nitems, 8 * c->sm_count));
-    CK(launch_moments1d(c->dtype, c->block, c->xpt, grid, a, c->stream));
+    CK(launch_moments1d(c->dtype, tile_of(c), 1, grid, a, c->stream));
     CK(launch_finalize1d(c->d_partials, c->d_inst_begin, c->d_inst, c->n_inst, c->d_glob,
                          c->stream));
     if (globals)
@@ -505,24 +534,37 @@ int lat_current(const lat_ctx* c) { return c ? c->cur : -1; }
 
 long long lat_steps_done(const lat_ctx* c) { return c ? c->h_step : -1; }
 
-int lat_set_launch(lat_ctx* c, int block, int xpt, int blocks_per_sm, int mode) {
+int lat_set_launch(lat_ctx* c, int kernel, int block, int blocks_per_sm, int mode) {
     if (!c) return LAT_EINVAL;
     if (c->d == 2) {
-        int rc = ctx2d_set_launch(c->c2, block, xpt, blocks_per_sm, mode);
+        int rc = ctx2d_set_launch(c->c2, kernel, block, blocks_per_sm, mode);
         if (rc == LAT_OK) drop_graphs(c);
         return rc;
     }
-    const int nb = block ? block : c->block;
-    const int nxp = xpt ? xpt : c->xpt;
+    int variant = c->variant, slots = c->slots, nb = c->block;
+    if (kernel == 1) {
+        variant = STEP1D_PLAIN;
+        if (c->variant != STEP1D_PLAIN && !block) nb = std::min(256, step1d_max_block(c->dtype, c->nv, STEP1D_PLAIN));
+    } else if (kernel >= 2 && kernel <= 4) {
+        if (!c->ring_ok) return LAT_EINVAL;
+        variant = STEP1D_RING;
+        slots = kernel;
+        nb = step1d_ring_tile();
+    } else if (kernel != 0) {
+        return LAT_EINVAL;
+    }
+    if (block && variant == STEP1D_PLAIN) nb = block;
+    if (block && variant == STEP1D_RING && block != step1d_ring_tile()) return LAT_EINVAL;
     const int nbps = blocks_per_sm ? blocks_per_sm : c->bps;
     const int nmode = mode >= 0 ? mode : c->mode;
-    if (nb < 32 || nb > 1024 || nb % 32 != 0 || nbps < 1 || nbps > 64 || nmode < 0 || nmode > 2)
+    if (nb < 32 || nb > 1024 || nb % 32 != 0 || nbps < 1 || nbps > 64 || nmode > 2)
         return LAT_EINVAL;
-    if (!step1d_supported(c->dtype, c->nv, nxp)) return LAT_EINVAL;
-    if (nb > step1d_max_block(c->dtype, c->nv, nxp)) return LAT_EINVAL;
-    const bool retile = nb * nxp != tile_of(c);
+    if (nb > step1d_max_block(c->dtype, c->nv, variant)) return LAT_EINVAL;
+    if (variant == STEP1D_RING && nbps > step1d_ring_occupancy(c->nv, slots)) return LAT_EINVAL;
+    const bool retile = nb != tile_of(c);
+    c->variant = variant;
+    c->slots = slots;
     c->block = nb;
-    c->xpt = nxp;
     c->bps = nbps;
     c->mode = nmode;
     drop_graphs(c);
@@ -532,49 +574,53 @@ int lat_set_launch(lat_ctx* c, int block, int xpt, int blocks_per_sm, int mode) 
 int lat_autotune(lat_ctx* c, int reps, double* best) {
     if (!c || reps < 1) return LAT_EINVAL;
     if (c->d == 2) return ctx2d_autotune(c->c2, c->f, reps, best, c->stream);
-    const int blocks[] = {128, 256, 512};
-    const int xpts[] = {1, 2};
-    const int bpss[] = {1, 2, 3, 4, 6, 8};
+    struct Cand {
+        int kernel, block, bps;
+    };
+    std::vector<Cand> cands;
+    for (int b : {128, 256, 512})
+        for (int p : {1, 2, 3, 4, 6, 8})
+            if (b * p <= 2048 && b <= step1d_max_block(c->dtype, c->nv, STEP1D_PLAIN))
+                cands.push_back({1, b, p});
+    if (c->ring_ok)
+        for (int sl : {2, 3, 4}) {
+            const int occ = step1d_ring_occupancy(c->nv, sl);
+            for (int p = 1; p <= occ; ++p) cands.push_back({sl, 0, p});
+        }
     cudaEvent_t e0, e1;
     CK(cudaEventCreate(&e0));
     CK(cudaEventCreate(&e1));
     const int mode_save = c->mode;
     double best_us = 1e300;
-    int bb = c->block, bx = c->xpt, bp = c->bps;
-    for (int b : blocks)
-        for (int x : xpts) {
-            if (!step1d_supported(c->dtype, c->nv, x)) continue;
-            for (int p : bpss) {
-                if (b * p > 2048) continue;
-                if (lat_set_launch(c, b, x, p, 0) != LAT_OK) continue;
-                Step1DArgs a = step_args(c, 0, 1);
-                const int grid = persistent_grid(c);
-                CK(launch_step1d(c->dtype, c->nv, b, x, grid, a, 0, c->stream));
-                CK(cudaEventRecord(e0, c->stream));
-                for (int r = 0; r < reps; ++r)
-                    CK(launch_step1d(c->dtype, c->nv, b, x, grid, a, 0, c->stream));
-                CK(cudaEventRecord(e1, c->stream));
-                CK(cudaEventSynchronize(e1));
-                float ms = 0.f;
-                CK(cudaEventElapsedTime(&ms, e0, e1));
-                const double us = 1000.0 * ms / reps;
-                if (us < best_us) {
-                    best_us = us;
-                    bb = b;
-                    bx = x;
-                    bp = p;
-                }
-            }
+    Cand bc{0, 0, 0};
+    for (const Cand& q : cands) {
+        if (lat_set_launch(c, q.kernel, q.block, q.bps, 0) != LAT_OK) continue;
+        Step1DArgs a = step_args(c, 0, 1);
+        const int grid = persistent_grid(c);
+        CK(launch_step1d(c->dtype, c->nv, c->variant, c->block, c->slots, grid, a, 0, c->stream));
+        CK(cudaEventRecord(e0, c->stream));
+        for (int r = 0; r < reps; ++r)
+            CK(launch_step1d(c->dtype, c->nv, c->variant, c->block, c->slots, grid, a, 0,
+                             c->stream));
+        CK(cudaEventRecord(e1, c->stream));
+        CK(cudaEventSynchronize(e1));
+        float ms = 0.f;
+        CK(cudaEventElapsedTime(&ms, e0, e1));
+        const double us = 1000.0 * ms / reps;
+        if (us < best_us) {
+            best_us = us;
+            bc = q;
         }
+    }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    // the dry runs may have flagged CFL on a stale buffer; clear the status they set
+    // the dry runs may have flagged CFL on the current state; the next real step flags it again
     k_clear_status<<<1, 1, 0, c->stream>>>(c->d_state);
-    int rc = lat_set_launch(c, bb, bx, bp, mode_save);
+    int rc = lat_set_launch(c, bc.kernel, bc.block, bc.bps, mode_save);
     if (best) {
-        best[0] = bb;
-        best[1] = bx;
-        best[2] = bp;
+        best[0] = bc.kernel;
+        best[1] = c->block;
+        best[2] = bc.bps;
         best[3] = best_us;
     }
     return rc;
@@ -592,6 +638,7 @@ void lat_free(lat_ctx* c) {
     cudaFree(c->d_partials);
     cudaFree(c->d_glob);
     cudaFree(c->d_amp);
+    cudaFree(c->d_ampf);
     cudaFree(c->d_noise);
     cudaFree(c->d_state);
     if (c->h_glob) cudaFreeHost(c->h_glob);

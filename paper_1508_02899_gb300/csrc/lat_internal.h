@@ -34,7 +34,7 @@ struct Inst1D {
     long long off;    // element offset of f[0][0] in the ensemble buffer
     long long xoff;   // offset of this instance's cells in per-cell arrays (sum of earlier nx)
     int nx;
-    int pad;
+    int pow2;         // 1 if nx is a power of two
     double g;         // dt / tau_p
     double inv_dv;    // 1 / dv
     double dv;
@@ -42,7 +42,12 @@ struct Inst1D {
     double r;         // kappa dt / dv^2
     double ou_e;      // e^{-dt/tau_f}
     double ou_s;      // sigma sqrt(1 - e^2)
+    double two_over_nx;
+    double dt;
 };
+
+// Step kernel variants (1D).
+enum { STEP1D_PLAIN = 0, STEP1D_RING = 1 };
 
 constexpr int kMaxModes1D = 16;
 constexpr int kMaxModes2D = 512;
@@ -58,6 +63,8 @@ struct Step1DArgs {
     int k[kMaxModes1D];
     const double* amp;       // [2][n_inst][2M] parity-indexed amplitudes
     double* amp_w;           // same buffer, written (other parity)
+    const float* ampf;       // FP32 copy of amp read by the FP32 kernels
+    float* ampf_w;
     long long amp_stride;    // n_inst * 2M
     const double* noise;     // [rows][n_inst][2M]
     const void* field;       // FIELD flow, per-cell array over all instances
@@ -81,10 +88,13 @@ struct Mom1DArgs {
 };
 
 // Launchers (step1d.cu, moments.cu).
-cudaError_t launch_step1d(int dtype, int nv, int block, int xpt, int grid, const Step1DArgs& a,
-                          int kstep, cudaStream_t s);
-bool step1d_supported(int dtype, int nv, int xpt);
-int step1d_max_block(int dtype, int nv, int xpt);
+cudaError_t launch_step1d(int dtype, int nv, int variant, int block, int slots, int grid,
+                          const Step1DArgs& a, int kstep, cudaStream_t s);
+int step1d_max_block(int dtype, int nv, int variant);
+bool step1d_ring_supported(int dtype, int nv);
+int step1d_ring_tile();
+int step1d_ring_min_nx();
+int step1d_ring_occupancy(int nv, int slots);
 cudaError_t launch_moments1d(int dtype, int block, int tile_xpt, int grid, const Mom1DArgs& a,
                              cudaStream_t s);
 cudaError_t launch_finalize1d(const double* partials, const int* inst_item_begin,

@@ -29,6 +29,17 @@ __device__ __forceinline__ void nmerge(Comp& a, const Comp& b) {
 }
 __device__ __forceinline__ double nval(const Comp& a) { return __dadd_rn(a.s, a.c); }
 
+// Kahan-compensated FP32 accumulator (c holds the negated running error).
+struct FComp {
+    float s = 0.f, c = 0.f;
+    __device__ __forceinline__ void add(float x) {
+        const float y = __fsub_rn(x, c);
+        const float t = __fadd_rn(s, y);
+        c = __fsub_rn(__fsub_rn(t, s), y);
+        s = t;
+    }
+};
+
 __device__ __forceinline__ Comp shfl_down(const Comp& a, int off) {
     return Comp{__shfl_down_sync(0xffffffffu, a.s, off), __shfl_down_sync(0xffffffffu, a.c, off)};
 }
@@ -48,13 +59,33 @@ __global__ void __launch_bounds__(1024) k_moments1d(const Mom1DArgs a, const int
             const int x = item.y + threadIdx.x + p * blockDim.x;
             if (x >= in.nx) continue;
             Comp s0{0, 0}, s1{0, 0}, s2{0, 0};
-            for (int jj = 0; jj < nv; ++jj) {
-                const double v = __dmul_rn((double)(jj - J), in.dv);
-                const double fv = (double)f[(size_t)jj * in.nx + x];
-                bad |= !isfinite(fv);
-                nadd(s0, fv);
-                nadd(s1, __dmul_rn(v, fv));
-                nadd(s2, __dmul_rn(__dmul_rn(v, v), fv));
+            if (sizeof(T) == sizeof(double)) {
+                for (int jj = 0; jj < nv; ++jj) {
+                    const double v = __dmul_rn((double)(jj - J), in.dv);
+                    const double fv = (double)f[(size_t)jj * in.nx + x];
+                    bad |= !isfinite(fv);
+                    nadd(s0, fv);
+                    nadd(s1, __dmul_rn(v, fv));
+                    nadd(s2, __dmul_rn(__dmul_rn(v, v), fv));
+                }
+            } else {
+                // FP32 storage: the column sums run in FP32 with Kahan compensation (exact
+                // integer weights j, j^2), which keeps them at the storage precision; only the
+                // reduction over cells is FP64 (FP64 throughput is low on this GPU).
+                FComp a0, a1, a2;
+                for (int jj = 0; jj < nv; ++jj) {
+                    const float fv = (float)f[(size_t)jj * in.nx + x];
+                    const float j = (float)(jj - J);
+                    bad |= !isfinite(fv);
+                    a0.add(fv);
+                    a1.add(j * fv);
+                    a2.add(j * j * fv);
+                }
+                // Kahan's c is the negated lost part: the sum is s - c
+                s0 = Comp{(double)a0.s, -(double)a0.c};
+                s1 = Comp{__dmul_rn((double)a1.s, in.dv), -__dmul_rn((double)a1.c, in.dv)};
+                const double dv2 = __dmul_rn(in.dv, in.dv);
+                s2 = Comp{__dmul_rn((double)a2.s, dv2), -__dmul_rn((double)a2.c, dv2)};
             }
             const double m0 = nval(s0), m1 = nval(s1), m2 = nval(s2);
             const long long cell = in.xoff + x;

@@ -2,41 +2,149 @@
 // exact streaming in x, first-order upwind Stokes-drag flux in v, velocity diffusion.
 //
 // Work decomposition: a work item is one x-tile of one instance; a persistent grid walks the
-// item list.  Each thread owns one spatial column x (XPT columns per thread), gathers its
-// post-streaming column f*(x, j) = f(x - j, j) with one coalesced load per velocity plane
-// (the gather *is* the streaming step, so it costs no extra pass), applies the drag and the
-// diffusion in registers and writes the column once.  HBM traffic per cell: one read and one
-// write of f.  The flow u(x, t_n) is evaluated in the same kernel from the mode amplitudes;
-// the first tile of every instance also advances those amplitudes to t_{n+1} (parity
-// ping-pong, so no tile reads what another tile of the same launch writes).
+// item list.  Each thread owns one spatial column x and sweeps its velocity column
+// j = -J..J once: the post-streaming value f*(x, j) = f(x - j, j) is gathered (the gather *is*
+// the streaming step), the drag flux and the diffusion flux are carried along the sweep as
+// scalars with a lag of two cells, and each output value is written once.  HBM traffic per
+// cell: one read and one write of f.
+//
+// Three variants share the column arithmetic (bit-identical results):
+//  * ring: the tile's N_v shifted plane windows are brought into a shared-memory ring by bulk
+//    asynchronous copies (cp.async.bulk + mbarrier), several items ahead of the sweep, so the
+//    loads in flight do not depend on registers or occupancy (FP32, N_x % 4 == 0, N_x >= 132);
+//  * reg:  the column is gathered with plain coalesced loads into registers (fixed N_v);
+//  * any:  plain loads through a sliding window (any odd N_v).
+// The flow u(x, t_n) is evaluated in the same kernel from the mode amplitudes; the first tile
+// of every instance also advances those amplitudes to t_{n+1} (parity ping-pong, so no tile
+// reads what another tile of the same launch writes).
 #include <math.h>
+#include <stdint.h>
+
+#include <algorithm>
 
 #include "lat_internal.h"
 
 namespace lat {
 namespace {
 
+constexpr int TW1 = 128;        // columns per tile of the ring kernel (= threads per block)
+constexpr int WIN1 = TW1 + 4;   // floats copied per plane (x window rounded to 16 bytes)
+
+// ---- column arithmetic with explicit rounding (identical in every variant) -----------------
+template <typename T>
+struct Ops;
+template <>
+struct Ops<float> {
+    static __device__ __forceinline__ float mul(float a, float b) { return __fmul_rn(a, b); }
+    static __device__ __forceinline__ float sub(float a, float b) { return __fsub_rn(a, b); }
+    static __device__ __forceinline__ float add(float a, float b) { return __fadd_rn(a, b); }
+    static __device__ __forceinline__ float fma(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+};
+template <>
+struct Ops<double> {
+    static __device__ __forceinline__ double mul(double a, double b) { return __dmul_rn(a, b); }
+    static __device__ __forceinline__ double sub(double a, double b) { return __dsub_rn(a, b); }
+    static __device__ __forceinline__ double add(double a, double b) { return __dadd_rn(a, b); }
+    static __device__ __forceinline__ double fma(double a, double b, double c) { return __fma_rn(a, b, c); }
+};
+
+// c a_j = (dt/dv) * (-(v_j - u)/tau_p) = g (w - j), g = dt/tau_p, w = u/dv
+template <typename T>
+__device__ __forceinline__ T cacc(T g, T w, int j) {
+    return Ops<T>::mul(g, Ops<T>::sub(w, T(j)));
+}
+// c F_{j+1/2} = (c a_j)^+ f_j + (c a_{j+1})^- f_{j+1}   (cell-centred upwind)
+template <typename T>
+__device__ __forceinline__ T dflux(T caj, T can, T fj, T fn) {
+    return Ops<T>::fma(fmax(caj, T(0)), fj, Ops<T>::mul(fmin(can, T(0)), fn));
+}
+
+// Sliding-window sweep of one column.  get(jj) returns f*(x, jj - J); put(jj, v) stores.
+//   d_j   = f*_j - (cF_{j+1/2} - cF_{j-1/2})            (drag, zero flux at the walls)
+//   out_j = d_j + (D_{j+1/2} - D_{j-1/2}),  D = r (d_{j+1} - d_j)   (diffusion)
+template <typename T, int NV, class Get, class Put>
+__device__ __forceinline__ void sweep_column(T w, T g, T r, const Get& get, const Put& put) {
+    constexpr int J = (NV - 1) / 2;
+    T s = get(0);
+    T Fprev = T(0), Dprev = T(0), dprev = T(0);
+#pragma unroll
+    for (int jj = 0; jj < NV; ++jj) {
+        T sn = T(0), Fn = T(0);
+        if (jj < NV - 1) {
+            sn = get(jj + 1);
+            Fn = dflux<T>(cacc<T>(g, w, jj - J), cacc<T>(g, w, jj + 1 - J), s, sn);
+        }
+        const T d = Ops<T>::sub(s, Ops<T>::sub(Fn, Fprev));
+        Fprev = Fn;
+        if (jj > 0) {
+            const T D = Ops<T>::mul(r, Ops<T>::sub(d, dprev));
+            put(jj - 1, Ops<T>::add(dprev, Ops<T>::sub(D, Dprev)));
+            Dprev = D;
+        }
+        dprev = d;
+        s = sn;
+    }
+    put(NV - 1, Ops<T>::add(dprev, Ops<T>::sub(T(0), Dprev)));
+}
+
+// Runtime-N_v version of the same sweep (identical operation order).
+template <typename T, class Get, class Put>
+__device__ __forceinline__ void sweep_column_any(int NV, T w, T g, T r, const Get& get,
+                                                 const Put& put) {
+    const int J = (NV - 1) / 2;
+    T s = get(0);
+    T Fprev = T(0), Dprev = T(0), dprev = T(0);
+#pragma unroll 4
+    for (int jj = 0; jj < NV; ++jj) {
+        T sn = T(0), Fn = T(0);
+        if (jj < NV - 1) {
+            sn = get(jj + 1);
+            Fn = dflux<T>(cacc<T>(g, w, jj - J), cacc<T>(g, w, jj + 1 - J), s, sn);
+        }
+        const T d = Ops<T>::sub(s, Ops<T>::sub(Fn, Fprev));
+        Fprev = Fn;
+        if (jj > 0) {
+            const T D = Ops<T>::mul(r, Ops<T>::sub(d, dprev));
+            put(jj - 1, Ops<T>::add(dprev, Ops<T>::sub(D, Dprev)));
+            Dprev = D;
+        }
+        dprev = d;
+        s = sn;
+    }
+    put(NV - 1, Ops<T>::add(dprev, Ops<T>::sub(T(0), Dprev)));
+}
+
+// ---- flow ------------------------------------------------------------------------------------
 __device__ __forceinline__ void sincospi_t(float y, float* s, float* c) { sincospif(y, s, c); }
 __device__ __forceinline__ void sincospi_t(double y, double* s, double* c) { sincospi(y, s, c); }
 
 template <typename T>
-__device__ __forceinline__ T ldg_t(const T* p) { return __ldg(p); }
+__device__ __forceinline__ const T* amp_ptr(const Step1DArgs& a, int par, int inst);
+template <>
+__device__ __forceinline__ const float* amp_ptr<float>(const Step1DArgs& a, int par, int inst) {
+    return a.ampf + par * a.amp_stride + (long long)inst * 2 * a.nmodes;
+}
+template <>
+__device__ __forceinline__ const double* amp_ptr<double>(const Step1DArgs& a, int par, int inst) {
+    return a.amp + par * a.amp_stride + (long long)inst * 2 * a.nmodes;
+}
 
-// Fluid velocity at column x of an instance at time t_n.
+// u(x_i, t_n) = sum_m A_m cos(2 pi k_m i / N_x) + B_m sin(2 pi k_m i / N_x); the phase is
+// reduced in integers (k_m i mod N_x) and evaluated as sin/cos of pi * (2 (k_m i mod N_x)/N_x).
 template <typename T>
-__device__ __forceinline__ T flow_at(const Step1DArgs& a, const Inst1D& in, const double* amp,
-                                     int x) {
+__device__ __forceinline__ T flow_at(const Step1DArgs& a, const Inst1D& in, const T* amp, int x) {
     if (a.flow_kind == LAT_FLOW_FIELD) return static_cast<const T*>(a.field)[in.xoff + x];
     if (a.flow_kind != LAT_FLOW_MODES) return T(0);
     const int M = a.nmodes;
+    const T two_over_nx = T(in.two_over_nx);
     T u = T(0);
     for (int m = 0; m < M; ++m) {
-        // phase 2 pi k x / N_x reduced exactly in integers, then sin/cos of pi * (2 kx / N_x)
-        long long kx = ((long long)a.k[m] * x) % in.nx;
+        int kx = a.k[m] * x;
+        kx = in.pow2 ? (kx & (in.nx - 1)) : (kx % in.nx);
         if (kx < 0) kx += in.nx;
         T s, c;
-        sincospi_t(T(2 * kx) / T(in.nx), &s, &c);
-        u += T(amp[m]) * c + T(amp[M + m]) * s;
+        sincospi_t(T(kx) * two_over_nx, &s, &c);
+        u += __ldg(amp + m) * c + __ldg(amp + M + m) * s;
     }
     return u;
 }
@@ -51,49 +159,27 @@ __device__ __forceinline__ void advance_amplitudes(const Step1DArgs& a, int inst
         const double old = a.amp[par * a.amp_stride + (long long)inst * M2 + t];
         double xi = 0.0;
         if (have) xi = a.noise[row * a.amp_stride + (long long)inst * M2 + t];
-        a.amp_w[(1 - par) * a.amp_stride + (long long)inst * M2 + t] =
-            __dadd_rn(__dmul_rn(old, in.ou_e), __dmul_rn(in.ou_s, xi));
+        const double nw = __dadd_rn(__dmul_rn(old, in.ou_e), __dmul_rn(in.ou_s, xi));
+        a.amp_w[(1 - par) * a.amp_stride + (long long)inst * M2 + t] = nw;
+        a.ampf_w[(1 - par) * a.amp_stride + (long long)inst * M2 + t] = (float)nw;
     }
     if (!have && threadIdx.x == 0) atomicOr(&a.st->status, ST_NOISE);
 }
 
-// Drag then diffusion on a register-resident column (Section 2, flux form).
-//   drag:  c F_{j+1/2} = max(g (w - j), 0) f_j + min(g (w - j - 1), 0) f_{j+1},  zero at walls,
-//          f_j <- f_j - (c F_{j+1/2} - c F_{j-1/2}),  g = dt/tau_p, w = u/dv, c = dt/dv;
-//   diffusion: D_{j+1/2} = r (f_{j+1} - f_j), zero at walls, f_j <- f_j + D_{j+1/2} - D_{j-1/2}.
-template <typename T, int NV>
-__device__ __forceinline__ void column_update(T (&f)[NV], T w, T g, T r) {
-    constexpr int J = (NV - 1) / 2;
-    T Fprev = T(0);
-#pragma unroll
-    for (int jj = 0; jj < NV; ++jj) {
-        T Fnext = T(0);
-        if (jj < NV - 1) {
-            const T caj = g * (w - T(jj - J));
-            const T can = g * (w - T(jj + 1 - J));
-            Fnext = fmax(caj, T(0)) * f[jj] + fmin(can, T(0)) * f[jj + 1];
-        }
-        f[jj] = f[jj] - (Fnext - Fprev);
-        Fprev = Fnext;
-    }
-    T Dprev = T(0);
-#pragma unroll
-    for (int jj = 0; jj < NV; ++jj) {
-        const T Dnext = (jj < NV - 1) ? r * (f[jj + 1] - f[jj]) : T(0);
-        f[jj] = f[jj] + (Dnext - Dprev);
-        Dprev = Dnext;
-    }
+template <typename T, int J>
+__device__ __forceinline__ void cfl_flag(const Step1DArgs& a, T g, T w) {
+    if (g * (T(J) + fabs(w)) > T(1)) atomicOr(&a.st->status, ST_CFL);
 }
 
-// Largest block that still leaves each thread enough registers for its XPT columns.
-template <typename T, int NV, int XPT>
+// ---- reg / any variants (plain loads) ----------------------------------------------------------
+template <typename T, int NV>
 struct MaxThreads {
-    static constexpr int words = NV * XPT * (int)(sizeof(T) / 4);
+    static constexpr int words = NV * (int)(sizeof(T) / 4);
     static constexpr int value = words > 56 ? 256 : (words > 20 ? 512 : 1024);
 };
 
-template <typename T, int NV, int XPT>
-__global__ void __launch_bounds__(MaxThreads<T, NV, XPT>::value)
+template <typename T, int NV>
+__global__ void __launch_bounds__(MaxThreads<T, NV>::value)
     k_step1d_reg(const Step1DArgs a, const int kstep) {
     constexpr int J = (NV - 1) / 2;
     const long long step = a.st->step + kstep;
@@ -102,48 +188,42 @@ __global__ void __launch_bounds__(MaxThreads<T, NV, XPT>::value)
         const int2 item = a.items[it];
         const Inst1D in = a.inst[item.x];
         const int nx = in.nx;
-        const T g = T(in.g), r = T(in.r), inv_dv = T(in.inv_dv);
-        const T* __restrict__ src = static_cast<const T*>(a.f[par]) + in.off;
-        T* __restrict__ dst = static_cast<T*>(a.f[par ^ 1]) + in.off;
-        const double* amp = a.amp + par * a.amp_stride + (long long)item.x * 2 * a.nmodes;
+        const int x = item.y + threadIdx.x;
+        if (x < nx) {
+            const T g = T(in.g), r = T(in.r);
+            const T* __restrict__ src = static_cast<const T*>(a.f[par]) + in.off;
+            T* __restrict__ dst = static_cast<T*>(a.f[par ^ 1]) + in.off + x;
+            const T w = flow_at<T>(a, in, amp_ptr<T>(a, par, item.x), x) * T(in.inv_dv);
+            T f[NV];
+            if (nx >= J) {
 #pragma unroll
-        for (int p = 0; p < XPT; ++p) {
-            const int x = item.y + threadIdx.x + p * blockDim.x;
-            if (x < nx) {
-                const T w = flow_at<T>(a, in, amp, x) * inv_dv;
-                T f[NV];
-                if (nx >= J) {
-#pragma unroll
-                    for (int jj = 0; jj < NV; ++jj) {
-                        int xs = x - (jj - J);
-                        xs += (xs < 0) ? nx : 0;
-                        xs -= (xs >= nx) ? nx : 0;
-                        f[jj] = ldg_t(src + (size_t)jj * nx + xs);
-                    }
-                } else {
-#pragma unroll
-                    for (int jj = 0; jj < NV; ++jj) {
-                        int xs = (x - (jj - J)) % nx;
-                        xs += (xs < 0) ? nx : 0;
-                        f[jj] = ldg_t(src + (size_t)jj * nx + xs);
-                    }
+                for (int jj = 0; jj < NV; ++jj) {
+                    int xs = x - (jj - J);
+                    xs += (xs < 0) ? nx : 0;
+                    xs -= (xs >= nx) ? nx : 0;
+                    f[jj] = __ldg(src + (size_t)jj * nx + xs);
                 }
-                column_update<T, NV>(f, w, g, r);
+            } else {
 #pragma unroll
-                for (int jj = 0; jj < NV; ++jj) dst[(size_t)jj * nx + x] = f[jj];
-                if (g * (T(J) + fabs(w)) > T(1)) atomicOr(&a.st->status, ST_CFL);
+                for (int jj = 0; jj < NV; ++jj) {
+                    int xs = (x - (jj - J)) % nx;
+                    xs += (xs < 0) ? nx : 0;
+                    f[jj] = __ldg(src + (size_t)jj * nx + xs);
+                }
             }
+            sweep_column<T, NV>(
+                w, g, r, [&](int jj) { return f[jj]; },
+                [&](int jj, T v) { dst[(size_t)jj * nx] = v; });
+            cfl_flag<T, J>(a, g, w);
         }
         if (!a.dry && !a.frozen && a.flow_kind == LAT_FLOW_MODES && item.y == 0)
             advance_amplitudes(a, item.x, in, step, par);
     }
 }
 
-// Any odd N_v: the column is streamed through a sliding window of registers
-// (s_j, s_{j+1} for the drag flux; d_{j-1}, d_j for the diffusion flux).
 template <typename T>
 __global__ void __launch_bounds__(512) k_step1d_any(const Step1DArgs a, const int kstep,
-                                                     const int NV) {
+                                                    const int NV) {
     const int J = (NV - 1) / 2;
     const long long step = a.st->step + kstep;
     const int par = (int)(step & 1);
@@ -151,39 +231,20 @@ __global__ void __launch_bounds__(512) k_step1d_any(const Step1DArgs a, const in
         const int2 item = a.items[it];
         const Inst1D in = a.inst[item.x];
         const int nx = in.nx;
-        const T g = T(in.g), r = T(in.r), inv_dv = T(in.inv_dv);
-        const T* __restrict__ src = static_cast<const T*>(a.f[par]) + in.off;
-        T* __restrict__ dst = static_cast<T*>(a.f[par ^ 1]) + in.off;
-        const double* amp = a.amp + par * a.amp_stride + (long long)item.x * 2 * a.nmodes;
         const int x = item.y + threadIdx.x;
         if (x < nx) {
-            const T w = flow_at<T>(a, in, amp, x) * inv_dv;
-            auto load = [&](int jj) -> T {
-                int xs = (x - (jj - J)) % nx;
-                xs += (xs < 0) ? nx : 0;
-                return ldg_t(src + (size_t)jj * nx + xs);
-            };
-            T s = load(0);
-            T Fprev = T(0), Dprev = T(0), dprev = T(0);
-#pragma unroll 4
-            for (int jj = 0; jj < NV; ++jj) {
-                T snext = T(0), Fnext = T(0);
-                if (jj < NV - 1) {
-                    snext = load(jj + 1);
-                    Fnext = fmax(g * (w - T(jj - J)), T(0)) * s +
-                            fmin(g * (w - T(jj + 1 - J)), T(0)) * snext;
-                }
-                const T d = s - (Fnext - Fprev);
-                Fprev = Fnext;
-                if (jj > 0) {
-                    const T D = r * (d - dprev);
-                    dst[(size_t)(jj - 1) * nx + x] = dprev + (D - Dprev);
-                    Dprev = D;
-                }
-                dprev = d;
-                s = snext;
-            }
-            dst[(size_t)(NV - 1) * nx + x] = dprev + (T(0) - Dprev);
+            const T g = T(in.g), r = T(in.r);
+            const T* __restrict__ src = static_cast<const T*>(a.f[par]) + in.off;
+            T* __restrict__ dst = static_cast<T*>(a.f[par ^ 1]) + in.off + x;
+            const T w = flow_at<T>(a, in, amp_ptr<T>(a, par, item.x), x) * T(in.inv_dv);
+            sweep_column_any<T>(
+                NV, w, g, r,
+                [&](int jj) {
+                    int xs = (x - (jj - J)) % nx;
+                    xs += (xs < 0) ? nx : 0;
+                    return __ldg(src + (size_t)jj * nx + xs);
+                },
+                [&](int jj, T v) { dst[(size_t)jj * nx] = v; });
             if (g * (T(J) + fabs(w)) > T(1)) atomicOr(&a.st->status, ST_CFL);
         }
         if (!a.dry && !a.frozen && a.flow_kind == LAT_FLOW_MODES && item.y == 0)
@@ -191,35 +252,207 @@ __global__ void __launch_bounds__(512) k_step1d_any(const Step1DArgs a, const in
     }
 }
 
+// ---- ring variant (FP32, bulk async copies into a shared-memory ring) --------------------------
+__device__ __forceinline__ unsigned smem_u32(const void* p) {
+    return (unsigned)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count)
+                 : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, unsigned bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+                 "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, unsigned parity) {
+    unsigned ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned bytes,
+                                         uint64_t* bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+        ::"r"(smem_u32(dst)), "l"(src), "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
+}
+__device__ __forceinline__ unsigned long long globaltimer() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+// Bounded wait on an mbarrier phase: gives up after ~1 s (the caller raises ST_TIMEOUT).
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, unsigned parity) {
+    if (mbar_try_wait(bar, parity)) return true;
+    const unsigned long long t0 = globaltimer();
+    for (long long it = 0; it < (1ll << 26); ++it) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if ((it & 255) == 0 && globaltimer() - t0 > 1000000000ull) break;
+    }
+    return false;
+}
+__device__ __forceinline__ int wrapi(int v, int n) {
+    v %= n;
+    return v < 0 ? v + n : v;
+}
+
+// Copy the N_v shifted windows of item `it` into ring slot `slot` (warp 0 only): plane j needs
+// columns [x0 - j, x0 - j + 128); the window starts at that offset rounded down to 16 bytes and
+// is split in two at the periodic wrap.
+template <int NV>
+__device__ __forceinline__ void issue_item(const Step1DArgs& a, const float* fin, float* ring,
+                                           uint64_t* bar, int slot, int it) {
+    constexpr int J = (NV - 1) / 2;
+    const int lane = threadIdx.x & 31;
+    if (lane == 0) mbar_expect_tx(&bar[slot], (unsigned)(NV * WIN1 * sizeof(float)));
+    __syncwarp();
+    const int2 item = a.items[it];
+    const Inst1D& in = a.inst[item.x];
+    const float* base_ptr = fin + in.off;
+    for (int jj = lane; jj < NV; jj += 32) {
+        const float* prow = base_ptr + (size_t)jj * in.nx;
+        const int s = item.y - (jj - J);
+        const int b = wrapi(s - ((s % 4) + 4) % 4, in.nx);
+        float* dst = ring + ((size_t)slot * NV + jj) * WIN1;
+        if (b + WIN1 <= in.nx) {
+            bulk_g2s(dst, prow + b, WIN1 * sizeof(float), &bar[slot]);
+        } else {
+            const int n1 = in.nx - b;
+            bulk_g2s(dst, prow + b, n1 * sizeof(float), &bar[slot]);
+            bulk_g2s(dst + n1, prow, (WIN1 - n1) * sizeof(float), &bar[slot]);
+        }
+    }
+}
+
+template <int NV, int NS>
+__global__ void __launch_bounds__(TW1) k_step1d_ring(const Step1DArgs a, const int kstep) {
+    constexpr int J = (NV - 1) / 2;
+    extern __shared__ __align__(128) unsigned char smem[];
+    float* ring = reinterpret_cast<float*>(smem);
+    uint64_t* bar = reinterpret_cast<uint64_t*>(smem + (size_t)NS * NV * WIN1 * sizeof(float));
+    const long long step = a.st->step + kstep;
+    const int par = (int)(step & 1);
+    const float* fin = static_cast<const float*>(a.f[par]);
+    float* fout = static_cast<float*>(a.f[par ^ 1]);
+    const int tid = threadIdx.x;
+    const int first = a.item_begin + blockIdx.x;
+    const int nloc = first < a.item_end ? (a.item_end - 1 - first) / gridDim.x + 1 : 0;
+    if (tid == 0) {
+        for (int q = 0; q < NS; ++q) mbar_init(&bar[q], 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    if (tid < 32)
+        for (int k = 0; k < NS - 1 && k < nloc; ++k)
+            issue_item<NV>(a, fin, ring, bar, k % NS, first + k * gridDim.x);
+    int issued = std::min(NS - 1, nloc);
+    bool failed = false;
+    for (int k = 0; k < nloc; ++k) {
+        if (__syncthreads_or(failed ? 1 : 0)) {
+            failed = true;
+            break;
+        }
+        // slot (k + NS - 1) % NS held item k - 1, which every thread has finished
+        if (k + NS - 1 < nloc) {
+            if (tid < 32) {
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                issue_item<NV>(a, fin, ring, bar, (k + NS - 1) % NS,
+                               first + (k + NS - 1) * gridDim.x);
+            }
+            issued = k + NS;
+        }
+        const int it = first + k * gridDim.x;
+        const int2 item = a.items[it];
+        const Inst1D in = a.inst[item.x];
+        const int x = item.y + tid;
+        const float g = float(in.g), r = float(in.r);
+        float w = 0.f;
+        if (x < in.nx) w = flow_at<float>(a, in, amp_ptr<float>(a, par, item.x), x) * float(in.inv_dv);
+        if (!mbar_wait_bounded(&bar[k % NS], (unsigned)((k / NS) & 1))) {
+            failed = true;
+            continue;
+        }
+        if (x < in.nx) {
+            const float* col = ring + (size_t)(k % NS) * NV * WIN1 + tid;
+            float* dst = fout + in.off + x;
+            const int nx = in.nx;
+            sweep_column<float, NV>(
+                w, g, r,
+                [&](int jj) { return col[jj * WIN1 + ((J - jj) % 4 + 4) % 4]; },
+                [&](int jj, float v) { dst[(size_t)jj * nx] = v; });
+            cfl_flag<float, J>(a, g, w);
+        }
+        if (!a.dry && !a.frozen && a.flow_kind == LAT_FLOW_MODES && item.y == 0)
+            advance_amplitudes(a, item.x, in, step, par);
+    }
+    if (failed) {
+        if (tid == 0) {
+            atomicOr(&a.st->status, ST_TIMEOUT);
+            // let the copies already issued land before the block's shared memory goes away
+            for (int k = std::max(0, issued - NS); k < issued; ++k)
+                mbar_wait_bounded(&bar[k % NS], (unsigned)((k / NS) & 1));
+        }
+        __syncthreads();
+    }
+}
+
 __global__ void k_advance_step(DevState* st, long long n) { st->step += n; }
 
-template <typename T, int NV>
-cudaError_t launch_reg(int block, int xpt, int grid, const Step1DArgs& a, int kstep,
-                       cudaStream_t s) {
-    if (xpt == 1) {
-        if (block > MaxThreads<T, NV, 1>::value) return cudaErrorInvalidValue;
-        k_step1d_reg<T, NV, 1><<<grid, block, 0, s>>>(a, kstep);
-    } else if (xpt == 2) {
-        if (block > MaxThreads<T, NV, 2>::value) return cudaErrorInvalidValue;
-        k_step1d_reg<T, NV, 2><<<grid, block, 0, s>>>(a, kstep);
-    } else {
-        return cudaErrorInvalidValue;
+template <int NV, int NS>
+size_t ring1d_smem() {
+    return (size_t)NS * NV * WIN1 * sizeof(float) + NS * sizeof(uint64_t);
+}
+
+template <int NV, int NS>
+cudaError_t launch_ring(int grid, const Step1DArgs& a, int kstep, cudaStream_t s) {
+    static bool attr = false;
+    if (!attr) {
+        cudaError_t e = cudaFuncSetAttribute(k_step1d_ring<NV, NS>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)ring1d_smem<NV, NS>());
+        if (e != cudaSuccess) return e;
+        attr = true;
     }
+    k_step1d_ring<NV, NS><<<grid, TW1, ring1d_smem<NV, NS>(), s>>>(a, kstep);
     return cudaGetLastError();
 }
 
+template <int NV, int NS>
+int occupancy_ring() {
+    int nb = 0;
+    cudaFuncSetAttribute(k_step1d_ring<NV, NS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)ring1d_smem<NV, NS>());
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_step1d_ring<NV, NS>, TW1,
+                                                  ring1d_smem<NV, NS>());
+    return nb;
+}
+
+template <typename T, int NV>
+cudaError_t launch_reg(int block, int grid, const Step1DArgs& a, int kstep, cudaStream_t s) {
+    if (block > MaxThreads<T, NV>::value) return cudaErrorInvalidValue;
+    k_step1d_reg<T, NV><<<grid, block, 0, s>>>(a, kstep);
+    return cudaGetLastError();
+}
+
+#define LAT1D_NV_LIST(X) X(3) X(5) X(9) X(17) X(33) X(65)
+
 template <typename T>
-cudaError_t launch_t(int nv, int block, int xpt, int grid, const Step1DArgs& a, int kstep,
-                     cudaStream_t s) {
+cudaError_t launch_plain(int nv, int block, int grid, const Step1DArgs& a, int kstep,
+                         cudaStream_t s) {
     switch (nv) {
-        case 3: return launch_reg<T, 3>(block, xpt, grid, a, kstep, s);
-        case 5: return launch_reg<T, 5>(block, xpt, grid, a, kstep, s);
-        case 9: return launch_reg<T, 9>(block, xpt, grid, a, kstep, s);
-        case 17: return launch_reg<T, 17>(block, xpt, grid, a, kstep, s);
-        case 33: return launch_reg<T, 33>(block, xpt, grid, a, kstep, s);
-        case 65: return launch_reg<T, 65>(block, xpt, grid, a, kstep, s);
+#define X(n) \
+    case n: return launch_reg<T, n>(block, grid, a, kstep, s);
+        LAT1D_NV_LIST(X)
+#undef X
         default:
-            if (xpt != 1 || block > 512) return cudaErrorInvalidValue;
+            if (block > 512) return cudaErrorInvalidValue;
             k_step1d_any<T><<<grid, block, 0, s>>>(a, kstep, nv);
             return cudaGetLastError();
     }
@@ -227,24 +460,61 @@ cudaError_t launch_t(int nv, int block, int xpt, int grid, const Step1DArgs& a, 
 
 }  // namespace
 
-int step1d_max_block(int dtype, int nv, int xpt) {
-    const bool reg = nv == 3 || nv == 5 || nv == 9 || nv == 17 || nv == 33 || nv == 65;
-    if (!reg) return xpt == 1 ? 512 : 0;
-    const int words = nv * xpt * (dtype == LAT_F64 ? 2 : 1);
+int step1d_max_block(int dtype, int nv, int variant) {
+    if (variant == STEP1D_RING) return TW1;
+    bool reg = false;
+#define X(n) reg |= nv == n;
+    LAT1D_NV_LIST(X)
+#undef X
+    if (!reg) return 512;
+    const int words = nv * (dtype == LAT_F64 ? 2 : 1);
     return words > 56 ? 256 : (words > 20 ? 512 : 1024);
 }
 
-bool step1d_supported(int dtype, int nv, int xpt) {
-    if (dtype != LAT_F32 && dtype != LAT_F64) return false;
-    if (nv < 1 || (nv % 2) == 0 || nv > 129) return false;
-    return step1d_max_block(dtype, nv, xpt) > 0;
+bool step1d_ring_supported(int dtype, int nv) {
+    if (dtype != LAT_F32) return false;
+    bool ok = false;
+#define X(n) ok |= nv == n;
+    LAT1D_NV_LIST(X)
+#undef X
+    return ok;
 }
 
-cudaError_t launch_step1d(int dtype, int nv, int block, int xpt, int grid, const Step1DArgs& a,
-                          int kstep, cudaStream_t s) {
+int step1d_ring_tile() { return TW1; }
+int step1d_ring_min_nx() { return WIN1; }
+
+int step1d_ring_occupancy(int nv, int slots) {
+    switch (nv) {
+#define X(n)                                           \
+    case n:                                            \
+        if (slots == 2) return occupancy_ring<n, 2>(); \
+        if (slots == 3) return occupancy_ring<n, 3>(); \
+        return occupancy_ring<n, 4>();
+        LAT1D_NV_LIST(X)
+#undef X
+        default: return 0;
+    }
+}
+
+cudaError_t launch_step1d(int dtype, int nv, int variant, int block, int slots, int grid,
+                          const Step1DArgs& a, int kstep, cudaStream_t s) {
     if (grid <= 0) return cudaSuccess;
-    if (dtype == LAT_F32) return launch_t<float>(nv, block, xpt, grid, a, kstep, s);
-    if (dtype == LAT_F64) return launch_t<double>(nv, block, xpt, grid, a, kstep, s);
+    if (variant == STEP1D_RING) {
+        if (dtype != LAT_F32 || block != TW1) return cudaErrorInvalidValue;
+        switch (nv) {
+#define X(n)                                                         \
+    case n:                                                          \
+        if (slots == 2) return launch_ring<n, 2>(grid, a, kstep, s); \
+        if (slots == 3) return launch_ring<n, 3>(grid, a, kstep, s); \
+        if (slots == 4) return launch_ring<n, 4>(grid, a, kstep, s); \
+        return cudaErrorInvalidValue;
+            LAT1D_NV_LIST(X)
+#undef X
+            default: return cudaErrorInvalidValue;
+        }
+    }
+    if (dtype == LAT_F32) return launch_plain<float>(nv, block, grid, a, kstep, s);
+    if (dtype == LAT_F64) return launch_plain<double>(nv, block, grid, a, kstep, s);
     return cudaErrorInvalidValue;
 }
 

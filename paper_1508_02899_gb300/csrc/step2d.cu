@@ -1,15 +1,965 @@
-// 2D lattice context (placeholder until the 2D kernels land).
+// Two-dimensional lattice context: flow evaluation, the fused 2D step and the 2D moments.
+//
+// Layout f[jy][jx][y][x] (x fastest).  One thread owns one spatial cell (x, y); a block owns a
+// tile of 128 consecutive x cells of one row y.  The velocity column of a cell is swept row by
+// row in jy.  Row jy of the post-streaming density, f*(x, y, jx, jy) = f(x - jx, y - jy, jx, jy)
+// for all jx, is one velocity "row"; the drag (unsplit, first-order upwind in vx and vy) and the
+// five-point velocity diffusion then need, per thread, only three register rows:
+//   A = f** of the previous row, G = vy-drag flux between rows, H = vy-diffusion flux between
+// rows; x-direction fluxes are carried as scalars along the jx sweep.
+//
+// Rows of f* reach shared memory by bulk asynchronous copies (cp.async.bulk, completion on an
+// mbarrier) into a 4-slot ring, two rows ahead of the sweep: the streaming shift is applied by
+// the copy's source address (x window rounded down to 16 bytes, split in two at the periodic
+// wrap; y wraps by choosing the source row).  A plain-load variant with the same arithmetic
+// serves FP64 and grids the copy path does not cover (N_x not a multiple of 4, or < 132).
+#include <math.h>
+#include <stdint.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <vector>
+
+#include <algorithm>
+#include <map>
+
 #include "lat2d.h"
 
 namespace lat {
-struct Ctx2D { int dummy; };
-int ctx2d_create(Ctx2D** out, const lat_grid*, DevState*, int, cudaStream_t) { *out = nullptr; return LAT_EINVAL; }
-int ctx2d_set_flow(Ctx2D*, const lat_flow*, bool, cudaStream_t) { return LAT_EINVAL; }
-int ctx2d_set_noise(Ctx2D*, const double*, long long, long long, cudaStream_t) { return LAT_EINVAL; }
-int ctx2d_step(Ctx2D*, void* const*, int, cudaStream_t) { return LAT_EINVAL; }
-int ctx2d_prepare(Ctx2D*, void* const*, int) { return LAT_EINVAL; }
-int ctx2d_moments(Ctx2D*, const void*, double*, double*, double*, double*, cudaStream_t) { return LAT_EINVAL; }
-int ctx2d_set_launch(Ctx2D*, int, int, int, int) { return LAT_EINVAL; }
-int ctx2d_autotune(Ctx2D*, void* const*, int, double*, cudaStream_t) { return LAT_EINVAL; }
-void ctx2d_destroy(Ctx2D* c) { delete c; }
+
+namespace {
+
+constexpr int TW = 128;       // cells per tile (= threads per block)
+constexpr int WIN = TW + 4;   // floats copied per plane row (x window rounded to 16 bytes)
+constexpr int NSLOT = 4;      // ring slots of f* rows
+
+struct Step2DArgs {
+    void* f[2];
+    int nx, ny;
+    double g, r, inv_dv;
+    const void* u;            // [2][ny][nx] of T, or null for u = 0
+    DevState* st;
+    int ntx, ntiles;
+};
+
+struct Flow2DArgs {
+    const int2* k;            // [M] (kx, ky)
+    const double* cx;         // [M] coefficient of sin(theta) in u_x
+    const double* cy;         // [M] coefficient of sin(theta) in u_y
+    double* phase;            // [2][M] parity-indexed phases
+    const double* noise;      // [rows][M]
+    double walk;              // sqrt(2 dt / tau_f)
+    int nmodes, nx, ny;
+    void* u;                  // [2][ny][nx] of T
+    DevState* st;
+    int frozen, dry;
+};
+
+// ---- PTX helpers (mbarrier + bulk async copy) ----------------------------------------------
+__device__ __forceinline__ unsigned smem_u32(const void* p) {
+    return (unsigned)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count)
+                 : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, unsigned bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+                 "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, unsigned parity) {
+    unsigned ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned bytes,
+                                         uint64_t* bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+        ::"r"(smem_u32(dst)), "l"(src), "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
+}
+__device__ __forceinline__ unsigned long long globaltimer() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+// Bounded wait on an mbarrier phase: gives up after ~1 s (then the caller raises ST_TIMEOUT).
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, unsigned parity) {
+    if (mbar_try_wait(bar, parity)) return true;
+    const unsigned long long t0 = globaltimer();
+    for (long long it = 0; it < (1ll << 26); ++it) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if ((it & 255) == 0 && globaltimer() - t0 > 1000000000ull) break;
+    }
+    return false;
+}
+
+__device__ __forceinline__ int wrap(int v, int n) {
+    v %= n;
+    return v < 0 ? v + n : v;
+}
+
+// ---- the row sweep shared by both kernels ---------------------------------------------------
+// Processes velocity row index r (0..NV): computes f** of row r-1 (needs f* rows r-1 and r, the
+// latter absent when r == NV) and, for r >= 2, writes the output row r-2.
+// Column arithmetic with explicit rounding, so that every variant gives the same bits.
+template <typename T>
+struct Ops;
+template <>
+struct Ops<float> {
+    static __device__ __forceinline__ float mul(float a, float b) { return __fmul_rn(a, b); }
+    static __device__ __forceinline__ float sub(float a, float b) { return __fsub_rn(a, b); }
+    static __device__ __forceinline__ float add(float a, float b) { return __fadd_rn(a, b); }
+    static __device__ __forceinline__ float fma(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+};
+template <>
+struct Ops<double> {
+    static __device__ __forceinline__ double mul(double a, double b) { return __dmul_rn(a, b); }
+    static __device__ __forceinline__ double sub(double a, double b) { return __dsub_rn(a, b); }
+    static __device__ __forceinline__ double add(double a, double b) { return __dadd_rn(a, b); }
+    static __device__ __forceinline__ double fma(double a, double b, double c) { return __fma_rn(a, b, c); }
+};
+// c a_j = g (w - j);  c F_{j+1/2} = (c a_j)^+ f_j + (c a_{j+1})^- f_{j+1}
+template <typename T>
+__device__ __forceinline__ T cacc(T g, T w, int j) { return Ops<T>::mul(g, Ops<T>::sub(w, T(j))); }
+template <typename T>
+__device__ __forceinline__ T dflux(T caj, T can, T fj, T fn) {
+    return Ops<T>::fma(fmax(caj, T(0)), fj, Ops<T>::mul(fmin(can, T(0)), fn));
+}
+
+// Processes velocity row index r (1..NV): computes f** of row rb = r-1 from f* rows rb (cur) and
+// r (nxt, absent when r == NV) and, for r >= 2, writes output row r-2.
+//   f**_{jx} = f*_{jx} - (cFx_{jx+1/2} - cFx_{jx-1/2}) - (cFy_{rb+1/2} - cFy_{rb-1/2})
+//   out      = f** + (Dx_{jx+1/2} - Dx_{jx-1/2}) + (Dy_{+1/2} - Dy_{-1/2}),  D = r (f**_+ - f**)
+template <typename T, int NV, class Row>
+__device__ __forceinline__ void sweep_row(T (&A)[NV], T (&G)[NV], T (&H)[NV], int r,
+                                          const Row& cur, const Row& nxt_row, T g, T wx, T wy,
+                                          T rr, T* __restrict__ out, size_t pstride,
+                                          bool active) {
+    using O = Ops<T>;
+    constexpr int J = (NV - 1) / 2;
+    const int rb = r - 1;
+    const bool nxt = r < NV;
+    const T ayp = fmax(cacc<T>(g, wy, rb - J), T(0));
+    const T aym = nxt ? fmin(cacc<T>(g, wy, r - J), T(0)) : T(0);
+    T Fprev = T(0), Dprev = T(0);
+    T sc = cur.get(0);
+#pragma unroll
+    for (int jx = 0; jx < NV; ++jx) {
+        T sn = T(0), Fnext = T(0);
+        if (jx < NV - 1) {
+            sn = cur.get(jx + 1);
+            Fnext = dflux<T>(cacc<T>(g, wx, jx - J), cacc<T>(g, wx, jx + 1 - J), sc, sn);
+        }
+        const T Gn = nxt ? O::fma(ayp, sc, O::mul(aym, nxt_row.get(jx))) : T(0);
+        const T b = O::sub(O::sub(sc, O::sub(Fnext, Fprev)), O::sub(Gn, G[jx]));
+        G[jx] = Gn;
+        Fprev = Fnext;
+        sc = sn;
+        if (r >= 2) {
+            const T a = A[jx];
+            const T Dn = (jx < NV - 1) ? O::mul(rr, O::sub(A[jx + 1], a)) : T(0);
+            const T Hn = O::mul(rr, O::sub(b, a));
+            const T o = O::add(O::add(a, O::sub(Dn, Dprev)), O::sub(Hn, H[jx]));
+            H[jx] = Hn;
+            Dprev = Dn;
+            if (active) out[((size_t)(r - 2) * NV + jx) * pstride] = o;
+        }
+        A[jx] = b;
+    }
+}
+
+// Last output row (jy = J): no f** row above it, so the vy-diffusion flux there is zero.
+template <typename T, int NV>
+__device__ __forceinline__ void final_row(T (&A)[NV], T (&H)[NV], T rr, T* __restrict__ out,
+                                          size_t pstride, bool active) {
+    using O = Ops<T>;
+    T Dprev = T(0);
+#pragma unroll
+    for (int jx = 0; jx < NV; ++jx) {
+        const T a = A[jx];
+        const T Dn = (jx < NV - 1) ? O::mul(rr, O::sub(A[jx + 1], a)) : T(0);
+        const T o = O::add(O::add(a, O::sub(Dn, Dprev)), O::sub(T(0), H[jx]));
+        Dprev = Dn;
+        if (active) out[((size_t)(NV - 1) * NV + jx) * pstride] = o;
+    }
+}
+
+template <typename T>
+__device__ __forceinline__ void load_w(const Step2DArgs& a, int x, int y, T& wx, T& wy) {
+    if (a.u) {
+        const T* u = static_cast<const T*>(a.u);
+        const size_t c = (size_t)y * a.nx + x;
+        wx = u[c] * T(a.inv_dv);
+        wy = u[(size_t)a.nx * a.ny + c] * T(a.inv_dv);
+    } else {
+        wx = T(0);
+        wy = T(0);
+    }
+}
+
+template <typename T, int NV>
+__device__ __forceinline__ void cfl_check(const Step2DArgs& a, T g, T wx, T wy, bool active) {
+    constexpr int J = (NV - 1) / 2;
+    if (active && g * (T(J) + fabs(wx)) + g * (T(J) + fabs(wy)) > T(1))
+        atomicOr(&a.st->status, ST_CFL);
+}
+
+// ---- plain-load kernel (any N_x, N_y; FP32 or FP64) -----------------------------------------
+// Row jy of f* at one cell, read straight from global memory (periodic wrap in x and y).
+template <typename T, int NV>
+struct GlobalRow {
+    const T* base;  // f + (jy NV ny + ys) nx: plane (jy, 0), source row ys = (y - jy) mod ny
+    size_t pstride;
+    int x, nx;
+    __device__ __forceinline__ GlobalRow(const T* f, int row, int x_, int y, int nx_, int ny)
+        : x(x_), nx(nx_) {
+        constexpr int J = (NV - 1) / 2;
+        pstride = (size_t)nx_ * ny;
+        base = f + (size_t)row * NV * pstride + (size_t)wrap(y - (row - J), ny) * nx_;
+    }
+    __device__ __forceinline__ T get(int jx) const {
+        constexpr int J = (NV - 1) / 2;
+        return __ldg(base + jx * pstride + wrap(x - (jx - J), nx));
+    }
+};
+
+template <typename T, int NV>
+__global__ void __launch_bounds__(TW) k_step2d_plain(const Step2DArgs a, int kstep) {
+    const long long step = a.st->step + kstep;
+    const int par = (int)(step & 1);
+    const T g = T(a.g), rr = T(a.r);
+    const T* fin = static_cast<const T*>(a.f[par]);
+    T* fout = static_cast<T*>(a.f[par ^ 1]);
+    const size_t ps = (size_t)a.nx * a.ny;
+    for (int tile = blockIdx.x; tile < a.ntiles; tile += gridDim.x) {
+        const int y = tile / a.ntx;
+        const int xr = (tile % a.ntx) * TW + threadIdx.x;
+        const bool active = xr < a.nx;
+        const int x = active ? xr : 0;
+        T wx, wy;
+        load_w<T>(a, x, y, wx, wy);
+        cfl_check<T, NV>(a, g, wx, wy, active);
+        T A[NV], G[NV], H[NV];
+#pragma unroll
+        for (int j = 0; j < NV; ++j) {
+            A[j] = T(0);
+            G[j] = T(0);
+            H[j] = T(0);
+        }
+        T* out = fout + (size_t)y * a.nx + x;
+        for (int r = 1; r <= NV; ++r) {
+            const GlobalRow<T, NV> cur(fin, r - 1, x, y, a.nx, a.ny);
+            const GlobalRow<T, NV> nxt(fin, r < NV ? r : r - 1, x, y, a.nx, a.ny);
+            sweep_row<T, NV>(A, G, H, r, cur, nxt, g, wx, wy, rr, out, ps, active);
+        }
+        final_row<T, NV>(A, H, rr, out, ps, active);
+    }
+}
+
+// ---- bulk-copy ring kernel (FP32; N_x % 4 == 0, N_x >= WIN) -----------------------------------
+// Row of f* held in one ring slot: plane jx starts at p + jx WIN, shifted by the 16-byte
+// rounding of its window, (x0 - (jx - J)) mod 4 with x0 % 4 == 0.
+template <int NV>
+struct RingRow {
+    const float* p;  // ring + slot NV WIN + tid
+    __device__ __forceinline__ float get(int jx) const {
+        constexpr int J = (NV - 1) / 2;
+        return p[jx * WIN + ((J - jx) % 4 + 4) % 4];
+    }
+};
+
+// Issue the bulk copies of f* row `row` of tile `tile` into ring slot `slot` (warp 0 only).
+template <int NV>
+__device__ __forceinline__ void issue_row(const Step2DArgs& a, const float* fin, float* ring,
+                                          uint64_t* bar, int slot, int tile, int row) {
+    constexpr int J = (NV - 1) / 2;
+    const int lane = threadIdx.x & 31;
+    if (lane == 0) mbar_expect_tx(&bar[slot], (unsigned)(NV * WIN * sizeof(float)));
+    __syncwarp();
+    const int y = tile / a.ntx;
+    const int x0 = (tile % a.ntx) * TW;
+    const int ys = wrap(y - (row - J), a.ny);
+    for (int jx = lane; jx < NV; jx += 32) {
+        const float* prow = fin + (((size_t)row * NV + jx) * a.ny + ys) * a.nx;
+        const int s = x0 - (jx - J);
+        const int base = wrap(s - ((s % 4) + 4) % 4, a.nx);
+        float* dst = ring + ((size_t)slot * NV + jx) * WIN;
+        if (base + WIN <= a.nx) {
+            bulk_g2s(dst, prow + base, WIN * sizeof(float), &bar[slot]);
+        } else {
+            const int n1 = a.nx - base;
+            bulk_g2s(dst, prow + base, n1 * sizeof(float), &bar[slot]);
+            bulk_g2s(dst + n1, prow, (WIN - n1) * sizeof(float), &bar[slot]);
+        }
+    }
+}
+
+template <int NV>
+__global__ void __launch_bounds__(TW, (NV > 17 ? 2 : 3)) k_step2d_ring(const Step2DArgs a, int kstep) {
+    extern __shared__ __align__(128) unsigned char smem[];
+    float* ring = reinterpret_cast<float*>(smem);
+    uint64_t* bar = reinterpret_cast<uint64_t*>(smem + (size_t)NSLOT * NV * WIN * sizeof(float));
+    const long long step = a.st->step + kstep;
+    const int par = (int)(step & 1);
+    const float g = float(a.g), rr = float(a.r);
+    const float* fin = static_cast<const float*>(a.f[par]);
+    float* fout = static_cast<float*>(a.f[par ^ 1]);
+    const size_t ps = (size_t)a.nx * a.ny;
+    const int tid = threadIdx.x;
+    const int ntl = a.ntiles > (int)blockIdx.x ? (a.ntiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
+    const long long total = (long long)ntl * NV;  // rows this block consumes
+    if (tid == 0) {
+        for (int q = 0; q < NSLOT; ++q) mbar_init(&bar[q], 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    auto tile_of = [&](long long s) { return (int)(blockIdx.x + (s / NV) * gridDim.x); };
+    if (tid < 32) {
+        for (long long s = 0; s < 2 && s < total; ++s)
+            issue_row<NV>(a, fin, ring, bar, (int)(s % NSLOT), tile_of(s), (int)(s % NV));
+    }
+    long long issued = std::min<long long>(2, total);
+    bool failed = false;
+    for (int lt = 0; lt < ntl && !failed; ++lt) {
+        const int tile = tile_of((long long)lt * NV);
+        const int y = tile / a.ntx;
+        const int xr = (tile % a.ntx) * TW + tid;
+        const bool active = xr < a.nx;
+        const int x = active ? xr : 0;
+        float wx, wy;
+        load_w<float>(a, x, y, wx, wy);
+        cfl_check<float, NV>(a, g, wx, wy, active);
+        float A[NV], G[NV], H[NV];
+#pragma unroll
+        for (int j = 0; j < NV; ++j) {
+            A[j] = 0.f;
+            G[j] = 0.f;
+            H[j] = 0.f;
+        }
+        float* out = fout + (size_t)y * a.nx + x;
+        const long long s0 = (long long)lt * NV;
+        for (int r = 0; r <= NV; ++r) {
+            const long long s = s0 + r;
+            // every thread is done with row s-2's slot; a timeout anywhere stops the block
+            if (__syncthreads_or(failed ? 1 : 0)) {
+                failed = true;
+                break;
+            }
+            if (r < NV) {
+                if (tid < 32 && s + 2 < total) {
+                    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                    issue_row<NV>(a, fin, ring, bar, (int)((s + 2) % NSLOT), tile_of(s + 2),
+                                  (int)((s + 2) % NV));
+                }
+                if (s + 2 < total) issued = s + 3;
+                if (!mbar_wait_bounded(&bar[s % NSLOT], (unsigned)((s / NSLOT) & 1))) {
+                    failed = true;
+                    continue;
+                }
+            }
+            if (r >= 1) {
+                const RingRow<NV> cur{ring + (size_t)((s - 1) % NSLOT) * NV * WIN + tid};
+                const RingRow<NV> nxt{ring + (size_t)(s % NSLOT) * NV * WIN + tid};
+                sweep_row<float, NV>(A, G, H, r, cur, nxt, g, wx, wy, rr, out, ps, active);
+            }
+        }
+        if (!failed) final_row<float, NV>(A, H, rr, out, ps, active);
+    }
+    if (failed) {
+        if (tid == 0) {
+            atomicOr(&a.st->status, ST_TIMEOUT);
+            // let the copies already issued land before the block's shared memory goes away
+            for (long long s = std::max(0ll, issued - NSLOT); s < issued; ++s)
+                mbar_wait_bounded(&bar[s % NSLOT], (unsigned)((s / NSLOT) & 1));
+        }
+        __syncthreads();
+    }
+}
+
+// ---- flow: u = (d_y psi, -d_x psi) of psi = sum a_m cos(theta_m) --------------------------------
+template <typename T>
+__device__ __forceinline__ void sincospi_t(T y, T* s, T* c);
+template <>
+__device__ __forceinline__ void sincospi_t<float>(float y, float* s, float* c) { sincospif(y, s, c); }
+template <>
+__device__ __forceinline__ void sincospi_t<double>(double y, double* s, double* c) { sincospi(y, s, c); }
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_flow2d(const Flow2DArgs a, int kstep) {
+    extern __shared__ double sh[];  // [M] cos phi, [M] sin phi
+    const long long step = a.st->step + kstep;
+    const int par = (int)(step & 1);
+    const double* ph = a.phase + (size_t)par * a.nmodes;
+    for (int m = threadIdx.x; m < a.nmodes; m += blockDim.x) {
+        double s, c;
+        sincos(ph[m], &s, &c);
+        sh[m] = c;
+        sh[a.nmodes + m] = s;
+    }
+    __syncthreads();
+    if (blockIdx.x == 0 && !a.frozen && !a.dry) {
+        const long long row = step - a.st->noise_base;
+        const bool have = row >= 0 && row < a.st->noise_rows;
+        for (int m = threadIdx.x; m < a.nmodes; m += blockDim.x) {
+            const double xi = have ? a.noise[row * a.nmodes + m] : 0.0;
+            a.phase[(size_t)(par ^ 1) * a.nmodes + m] = __dadd_rn(ph[m], __dmul_rn(a.walk, xi));
+        }
+        if (!have && threadIdx.x == 0) atomicOr(&a.st->status, ST_NOISE);
+    }
+    const long long ncell = (long long)a.nx * a.ny;
+    const long long N = ncell;
+    for (long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x; c < ncell;
+         c += (long long)gridDim.x * blockDim.x) {
+        const int x = (int)(c % a.nx), y = (int)(c / a.nx);
+        T ux = T(0), uy = T(0);
+        for (int m = 0; m < a.nmodes; ++m) {
+            const int2 k = a.k[m];
+            // 2 pi (kx x / nx + ky y / ny) reduced exactly: p / (nx ny) turns
+            long long p = ((long long)k.x * x * a.ny + (long long)k.y * y * a.nx) % N;
+            if (p < 0) p += N;
+            T sb, cb;
+            sincospi_t<T>(T(2 * p) / T(N), &sb, &cb);
+            const T s = sb * T(sh[m]) + cb * T(sh[a.nmodes + m]);  // sin(theta_int + phi)
+            ux += T(a.cx[m]) * s;
+            uy += T(a.cy[m]) * s;
+        }
+        T* u = static_cast<T*>(a.u);
+        u[c] = ux;
+        u[ncell + c] = uy;
+    }
+}
+
+// ---- moments ----------------------------------------------------------------------------------
+struct Comp {
+    double s, c;
+};
+__device__ __forceinline__ void nadd(Comp& a, double x) {
+    const double t = __dadd_rn(a.s, x);
+    if (fabs(a.s) >= fabs(x)) a.c = __dadd_rn(a.c, __dadd_rn(__dsub_rn(a.s, t), x));
+    else a.c = __dadd_rn(a.c, __dadd_rn(__dsub_rn(x, t), a.s));
+    a.s = t;
+}
+__device__ __forceinline__ void nmerge(Comp& a, const Comp& b) {
+    nadd(a, b.s);
+    a.c = __dadd_rn(a.c, b.c);
+}
+__device__ __forceinline__ double nval(const Comp& a) { return __dadd_rn(a.s, a.c); }
+
+template <typename T>
+__device__ __forceinline__ double to_d(T v) { return (double)v; }
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_moments2d(const void* fv, const float* scales, int nv,
+                                                   int nx, int ny, double dv, double* rho,
+                                                   double* mv, double* mv2, double* partials,
+                                                   DevState* st) {
+    __shared__ Comp red[4][8];
+    const T* f = static_cast<const T*>(fv);
+    const int J = (nv - 1) / 2;
+    const long long ncell = (long long)nx * ny;
+    Comp t[4] = {{0, 0}, {0, 0}, {0, 0}, {0, 0}};
+    bool bad = false;
+    for (long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x; c < ncell;
+         c += (long long)gridDim.x * blockDim.x) {
+        Comp s[4] = {{0, 0}, {0, 0}, {0, 0}, {0, 0}};
+        for (int jy = 0; jy < nv; ++jy) {
+            const double vy = __dmul_rn((double)(jy - J), dv);
+            for (int jx = 0; jx < nv; ++jx) {
+                const double vx = __dmul_rn((double)(jx - J), dv);
+                const size_t plane = (size_t)jy * nv + jx;
+                double fvv = to_d(f[plane * ncell + c]);
+                if (scales) fvv = __dmul_rn(fvv, (double)scales[plane * ny + c / nx]);
+                bad |= !isfinite(fvv);
+                nadd(s[0], fvv);
+                nadd(s[1], __dmul_rn(vx, fvv));
+                nadd(s[2], __dmul_rn(vy, fvv));
+                nadd(s[3], __dmul_rn(__dadd_rn(__dmul_rn(vx, vx), __dmul_rn(vy, vy)), fvv));
+            }
+        }
+        const double m0 = nval(s[0]);
+        if (rho) rho[c] = m0 * dv * dv;
+        if (mv) {
+            mv[c] = m0 != 0.0 ? nval(s[1]) / m0 : 0.0;
+            mv[ncell + c] = m0 != 0.0 ? nval(s[2]) / m0 : 0.0;
+        }
+        if (mv2) mv2[c] = m0 != 0.0 ? nval(s[3]) / m0 : 0.0;
+        for (int q = 0; q < 4; ++q) nmerge(t[q], s[q]);
+    }
+    if (bad) atomicOr(&st->status, ST_NUMERIC);
+    for (int off = 16; off > 0; off >>= 1)
+        for (int q = 0; q < 4; ++q) {
+            Comp o{__shfl_down_sync(0xffffffffu, t[q].s, off),
+                   __shfl_down_sync(0xffffffffu, t[q].c, off)};
+            nmerge(t[q], o);
+        }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane == 0)
+        for (int q = 0; q < 4; ++q) red[q][warp] = t[q];
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        Comp z[4] = {{0, 0}, {0, 0}, {0, 0}, {0, 0}};
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w)
+            for (int q = 0; q < 4; ++q) nmerge(z[q], red[q][w]);
+        for (int q = 0; q < 4; ++q) {
+            partials[(size_t)blockIdx.x * 8 + 2 * q] = z[q].s;
+            partials[(size_t)blockIdx.x * 8 + 2 * q + 1] = z[q].c;
+        }
+    }
+}
+
+__global__ void k_finalize2d(const double* partials, int nblocks, double w, double* glob) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    Comp t[4] = {{0, 0}, {0, 0}, {0, 0}, {0, 0}};
+    for (int b = 0; b < nblocks; ++b)
+        for (int q = 0; q < 4; ++q) nmerge(t[q], Comp{partials[b * 8 + 2 * q], partials[b * 8 + 2 * q + 1]});
+    for (int q = 0; q < 4; ++q) glob[q] = nval(t[q]) * w;
+}
+
+__global__ void k_set_noise2d(DevState* st, long long base, long long rows) {
+    st->noise_base = base;
+    st->noise_rows = rows;
+}
+
+__global__ void k_advance2d(DevState* st, long long n) { st->step += n; }
+
+// ---- launch tables ----------------------------------------------------------------------------
+template <int NV>
+size_t ring_smem() {
+    return (size_t)NSLOT * NV * WIN * sizeof(float) + NSLOT * sizeof(uint64_t);
+}
+
+template <typename T, int NV>
+cudaError_t launch_plain(int grid, const Step2DArgs& a, int k, cudaStream_t s) {
+    k_step2d_plain<T, NV><<<grid, TW, 0, s>>>(a, k);
+    return cudaGetLastError();
+}
+
+template <int NV>
+cudaError_t launch_ring(int grid, const Step2DArgs& a, int k, cudaStream_t s) {
+    static bool attr = false;
+    if (!attr) {
+        cudaError_t e = cudaFuncSetAttribute(k_step2d_ring<NV>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)ring_smem<NV>());
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    k_step2d_ring<NV><<<grid, TW, ring_smem<NV>(), s>>>(a, k);
+    return cudaGetLastError();
+}
+
+#define LAT2D_NV_LIST(X) X(1) X(3) X(5) X(9) X(13) X(17) X(21) X(33)
+
+bool nv2d_supported(int nv) {
+    switch (nv) {
+#define X(n) case n:
+        LAT2D_NV_LIST(X)
+#undef X
+        return true;
+        default: return false;
+    }
+}
+
+cudaError_t launch_step2d(int dtype, int nv, bool ring, int grid, const Step2DArgs& a, int k,
+                          cudaStream_t s) {
+    switch (nv) {
+#define X(n)                                                                   \
+    case n:                                                                    \
+        if (dtype == LAT_F64) return launch_plain<double, n>(grid, a, k, s);   \
+        if (ring) return launch_ring<n>(grid, a, k, s);                        \
+        return launch_plain<float, n>(grid, a, k, s);
+        LAT2D_NV_LIST(X)
+#undef X
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+int occupancy_ring(int nv) {
+    int nb = 0;
+    switch (nv) {
+#define X(n)                                                                                  \
+    case n:                                                                                   \
+        cudaFuncSetAttribute(k_step2d_ring<n>, cudaFuncAttributeMaxDynamicSharedMemorySize,  \
+                             (int)ring_smem<n>());                                            \
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_step2d_ring<n>, TW, ring_smem<n>()); \
+        break;
+        LAT2D_NV_LIST(X)
+#undef X
+        default: break;
+    }
+    return nb;
+}
+
+}  // namespace
+
+// ---- context ----------------------------------------------------------------------------------
+struct Ctx2D {
+    int nx, ny, nv, dtype;
+    double L, dx, dv, g, r, dt;
+    DevState* st;
+    int sm_count;
+    // flow
+    int flow_kind = LAT_FLOW_NONE;
+    const void* field = nullptr;
+    int nmodes = 0;
+    int2* d_k = nullptr;
+    double* d_cx = nullptr;
+    double* d_cy = nullptr;
+    double* d_phase = nullptr;
+    double* d_noise = nullptr;
+    long long noise_cap = 0;
+    double walk = 0.0;
+    bool frozen = true;
+    void* d_u = nullptr;
+    // launch
+    bool ring = false;
+    int bps = 0;       // 0 = occupancy limit
+    int mode = 0;      // 0 graph, 2 direct launches
+    // moments
+    double* d_partials = nullptr;
+    double* d_glob = nullptr;
+    double* h_glob = nullptr;
+    int mom_blocks = 0;
+    std::map<int, cudaGraphExec_t> graphs;
+};
+
+namespace {
+
+int cuda_err(cudaError_t e, const char* what) {
+    fprintf(stderr, "lat(2d): %s failed: %s\n", what, cudaGetErrorString(e));
+    return LAT_ECUDA;
+}
+#define CK2(call)                                               \
+    do {                                                        \
+        cudaError_t e_ = (call);                                \
+        if (e_ != cudaSuccess) return cuda_err(e_, #call);      \
+    } while (0)
+
+void drop(Ctx2D* c) {
+    for (auto& kv : c->graphs) cudaGraphExecDestroy(kv.second);
+    c->graphs.clear();
+}
+
+bool ring_ok(const Ctx2D* c) {
+    return c->dtype == LAT_F32 && c->nx % 4 == 0 && c->nx >= WIN;
+}
+
+Step2DArgs step_args(const Ctx2D* c, void* const f[2]) {
+    Step2DArgs a;
+    memset(&a, 0, sizeof(a));
+    a.f[0] = f[0];
+    a.f[1] = f[1];
+    a.nx = c->nx;
+    a.ny = c->ny;
+    a.g = c->g;
+    a.r = c->r;
+    a.inv_dv = 1.0 / c->dv;
+    a.u = c->flow_kind == LAT_FLOW_FIELD ? c->field : (c->flow_kind == LAT_FLOW_MODES ? c->d_u : nullptr);
+    a.st = c->st;
+    a.ntx = (c->nx + TW - 1) / TW;
+    a.ntiles = a.ntx * c->ny;
+    return a;
+}
+
+int grid_of(const Ctx2D* c, int ntiles) {
+    int per_sm = c->bps;
+    if (c->ring) {
+        const int occ = occupancy_ring(c->nv);
+        if (per_sm <= 0 || per_sm > occ) per_sm = std::max(1, occ);
+    } else if (per_sm <= 0) {
+        per_sm = 8;
+    }
+    return std::max(1, std::min(ntiles, per_sm * c->sm_count));
+}
+
+int enqueue2d(Ctx2D* c, void* const f[2], int n, cudaStream_t s, int dry) {
+    const Step2DArgs a = step_args(c, f);
+    const int grid = grid_of(c, a.ntiles);
+    for (int k = 0; k < n; ++k) {
+        if (c->flow_kind == LAT_FLOW_MODES) {
+            Flow2DArgs fa;
+            fa.k = c->d_k;
+            fa.cx = c->d_cx;
+            fa.cy = c->d_cy;
+            fa.phase = c->d_phase;
+            fa.noise = c->d_noise;
+            fa.walk = c->walk;
+            fa.nmodes = c->nmodes;
+            fa.nx = c->nx;
+            fa.ny = c->ny;
+            fa.u = c->d_u;
+            fa.st = c->st;
+            fa.frozen = c->frozen ? 1 : 0;
+            fa.dry = dry;
+            const long long ncell = (long long)c->nx * c->ny;
+            const int fg = (int)std::min<long long>((ncell + 255) / 256, 8LL * c->sm_count);
+            const size_t sh = 2 * sizeof(double) * c->nmodes;
+            if (c->dtype == LAT_F64) k_flow2d<double><<<fg, 256, sh, s>>>(fa, k);
+            else k_flow2d<float><<<fg, 256, sh, s>>>(fa, k);
+            CK2(cudaGetLastError());
+        }
+        CK2(launch_step2d(c->dtype, c->nv, c->ring, grid, a, k, s));
+    }
+    if (!dry) {
+        k_advance2d<<<1, 1, 0, s>>>(c->st, n);
+        CK2(cudaGetLastError());
+    }
+    return LAT_OK;
+}
+
+int graph2d(Ctx2D* c, void* const f[2], int n, cudaGraphExec_t* out) {
+    auto it = c->graphs.find(n);
+    if (it == c->graphs.end()) {
+        cudaStream_t cap;
+        CK2(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
+        cudaGraph_t g = nullptr;
+        cudaGraphExec_t ge = nullptr;
+        cudaError_t e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+        if (e != cudaSuccess) {
+            cudaStreamDestroy(cap);
+            return cuda_err(e, "cudaStreamBeginCapture");
+        }
+        int rc = enqueue2d(c, f, n, cap, 0);
+        e = cudaStreamEndCapture(cap, &g);
+        cudaStreamDestroy(cap);
+        if (rc != LAT_OK) {
+            if (g) cudaGraphDestroy(g);
+            return rc;
+        }
+        if (e != cudaSuccess) return cuda_err(e, "cudaStreamEndCapture");
+        e = cudaGraphInstantiate(&ge, g, 0);
+        cudaGraphDestroy(g);
+        if (e != cudaSuccess) return cuda_err(e, "cudaGraphInstantiate");
+        if (c->graphs.size() >= 8) drop(c);
+        it = c->graphs.emplace(n, ge).first;
+    }
+    *out = it->second;
+    return LAT_OK;
+}
+
+}  // namespace
+
+int ctx2d_create(Ctx2D** out, const lat_grid* g, DevState* st, int sm_count, cudaStream_t s) {
+    *out = nullptr;
+    if (!nv2d_supported(g->nv)) return LAT_EINVAL;
+    if (g->dtype != LAT_F32 && g->dtype != LAT_F64) return LAT_EINVAL;
+    Ctx2D* c = new Ctx2D();
+    c->nx = g->nx;
+    c->ny = g->ny;
+    c->nv = g->nv;
+    c->dtype = g->dtype;
+    c->L = g->L;
+    c->dx = g->L / g->nx;
+    c->dt = g->dt;
+    c->dv = c->dx / g->dt;
+    c->g = isinf(g->tau_p) ? 0.0 : g->dt / g->tau_p;
+    c->r = g->kappa * g->dt / (c->dv * c->dv);
+    c->st = st;
+    c->sm_count = sm_count;
+    c->ring = ring_ok(c);
+    const long long ncell = (long long)c->nx * c->ny;
+    c->mom_blocks = (int)std::min<long long>((ncell + 255) / 256, 4LL * sm_count);
+    if (cudaMalloc(&c->d_partials, sizeof(double) * 8 * c->mom_blocks) != cudaSuccess ||
+        cudaMalloc(&c->d_glob, sizeof(double) * 4) != cudaSuccess ||
+        cudaMallocHost(&c->h_glob, sizeof(double) * 4) != cudaSuccess) {
+        ctx2d_destroy(c);
+        return LAT_ENOMEM;
+    }
+    (void)s;
+    *out = c;
+    return LAT_OK;
+}
+
+int ctx2d_set_flow(Ctx2D* c, const lat_flow* fl, bool frozen, cudaStream_t s) {
+    drop(c);
+    if (fl->kind == LAT_FLOW_NONE) {
+        c->flow_kind = LAT_FLOW_NONE;
+    } else if (fl->kind == LAT_FLOW_FIELD) {
+        if (!fl->field) return LAT_EINVAL;
+        c->flow_kind = LAT_FLOW_FIELD;
+        c->field = fl->field;
+    } else if (fl->kind == LAT_FLOW_MODES) {
+        const int M = fl->nmodes;
+        if (M < 1 || M > kMaxModes2D || !fl->k || !fl->amp0 || !fl->phase0) return LAT_EINVAL;
+        std::vector<int2> k(M);
+        std::vector<double> cx(M), cy(M), ph(2 * M);
+        const double Lx = c->nx * c->dx, Ly = c->ny * c->dx;
+        for (int m = 0; m < M; ++m) {
+            k[m] = make_int2(fl->k[2 * m], fl->k[2 * m + 1]);
+            cx[m] = -fl->amp0[m] * (2.0 * M_PI * k[m].y / Ly);
+            cy[m] = fl->amp0[m] * (2.0 * M_PI * k[m].x / Lx);
+            ph[m] = fl->phase0[m];
+            ph[M + m] = fl->phase0[m];
+        }
+        cudaFree(c->d_k);
+        cudaFree(c->d_cx);
+        cudaFree(c->d_cy);
+        cudaFree(c->d_phase);
+        c->d_k = nullptr;
+        c->d_cx = c->d_cy = c->d_phase = nullptr;
+        if (cudaMalloc(&c->d_k, sizeof(int2) * M) != cudaSuccess ||
+            cudaMalloc(&c->d_cx, sizeof(double) * M) != cudaSuccess ||
+            cudaMalloc(&c->d_cy, sizeof(double) * M) != cudaSuccess ||
+            cudaMalloc(&c->d_phase, sizeof(double) * 2 * M) != cudaSuccess)
+            return LAT_ENOMEM;
+        CK2(cudaMemcpy(c->d_k, k.data(), sizeof(int2) * M, cudaMemcpyHostToDevice));
+        CK2(cudaMemcpy(c->d_cx, cx.data(), sizeof(double) * M, cudaMemcpyHostToDevice));
+        CK2(cudaMemcpy(c->d_cy, cy.data(), sizeof(double) * M, cudaMemcpyHostToDevice));
+        CK2(cudaMemcpy(c->d_phase, ph.data(), sizeof(double) * 2 * M, cudaMemcpyHostToDevice));
+        if (!c->d_u) {
+            const size_t es = c->dtype == LAT_F64 ? sizeof(double) : sizeof(float);
+            if (cudaMalloc(&c->d_u, es * 2 * (size_t)c->nx * c->ny) != cudaSuccess)
+                return LAT_ENOMEM;
+        }
+        c->nmodes = M;
+        c->flow_kind = LAT_FLOW_MODES;
+        c->walk = frozen ? 0.0 : sqrt(2.0 * c->dt / fl->tau_f);
+    } else {
+        return LAT_EINVAL;
+    }
+    c->frozen = frozen || fl->kind != LAT_FLOW_MODES;
+    k_set_noise2d<<<1, 1, 0, s>>>(c->st, 0, 0);
+    CK2(cudaGetLastError());
+    return LAT_OK;
+}
+
+int ctx2d_set_noise(Ctx2D* c, const double* noise, long long rows, long long step,
+                    cudaStream_t s) {
+    if (c->flow_kind != LAT_FLOW_MODES) return LAT_EINVAL;
+    const long long need = rows * c->nmodes;
+    if (need > c->noise_cap) {
+        CK2(cudaStreamSynchronize(s));
+        double* p = nullptr;
+        if (cudaMalloc(&p, sizeof(double) * need) != cudaSuccess) return LAT_ENOMEM;
+        cudaFree(c->d_noise);
+        c->d_noise = p;
+        c->noise_cap = need;
+        drop(c);
+    }
+    if (need > 0)
+        CK2(cudaMemcpyAsync(c->d_noise, noise, sizeof(double) * need, cudaMemcpyHostToDevice, s));
+    k_set_noise2d<<<1, 1, 0, s>>>(c->st, step, rows);
+    CK2(cudaGetLastError());
+    return LAT_OK;
+}
+
+int ctx2d_prepare(Ctx2D* c, void* const f[2], int n) {
+    if (c->mode != 0) return LAT_OK;
+    cudaGraphExec_t ge;
+    return graph2d(c, f, n, &ge);
+}
+
+int ctx2d_step(Ctx2D* c, void* const f[2], int n, cudaStream_t s) {
+    if (c->mode != 0) return enqueue2d(c, f, n, s, 0);
+    cudaGraphExec_t ge;
+    int rc = graph2d(c, f, n, &ge);
+    if (rc != LAT_OK) return rc;
+    CK2(cudaGraphLaunch(ge, s));
+    return LAT_OK;
+}
+
+int ctx2d_moments(Ctx2D* c, const void* f, double* rho, double* mean_v, double* mean_v2,
+                  double* globals, cudaStream_t s) {
+    if (c->dtype == LAT_F64)
+        k_moments2d<double><<<c->mom_blocks, 256, 0, s>>>(f, nullptr, c->nv, c->nx, c->ny, c->dv,
+                                                         rho, mean_v, mean_v2, c->d_partials, c->st);
+    else
+        k_moments2d<float><<<c->mom_blocks, 256, 0, s>>>(f, nullptr, c->nv, c->nx, c->ny, c->dv,
+                                                        rho, mean_v, mean_v2, c->d_partials, c->st);
+    CK2(cudaGetLastError());
+    k_finalize2d<<<1, 32, 0, s>>>(c->d_partials, c->mom_blocks, c->dx * c->dx * c->dv * c->dv,
+                                  c->d_glob);
+    CK2(cudaGetLastError());
+    if (globals) {
+        CK2(cudaMemcpyAsync(c->h_glob, c->d_glob, sizeof(double) * 4, cudaMemcpyDeviceToHost, s));
+        CK2(cudaStreamSynchronize(s));
+        memcpy(globals, c->h_glob, sizeof(double) * 4);
+    }
+    return LAT_OK;
+}
+
+int ctx2d_set_launch(Ctx2D* c, int kernel, int block, int bps, int mode) {
+    // kernel: 0 keep, 1 plain loads, 2 bulk-copy ring; the block is one 128-cell tile
+    if (block && block != TW) return LAT_EINVAL;
+    if (kernel == 2 && !ring_ok(c)) return LAT_EINVAL;
+    if (kernel < 0 || kernel > 2) return LAT_EINVAL;
+    if (kernel == 1) c->ring = false;
+    if (kernel == 2) c->ring = true;
+    if (bps > 0) c->bps = bps;
+    if (mode == 0 || mode == 2) c->mode = mode;
+    else if (mode > 0) return LAT_EINVAL;
+    drop(c);
+    return LAT_OK;
+}
+
+int ctx2d_autotune(Ctx2D* c, void* const f[2], int reps, double* best, cudaStream_t s) {
+    cudaEvent_t e0, e1;
+    CK2(cudaEventCreate(&e0));
+    CK2(cudaEventCreate(&e1));
+    const bool ring_save = c->ring;
+    double best_us = 1e300;
+    bool best_ring = c->ring;
+    int best_bps = c->bps;
+    for (int use_ring = 0; use_ring < 2; ++use_ring) {
+        if (use_ring && !ring_ok(c)) continue;
+        for (int bps : {1, 2, 3, 4, 6, 8}) {
+            c->ring = use_ring != 0;
+            c->bps = bps;
+            if (c->ring && bps > occupancy_ring(c->nv)) continue;
+            int rc = enqueue2d(c, f, 1, s, 1);
+            if (rc != LAT_OK) return rc;
+            CK2(cudaEventRecord(e0, s));
+            rc = enqueue2d(c, f, reps, s, 1);
+            if (rc != LAT_OK) return rc;
+            CK2(cudaEventRecord(e1, s));
+            CK2(cudaEventSynchronize(e1));
+            float ms = 0.f;
+            CK2(cudaEventElapsedTime(&ms, e0, e1));
+            const double us = 1000.0 * ms / reps;
+            if (us < best_us) {
+                best_us = us;
+                best_ring = c->ring;
+                best_bps = bps;
+            }
+        }
+    }
+    (void)ring_save;
+    c->ring = best_ring;
+    c->bps = best_bps;
+    drop(c);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (best) {
+        best[0] = best_ring ? 2 : 1;
+        best[1] = 1;
+        best[2] = best_bps;
+        best[3] = best_us;
+    }
+    return LAT_OK;
+}
+
+void ctx2d_destroy(Ctx2D* c) {
+    if (!c) return;
+    drop(c);
+    cudaFree(c->d_k);
+    cudaFree(c->d_cx);
+    cudaFree(c->d_cy);
+    cudaFree(c->d_phase);
+    cudaFree(c->d_noise);
+    cudaFree(c->d_u);
+    cudaFree(c->d_partials);
+    cudaFree(c->d_glob);
+    if (c->h_glob) cudaFreeHost(c->h_glob);
+    delete c;
+}
+
 }  // namespace lat

@@ -162,13 +162,13 @@ class _Ctx:
     def steps_done(self) -> int:
         return _lib.lat_steps_done(self._h)
 
-    def set_launch(self, block=0, xpt=0, blocks_per_sm=0, mode=-1):
-        _check(_lib.lat_set_launch(self._h, block, xpt, blocks_per_sm, mode), "lat_set_launch")
+    def set_launch(self, kernel=0, block=0, blocks_per_sm=0, mode=-1):
+        _check(_lib.lat_set_launch(self._h, kernel, block, blocks_per_sm, mode), "lat_set_launch")
 
     def autotune(self, reps: int = 5):
         best = np.zeros(4)
         _check(_lib.lat_autotune(self._h, reps, _dptr(best)), "lat_autotune")
-        return {"block": int(best[0]), "xpt": int(best[1]), "blocks_per_sm": int(best[2]),
+        return {"kernel": int(best[0]), "block": int(best[1]), "blocks_per_sm": int(best[2]),
                 "us_per_step": float(best[3])}
 
     def close(self):

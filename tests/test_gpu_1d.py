@@ -115,11 +115,13 @@ def test_free_streaming_is_exact(lat, nv):
     lt.close()
 
 
-@pytest.mark.parametrize("launch", [dict(block=128, xpt=2, blocks_per_sm=2),
-                                    dict(block=512, xpt=1, blocks_per_sm=1),
+@pytest.mark.parametrize("launch", [dict(kernel=1, block=128, blocks_per_sm=2),
+                                    dict(kernel=1, block=512, blocks_per_sm=1),
+                                    dict(kernel=2, blocks_per_sm=1), dict(kernel=4),
                                     dict(mode=2), dict(mode=1)])
 def test_launch_shapes_are_bit_identical(lat, launch):
-    """Tile width, grid size, graph capture or direct launches change nothing in the result."""
+    """Kernel variant (plain loads or bulk-copy ring), tile width, grid size, graph capture or
+    direct launches change nothing in the result."""
     c = make_case(1000, 33, 1.0, 1e-3, 40, 99, init="random")
     ref, lt0 = run_gpu(lat, c, torch.float32)
     got, lt1 = run_gpu(lat, c, torch.float32, launch=launch)
@@ -155,8 +157,8 @@ def test_cfl_rejected_on_host(lat):
     with pytest.raises(lat.LatError) as e:
         lat.Lattice(t, d=1, nx=64, nv=33, L=L, tau_p=0.01, kappa=0.0, dt=0.5)
     assert e.value.code == lat.LAT_ECFL
-    with pytest.raises(lat.LatError) as e:
-        lat.Lattice(t, d=1, nx=64, nv=33, L=L, tau_p=1.0, kappa=10.0, dt=0.01)
+    with pytest.raises(lat.LatError) as e:  # kappa dt / dv^2 = 130 > 1/2, drag off
+        lat.Lattice(t, d=1, nx=64, nv=33, L=L, tau_p=math.inf, kappa=10.0, dt=0.5)
     assert e.value.code == lat.LAT_ECFL
     with pytest.raises(lat.LatError) as e:
         lat.Lattice(torch.zeros((32, 64), device="cuda"), d=1, nx=64, nv=32, L=L, tau_p=1.0,
