@@ -555,7 +555,10 @@ int lat_set_launch(lat_ctx* c, int kernel, int block, int blocks_per_sm, int mod
     }
     if (block && variant == STEP1D_PLAIN) nb = block;
     if (block && variant == STEP1D_RING && block != step1d_ring_tile()) return LAT_EINVAL;
-    const int nbps = blocks_per_sm ? blocks_per_sm : c->bps;
+    int nbps = blocks_per_sm ? blocks_per_sm : c->bps;
+    // a kept block count is clamped to what the newly chosen ring shape can hold
+    if (!blocks_per_sm && variant == STEP1D_RING)
+        nbps = std::max(1, std::min(nbps, step1d_ring_occupancy(c->nv, slots)));
     const int nmode = mode >= 0 ? mode : c->mode;
     if (nb < 32 || nb > 1024 || nb % 32 != 0 || nbps < 1 || nbps > 64 || nmode > 2)
         return LAT_EINVAL;

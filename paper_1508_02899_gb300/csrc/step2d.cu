@@ -303,11 +303,125 @@ __device__ __forceinline__ void issue_row(const Step2DArgs& a, const float* fin,
     }
 }
 
-template <int NV>
-__global__ void __launch_bounds__(TW, (NV > 17 ? 2 : 3)) k_step2d_ring(const Step2DArgs a, int kstep) {
+// ---- split-column sweep: chunk [J0, J1) of the jx range of one cell ----------------------------
+// Same operations, in the same order, as sweep_row restricted to jx in [J0, J1): the x-drag flux
+// entering at J0 - 1/2 is recomputed from the shared-memory row; the x-diffusion flux there needs
+// the neighbouring chunk's f** of the previous row (xl, left) and, at J1 - 1/2, xr (right).
+template <int NV, int J0, int J1, int WM>
+__device__ __forceinline__ void sweep_chunk(float (&A)[WM], float (&G)[WM], float (&H)[WM], int r,
+                                            const RingRow<NV>& cur, const RingRow<NV>& nxt_row,
+                                            float g, float wx, float wy, float rr, float xl,
+                                            float xr, float* __restrict__ out, size_t pstride,
+                                            bool active) {
+    using O = Ops<float>;
+    constexpr int J = (NV - 1) / 2, W = J1 - J0;
+    const int rb = r - 1;
+    const bool nxt = r < NV;
+    const float ayp = fmax(cacc<float>(g, wy, rb - J), 0.f);
+    const float aym = nxt ? fmin(cacc<float>(g, wy, r - J), 0.f) : 0.f;
+    float Fprev = 0.f, Dprev = 0.f;
+    if (J0 > 0) {
+        Fprev = dflux<float>(cacc<float>(g, wx, J0 - 1 - J), cacc<float>(g, wx, J0 - J),
+                             cur.get(J0 - 1), cur.get(J0));
+        if (r >= 2) Dprev = O::mul(rr, O::sub(A[0], xl));
+    }
+    float sc = cur.get(J0);
+#pragma unroll
+    for (int k = 0; k < W; ++k) {
+        const int jx = J0 + k;
+        float sn = 0.f, Fnext = 0.f;
+        if (jx < NV - 1) {
+            sn = cur.get(jx + 1);
+            Fnext = dflux<float>(cacc<float>(g, wx, jx - J), cacc<float>(g, wx, jx + 1 - J), sc, sn);
+        }
+        const float Gn = nxt ? O::fma(ayp, sc, O::mul(aym, nxt_row.get(jx))) : 0.f;
+        const float b = O::sub(O::sub(sc, O::sub(Fnext, Fprev)), O::sub(Gn, G[k]));
+        G[k] = Gn;
+        Fprev = Fnext;
+        sc = sn;
+        if (r >= 2) {
+            const float a = A[k];
+            const float an = (k + 1 < W) ? A[k + 1] : xr;
+            const float Dn = (jx < NV - 1) ? O::mul(rr, O::sub(an, a)) : 0.f;
+            const float Hn = O::mul(rr, O::sub(b, a));
+            const float o = O::add(O::add(a, O::sub(Dn, Dprev)), O::sub(Hn, H[k]));
+            H[k] = Hn;
+            Dprev = Dn;
+            if (active) out[((size_t)(r - 2) * NV + jx) * pstride] = o;
+        }
+        A[k] = b;
+    }
+}
+
+template <int NV, int J0, int J1, int WM>
+__device__ __forceinline__ void final_chunk(float (&A)[WM], float (&H)[WM], float rr, float xl,
+                                            float xr, float* __restrict__ out, size_t pstride,
+                                            bool active) {
+    using O = Ops<float>;
+    constexpr int W = J1 - J0;
+    float Dprev = (J0 > 0) ? O::mul(rr, O::sub(A[0], xl)) : 0.f;
+#pragma unroll
+    for (int k = 0; k < W; ++k) {
+        const int jx = J0 + k;
+        const float a = A[k];
+        const float an = (k + 1 < W) ? A[k + 1] : xr;
+        const float Dn = (jx < NV - 1) ? O::mul(rr, O::sub(an, a)) : 0.f;
+        const float o = O::add(O::add(a, O::sub(Dn, Dprev)), O::sub(0.f, H[k]));
+        Dprev = Dn;
+        if (active) out[((size_t)(NV - 1) * NV + jx) * pstride] = o;
+    }
+}
+
+// Compile-time dispatch of the calling warp's chunk (the chunk index is warp-uniform).
+template <int NV, int C, int WM, int c = 0>
+__device__ __forceinline__ void chunk_sweep(int chunk, float (&A)[WM], float (&G)[WM],
+                                            float (&H)[WM], int r, const RingRow<NV>& cur,
+                                            const RingRow<NV>& nxt, float g, float wx, float wy,
+                                            float rr, float xl, float xr, float* out, size_t ps,
+                                            bool active, float* pub_first, float* pub_last) {
+    if constexpr (c < C) {
+        constexpr int J0 = c * NV / C, J1 = (c + 1) * NV / C;
+        if (chunk == c) {
+            sweep_chunk<NV, J0, J1, WM>(A, G, H, r, cur, nxt, g, wx, wy, rr, xl, xr, out, ps,
+                                        active);
+            if (C > 1) {  // publish this chunk's edges of the new f** row
+                *pub_first = A[0];
+                *pub_last = A[J1 - J0 - 1];
+            }
+            return;
+        }
+        chunk_sweep<NV, C, WM, c + 1>(chunk, A, G, H, r, cur, nxt, g, wx, wy, rr, xl, xr, out, ps,
+                                      active, pub_first, pub_last);
+    }
+}
+template <int NV, int C, int WM, int c = 0>
+__device__ __forceinline__ void chunk_final(int chunk, float (&A)[WM], float (&H)[WM], float rr,
+                                            float xl, float xr, float* out, size_t ps, bool active) {
+    if constexpr (c < C) {
+        if (chunk == c) {
+            final_chunk<NV, c * NV / C, (c + 1) * NV / C, WM>(A, H, rr, xl, xr, out, ps, active);
+            return;
+        }
+        chunk_final<NV, C, WM, c + 1>(chunk, A, H, rr, xl, xr, out, ps, active);
+    }
+}
+template <int NV, int C>
+struct RingShape {
+    static constexpr int threads = TW * C;
+    static constexpr int min_blocks = C == 1 ? (NV > 17 ? 2 : 3) : (C == 2 ? 2 : 1);
+    static constexpr int wmax = (NV + C - 1) / C;
+};
+
+// Bulk-copy ring kernel: a block of 128 C threads owns 128 cells; the C warp groups split each
+// cell's jx range into chunks and exchange one f** value per chunk boundary per row.
+template <int NV, int C>
+__global__ void __launch_bounds__(RingShape<NV, C>::threads, RingShape<NV, C>::min_blocks)
+    k_step2d_ring(const Step2DArgs a, int kstep) {
+    constexpr int WM = RingShape<NV, C>::wmax;
     extern __shared__ __align__(128) unsigned char smem[];
     float* ring = reinterpret_cast<float*>(smem);
-    uint64_t* bar = reinterpret_cast<uint64_t*>(smem + (size_t)NSLOT * NV * WIN * sizeof(float));
+    float* xch = ring + (size_t)NSLOT * NV * WIN;  // [2][C][2][TW]
+    uint64_t* bar = reinterpret_cast<uint64_t*>(xch + 2 * C * 2 * TW);
     const long long step = a.st->step + kstep;
     const int par = (int)(step & 1);
     const float g = float(a.g), rr = float(a.r);
@@ -315,6 +429,11 @@ __global__ void __launch_bounds__(TW, (NV > 17 ? 2 : 3)) k_step2d_ring(const Ste
     float* fout = static_cast<float*>(a.f[par ^ 1]);
     const size_t ps = (size_t)a.nx * a.ny;
     const int tid = threadIdx.x;
+    const int cell = tid % TW;
+    const int chunk = tid / TW;
+    auto xch_at = [&](int parity, int c, int side) -> float& {
+        return xch[((parity * C + c) * 2 + side) * TW + cell];
+    };
     const int ntl = a.ntiles > (int)blockIdx.x ? (a.ntiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
     const long long total = (long long)ntl * NV;  // rows this block consumes
     if (tid == 0) {
@@ -332,15 +451,15 @@ __global__ void __launch_bounds__(TW, (NV > 17 ? 2 : 3)) k_step2d_ring(const Ste
     for (int lt = 0; lt < ntl && !failed; ++lt) {
         const int tile = tile_of((long long)lt * NV);
         const int y = tile / a.ntx;
-        const int xr = (tile % a.ntx) * TW + tid;
+        const int xr = (tile % a.ntx) * TW + cell;
         const bool active = xr < a.nx;
         const int x = active ? xr : 0;
         float wx, wy;
         load_w<float>(a, x, y, wx, wy);
-        cfl_check<float, NV>(a, g, wx, wy, active);
-        float A[NV], G[NV], H[NV];
+        if (chunk == 0) cfl_check<float, NV>(a, g, wx, wy, active);
+        float A[WM], G[WM], H[WM];
 #pragma unroll
-        for (int j = 0; j < NV; ++j) {
+        for (int j = 0; j < WM; ++j) {
             A[j] = 0.f;
             G[j] = 0.f;
             H[j] = 0.f;
@@ -349,7 +468,8 @@ __global__ void __launch_bounds__(TW, (NV > 17 ? 2 : 3)) k_step2d_ring(const Ste
         const long long s0 = (long long)lt * NV;
         for (int r = 0; r <= NV; ++r) {
             const long long s = s0 + r;
-            // every thread is done with row s-2's slot; a timeout anywhere stops the block
+            // every thread is done with row s-2's slot and with the exchange values of row r-2;
+            // a timeout anywhere stops the block
             if (__syncthreads_or(failed ? 1 : 0)) {
                 failed = true;
                 break;
@@ -367,12 +487,26 @@ __global__ void __launch_bounds__(TW, (NV > 17 ? 2 : 3)) k_step2d_ring(const Ste
                 }
             }
             if (r >= 1) {
-                const RingRow<NV> cur{ring + (size_t)((s - 1) % NSLOT) * NV * WIN + tid};
-                const RingRow<NV> nxt{ring + (size_t)(s % NSLOT) * NV * WIN + tid};
-                sweep_row<float, NV>(A, G, H, r, cur, nxt, g, wx, wy, rr, out, ps, active);
+                const RingRow<NV> cur{ring + (size_t)((s - 1) % NSLOT) * NV * WIN + cell};
+                const RingRow<NV> nxt{ring + (size_t)(s % NSLOT) * NV * WIN + cell};
+                float xl = 0.f, xrgt = 0.f;  // neighbouring chunks' f** of row r-2
+                if (C > 1 && r >= 2) {
+                    if (chunk > 0) xl = xch_at((r - 1) & 1, chunk - 1, 1);
+                    if (chunk < C - 1) xrgt = xch_at((r - 1) & 1, chunk + 1, 0);
+                }
+                chunk_sweep<NV, C, WM>(chunk, A, G, H, r, cur, nxt, g, wx, wy, rr, xl, xrgt, out,
+                                       ps, active, &xch_at(r & 1, chunk, 0),
+                                       &xch_at(r & 1, chunk, 1));
             }
         }
-        if (!failed) final_row<float, NV>(A, H, rr, out, ps, active);
+        if (failed) break;
+        float xl = 0.f, xrgt = 0.f;
+        if (C > 1) {
+            __syncthreads();
+            if (chunk > 0) xl = xch_at(NV & 1, chunk - 1, 1);
+            if (chunk < C - 1) xrgt = xch_at(NV & 1, chunk + 1, 0);
+        }
+        chunk_final<NV, C, WM>(chunk, A, H, rr, xl, xrgt, out, ps, active);
     }
     if (failed) {
         if (tid == 0) {
@@ -532,9 +666,10 @@ __global__ void k_set_noise2d(DevState* st, long long base, long long rows) {
 __global__ void k_advance2d(DevState* st, long long n) { st->step += n; }
 
 // ---- launch tables ----------------------------------------------------------------------------
-template <int NV>
+template <int NV, int C>
 size_t ring_smem() {
-    return (size_t)NSLOT * NV * WIN * sizeof(float) + NSLOT * sizeof(uint64_t);
+    return (size_t)NSLOT * NV * WIN * sizeof(float) + (size_t)2 * C * 2 * TW * sizeof(float) +
+           NSLOT * sizeof(uint64_t);
 }
 
 template <typename T, int NV>
@@ -543,21 +678,33 @@ cudaError_t launch_plain(int grid, const Step2DArgs& a, int k, cudaStream_t s) {
     return cudaGetLastError();
 }
 
-template <int NV>
+template <int NV, int C>
 cudaError_t launch_ring(int grid, const Step2DArgs& a, int k, cudaStream_t s) {
     static bool attr = false;
     if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute(k_step2d_ring<NV>,
+        cudaError_t e = cudaFuncSetAttribute(k_step2d_ring<NV, C>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)ring_smem<NV>());
+                                             (int)ring_smem<NV, C>());
         if (e != cudaSuccess) return e;
         attr = true;
     }
-    k_step2d_ring<NV><<<grid, TW, ring_smem<NV>(), s>>>(a, k);
+    k_step2d_ring<NV, C><<<grid, RingShape<NV, C>::threads, ring_smem<NV, C>(), s>>>(a, k);
     return cudaGetLastError();
 }
 
+template <int NV, int C>
+int occupancy_ring_t() {
+    int nb = 0;
+    cudaFuncSetAttribute(k_step2d_ring<NV, C>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)ring_smem<NV, C>());
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_step2d_ring<NV, C>,
+                                                  RingShape<NV, C>::threads, ring_smem<NV, C>());
+    return nb;
+}
+
 #define LAT2D_NV_LIST(X) X(1) X(3) X(5) X(9) X(13) X(17) X(21) X(33)
+// velocity lattices whose columns may be split over several warp groups
+#define LAT2D_SPLIT(n) ((n) >= 17)
 
 bool nv2d_supported(int nv) {
     switch (nv) {
@@ -569,13 +716,39 @@ bool nv2d_supported(int nv) {
     }
 }
 
-cudaError_t launch_step2d(int dtype, int nv, bool ring, int grid, const Step2DArgs& a, int k,
-                          cudaStream_t s) {
+bool chunks_supported(int nv, int chunks) {
+    return chunks == 1 || (chunks >= 2 && chunks <= 4 && LAT2D_SPLIT(nv));
+}
+
+template <int NV>
+cudaError_t launch_ring_c(int chunks, int grid, const Step2DArgs& a, int k, cudaStream_t s) {
+    if constexpr (LAT2D_SPLIT(NV)) {
+        if (chunks == 2) return launch_ring<NV, 2>(grid, a, k, s);
+        if (chunks == 3) return launch_ring<NV, 3>(grid, a, k, s);
+        if (chunks == 4) return launch_ring<NV, 4>(grid, a, k, s);
+    }
+    if (chunks == 1) return launch_ring<NV, 1>(grid, a, k, s);
+    return cudaErrorInvalidValue;
+}
+
+template <int NV>
+int occupancy_ring_c(int chunks) {
+    if constexpr (LAT2D_SPLIT(NV)) {
+        if (chunks == 2) return occupancy_ring_t<NV, 2>();
+        if (chunks == 3) return occupancy_ring_t<NV, 3>();
+        if (chunks == 4) return occupancy_ring_t<NV, 4>();
+    }
+    if (chunks == 1) return occupancy_ring_t<NV, 1>();
+    return 0;
+}
+
+cudaError_t launch_step2d(int dtype, int nv, bool ring, int chunks, int grid,
+                          const Step2DArgs& a, int k, cudaStream_t s) {
     switch (nv) {
 #define X(n)                                                                   \
     case n:                                                                    \
         if (dtype == LAT_F64) return launch_plain<double, n>(grid, a, k, s);   \
-        if (ring) return launch_ring<n>(grid, a, k, s);                        \
+        if (ring) return launch_ring_c<n>(chunks, grid, a, k, s);              \
         return launch_plain<float, n>(grid, a, k, s);
         LAT2D_NV_LIST(X)
 #undef X
@@ -583,20 +756,14 @@ cudaError_t launch_step2d(int dtype, int nv, bool ring, int grid, const Step2DAr
     }
 }
 
-int occupancy_ring(int nv) {
-    int nb = 0;
+int occupancy_ring(int nv, int chunks) {
     switch (nv) {
-#define X(n)                                                                                  \
-    case n:                                                                                   \
-        cudaFuncSetAttribute(k_step2d_ring<n>, cudaFuncAttributeMaxDynamicSharedMemorySize,  \
-                             (int)ring_smem<n>());                                            \
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_step2d_ring<n>, TW, ring_smem<n>()); \
-        break;
+#define X(n) \
+    case n: return occupancy_ring_c<n>(chunks);
         LAT2D_NV_LIST(X)
 #undef X
-        default: break;
+        default: return 0;
     }
-    return nb;
 }
 
 }  // namespace
@@ -622,6 +789,7 @@ struct Ctx2D {
     void* d_u = nullptr;
     // launch
     bool ring = false;
+    int chunks = 1;    // warp groups per cell column in the ring kernel
     int bps = 0;       // 0 = occupancy limit
     int mode = 0;      // 0 graph, 2 direct launches
     // moments
@@ -673,7 +841,7 @@ Step2DArgs step_args(const Ctx2D* c, void* const f[2]) {
 int grid_of(const Ctx2D* c, int ntiles) {
     int per_sm = c->bps;
     if (c->ring) {
-        const int occ = occupancy_ring(c->nv);
+        const int occ = occupancy_ring(c->nv, c->chunks);
         if (per_sm <= 0 || per_sm > occ) per_sm = std::max(1, occ);
     } else if (per_sm <= 0) {
         per_sm = 8;
@@ -681,10 +849,13 @@ int grid_of(const Ctx2D* c, int ntiles) {
     return std::max(1, std::min(ntiles, per_sm * c->sm_count));
 }
 
+// Enqueue n steps.  Dry runs (autotuning) repeat step 0 n times: every repetition reads the
+// current buffer and writes the other one, so the state and the flow are left as they were.
 int enqueue2d(Ctx2D* c, void* const f[2], int n, cudaStream_t s, int dry) {
     const Step2DArgs a = step_args(c, f);
     const int grid = grid_of(c, a.ntiles);
-    for (int k = 0; k < n; ++k) {
+    for (int kk = 0; kk < n; ++kk) {
+        const int k = dry ? 0 : kk;
         if (c->flow_kind == LAT_FLOW_MODES) {
             Flow2DArgs fa;
             fa.k = c->d_k;
@@ -707,7 +878,7 @@ int enqueue2d(Ctx2D* c, void* const f[2], int n, cudaStream_t s, int dry) {
             else k_flow2d<float><<<fg, 256, sh, s>>>(fa, k);
             CK2(cudaGetLastError());
         }
-        CK2(launch_step2d(c->dtype, c->nv, c->ring, grid, a, k, s));
+        CK2(launch_step2d(c->dtype, c->nv, c->ring, c->chunks, grid, a, k, s));
     }
     if (!dry) {
         k_advance2d<<<1, 1, 0, s>>>(c->st, n);
@@ -766,6 +937,7 @@ int ctx2d_create(Ctx2D** out, const lat_grid* g, DevState* st, int sm_count, cud
     c->st = st;
     c->sm_count = sm_count;
     c->ring = ring_ok(c);
+    c->chunks = chunks_supported(c->nv, 3) ? 3 : 1;
     const long long ncell = (long long)c->nx * c->ny;
     c->mom_blocks = (int)std::min<long long>((ncell + 255) / 256, 4LL * sm_count);
     if (cudaMalloc(&c->d_partials, sizeof(double) * 8 * c->mom_blocks) != cudaSuccess ||
@@ -888,15 +1060,23 @@ int ctx2d_moments(Ctx2D* c, const void* f, double* rho, double* mean_v, double* 
 }
 
 int ctx2d_set_launch(Ctx2D* c, int kernel, int block, int bps, int mode) {
-    // kernel: 0 keep, 1 plain loads, 2 bulk-copy ring; the block is one 128-cell tile
-    if (block && block != TW) return LAT_EINVAL;
-    if (kernel == 2 && !ring_ok(c)) return LAT_EINVAL;
-    if (kernel < 0 || kernel > 2) return LAT_EINVAL;
-    if (kernel == 1) c->ring = false;
-    if (kernel == 2) c->ring = true;
+    // kernel: 0 keep, 1 plain loads (128 threads), >= 2 bulk-copy ring; for the ring, block =
+    // 128 C threads splits every cell's jx range over C warp groups (C = 1..4)
+    if (kernel < 0 || kernel > 4) return LAT_EINVAL;
+    if (kernel >= 2 && !ring_ok(c)) return LAT_EINVAL;
+    const bool ring = kernel == 0 ? c->ring : kernel >= 2;
+    int chunks = c->chunks;
+    if (block) {
+        if (block % TW != 0) return LAT_EINVAL;
+        if (!ring && block != TW) return LAT_EINVAL;
+        if (ring) chunks = block / TW;
+    }
+    if (ring && !chunks_supported(c->nv, chunks)) return LAT_EINVAL;
+    if (mode == 1 || mode > 2) return LAT_EINVAL;
+    c->ring = ring;
+    c->chunks = chunks;
     if (bps > 0) c->bps = bps;
     if (mode == 0 || mode == 2) c->mode = mode;
-    else if (mode > 0) return LAT_EINVAL;
     drop(c);
     return LAT_OK;
 }
@@ -905,16 +1085,16 @@ int ctx2d_autotune(Ctx2D* c, void* const f[2], int reps, double* best, cudaStrea
     cudaEvent_t e0, e1;
     CK2(cudaEventCreate(&e0));
     CK2(cudaEventCreate(&e1));
-    const bool ring_save = c->ring;
     double best_us = 1e300;
     bool best_ring = c->ring;
-    int best_bps = c->bps;
-    for (int use_ring = 0; use_ring < 2; ++use_ring) {
-        if (use_ring && !ring_ok(c)) continue;
+    int best_bps = c->bps, best_chunks = c->chunks;
+    for (int variant = 0; variant <= 4; ++variant) {  // 0 plain, 1..4 ring with that many chunks
+        if (variant > 0 && (!ring_ok(c) || !chunks_supported(c->nv, variant))) continue;
         for (int bps : {1, 2, 3, 4, 6, 8}) {
-            c->ring = use_ring != 0;
+            c->ring = variant > 0;
+            c->chunks = variant > 0 ? variant : c->chunks;
             c->bps = bps;
-            if (c->ring && bps > occupancy_ring(c->nv)) continue;
+            if (c->ring && bps > occupancy_ring(c->nv, c->chunks)) continue;
             int rc = enqueue2d(c, f, 1, s, 1);
             if (rc != LAT_OK) return rc;
             CK2(cudaEventRecord(e0, s));
@@ -928,19 +1108,20 @@ int ctx2d_autotune(Ctx2D* c, void* const f[2], int reps, double* best, cudaStrea
             if (us < best_us) {
                 best_us = us;
                 best_ring = c->ring;
+                best_chunks = c->chunks;
                 best_bps = bps;
             }
         }
     }
-    (void)ring_save;
     c->ring = best_ring;
+    c->chunks = best_chunks;
     c->bps = best_bps;
     drop(c);
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (best) {
         best[0] = best_ring ? 2 : 1;
-        best[1] = 1;
+        best[1] = best_ring ? TW * best_chunks : TW;
         best[2] = best_bps;
         best[3] = best_us;
     }

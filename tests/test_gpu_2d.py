@@ -153,20 +153,64 @@ def test_cfl_rejected_on_host_2d(lat):
     assert e.value.code == lat.LAT_ECFL
 
 
-def _one_cell_oracle(f0, x, y, ux, uy, tau_p, kappa, dt, dv):
+def _one_cell_oracle(f0, x, y, ux, uy, tau_p, kappa, dt, dv, gathered=False):
     """Oracle output column of one cell after one step: gather its post-streaming column
-    f*(x, y, jx, jy) = f0(x - jx, y - jy, jx, jy) and apply the oracle's drag and diffusion."""
+    f*(x, y, jx, jy) = f0(x - jx, y - jy, jx, jy) (already done when ``gathered``) and apply the
+    oracle's drag and diffusion."""
     nv, _, ny, nx = f0.shape
     J = (nv - 1) // 2
     col = np.empty((nv, nv, 1, 1))
     for jy in range(nv):
         for jx in range(nv):
-            col[jy, jx, 0, 0] = f0[jy, jx, (y - (jy - J)) % ny, (x - (jx - J)) % nx]
+            col[jy, jx, 0, 0] = (f0[jy, jx, 0, 0] if gathered else
+                                 f0[jy, jx, (y - (jy - J)) % ny, (x - (jx - J)) % nx])
     g = O.drag_2d(col, np.array([[ux]]), np.array([[uy]]), tau_p, dt, dv)
     return O.diffuse_2d(g, kappa, dt, dv)[:, :, 0, 0]
 
 
-def test_full_size_512_sampled(lat):
+@pytest.mark.parametrize("kernel", [1, 2])
+def test_many_tiles_per_block_match_oracle(lat, kernel):
+    """136 x 200 x 9^2 with one resident block per SM: 400 tiles on at most 152 blocks, so every
+    block carries its pipeline across several tiles."""
+    c = make2d(136, 200, 9, 1.0, 1e-3, 6, 31)
+    want = oracle2d(c)
+    t = torch.tensor(c["f0"], dtype=torch.float32, device="cuda")
+    lt = lat.Lattice(t, d=2, nx=136, ny=200, nv=9, L=L, tau_p=c["tau_p"], kappa=c["kappa"],
+                     dt=c["dt"])
+    lt.set_launch(kernel=kernel, blocks_per_sm=1)
+    fl = c["fl"]
+    lt.set_flow_modes_2d(fl.kvec, fl.a, fl.phi0, fl.tau_f)
+    lt.set_noise(fl.noise)
+    lt.step(6)
+    assert lt.status() == 0
+    got = lt.state.double().cpu().numpy()
+    assert rel_l1(got, want) <= 1e-5, rel_l1(got, want)
+    lt.close()
+
+
+def test_ring_equals_plain_at_full_size(lat):
+    nx = ny = 512
+    nv = 33
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(9)
+    f0 = torch.rand((nv, nv, ny, nx), generator=gen, device="cuda") + 0.1
+    dt = I.choose_dt(2, nx, L, nv, L, 1e-3)
+    fl = I.flow2d_inputs(10, 3, nx, ny, L / nx)
+    outs = []
+    for kernel in (1, 2):
+        lt = lat.Lattice(f0.clone(), d=2, nx=nx, ny=ny, nv=nv, L=L, tau_p=L, kappa=1e-3, dt=dt)
+        lt.set_launch(kernel=kernel)
+        lt.set_flow_modes_2d(fl.kvec, fl.a, fl.phi0, fl.tau_f)
+        lt.set_noise(fl.noise)
+        lt.step(2)
+        assert lt.status() == 0
+        outs.append(lt.state.clone())
+        lt.close()
+    assert torch.equal(outs[0], outs[1])
+
+
+@pytest.mark.parametrize("flow", ["none", "modes"])
+def test_full_size_512_sampled(lat, flow):
     """512^2 x 33^2 FP32 (2.85e8 cells) in the launch shape the bench uses: one step from a
     random state, 24 sampled cells recomputed by the oracle one by one; then 20 more steps
     with mass conservation and positivity checked at full size."""
@@ -183,24 +227,26 @@ def test_full_size_512_sampled(lat):
     f0 = t.clone()
     fl = I.flow2d_inputs(6, 21, nx, ny, dx)
     lt = lat.Lattice(t, d=2, nx=nx, ny=ny, nv=nv, L=L, tau_p=tau_p, kappa=kappa, dt=dt)
-    lt.set_flow_modes_2d(fl.kvec, fl.a, fl.phi0, fl.tau_f)
-    lt.set_noise(fl.noise)
+    if flow == "modes":
+        lt.set_flow_modes_2d(fl.kvec, fl.a, fl.phi0, fl.tau_f)
+        lt.set_noise(fl.noise)
+        ux, uy = O.flow2d_u(fl.a, fl.kvec, fl.phi0, nx, ny, dx)
+    else:
+        ux = uy = np.zeros((ny, nx))
     lt.autotune(reps=2)
     lt.step(1)
     out = lt.state
-    ux, uy = O.flow2d_u(fl.a, fl.kvec, fl.phi0, nx, ny, dx)
     rng = np.random.default_rng(7)
+    J = (nv - 1) // 2
+    jj = np.arange(nv)
     for _ in range(24):
         x, y = int(rng.integers(nx)), int(rng.integers(ny))
-        sub = np.zeros((nv, nv, ny, nx))  # only the gathered entries matter
-        J = (nv - 1) // 2
         ys = [(y - (jy - J)) % ny for jy in range(nv)]
         xs = [(x - (jx - J)) % nx for jx in range(nv)]
-        f0c = f0[:, :, ys][:, :, :, xs].double().cpu().numpy()
-        for jy in range(nv):
-            for jx in range(nv):
-                sub[jy, jx, ys[jy], xs[jx]] = f0c[jy, jx, jy, jx]
-        want = _one_cell_oracle(sub, x, y, ux[y, x], uy[y, x], tau_p, kappa, dt, dv)
+        block = f0[:, :, ys][:, :, :, xs].double().cpu().numpy()   # [jy, jx, a, b]
+        col = block[jj[:, None], jj[None, :], jj[:, None], jj[None, :]]  # f*(x, y, jx, jy)
+        want = _one_cell_oracle(col[:, :, None, None], 0, 0, ux[y, x], uy[y, x], tau_p, kappa,
+                                dt, dv, gathered=True)
         got = out[:, :, y, x].double().cpu().numpy()
         assert rel_l1(got, want) <= 1e-6, (x, y, rel_l1(got, want))
     m0 = f0.double().sum().item()
