@@ -182,6 +182,41 @@ const char* lat_strerror(int status);
 /* Release the context's scratch.  Does not touch f_a, f_b or a caller's field. */
 void lat_free(lat_ctx* c);
 
+/* ---- allocation-free entry point ---------------------------------------------------------- */
+
+/* Largest number of 128-column tiles lat_moments1d_noalloc accepts: N_x <= 8192 * 128. */
+#define LAT_NOALLOC_MAX_TILES 8192
+
+/*
+ * Global moments [M, P, E] = sum f dx dv * [1, v, v^2] of one 1D FP32 lattice, computed without
+ * allocating anything.  It gives the same result as the globals of lat_moments on the same
+ * state, to rounding order.  The paper has no counterpart; this call exists for callers that
+ * must not allocate device memory, for example:
+ *  - code running inside another runtime that has reserved the GPU's memory for its own pool;
+ *  - latency-critical loops in which cudaMalloc or cudaFree would synchronise the device.
+ * Such callers cannot create a lat_ctx, whose scratch is allocated with cudaMalloc.
+ *
+ *   f        DEVICE array f[j][x] of nv * nx floats (layout of include/lat.h), caller-owned.
+ *   nv, nx   odd N_v >= 1; 1 <= N_x <= LAT_NOALLOC_MAX_TILES * 128, else LAT_EINVAL with a
+ *            message on stderr, before anything is launched.
+ *   dx, dv   lattice spacings (> 0).
+ *   globals  DEVICE array of 3 doubles, caller-owned, written asynchronously.
+ *   stream   cudaStream_t or NULL.
+ *
+ * The scratch is a fixed static device array of LAT_NOALLOC_MAX_TILES * 6 doubles (384 KiB).
+ * Every GPU that loads this library holds it until the process exits.  The function calls no
+ * cudaMalloc, cudaFree or any other allocating routine.
+ *
+ * The first call on each device looks up that array's device address (cudaGetSymbolAddress,
+ * with the device current).  Make that first call before any stream capture on the device.
+ *
+ * Every call shares the one array and overwrites the slots it uses, so nothing needs clearing.
+ * Calls that overlap on the GPU (on different streams, or from several threads without
+ * ordering) race on the array and give wrong results.  Returns LAT_OK, LAT_EINVAL or LAT_ECUDA.
+ */
+int lat_moments1d_noalloc(const float* f, int nv, int nx, double dx, double dv, double* globals,
+                          void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -6,6 +6,9 @@
 // (warp shuffles in a fixed butterfly order, then shared memory).  Pass 2: one block per
 // instance folds that instance's item partials in item order.  Both passes are deterministic.
 #include <math.h>
+#include <stdio.h>
+
+#include <mutex>
 
 #include "lat_internal.h"
 
@@ -146,6 +149,90 @@ __global__ void k_finalize1d(const double* partials, const int* begin, const Ins
     for (int q = 0; q < 3; ++q) glob[i * 3 + q] = nval(t[q]) * w;
 }
 
+// ---- allocation-free variant: global moments of one FP32 lattice, static scratch ------------
+constexpr int kNoAllocTile = 128;
+
+// Per-tile compensated partials of lat_moments1d_noalloc: [tile][M, P, E][sum, compensation].
+// Every GPU that loads this library holds this array until the process exits.
+static __device__ __align__(256) double g_noalloc_partials[LAT_NOALLOC_MAX_TILES * 6];
+
+// One block per 128-column tile: FP32 Kahan column sums, Neumaier over the tile's columns.
+__global__ void __launch_bounds__(kNoAllocTile)
+    k_moments1d_noalloc(const float* f, int nv, int nx, double dv, double* partials) {
+    __shared__ Comp red[3][kNoAllocTile / 32];
+    const int J = (nv - 1) / 2;
+    const int x = blockIdx.x * kNoAllocTile + threadIdx.x;
+    Comp t0{0, 0}, t1{0, 0}, t2{0, 0};
+    if (x < nx) {
+        FComp a0, a1, a2;
+        for (int jj = 0; jj < nv; ++jj) {
+            const float fv = f[(size_t)jj * nx + x];
+            const float j = (float)(jj - J);
+            a0.add(fv);
+            a1.add(j * fv);
+            a2.add(j * j * fv);
+        }
+        const double dv2 = __dmul_rn(dv, dv);
+        t0 = Comp{(double)a0.s, -(double)a0.c};
+        t1 = Comp{__dmul_rn((double)a1.s, dv), -__dmul_rn((double)a1.c, dv)};
+        t2 = Comp{__dmul_rn((double)a2.s, dv2), -__dmul_rn((double)a2.c, dv2)};
+    }
+    for (int off = 16; off > 0; off >>= 1) {
+        Comp o0 = shfl_down(t0, off), o1 = shfl_down(t1, off), o2 = shfl_down(t2, off);
+        nmerge(t0, o0);
+        nmerge(t1, o1);
+        nmerge(t2, o2);
+    }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane == 0) {
+        red[0][warp] = t0;
+        red[1][warp] = t1;
+        red[2][warp] = t2;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        Comp z[3] = {{0, 0}, {0, 0}, {0, 0}};
+        for (int w = 0; w < kNoAllocTile / 32; ++w)
+            for (int q = 0; q < 3; ++q) nmerge(z[q], red[q][w]);
+        double* p = partials + (size_t)blockIdx.x * 6;
+        for (int q = 0; q < 3; ++q) {
+            p[2 * q] = z[q].s;
+            p[2 * q + 1] = z[q].c;
+        }
+    }
+}
+
+// Fold the tile partials in tile order: out = [M, P, E] * dx dv.
+__global__ void k_finalize_noalloc(const double* partials, int ntiles, double w, double* out) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    Comp t[3] = {{0, 0}, {0, 0}, {0, 0}};
+    for (int b = 0; b < ntiles; ++b)
+        for (int q = 0; q < 3; ++q) nmerge(t[q], Comp{partials[b * 6 + 2 * q], partials[b * 6 + 2 * q + 1]});
+    for (int q = 0; q < 3; ++q) out[q] = nval(t[q]) * w;
+}
+
+// Device address of the static scratch, looked up once per device (with that device current).
+int noalloc_scratch(double** out) {
+    constexpr int kMaxDevices = 64;
+    static std::mutex mu;
+    static double* addr[kMaxDevices] = {nullptr};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return LAT_ECUDA;
+    std::lock_guard<std::mutex> lock(mu);
+    if (!addr[dev]) {
+        void* p = nullptr;
+        const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_partials);
+        if (e != cudaSuccess) {
+            fprintf(stderr, "lat_moments1d_noalloc: cudaGetSymbolAddress failed: %s\n",
+                    cudaGetErrorString(e));
+            return LAT_ECUDA;
+        }
+        addr[dev] = static_cast<double*>(p);
+    }
+    *out = addr[dev];
+    return LAT_OK;
+}
+
 }  // namespace
 
 cudaError_t launch_moments1d(int dtype, int block, int xpt, int grid, const Mom1DArgs& a,
@@ -165,3 +252,28 @@ cudaError_t launch_finalize1d(const double* partials, const int* inst_item_begin
 }
 
 }  // namespace lat
+
+extern "C" int lat_moments1d_noalloc(const float* f, int nv, int nx, double dx, double dv,
+                                     double* globals, void* stream) {
+    if (!f || !globals || nv < 1 || nv % 2 == 0 || nx < 1 || !(dx > 0) || !(dv > 0))
+        return LAT_EINVAL;
+    const int ntiles = (nx + lat::kNoAllocTile - 1) / lat::kNoAllocTile;
+    if (ntiles > LAT_NOALLOC_MAX_TILES) {
+        fprintf(stderr,
+                "lat_moments1d_noalloc: N_x = %d exceeds the static scratch limit of %d columns\n",
+                nx, LAT_NOALLOC_MAX_TILES * lat::kNoAllocTile);
+        return LAT_EINVAL;
+    }
+    double* scratch = nullptr;
+    const int rc = lat::noalloc_scratch(&scratch);
+    if (rc != LAT_OK) return rc;
+    const cudaStream_t s = (cudaStream_t)stream;
+    lat::k_moments1d_noalloc<<<ntiles, lat::kNoAllocTile, 0, s>>>(f, nv, nx, dv, scratch);
+    lat::k_finalize_noalloc<<<1, 32, 0, s>>>(scratch, ntiles, dx * dv, globals);
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) {
+        fprintf(stderr, "lat_moments1d_noalloc: launch failed: %s\n", cudaGetErrorString(e));
+        return LAT_ECUDA;
+    }
+    return LAT_OK;
+}

@@ -62,6 +62,7 @@ def _load():
         "lat_autotune": (c_int, [P, c_int, POINTER(c_double)]),
         "lat_strerror": (ctypes.c_char_p, [c_int]),
         "lat_free": (None, [P]),
+        "lat_moments1d_noalloc": (c_int, [P, c_int, c_int, c_double, c_double, P, P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
