@@ -63,6 +63,25 @@ def measured_peaks():
         return 6800.0, "fallback"
 
 
+def rank_seeds(rank: int):
+    """Seeds of one rank's ensemble and flow: every rank advances its own independent set of
+    realisations (weak scaling, no data-path collective)."""
+    return SEED + rank, SEED + 7 + rank
+
+
+def max_over_ranks(ms: float, world: int, dist, torch, dev) -> float:
+    """The job's time is the slowest rank's time."""
+    t = torch.tensor([ms], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(cells_per_rank: int, steps: int, world: int, ms_max: float) -> float:
+    """Whole-job phase-space cell updates per second, in units of 1e9."""
+    return world * cells_per_rank * steps / (ms_max / 1e3) / 1e9
+
+
 def profile_traffic(kernel_file: str, src: str):
     """DRAM bytes per launch from the committed ncu summary, if it was taken on this source."""
     import hashlib
@@ -218,8 +237,9 @@ WORKLOAD_2D = ("2D FP32: periodic 512x512 grid, 33x33 velocity lattice (2.85e8 c
 
 def build_ensemble(args, I, lat, torch, dev, rank, nsteps):
     n_inst = args.instances
-    tab = I.ensemble_table(n_inst, SEED + rank, nv=NV)
-    fl = I.flow1d_inputs(SEED + 7 + rank, nsteps, n_inst=n_inst)
+    seed_tab, seed_flow = rank_seeds(rank)
+    tab = I.ensemble_table(n_inst, seed_tab, nv=NV)
+    fl = I.flow1d_inputs(seed_flow, nsteps, n_inst=n_inst)
     f0 = I.ensemble_initial(tab, NV, torch.float32, dev)
     ens = lat.Ensemble(f0, nv=NV, nx=tab.nx, L=tab.L, tau_p=tab.tau_p, kappa=tab.kappa,
                        dt=tab.dt)
@@ -264,10 +284,7 @@ def timed(ctx, K, W, torch, dist, world, local, dev):
     ck = clocks.stop()
     if world > 1:
         dist.barrier()
-    t = torch.tensor([ev0.elapsed_time(ev1)], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    return float(t.item()), ck
+    return max_over_ranks(ev0.elapsed_time(ev1), world, dist, torch, dev), ck
 
 
 def end_to_end(ctx, noise_row, glob, steps, torch):
@@ -349,7 +366,7 @@ def main():
 
     ms_max, ck = timed(ctx, K, W, torch, dist, world, local, dev)
     status = ctx.status()
-    value = world * cells * K / (ms_max / 1e3) / 1e9
+    value = job_throughput(cells, K, world, ms_max)
     e2e_s, h2d, d2h = end_to_end(ctx, noise_row, glob, K_e2e, torch)
     e2e_value = world * cells * K_e2e / e2e_s / 1e9
 

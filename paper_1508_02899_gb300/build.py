@@ -31,7 +31,8 @@ def build(verbose: bool = False, ptxas_v: bool = False) -> str:
 
     def compile_one(pair):
         src, obj = pair
-        cmd = [nvcc(), *ARCH, *FLAGS, "-c", src, "-o", obj]
+        extra = os.environ.get("LAT_NVCC_EXTRA", "").split()  # e.g. -DLAT_RING2D_SLOTS=6
+        cmd = [nvcc(), *ARCH, *FLAGS, *extra, "-c", src, "-o", obj]
         if ptxas_v:
             cmd.insert(1, "-Xptxas=-v")
         r = subprocess.run(cmd, capture_output=True, text=True)

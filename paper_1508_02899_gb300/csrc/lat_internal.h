@@ -9,6 +9,13 @@
 
 #include "../../include/lat.h"
 
+// The bulk-copy rings refill a shared-memory slot only after a block barrier that follows every
+// thread's last read of it; build with -DLAT_RING_PROXY_FENCE=1 to also issue a generic-to-async
+// proxy fence before each refill.
+#ifndef LAT_RING_PROXY_FENCE
+#define LAT_RING_PROXY_FENCE 0
+#endif
+
 namespace lat {
 
 // Device status bits; translated to LAT_E* codes by the host.

@@ -362,7 +362,9 @@ __global__ void __launch_bounds__(TW1) k_step1d_ring(const Step1DArgs a, const i
         // slot (k + NS - 1) % NS held item k - 1, which every thread has finished
         if (k + NS - 1 < nloc) {
             if (tid < 32) {
+#if LAT_RING_PROXY_FENCE
                 asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+#endif
                 issue_item<NV>(a, fin, ring, bar, (k + NS - 1) % NS,
                                first + (k + NS - 1) * gridDim.x);
             }

@@ -31,7 +31,11 @@ namespace {
 
 constexpr int TW = 128;       // cells per tile (= threads per block)
 constexpr int WIN = TW + 4;   // floats copied per plane row (x window rounded to 16 bytes)
-constexpr int NSLOT = 4;      // ring slots of f* rows
+#ifndef LAT_RING2D_SLOTS
+#define LAT_RING2D_SLOTS 4
+#endif
+constexpr int NSLOT = LAT_RING2D_SLOTS;  // ring slots of f* rows
+constexpr int LOOK = NSLOT - 2;          // rows in flight ahead of the one being waited for
 
 struct Step2DArgs {
     void* f[2];
@@ -49,6 +53,9 @@ struct Flow2DArgs {
     double* phase;            // [2][M] parity-indexed phases
     const double* noise;      // [rows][M]
     double walk;              // sqrt(2 dt / tau_f)
+    const void* xtab;         // [2 kmax+1][nx][2] of T
+    const void* ytab;         // [2 kmax+1][ny][2] of T
+    int kmax;
     int nmodes, nx, ny;
     void* u;                  // [2][ny][nx] of T
     DevState* st;
@@ -443,10 +450,10 @@ __global__ void __launch_bounds__(RingShape<NV, C>::threads, RingShape<NV, C>::m
     __syncthreads();
     auto tile_of = [&](long long s) { return (int)(blockIdx.x + (s / NV) * gridDim.x); };
     if (tid < 32) {
-        for (long long s = 0; s < 2 && s < total; ++s)
+        for (long long s = 0; s < LOOK && s < total; ++s)
             issue_row<NV>(a, fin, ring, bar, (int)(s % NSLOT), tile_of(s), (int)(s % NV));
     }
-    long long issued = std::min<long long>(2, total);
+    long long issued = std::min<long long>(LOOK, total);
     bool failed = false;
     for (int lt = 0; lt < ntl && !failed; ++lt) {
         const int tile = tile_of((long long)lt * NV);
@@ -475,12 +482,15 @@ __global__ void __launch_bounds__(RingShape<NV, C>::threads, RingShape<NV, C>::m
                 break;
             }
             if (r < NV) {
-                if (tid < 32 && s + 2 < total) {
+                // slot (s + LOOK) % NSLOT last held row s - 2, released by the barrier above
+                if (tid < 32 && s + LOOK < total) {
+#if LAT_RING_PROXY_FENCE
                     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-                    issue_row<NV>(a, fin, ring, bar, (int)((s + 2) % NSLOT), tile_of(s + 2),
-                                  (int)((s + 2) % NV));
+#endif
+                    issue_row<NV>(a, fin, ring, bar, (int)((s + LOOK) % NSLOT),
+                                  tile_of(s + LOOK), (int)((s + LOOK) % NV));
                 }
-                if (s + 2 < total) issued = s + 3;
+                if (s + LOOK < total) issued = s + LOOK + 1;
                 if (!mbar_wait_bounded(&bar[s % NSLOT], (unsigned)((s / NSLOT) & 1))) {
                     failed = true;
                     continue;
@@ -520,24 +530,22 @@ __global__ void __launch_bounds__(RingShape<NV, C>::threads, RingShape<NV, C>::m
 }
 
 // ---- flow: u = (d_y psi, -d_x psi) of psi = sum a_m cos(theta_m) --------------------------------
-template <typename T>
-__device__ __forceinline__ void sincospi_t(T y, T* s, T* c);
-template <>
-__device__ __forceinline__ void sincospi_t<float>(float y, float* s, float* c) { sincospif(y, s, c); }
-template <>
-__device__ __forceinline__ void sincospi_t<double>(double y, double* s, double* c) { sincospi(y, s, c); }
 
 template <typename T>
 __global__ void __launch_bounds__(256) k_flow2d(const Flow2DArgs a, int kstep) {
-    extern __shared__ double sh[];  // [M] cos phi, [M] sin phi
+    extern __shared__ double sh_raw[];
+    T* sh = reinterpret_cast<T*>(sh_raw);  // [M] cos phi, [M] sin phi, [M] c_x, [M] c_y
+    const int M = a.nmodes;
     const long long step = a.st->step + kstep;
     const int par = (int)(step & 1);
-    const double* ph = a.phase + (size_t)par * a.nmodes;
-    for (int m = threadIdx.x; m < a.nmodes; m += blockDim.x) {
+    const double* ph = a.phase + (size_t)par * M;
+    for (int m = threadIdx.x; m < M; m += blockDim.x) {
         double s, c;
         sincos(ph[m], &s, &c);
-        sh[m] = c;
-        sh[a.nmodes + m] = s;
+        sh[m] = T(c);
+        sh[M + m] = T(s);
+        sh[2 * M + m] = T(a.cx[m]);
+        sh[3 * M + m] = T(a.cy[m]);
     }
     __syncthreads();
     if (blockIdx.x == 0 && !a.frozen && !a.dry) {
@@ -550,21 +558,22 @@ __global__ void __launch_bounds__(256) k_flow2d(const Flow2DArgs a, int kstep) {
         if (!have && threadIdx.x == 0) atomicOr(&a.st->status, ST_NOISE);
     }
     const long long ncell = (long long)a.nx * a.ny;
-    const long long N = ncell;
+    const T* xt = static_cast<const T*>(a.xtab);  // [kx + kmax][x][cos, sin] of 2 pi kx x / nx
+    const T* yt = static_cast<const T*>(a.ytab);  // [ky + kmax][y][cos, sin] of 2 pi ky y / ny
     for (long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x; c < ncell;
          c += (long long)gridDim.x * blockDim.x) {
         const int x = (int)(c % a.nx), y = (int)(c / a.nx);
         T ux = T(0), uy = T(0);
-        for (int m = 0; m < a.nmodes; ++m) {
+        for (int m = 0; m < M; ++m) {
             const int2 k = a.k[m];
-            // 2 pi (kx x / nx + ky y / ny) reduced exactly: p / (nx ny) turns
-            long long p = ((long long)k.x * x * a.ny + (long long)k.y * y * a.nx) % N;
-            if (p < 0) p += N;
-            T sb, cb;
-            sincospi_t<T>(T(2 * p) / T(N), &sb, &cb);
-            const T s = sb * T(sh[m]) + cb * T(sh[a.nmodes + m]);  // sin(theta_int + phi)
-            ux += T(a.cx[m]) * s;
-            uy += T(a.cy[m]) * s;
+            const T* X = xt + 2 * ((size_t)(k.x + a.kmax) * a.nx + x);
+            const T* Y = yt + 2 * ((size_t)(k.y + a.kmax) * a.ny + y);
+            // e^{i theta_int} = e^{i 2 pi kx x / nx} e^{i 2 pi ky y / ny}
+            const T zr = X[0] * Y[0] - X[1] * Y[1];
+            const T zi = X[0] * Y[1] + X[1] * Y[0];
+            const T s = zi * sh[m] + zr * sh[M + m];  // sin(theta_int + phi)
+            ux += sh[2 * M + m] * s;
+            uy += sh[3 * M + m] * s;
         }
         T* u = static_cast<T*>(a.u);
         u[c] = ux;
@@ -782,6 +791,9 @@ struct Ctx2D {
     double* d_cx = nullptr;
     double* d_cy = nullptr;
     double* d_phase = nullptr;
+    void* d_xtab = nullptr;   // separable flow tables (see k_flow2d)
+    void* d_ytab = nullptr;
+    int kmax = 0;
     double* d_noise = nullptr;
     long long noise_cap = 0;
     double walk = 0.0;
@@ -864,6 +876,9 @@ int enqueue2d(Ctx2D* c, void* const f[2], int n, cudaStream_t s, int dry) {
             fa.phase = c->d_phase;
             fa.noise = c->d_noise;
             fa.walk = c->walk;
+            fa.xtab = c->d_xtab;
+            fa.ytab = c->d_ytab;
+            fa.kmax = c->kmax;
             fa.nmodes = c->nmodes;
             fa.nx = c->nx;
             fa.ny = c->ny;
@@ -873,7 +888,7 @@ int enqueue2d(Ctx2D* c, void* const f[2], int n, cudaStream_t s, int dry) {
             fa.dry = dry;
             const long long ncell = (long long)c->nx * c->ny;
             const int fg = (int)std::min<long long>((ncell + 255) / 256, 8LL * c->sm_count);
-            const size_t sh = 2 * sizeof(double) * c->nmodes;
+            const size_t sh = 4 * sizeof(double) * c->nmodes;
             if (c->dtype == LAT_F64) k_flow2d<double><<<fg, 256, sh, s>>>(fa, k);
             else k_flow2d<float><<<fg, 256, sh, s>>>(fa, k);
             CK2(cudaGetLastError());
@@ -987,11 +1002,41 @@ int ctx2d_set_flow(Ctx2D* c, const lat_flow* fl, bool frozen, cudaStream_t s) {
         CK2(cudaMemcpy(c->d_cx, cx.data(), sizeof(double) * M, cudaMemcpyHostToDevice));
         CK2(cudaMemcpy(c->d_cy, cy.data(), sizeof(double) * M, cudaMemcpyHostToDevice));
         CK2(cudaMemcpy(c->d_phase, ph.data(), sizeof(double) * 2 * M, cudaMemcpyHostToDevice));
+        const size_t es = c->dtype == LAT_F64 ? sizeof(double) : sizeof(float);
         if (!c->d_u) {
-            const size_t es = c->dtype == LAT_F64 ? sizeof(double) : sizeof(float);
             if (cudaMalloc(&c->d_u, es * 2 * (size_t)c->nx * c->ny) != cudaSuccess)
                 return LAT_ENOMEM;
         }
+        // separable tables of e^{i 2 pi k x / n}: the phase k x mod n is reduced in integers and
+        // evaluated in FP64, then stored in the flow's precision
+        int kmax = 0;
+        for (int m = 0; m < M; ++m) kmax = std::max(kmax, std::max(abs(k[m].x), abs(k[m].y)));
+        auto table = [&](int n, void** dst) -> int {
+            const size_t cnt = (size_t)(2 * kmax + 1) * n * 2;
+            std::vector<double> t(cnt);
+            for (int kk = -kmax; kk <= kmax; ++kk)
+                for (int i = 0; i < n; ++i) {
+                    long long p = ((long long)kk * i) % n;
+                    if (p < 0) p += n;
+                    const double th = 2.0 * M_PI * (double)p / (double)n;
+                    t[2 * ((size_t)(kk + kmax) * n + i)] = cos(th);
+                    t[2 * ((size_t)(kk + kmax) * n + i) + 1] = sin(th);
+                }
+            cudaFree(*dst);
+            *dst = nullptr;
+            if (cudaMalloc(dst, es * cnt) != cudaSuccess) return LAT_ENOMEM;
+            if (es == sizeof(double)) {
+                CK2(cudaMemcpy(*dst, t.data(), es * cnt, cudaMemcpyHostToDevice));
+            } else {
+                std::vector<float> tf(t.begin(), t.end());
+                CK2(cudaMemcpy(*dst, tf.data(), es * cnt, cudaMemcpyHostToDevice));
+            }
+            return LAT_OK;
+        };
+        int trc = table(c->nx, &c->d_xtab);
+        if (trc == LAT_OK) trc = table(c->ny, &c->d_ytab);
+        if (trc != LAT_OK) return trc;
+        c->kmax = kmax;
         c->nmodes = M;
         c->flow_kind = LAT_FLOW_MODES;
         c->walk = frozen ? 0.0 : sqrt(2.0 * c->dt / fl->tau_f);
@@ -1135,6 +1180,8 @@ void ctx2d_destroy(Ctx2D* c) {
     cudaFree(c->d_cx);
     cudaFree(c->d_cy);
     cudaFree(c->d_phase);
+    cudaFree(c->d_xtab);
+    cudaFree(c->d_ytab);
     cudaFree(c->d_noise);
     cudaFree(c->d_u);
     cudaFree(c->d_partials);
