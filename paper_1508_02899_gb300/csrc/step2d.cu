@@ -146,19 +146,34 @@ __device__ __forceinline__ T dflux(T caj, T can, T fj, T fn) {
 // r (nxt, absent when r == NV) and, for r >= 2, writes output row r-2.
 //   f**_{jx} = f*_{jx} - (cFx_{jx+1/2} - cFx_{jx-1/2}) - (cFy_{rb+1/2} - cFy_{rb-1/2})
 //   out      = f** + (Dx_{jx+1/2} - Dx_{jx-1/2}) + (Dy_{+1/2} - Dy_{-1/2}),  D = r (f**_+ - f**)
-template <typename T, int NV, class Row>
-__device__ __forceinline__ void sweep_row(T (&A)[NV], T (&G)[NV], T (&H)[NV], int r,
-                                          const Row& cur, const Row& nxt_row, T g, T wx, T wy,
-                                          T rr, T* __restrict__ out, size_t pstride,
+// Opaque copy: keeps the compiler from hoisting per-jx invariants (drag coefficients, store
+// offsets) out of the row loop into NV live registers each.
+__device__ __forceinline__ float opaque(float v) {
+    float r;
+    asm volatile("mov.b32 %0, %1;" : "=f"(r) : "f"(v));
+    return r;
+}
+__device__ __forceinline__ double opaque(double v) {
+    double r;
+    asm volatile("mov.b64 %0, %1;" : "=d"(r) : "d"(v));
+    return r;
+}
+
+template <typename T, int NV, class Row, class GArr>
+__device__ __forceinline__ void sweep_row(T (&A)[NV], GArr& G, T (&H)[NV], int r,
+                                          const Row& cur, const Row& nxt_row, T g_in, T wx_in,
+                                          T wy, T rr, T* __restrict__ out, size_t pstride,
                                           bool active) {
     using O = Ops<T>;
     constexpr int J = (NV - 1) / 2;
     const int rb = r - 1;
     const bool nxt = r < NV;
+    const T g = opaque(g_in), wx = opaque(wx_in);
     const T ayp = fmax(cacc<T>(g, wy, rb - J), T(0));
     const T aym = nxt ? fmin(cacc<T>(g, wy, r - J), T(0)) : T(0);
     T Fprev = T(0), Dprev = T(0);
     T sc = cur.get(0);
+    T* o_ptr = out + (size_t)(r >= 2 ? r - 2 : 0) * NV * pstride;
 #pragma unroll
     for (int jx = 0; jx < NV; ++jx) {
         T sn = T(0), Fnext = T(0);
@@ -178,7 +193,8 @@ __device__ __forceinline__ void sweep_row(T (&A)[NV], T (&G)[NV], T (&H)[NV], in
             const T o = O::add(O::add(a, O::sub(Dn, Dprev)), O::sub(Hn, H[jx]));
             H[jx] = Hn;
             Dprev = Dn;
-            if (active) out[((size_t)(r - 2) * NV + jx) * pstride] = o;
+            if (active) *o_ptr = o;
+            o_ptr += pstride;
         }
         A[jx] = b;
     }
@@ -190,13 +206,15 @@ __device__ __forceinline__ void final_row(T (&A)[NV], T (&H)[NV], T rr, T* __res
                                           size_t pstride, bool active) {
     using O = Ops<T>;
     T Dprev = T(0);
+    T* o_ptr = out + (size_t)(NV - 1) * NV * pstride;
 #pragma unroll
     for (int jx = 0; jx < NV; ++jx) {
         const T a = A[jx];
         const T Dn = (jx < NV - 1) ? O::mul(rr, O::sub(A[jx + 1], a)) : T(0);
         const T o = O::add(O::add(a, O::sub(Dn, Dprev)), O::sub(T(0), H[jx]));
         Dprev = Dn;
-        if (active) out[((size_t)(NV - 1) * NV + jx) * pstride] = o;
+        if (active) *o_ptr = o;
+        o_ptr += pstride;
     }
 }
 
@@ -529,6 +547,121 @@ __global__ void __launch_bounds__(RingShape<NV, C>::threads, RingShape<NV, C>::m
     }
 }
 
+// ---- producer/consumer kernel: no block-wide barrier per row ------------------------------------
+// Four consumer warps own 128 cells (one cell column per thread, as in the plain kernel); a fifth
+// warp only produces: it refills a ring slot as soon as every consumer warp has released it
+// (per-slot "empty" mbarrier, one arrival per consumer warp) and the consumers wait only on the
+// per-slot "full" mbarrier the bulk copies complete.  Warps drift freely within the ring's slack.
+// With GSM the vy-drag flux row G lives in shared memory (private per thread) instead of
+// registers, which lowers register pressure and raises occupancy.
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+struct SmemCol {  // one thread's column in a [NV][TW] shared array
+    float* p;
+    __device__ __forceinline__ float& operator[](int j) const { return p[j * TW]; }
+};
+
+template <int NV, int NS, bool GSM>
+struct PCShape {
+    static constexpr int consumers = TW / 32;
+    static constexpr int threads = 32 * (consumers + 1);
+    static constexpr int min_blocks = (GSM && NS == 3) ? 3 : 2;
+};
+
+template <int NV, int NS, bool GSM>
+size_t pc_smem() {
+    return (size_t)NS * NV * WIN * sizeof(float) + (GSM ? (size_t)NV * TW * sizeof(float) : 0) +
+           2 * NS * sizeof(uint64_t);
+}
+
+template <int NV, int NS, bool GSM>
+__global__ void __launch_bounds__(PCShape<NV, NS, GSM>::threads, PCShape<NV, NS, GSM>::min_blocks)
+    k_step2d_pc(const Step2DArgs a, int kstep) {
+    constexpr int NC = PCShape<NV, NS, GSM>::consumers;
+    extern __shared__ __align__(128) unsigned char smem[];
+    float* ring = reinterpret_cast<float*>(smem);
+    float* gsm = ring + (size_t)NS * NV * WIN;
+    uint64_t* full = reinterpret_cast<uint64_t*>(gsm + (GSM ? NV * TW : 0));
+    uint64_t* empty = full + NS;
+    const long long step = a.st->step + kstep;
+    const int par = (int)(step & 1);
+    const float g = float(a.g), rr = float(a.r);
+    const float* fin = static_cast<const float*>(a.f[par]);
+    float* fout = static_cast<float*>(a.f[par ^ 1]);
+    const size_t ps = (size_t)a.nx * a.ny;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int ntl = a.ntiles > (int)blockIdx.x ? (a.ntiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
+    const long long total = (long long)ntl * NV;
+    auto tile_of = [&](long long s) { return (int)(blockIdx.x + (s / NV) * gridDim.x); };
+    if (threadIdx.x == 0) {
+        for (int q = 0; q < NS; ++q) {
+            mbar_init(&full[q], 1);
+            mbar_init(&empty[q], NC);
+        }
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    if (warp == NC) {
+        // producer: fill f goes to slot f % NS once the consumers released that slot's previous
+        // content (fill f - NS)
+        long long f = 0;
+        for (; f < total; ++f) {
+            const int q = (int)(f % NS);
+            if (f >= NS && !mbar_wait_bounded(&empty[q], (unsigned)(((f / NS) + 1) & 1))) {
+                if (lane == 0) atomicOr(&a.st->status, ST_TIMEOUT);
+                break;
+            }
+            issue_row<NV>(a, fin, ring, full, q, tile_of(f), (int)(f % NV));
+        }
+        // the copies issued last must land before this warp leaves (the block may finish early)
+        for (long long d = std::max(0ll, f - NS); d < f; ++d)
+            mbar_wait_bounded(&full[d % NS], (unsigned)((d / NS) & 1));
+        return;
+    }
+    const int cell = threadIdx.x;
+    bool failed = false;
+    for (int lt = 0; lt < ntl && !failed; ++lt) {
+        const int tile = tile_of((long long)lt * NV);
+        const int y = tile / a.ntx;
+        const int xr = (tile % a.ntx) * TW + cell;
+        const bool active = xr < a.nx;
+        const int x = active ? xr : 0;
+        float wx, wy;
+        load_w<float>(a, x, y, wx, wy);
+        cfl_check<float, NV>(a, g, wx, wy, active);
+        float A[NV], H[NV], Greg[NV];
+        SmemCol Gs{gsm + cell};
+#pragma unroll
+        for (int j = 0; j < NV; ++j) {
+            A[j] = 0.f;
+            H[j] = 0.f;
+            if (GSM) Gs[j] = 0.f;
+            else Greg[j] = 0.f;
+        }
+        float* out = fout + (size_t)y * a.nx + x;
+        const long long s0 = (long long)lt * NV;
+        for (int r = 0; r <= NV; ++r) {
+            const long long s = s0 + r;
+            if (r < NV && !mbar_wait_bounded(&full[s % NS], (unsigned)((s / NS) & 1))) {
+                failed = true;
+                break;
+            }
+            if (r >= 1) {
+                const RingRow<NV> cur{ring + (size_t)((s - 1) % NS) * NV * WIN + cell};
+                const RingRow<NV> nxt{ring + (size_t)(s % NS) * NV * WIN + cell};
+                if (GSM) sweep_row<float, NV>(A, Gs, H, r, cur, nxt, g, wx, wy, rr, out, ps, active);
+                else sweep_row<float, NV>(A, Greg, H, r, cur, nxt, g, wx, wy, rr, out, ps, active);
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&empty[(s - 1) % NS]);  // row s - 1 is done
+            }
+        }
+        if (!failed) final_row<float, NV>(A, H, rr, out, ps, active);
+    }
+    if (failed && lane == 0) atomicOr(&a.st->status, ST_TIMEOUT);
+}
+
 // ---- flow: u = (d_y psi, -d_x psi) of psi = sum a_m cos(theta_m) --------------------------------
 
 template <typename T>
@@ -751,12 +884,72 @@ int occupancy_ring_c(int chunks) {
     return 0;
 }
 
-cudaError_t launch_step2d(int dtype, int nv, bool ring, int chunks, int grid,
+// Producer/consumer variants: 3 = G in registers, 4-slot ring; 4 = G in shared memory, 4 slots;
+// 5 = G in shared memory, 3 slots.
+#define LAT2D_PC(n) ((n) >= 9)
+
+template <int NV, int NS, bool GSM>
+cudaError_t launch_pc(int grid, const Step2DArgs& a, int k, cudaStream_t s) {
+    static bool attr = false;
+    if (!attr) {
+        cudaError_t e = cudaFuncSetAttribute(k_step2d_pc<NV, NS, GSM>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)pc_smem<NV, NS, GSM>());
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    k_step2d_pc<NV, NS, GSM><<<grid, PCShape<NV, NS, GSM>::threads, pc_smem<NV, NS, GSM>(), s>>>(a, k);
+    return cudaGetLastError();
+}
+
+template <int NV, int NS, bool GSM>
+int occupancy_pc_t() {
+    int nb = 0;
+    cudaFuncSetAttribute(k_step2d_pc<NV, NS, GSM>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)pc_smem<NV, NS, GSM>());
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_step2d_pc<NV, NS, GSM>,
+                                                  PCShape<NV, NS, GSM>::threads,
+                                                  pc_smem<NV, NS, GSM>());
+    return nb;
+}
+
+template <int NV>
+cudaError_t launch_pc_v(int v, int grid, const Step2DArgs& a, int k, cudaStream_t s) {
+    if constexpr (LAT2D_PC(NV)) {
+        if (v == 3) return launch_pc<NV, 4, false>(grid, a, k, s);
+        if (v == 4) return launch_pc<NV, 4, true>(grid, a, k, s);
+        if (v == 5) return launch_pc<NV, 3, true>(grid, a, k, s);
+    }
+    return cudaErrorInvalidValue;
+}
+
+template <int NV>
+int occupancy_pc_v(int v) {
+    if constexpr (LAT2D_PC(NV)) {
+        if (v == 3) return occupancy_pc_t<NV, 4, false>();
+        if (v == 4) return occupancy_pc_t<NV, 4, true>();
+        if (v == 5) return occupancy_pc_t<NV, 3, true>();
+    }
+    return 0;
+}
+
+bool pc_supported(int nv) {
+    switch (nv) {
+#define X(n) \
+    case n: return LAT2D_PC(n);
+        LAT2D_NV_LIST(X)
+#undef X
+        default: return false;
+    }
+}
+
+cudaError_t launch_step2d(int dtype, int nv, bool ring, int chunks, int pcv, int grid,
                           const Step2DArgs& a, int k, cudaStream_t s) {
     switch (nv) {
 #define X(n)                                                                   \
     case n:                                                                    \
         if (dtype == LAT_F64) return launch_plain<double, n>(grid, a, k, s);   \
+        if (ring && pcv) return launch_pc_v<n>(pcv, grid, a, k, s);            \
         if (ring) return launch_ring_c<n>(chunks, grid, a, k, s);              \
         return launch_plain<float, n>(grid, a, k, s);
         LAT2D_NV_LIST(X)
@@ -765,10 +958,10 @@ cudaError_t launch_step2d(int dtype, int nv, bool ring, int chunks, int grid,
     }
 }
 
-int occupancy_ring(int nv, int chunks) {
+int occupancy_ring(int nv, int chunks, int pcv) {
     switch (nv) {
 #define X(n) \
-    case n: return occupancy_ring_c<n>(chunks);
+    case n: return pcv ? occupancy_pc_v<n>(pcv) : occupancy_ring_c<n>(chunks);
         LAT2D_NV_LIST(X)
 #undef X
         default: return 0;
@@ -802,6 +995,7 @@ struct Ctx2D {
     // launch
     bool ring = false;
     int chunks = 1;    // warp groups per cell column in the ring kernel
+    int pcv = 0;       // 0: ring kernel; 3..5: producer/consumer variant
     int bps = 0;       // 0 = occupancy limit
     int mode = 0;      // 0 graph, 2 direct launches
     // moments
@@ -853,7 +1047,7 @@ Step2DArgs step_args(const Ctx2D* c, void* const f[2]) {
 int grid_of(const Ctx2D* c, int ntiles) {
     int per_sm = c->bps;
     if (c->ring) {
-        const int occ = occupancy_ring(c->nv, c->chunks);
+        const int occ = occupancy_ring(c->nv, c->chunks, c->pcv);
         if (per_sm <= 0 || per_sm > occ) per_sm = std::max(1, occ);
     } else if (per_sm <= 0) {
         per_sm = 8;
@@ -893,7 +1087,7 @@ int enqueue2d(Ctx2D* c, void* const f[2], int n, cudaStream_t s, int dry) {
             else k_flow2d<float><<<fg, 256, sh, s>>>(fa, k);
             CK2(cudaGetLastError());
         }
-        CK2(launch_step2d(c->dtype, c->nv, c->ring, c->chunks, grid, a, k, s));
+        CK2(launch_step2d(c->dtype, c->nv, c->ring, c->chunks, c->pcv, grid, a, k, s));
     }
     if (!dry) {
         k_advance2d<<<1, 1, 0, s>>>(c->st, n);
@@ -953,6 +1147,7 @@ int ctx2d_create(Ctx2D** out, const lat_grid* g, DevState* st, int sm_count, cud
     c->sm_count = sm_count;
     c->ring = ring_ok(c);
     c->chunks = chunks_supported(c->nv, 3) ? 3 : 1;
+    c->pcv = c->ring && pc_supported(c->nv) ? 4 : 0;
     const long long ncell = (long long)c->nx * c->ny;
     c->mom_blocks = (int)std::min<long long>((ncell + 255) / 256, 4LL * sm_count);
     if (cudaMalloc(&c->d_partials, sizeof(double) * 8 * c->mom_blocks) != cudaSuccess ||
@@ -1107,19 +1302,23 @@ int ctx2d_moments(Ctx2D* c, const void* f, double* rho, double* mean_v, double* 
 int ctx2d_set_launch(Ctx2D* c, int kernel, int block, int bps, int mode) {
     // kernel: 0 keep, 1 plain loads (128 threads), >= 2 bulk-copy ring; for the ring, block =
     // 128 C threads splits every cell's jx range over C warp groups (C = 1..4)
-    if (kernel < 0 || kernel > 4) return LAT_EINVAL;
+    // kernel 3..5: producer/consumer variants (block fixed at 160 threads)
+    if (kernel < 0 || kernel > 5) return LAT_EINVAL;
     if (kernel >= 2 && !ring_ok(c)) return LAT_EINVAL;
+    if (kernel >= 3 && !pc_supported(c->nv)) return LAT_EINVAL;
     const bool ring = kernel == 0 ? c->ring : kernel >= 2;
+    const int pcv = kernel == 0 ? c->pcv : (kernel >= 3 ? kernel : 0);
     int chunks = c->chunks;
-    if (block) {
+    if (block && !pcv) {
         if (block % TW != 0) return LAT_EINVAL;
         if (!ring && block != TW) return LAT_EINVAL;
         if (ring) chunks = block / TW;
     }
-    if (ring && !chunks_supported(c->nv, chunks)) return LAT_EINVAL;
+    if (ring && !pcv && !chunks_supported(c->nv, chunks)) return LAT_EINVAL;
     if (mode == 1 || mode > 2) return LAT_EINVAL;
     c->ring = ring;
     c->chunks = chunks;
+    c->pcv = pcv;
     if (bps > 0) c->bps = bps;
     if (mode == 0 || mode == 2) c->mode = mode;
     drop(c);
@@ -1132,14 +1331,18 @@ int ctx2d_autotune(Ctx2D* c, void* const f[2], int reps, double* best, cudaStrea
     CK2(cudaEventCreate(&e1));
     double best_us = 1e300;
     bool best_ring = c->ring;
-    int best_bps = c->bps, best_chunks = c->chunks;
-    for (int variant = 0; variant <= 4; ++variant) {  // 0 plain, 1..4 ring with that many chunks
-        if (variant > 0 && (!ring_ok(c) || !chunks_supported(c->nv, variant))) continue;
+    int best_bps = c->bps, best_chunks = c->chunks, best_pcv = c->pcv;
+    // variant 0: plain loads; 1..4: ring with that many chunks; 5..7: producer/consumer 3..5
+    for (int variant = 0; variant <= 7; ++variant) {
+        if (variant > 0 && !ring_ok(c)) continue;
+        if (variant >= 1 && variant <= 4 && !chunks_supported(c->nv, variant)) continue;
+        if (variant >= 5 && !pc_supported(c->nv)) continue;
         for (int bps : {1, 2, 3, 4, 6, 8}) {
             c->ring = variant > 0;
-            c->chunks = variant > 0 ? variant : c->chunks;
+            c->chunks = (variant >= 1 && variant <= 4) ? variant : 1;
+            c->pcv = variant >= 5 ? variant - 2 : 0;
             c->bps = bps;
-            if (c->ring && bps > occupancy_ring(c->nv, c->chunks)) continue;
+            if (c->ring && bps > occupancy_ring(c->nv, c->chunks, c->pcv)) continue;
             int rc = enqueue2d(c, f, 1, s, 1);
             if (rc != LAT_OK) return rc;
             CK2(cudaEventRecord(e0, s));
@@ -1154,19 +1357,21 @@ int ctx2d_autotune(Ctx2D* c, void* const f[2], int reps, double* best, cudaStrea
                 best_us = us;
                 best_ring = c->ring;
                 best_chunks = c->chunks;
+                best_pcv = c->pcv;
                 best_bps = bps;
             }
         }
     }
     c->ring = best_ring;
     c->chunks = best_chunks;
+    c->pcv = best_pcv;
     c->bps = best_bps;
     drop(c);
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (best) {
-        best[0] = best_ring ? 2 : 1;
-        best[1] = best_ring ? TW * best_chunks : TW;
+        best[0] = best_pcv ? best_pcv : (best_ring ? 2 : 1);
+        best[1] = best_pcv ? TW + 32 : (best_ring ? TW * best_chunks : TW);
         best[2] = best_bps;
         best[3] = best_us;
     }
