@@ -158,12 +158,18 @@ int lat_current(const lat_ctx* c);
 /* Steps taken since init. */
 long long lat_steps_done(const lat_ctx* c);
 
-/* Launch shape of the step kernel.
- *  kernel: 0 keep; 1 plain coalesced loads; 2..4 bulk asynchronous copies of the shifted plane
- *          windows into a shared-memory ring of that many slots (FP32 only, every N_x a multiple
- *          of 4 and >= 132; 2D uses a fixed 4-slot ring for any value >= 2).  Every variant
- *          gives the same bits.
- *  block:  threads per block (= x cells per tile) for kernel 1; the ring fixes 128; 0 keeps.
+/* Launch shape of the step kernel.  Every variant gives the same bits.
+ *  kernel: 0 keep; 1 plain coalesced loads (any size, FP32 or FP64).  The others bring the
+ *          shifted plane windows into shared memory with bulk asynchronous copies (FP32; every
+ *          N_x a multiple of 4 and >= 132):
+ *          d = 1: 2..4 ring of that many item slots refilled after a block barrier;
+ *                 5..7 producer warp + consumer warps on a ring of 2..4 slots (no barrier).
+ *          d = 2: 2 ring refilled after a block barrier (block = 128 C threads splits each
+ *                 cell's jx range over C = 1..4 warp groups);
+ *                 3..5 producer warp + consumer warps (3: vy-flux row in registers, 4 slots;
+ *                 4: in shared memory, 4 slots; 5: in shared memory, 3 slots).
+ *  block:  threads per block (= x cells per tile) for kernel 1; the copy pipelines fix a 128-cell
+ *          tile (2D kernel 2: 128 C threads); 0 keeps.
  *  blocks_per_sm: resident blocks per SM of the persistent grid; 0 keeps.
  *  mode:   -1 keep; 0 one persistent launch per step, n steps captured in one CUDA graph;
  *          1 one launch per instance per step (the unbatched baseline, 1D); 2 persistent

@@ -279,16 +279,16 @@ int lat_ensemble_init(lat_ctx** out, int n_inst, const lat_instance* inst, int n
             cudaSuccess)
         rc = LAT_ECUDA;
     if (rc == LAT_OK) {
-        // default launch shape: the bulk-copy ring where every instance allows it, else plain
-        // loads with 256 threads; one x column per thread
+        // default launch shape: the producer/consumer bulk-copy pipeline where every instance
+        // allows it, else plain loads with 256 threads; one x column per thread
         c->ring_ok = step1d_ring_supported(dtype, nv);
         for (int i = 0; i < n_inst; ++i)
             if (inst[i].nx % 4 != 0 || inst[i].nx < step1d_ring_min_nx()) c->ring_ok = false;
         if (c->ring_ok) {
-            c->variant = STEP1D_RING;
+            c->variant = STEP1D_PC;
             c->block = step1d_ring_tile();
-            c->slots = 3;
-            c->bps = std::max(1, step1d_ring_occupancy(nv, 3));
+            c->slots = 2;
+            c->bps = std::max(1, step1d_ring_occupancy(nv, 2, STEP1D_PC));
         } else {
             c->variant = STEP1D_PLAIN;
             c->block = std::min(256, step1d_max_block(dtype, nv, STEP1D_PLAIN));
@@ -545,25 +545,26 @@ int lat_set_launch(lat_ctx* c, int kernel, int block, int blocks_per_sm, int mod
     if (kernel == 1) {
         variant = STEP1D_PLAIN;
         if (c->variant != STEP1D_PLAIN && !block) nb = std::min(256, step1d_max_block(c->dtype, c->nv, STEP1D_PLAIN));
-    } else if (kernel >= 2 && kernel <= 4) {
+    } else if (kernel >= 2 && kernel <= 7) {
         if (!c->ring_ok) return LAT_EINVAL;
-        variant = STEP1D_RING;
-        slots = kernel;
+        variant = kernel <= 4 ? STEP1D_RING : STEP1D_PC;
+        slots = kernel <= 4 ? kernel : kernel - 3;
         nb = step1d_ring_tile();
     } else if (kernel != 0) {
         return LAT_EINVAL;
     }
-    if (block && variant == STEP1D_PLAIN) nb = block;
-    if (block && variant == STEP1D_RING && block != step1d_ring_tile()) return LAT_EINVAL;
+    const bool piped = variant != STEP1D_PLAIN;
+    if (block && !piped) nb = block;
+    if (block && piped && block != step1d_ring_tile()) return LAT_EINVAL;
     int nbps = blocks_per_sm ? blocks_per_sm : c->bps;
-    // a kept block count is clamped to what the newly chosen ring shape can hold
-    if (!blocks_per_sm && variant == STEP1D_RING)
-        nbps = std::max(1, std::min(nbps, step1d_ring_occupancy(c->nv, slots)));
+    // a kept block count is clamped to what the newly chosen pipeline shape can hold
+    if (!blocks_per_sm && piped)
+        nbps = std::max(1, std::min(nbps, step1d_ring_occupancy(c->nv, slots, variant)));
     const int nmode = mode >= 0 ? mode : c->mode;
     if (nb < 32 || nb > 1024 || nb % 32 != 0 || nbps < 1 || nbps > 64 || nmode > 2)
         return LAT_EINVAL;
     if (nb > step1d_max_block(c->dtype, c->nv, variant)) return LAT_EINVAL;
-    if (variant == STEP1D_RING && nbps > step1d_ring_occupancy(c->nv, slots)) return LAT_EINVAL;
+    if (piped && nbps > step1d_ring_occupancy(c->nv, slots, variant)) return LAT_EINVAL;
     const bool retile = nb != tile_of(c);
     c->variant = variant;
     c->slots = slots;
@@ -587,8 +588,10 @@ int lat_autotune(lat_ctx* c, int reps, double* best) {
                 cands.push_back({1, b, p});
     if (c->ring_ok)
         for (int sl : {2, 3, 4}) {
-            const int occ = step1d_ring_occupancy(c->nv, sl);
+            const int occ = step1d_ring_occupancy(c->nv, sl, STEP1D_RING);
             for (int p = 1; p <= occ; ++p) cands.push_back({sl, 0, p});
+            const int occp = step1d_ring_occupancy(c->nv, sl, STEP1D_PC);
+            for (int p = 1; p <= occp; ++p) cands.push_back({sl + 3, 0, p});
         }
     cudaEvent_t e0, e1;
     CK(cudaEventCreate(&e0));

@@ -54,7 +54,7 @@ struct Inst1D {
 };
 
 // Step kernel variants (1D).
-enum { STEP1D_PLAIN = 0, STEP1D_RING = 1 };
+enum { STEP1D_PLAIN = 0, STEP1D_RING = 1, STEP1D_PC = 2 };
 
 constexpr int kMaxModes1D = 16;
 constexpr int kMaxModes2D = 512;
@@ -101,7 +101,7 @@ int step1d_max_block(int dtype, int nv, int variant);
 bool step1d_ring_supported(int dtype, int nv);
 int step1d_ring_tile();
 int step1d_ring_min_nx();
-int step1d_ring_occupancy(int nv, int slots);
+int step1d_ring_occupancy(int nv, int slots, int variant);
 cudaError_t launch_moments1d(int dtype, int block, int tile_xpt, int grid, const Mom1DArgs& a,
                              cudaStream_t s);
 cudaError_t launch_finalize1d(const double* partials, const int* inst_item_begin,

@@ -405,7 +405,115 @@ __global__ void __launch_bounds__(TW1) k_step1d_ring(const Step1DArgs a, const i
     }
 }
 
+// ---- producer/consumer variant: no block-wide barrier per item -------------------------------
+// Four consumer warps own the 128 columns of an item; a fifth warp only produces: it refills a
+// ring slot with the next item's plane windows once every consumer warp has released the slot
+// (per-slot "empty" mbarrier, one arrival per consumer warp).  Consumers wait only on the
+// per-slot "full" mbarrier that the bulk copies complete, so warps drift freely.
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+constexpr int PC1_CONSUMERS = TW1 / 32;
+constexpr int PC1_THREADS = 32 * (PC1_CONSUMERS + 1);
+
+template <int NV, int NS>
+size_t pc1d_smem() {
+    return (size_t)NS * NV * WIN1 * sizeof(float) + 2 * NS * sizeof(uint64_t);
+}
+
+template <int NV, int NS>
+__global__ void __launch_bounds__(PC1_THREADS) k_step1d_pc(const Step1DArgs a, const int kstep) {
+    constexpr int J = (NV - 1) / 2;
+    extern __shared__ __align__(128) unsigned char smem[];
+    float* ring = reinterpret_cast<float*>(smem);
+    uint64_t* full = reinterpret_cast<uint64_t*>(smem + (size_t)NS * NV * WIN1 * sizeof(float));
+    uint64_t* empty = full + NS;
+    const long long step = a.st->step + kstep;
+    const int par = (int)(step & 1);
+    const float* fin = static_cast<const float*>(a.f[par]);
+    float* fout = static_cast<float*>(a.f[par ^ 1]);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int first = a.item_begin + blockIdx.x;
+    const int nloc = first < a.item_end ? (a.item_end - 1 - first) / gridDim.x + 1 : 0;
+    if (threadIdx.x == 0) {
+        for (int q = 0; q < NS; ++q) {
+            mbar_init(&full[q], 1);
+            mbar_init(&empty[q], PC1_CONSUMERS);
+        }
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    if (warp == PC1_CONSUMERS) {
+        int k = 0;
+        for (; k < nloc; ++k) {
+            const int q = k % NS;
+            if (k >= NS && !mbar_wait_bounded(&empty[q], (unsigned)(((k / NS) + 1) & 1))) {
+                if (lane == 0) atomicOr(&a.st->status, ST_TIMEOUT);
+                break;
+            }
+            issue_item<NV>(a, fin, ring, full, q, first + k * gridDim.x);
+        }
+        // the copies issued last must land before this warp leaves
+        for (int d = std::max(0, k - NS); d < k; ++d)
+            mbar_wait_bounded(&full[d % NS], (unsigned)((d / NS) & 1));
+        return;
+    }
+    const int tid = threadIdx.x;
+    for (int k = 0; k < nloc; ++k) {
+        const int it = first + k * gridDim.x;
+        const int2 item = a.items[it];
+        const Inst1D in = a.inst[item.x];
+        const int x = item.y + tid;
+        const float g = float(in.g), r = float(in.r);
+        float w = 0.f;
+        if (x < in.nx) w = flow_at<float>(a, in, amp_ptr<float>(a, par, item.x), x) * float(in.inv_dv);
+        if (!mbar_wait_bounded(&full[k % NS], (unsigned)((k / NS) & 1))) {
+            if (lane == 0) atomicOr(&a.st->status, ST_TIMEOUT);
+            break;
+        }
+        if (x < in.nx) {
+            const float* col = ring + (size_t)(k % NS) * NV * WIN1 + tid;
+            float* dst = fout + in.off + x;
+            const int nx = in.nx;
+            sweep_column<float, NV>(
+                w, g, r,
+                [&](int jj) { return col[jj * WIN1 + ((J - jj) % 4 + 4) % 4]; },
+                [&](int jj, float v) { dst[(size_t)jj * nx] = v; });
+            cfl_flag<float, J>(a, g, w);
+        }
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&empty[k % NS]);
+        if (!a.dry && !a.frozen && a.flow_kind == LAT_FLOW_MODES && item.y == 0)
+            advance_amplitudes(a, item.x, in, step, par);
+    }
+}
+
 __global__ void k_advance_step(DevState* st, long long n) { st->step += n; }
+
+template <int NV, int NS>
+cudaError_t launch_pc1(int grid, const Step1DArgs& a, int kstep, cudaStream_t s) {
+    static bool attr = false;
+    if (!attr) {
+        cudaError_t e = cudaFuncSetAttribute(k_step1d_pc<NV, NS>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)pc1d_smem<NV, NS>());
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    k_step1d_pc<NV, NS><<<grid, PC1_THREADS, pc1d_smem<NV, NS>(), s>>>(a, kstep);
+    return cudaGetLastError();
+}
+
+template <int NV, int NS>
+int occupancy_pc1() {
+    int nb = 0;
+    cudaFuncSetAttribute(k_step1d_pc<NV, NS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)pc1d_smem<NV, NS>());
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_step1d_pc<NV, NS>, PC1_THREADS,
+                                                  pc1d_smem<NV, NS>());
+    return nb;
+}
 
 template <int NV, int NS>
 size_t ring1d_smem() {
@@ -463,7 +571,7 @@ cudaError_t launch_plain(int nv, int block, int grid, const Step1DArgs& a, int k
 }  // namespace
 
 int step1d_max_block(int dtype, int nv, int variant) {
-    if (variant == STEP1D_RING) return TW1;
+    if (variant == STEP1D_RING || variant == STEP1D_PC) return TW1;
     bool reg = false;
 #define X(n) reg |= nv == n;
     LAT1D_NV_LIST(X)
@@ -485,12 +593,17 @@ bool step1d_ring_supported(int dtype, int nv) {
 int step1d_ring_tile() { return TW1; }
 int step1d_ring_min_nx() { return WIN1; }
 
-int step1d_ring_occupancy(int nv, int slots) {
+int step1d_ring_occupancy(int nv, int slots, int variant) {
     switch (nv) {
-#define X(n)                                           \
-    case n:                                            \
-        if (slots == 2) return occupancy_ring<n, 2>(); \
-        if (slots == 3) return occupancy_ring<n, 3>(); \
+#define X(n)                                                                    \
+    case n:                                                                     \
+        if (variant == STEP1D_PC) {                                             \
+            if (slots == 2) return occupancy_pc1<n, 2>();                       \
+            if (slots == 3) return occupancy_pc1<n, 3>();                       \
+            return occupancy_pc1<n, 4>();                                       \
+        }                                                                       \
+        if (slots == 2) return occupancy_ring<n, 2>();                          \
+        if (slots == 3) return occupancy_ring<n, 3>();                          \
         return occupancy_ring<n, 4>();
         LAT1D_NV_LIST(X)
 #undef X
@@ -501,6 +614,20 @@ int step1d_ring_occupancy(int nv, int slots) {
 cudaError_t launch_step1d(int dtype, int nv, int variant, int block, int slots, int grid,
                           const Step1DArgs& a, int kstep, cudaStream_t s) {
     if (grid <= 0) return cudaSuccess;
+    if (variant == STEP1D_PC) {
+        if (dtype != LAT_F32 || block != TW1) return cudaErrorInvalidValue;
+        switch (nv) {
+#define X(n)                                                         \
+    case n:                                                          \
+        if (slots == 2) return launch_pc1<n, 2>(grid, a, kstep, s);  \
+        if (slots == 3) return launch_pc1<n, 3>(grid, a, kstep, s);  \
+        if (slots == 4) return launch_pc1<n, 4>(grid, a, kstep, s);  \
+        return cudaErrorInvalidValue;
+            LAT1D_NV_LIST(X)
+#undef X
+            default: return cudaErrorInvalidValue;
+        }
+    }
     if (variant == STEP1D_RING) {
         if (dtype != LAT_F32 || block != TW1) return cudaErrorInvalidValue;
         switch (nv) {

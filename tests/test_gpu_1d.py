@@ -118,7 +118,8 @@ def test_free_streaming_is_exact(lat, nv):
 @pytest.mark.parametrize("launch", [dict(kernel=1, block=128, blocks_per_sm=2),
                                     dict(kernel=1, block=512, blocks_per_sm=1),
                                     dict(kernel=2, blocks_per_sm=1), dict(kernel=4),
-                                    dict(mode=2), dict(mode=1)])
+                                    dict(kernel=5), dict(kernel=6, blocks_per_sm=1),
+                                    dict(kernel=7), dict(kernel=1, mode=2), dict(mode=1)])
 def test_launch_shapes_are_bit_identical(lat, launch):
     """Kernel variant (plain loads or bulk-copy ring), tile width, grid size, graph capture or
     direct launches change nothing in the result."""

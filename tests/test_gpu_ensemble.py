@@ -125,7 +125,7 @@ def test_autotune_keeps_state(lat):
     a, _ = build(lat, tab, nv, torch.float32, fl)
     b, _ = build(lat, tab, nv, torch.float32, fl)
     best = b.autotune(reps=2)
-    assert best["kernel"] in (1, 2, 3, 4) and best["us_per_step"] > 0
+    assert best["kernel"] in (1, 2, 3, 4, 5, 6, 7) and best["us_per_step"] > 0
     a.step(nsteps)
     b.step(nsteps)
     assert np.array_equal(a.state.cpu().numpy(), b.state.cpu().numpy())
