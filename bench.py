@@ -296,10 +296,10 @@ def end_to_end(ctx, noise_row, glob, steps, torch):
     t0 = time.perf_counter()
     for _ in range(steps):
         ctx.set_noise_pinned(pinned)
-        ctx.step(1)
         if glob.ndim == 2:
-            ctx.moments(per_cell=False, globals_out=glob)
+            ctx.step_moments(1, per_cell=False, globals_out=glob)  # moments fused into the step
         else:
+            ctx.step(1)
             code, *_ , g = ctx.moments(per_cell=False)
             glob[:] = g
     torch.cuda.synchronize()
@@ -307,10 +307,16 @@ def end_to_end(ctx, noise_row, glob, steps, torch):
 
 
 def kernel_label(workload, best, nv):
+    k = best["kernel"] if best else 0
     if workload == "2d":
-        return f"k_step2d_{'ring' if best and best['kernel'] == 2 else 'plain'}<{nv}>"
-    if best and best["kernel"] >= 2:
-        return f"k_step1d_ring<{nv},{best['kernel']}>"
+        if k >= 3:
+            return {3: f"k_step2d_pc<{nv},4,false>", 4: f"k_step2d_pc<{nv},4,true>",
+                    5: f"k_step2d_pc<{nv},3,true>"}[k]
+        return f"k_step2d_{'ring' if k == 2 else 'plain'}<{nv}>"
+    if k >= 5:
+        return f"k_step1d_pc<{nv},{k - 3}>"
+    if k >= 2:
+        return f"k_step1d_ring<{nv},{k}>"
     return f"k_step1d_reg<float,{nv}>"
 
 

@@ -149,6 +149,14 @@ int lat_prepare(lat_ctx* c, int n);
  * Synchronises; returns the pending device status (LAT_ECFL, LAT_ENUMERIC, ...) if any. */
 int lat_moments(lat_ctx* c, double* rho, double* mean_v, double* mean_v2, double* globals);
 
+/* lat_step(c, n) followed by lat_moments(c, ...), with the moments of the final state computed
+ * inside the last step (no second pass over f) when the 1D producer/consumer kernel is in use;
+ * otherwise exactly the two calls.  Same arguments, outputs, synchronisation and status as
+ * lat_moments.  The per-cell outputs equal lat_moments' bit for bit; the globals agree to the
+ * rounding order of the compensated sums. */
+int lat_step_moments(lat_ctx* c, int n, double* rho, double* mean_v, double* mean_v2,
+                     double* globals);
+
 /* Synchronise, return and clear the pending device status. */
 int lat_status(lat_ctx* c);
 

@@ -124,7 +124,9 @@ int build_items(lat_ctx* c) {
     c->nitems = (int)items.size();
     if (cudaMalloc(&c->d_items, sizeof(int2) * items.size()) != cudaSuccess ||
         cudaMalloc(&c->d_inst_begin, sizeof(int) * (c->n_inst + 1)) != cudaSuccess ||
-        cudaMalloc(&c->d_partials, sizeof(double) * 6 * items.size()) != cudaSuccess)
+        cudaMalloc(&c->d_partials,
+                   sizeof(double) * 6 * std::max(kPcConsumerWarps, tile / 32) * items.size()) !=
+            cudaSuccess)
         return LAT_ENOMEM;
     CK(cudaMemcpy(c->d_items, items.data(), sizeof(int2) * items.size(), cudaMemcpyHostToDevice));
     CK(cudaMemcpy(c->d_inst_begin, c->h_inst_begin.data(), sizeof(int) * (c->n_inst + 1),
@@ -521,7 +523,41 @@ int lat_moments(lat_ctx* c, double* rho, double* mean_v, double* mean_v2, double
     const int grid = std::max(1, std::min(c->nitems, 8 * c->sm_count));
     CK(launch_moments1d(c->dtype, tile_of(c), 1, grid, a, c->stream));
     CK(launch_finalize1d(c->d_partials, c->d_inst_begin, c->d_inst, c->n_inst, c->d_glob,
+                         tile_of(c) / 32,
                          c->stream));
+    if (globals)
+        CK(cudaMemcpyAsync(c->h_glob, c->d_glob, sizeof(double) * 3 * c->n_inst,
+                           cudaMemcpyDeviceToHost, c->stream));
+    int rc = lat_status(c);  // synchronises
+    if (globals) memcpy(globals, c->h_glob, sizeof(double) * 3 * c->n_inst);
+    return rc;
+}
+
+int lat_step_moments(lat_ctx* c, int n, double* rho, double* mean_v, double* mean_v2,
+                     double* globals) {
+    if (!c || n < 1) return LAT_EINVAL;
+    const bool fused = c->d == 1 && c->variant == STEP1D_PC && c->mode != 1 &&
+                       step1d_moments_supported(c->dtype, c->nv);
+    if (!fused) {
+        int rc = lat_step(c, n);
+        if (rc != LAT_OK) return rc;
+        return lat_moments(c, rho, mean_v, mean_v2, globals);
+    }
+    if (n > 1) {
+        int rc = lat_step(c, n - 1);
+        if (rc != LAT_OK) return rc;
+    }
+    Step1DArgs a = step_args(c, 0, 0);
+    a.m_rho = rho;
+    a.m_mv = mean_v;
+    a.m_mv2 = mean_v2;
+    a.m_partials = c->d_partials;
+    CK(launch_step1d_moments(c->nv, persistent_grid(c), a, c->stream));
+    CK(launch_advance_step(c->d_state, 1, c->stream));
+    CK(launch_finalize1d(c->d_partials, c->d_inst_begin, c->d_inst, c->n_inst, c->d_glob,
+                         kPcConsumerWarps, c->stream));
+    c->h_step += 1;
+    c->cur = (int)(c->h_step & 1);
     if (globals)
         CK(cudaMemcpyAsync(c->h_glob, c->d_glob, sizeof(double) * 3 * c->n_inst,
                            cudaMemcpyDeviceToHost, c->stream));

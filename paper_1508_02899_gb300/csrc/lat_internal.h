@@ -78,7 +78,14 @@ struct Step1DArgs {
     DevState* st;
     int dry;                 // 1: do not advance the flow (autotuning)
     int frozen;              // 1: flow frozen (tau_f infinite)
+    // moments of the new state, fused into the step (k_step1d_pc with moments); may be null
+    double* m_rho;
+    double* m_mv;
+    double* m_mv2;
+    double* m_partials;      // [item][consumer warp][M, P, E][sum, compensation]
 };
+
+constexpr int kPcConsumerWarps = 4;
 
 // Arguments of the moment kernels (1D).
 struct Mom1DArgs {
@@ -102,10 +109,15 @@ bool step1d_ring_supported(int dtype, int nv);
 int step1d_ring_tile();
 int step1d_ring_min_nx();
 int step1d_ring_occupancy(int nv, int slots, int variant);
+// One producer/consumer step (2 slots) that also writes the moments of the new state.
+cudaError_t launch_step1d_moments(int nv, int grid, const Step1DArgs& a, cudaStream_t s);
+bool step1d_moments_supported(int dtype, int nv);
 cudaError_t launch_moments1d(int dtype, int block, int tile_xpt, int grid, const Mom1DArgs& a,
                              cudaStream_t s);
+// Fold per-instance partials: instance i owns partials [per_item begin[i], per_item begin[i+1]).
 cudaError_t launch_finalize1d(const double* partials, const int* inst_item_begin,
-                              const Inst1D* inst, int n_inst, double* glob, cudaStream_t s);
+                              const Inst1D* inst, int n_inst, double* glob, int per_item,
+                              cudaStream_t s);
 cudaError_t launch_advance_step(DevState* st, long long n, cudaStream_t s);
 
 }  // namespace lat

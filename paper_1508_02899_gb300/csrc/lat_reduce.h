@@ -1,0 +1,114 @@
+// Compensated summation helpers shared by the moment reductions (device code only).
+#pragma once
+
+#include <cuda_runtime.h>
+
+namespace lat {
+namespace cs {
+
+// FP64 value with a Neumaier compensation term: the sum is s + c.
+struct Comp {
+    double s, c;
+};
+
+// Neumaier's compensated addition.
+__device__ __forceinline__ void nadd(Comp& a, double x) {
+    const double t = __dadd_rn(a.s, x);
+    if (fabs(a.s) >= fabs(x)) a.c = __dadd_rn(a.c, __dadd_rn(__dsub_rn(a.s, t), x));
+    else a.c = __dadd_rn(a.c, __dadd_rn(__dsub_rn(x, t), a.s));
+    a.s = t;
+}
+__device__ __forceinline__ void nmerge(Comp& a, const Comp& b) {
+    nadd(a, b.s);
+    a.c = __dadd_rn(a.c, b.c);
+}
+__device__ __forceinline__ double nval(const Comp& a) { return __dadd_rn(a.s, a.c); }
+
+__device__ __forceinline__ Comp shfl_down(const Comp& a, int off) {
+    return Comp{__shfl_down_sync(0xffffffffu, a.s, off), __shfl_down_sync(0xffffffffu, a.c, off)};
+}
+
+// Kahan-compensated FP32 accumulator (c holds the negated running error: the sum is s - c).
+struct FComp {
+    float s = 0.f, c = 0.f;
+    __device__ __forceinline__ void add(float x) {
+        const float y = __fsub_rn(x, c);
+        const float t = __fadd_rn(s, y);
+        c = __fsub_rn(__fsub_rn(t, s), y);
+        s = t;
+    }
+    // (s - c) + (o.s - o.c): s + o.s by Knuth's branch-free TwoSum (t + e exactly, whatever the
+    // magnitudes), then both error terms and e fold into c.  Only the rounding of c is lost,
+    // about u^2 of the partial sums per merge (u = 2^-24).
+    __device__ __forceinline__ void merge(const FComp& o) {
+        const float t = __fadd_rn(s, o.s);
+        const float bb = __fsub_rn(t, s);
+        const float e = __fadd_rn(__fsub_rn(s, __fsub_rn(t, bb)), __fsub_rn(o.s, bb));
+        s = t;
+        c = __fsub_rn(__fadd_rn(c, o.c), e);
+    }
+    __device__ __forceinline__ Comp to_comp(double scale) const {
+        return Comp{__dmul_rn((double)s, scale), -__dmul_rn((double)c, scale)};
+    }
+};
+
+__device__ __forceinline__ FComp shfl_down(const FComp& a, int off) {
+    FComp r;
+    r.s = __shfl_down_sync(0xffffffffu, a.s, off);
+    r.c = __shfl_down_sync(0xffffffffu, a.c, off);
+    return r;
+}
+
+// Butterfly reduction of an FP32 compensated sum over a warp, in a fixed order (lane 0).
+__device__ __forceinline__ void warp_reduce(FComp& t) {
+    for (int off = 16; off > 0; off >>= 1) t.merge(shfl_down(t, off));
+}
+__device__ __forceinline__ void warp_reduce(Comp& t) {
+    for (int off = 16; off > 0; off >>= 1) nmerge(t, shfl_down(t, off));
+}
+
+// Column sums of one 1D column [sum f, sum j f, sum j^2 f] accumulated in FP32 (Kahan) and
+// returned as FP64 compensated values scaled to [M0, M1 = sum v f, M2 = sum v^2 f] / dv.
+struct ColumnSums {
+    FComp a0, a1, a2;
+    __device__ __forceinline__ void add(float j, float fv) {
+        a0.add(fv);
+        a1.add(j * fv);
+        a2.add(j * j * fv);
+    }
+    __device__ __forceinline__ void result(double dv, Comp& s0, Comp& s1, Comp& s2) const {
+        const double dv2 = __dmul_rn(dv, dv);
+        s0 = Comp{(double)a0.s, -(double)a0.c};
+        s1 = Comp{__dmul_rn((double)a1.s, dv), -__dmul_rn((double)a1.c, dv)};
+        s2 = Comp{__dmul_rn((double)a2.s, dv2), -__dmul_rn((double)a2.c, dv2)};
+    }
+};
+
+// Butterfly reduction of three compensated sums over a warp (result in lane 0).
+__device__ __forceinline__ void warp_reduce3(Comp& t0, Comp& t1, Comp& t2) {
+    for (int off = 16; off > 0; off >>= 1) {
+        Comp o0 = shfl_down(t0, off), o1 = shfl_down(t1, off), o2 = shfl_down(t2, off);
+        nmerge(t0, o0);
+        nmerge(t1, o1);
+        nmerge(t2, o2);
+    }
+}
+
+// Per-warp partial of the 1D moments of FP32 columns: every lane holds the Kahan column sums of
+// its column (zero for an inactive lane); lane 0 writes [M, P, E] (sum, compensation) scaled to
+// [1, dv, dv^2] at p.  The cross-column part stays in FP32 Kahan form (FP64 is slow here).
+__device__ __forceinline__ void warp_partial_1d(const ColumnSums& cs_, double dv, double* p) {
+    FComp a0 = cs_.a0, a1 = cs_.a1, a2 = cs_.a2;
+    warp_reduce(a0);
+    warp_reduce(a1);
+    warp_reduce(a2);
+    if ((threadIdx.x & 31) == 0) {
+        const Comp t0 = a0.to_comp(1.0), t1 = a1.to_comp(dv), t2 = a2.to_comp(__dmul_rn(dv, dv));
+        p[0] = t0.s; p[1] = t0.c;
+        p[2] = t1.s; p[3] = t1.c;
+        p[4] = t2.s; p[5] = t2.c;
+    }
+}
+
+}  // namespace cs
+}  // namespace lat

@@ -23,6 +23,7 @@
 #include <algorithm>
 
 #include "lat_internal.h"
+#include "lat_reduce.h"
 
 namespace lat {
 namespace {
@@ -422,7 +423,9 @@ size_t pc1d_smem() {
     return (size_t)NS * NV * WIN1 * sizeof(float) + 2 * NS * sizeof(uint64_t);
 }
 
-template <int NV, int NS>
+// With MOM the consumers also reduce the moments of the columns they write (the same FP32
+// Kahan column sums, in the same order, as the moment kernel; compensated FP64 across cells).
+template <int NV, int NS, bool MOM = false>
 __global__ void __launch_bounds__(PC1_THREADS) k_step1d_pc(const Step1DArgs a, const int kstep) {
     constexpr int J = (NV - 1) / 2;
     extern __shared__ __align__(128) unsigned char smem[];
@@ -472,6 +475,7 @@ __global__ void __launch_bounds__(PC1_THREADS) k_step1d_pc(const Step1DArgs a, c
             if (lane == 0) atomicOr(&a.st->status, ST_TIMEOUT);
             break;
         }
+        cs::ColumnSums sums;
         if (x < in.nx) {
             const float* col = ring + (size_t)(k % NS) * NV * WIN1 + tid;
             float* dst = fout + in.off + x;
@@ -479,11 +483,28 @@ __global__ void __launch_bounds__(PC1_THREADS) k_step1d_pc(const Step1DArgs a, c
             sweep_column<float, NV>(
                 w, g, r,
                 [&](int jj) { return col[jj * WIN1 + ((J - jj) % 4 + 4) % 4]; },
-                [&](int jj, float v) { dst[(size_t)jj * nx] = v; });
+                [&](int jj, float v) {
+                    dst[(size_t)jj * nx] = v;
+                    if constexpr (MOM) sums.add((float)(jj - J), v);
+                });
             cfl_flag<float, J>(a, g, w);
         }
         __syncwarp();
         if (lane == 0) mbar_arrive(&empty[k % NS]);
+        if constexpr (MOM) {  // same per-warp partials as the moment kernel with 128 columns
+            if (x < in.nx) {
+                cs::Comp t0, t1, t2;
+                sums.result(in.dv, t0, t1, t2);
+                const double m0 = cs::nval(t0), m1 = cs::nval(t1), m2 = cs::nval(t2);
+                if (!isfinite(m0) || !isfinite(m2)) atomicOr(&a.st->status, ST_NUMERIC);
+                const long long cell = in.xoff + x;
+                if (a.m_rho) a.m_rho[cell] = m0 * in.dv;
+                if (a.m_mv) a.m_mv[cell] = (m0 != 0.0) ? m1 / m0 : 0.0;
+                if (a.m_mv2) a.m_mv2[cell] = (m0 != 0.0) ? m2 / m0 : 0.0;
+            }
+            cs::warp_partial_1d(sums, in.dv,
+                                a.m_partials + ((size_t)it * PC1_CONSUMERS + warp) * 6);
+        }
         if (!a.dry && !a.frozen && a.flow_kind == LAT_FLOW_MODES && item.y == 0)
             advance_amplitudes(a, item.x, in, step, par);
     }
@@ -491,17 +512,17 @@ __global__ void __launch_bounds__(PC1_THREADS) k_step1d_pc(const Step1DArgs a, c
 
 __global__ void k_advance_step(DevState* st, long long n) { st->step += n; }
 
-template <int NV, int NS>
+template <int NV, int NS, bool MOM = false>
 cudaError_t launch_pc1(int grid, const Step1DArgs& a, int kstep, cudaStream_t s) {
     static bool attr = false;
     if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute(k_step1d_pc<NV, NS>,
+        cudaError_t e = cudaFuncSetAttribute(k_step1d_pc<NV, NS, MOM>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)pc1d_smem<NV, NS>());
         if (e != cudaSuccess) return e;
         attr = true;
     }
-    k_step1d_pc<NV, NS><<<grid, PC1_THREADS, pc1d_smem<NV, NS>(), s>>>(a, kstep);
+    k_step1d_pc<NV, NS, MOM><<<grid, PC1_THREADS, pc1d_smem<NV, NS>(), s>>>(a, kstep);
     return cudaGetLastError();
 }
 
@@ -608,6 +629,19 @@ int step1d_ring_occupancy(int nv, int slots, int variant) {
         LAT1D_NV_LIST(X)
 #undef X
         default: return 0;
+    }
+}
+
+bool step1d_moments_supported(int dtype, int nv) { return step1d_ring_supported(dtype, nv); }
+
+cudaError_t launch_step1d_moments(int nv, int grid, const Step1DArgs& a, cudaStream_t s) {
+    if (grid <= 0) return cudaSuccess;
+    switch (nv) {
+#define X(n) \
+    case n: return launch_pc1<n, 2, true>(grid, a, 0, s);
+        LAT1D_NV_LIST(X)
+#undef X
+        default: return cudaErrorInvalidValue;
     }
 }
 

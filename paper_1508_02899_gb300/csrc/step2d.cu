@@ -24,6 +24,7 @@
 #include <map>
 
 #include "lat2d.h"
+#include "lat_reduce.h"
 
 namespace lat {
 
@@ -715,89 +716,116 @@ __global__ void __launch_bounds__(256) k_flow2d(const Flow2DArgs a, int kstep) {
 }
 
 // ---- moments ----------------------------------------------------------------------------------
-struct Comp {
-    double s, c;
-};
-__device__ __forceinline__ void nadd(Comp& a, double x) {
-    const double t = __dadd_rn(a.s, x);
-    if (fabs(a.s) >= fabs(x)) a.c = __dadd_rn(a.c, __dadd_rn(__dsub_rn(a.s, t), x));
-    else a.c = __dadd_rn(a.c, __dadd_rn(__dsub_rn(x, t), a.s));
-    a.s = t;
-}
-__device__ __forceinline__ void nmerge(Comp& a, const Comp& b) {
-    nadd(a, b.s);
-    a.c = __dadd_rn(a.c, b.c);
-}
-__device__ __forceinline__ double nval(const Comp& a) { return __dadd_rn(a.s, a.c); }
+using namespace cs;
 
 template <typename T>
 __device__ __forceinline__ double to_d(T v) { return (double)v; }
 
+constexpr int kMom2DWarps = 8;  // warps per moment block (256 threads)
+
+// Per cell: sums over the N_v^2 velocity cells of f, jx f, jy f, (jx^2 + jy^2) f; per-cell moments
+// and one compensated partial per warp: partials[block][warp][4][2].
+//   FP64 storage: Neumaier FP64 throughout.
+//   FP32 / FP16 / BF16 storage: FP32 Kahan sums per cell and across a thread's cells and the
+//   warp (exact integer weights); FP64 from the warp partials on (FP64 is slow on this GPU).
 template <typename T>
 __global__ void __launch_bounds__(256) k_moments2d(const void* fv, const float* scales, int nv,
                                                    int nx, int ny, double dv, double* rho,
                                                    double* mv, double* mv2, double* partials,
                                                    DevState* st) {
-    __shared__ Comp red[4][8];
     const T* f = static_cast<const T*>(fv);
     const int J = (nv - 1) / 2;
     const long long ncell = (long long)nx * ny;
-    Comp t[4] = {{0, 0}, {0, 0}, {0, 0}, {0, 0}};
+    const double dv2 = __dmul_rn(dv, dv);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    double* p = partials + ((size_t)blockIdx.x * (blockDim.x >> 5) + warp) * 8;
     bool bad = false;
-    for (long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x; c < ncell;
-         c += (long long)gridDim.x * blockDim.x) {
-        Comp s[4] = {{0, 0}, {0, 0}, {0, 0}, {0, 0}};
-        for (int jy = 0; jy < nv; ++jy) {
-            const double vy = __dmul_rn((double)(jy - J), dv);
-            for (int jx = 0; jx < nv; ++jx) {
-                const double vx = __dmul_rn((double)(jx - J), dv);
-                const size_t plane = (size_t)jy * nv + jx;
-                double fvv = to_d(f[plane * ncell + c]);
-                if (scales) fvv = __dmul_rn(fvv, (double)scales[plane * ny + c / nx]);
-                bad |= !isfinite(fvv);
-                nadd(s[0], fvv);
-                nadd(s[1], __dmul_rn(vx, fvv));
-                nadd(s[2], __dmul_rn(vy, fvv));
-                nadd(s[3], __dmul_rn(__dadd_rn(__dmul_rn(vx, vx), __dmul_rn(vy, vy)), fvv));
+    if (sizeof(T) == sizeof(double)) {
+        Comp t[4] = {{0, 0}, {0, 0}, {0, 0}, {0, 0}};
+        for (long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x; c < ncell;
+             c += (long long)gridDim.x * blockDim.x) {
+            Comp s[4] = {{0, 0}, {0, 0}, {0, 0}, {0, 0}};
+            for (int jy = 0; jy < nv; ++jy) {
+                const double vy = __dmul_rn((double)(jy - J), dv);
+                for (int jx = 0; jx < nv; ++jx) {
+                    const double vx = __dmul_rn((double)(jx - J), dv);
+                    const size_t plane = (size_t)jy * nv + jx;
+                    const double fvv = to_d(f[plane * ncell + c]);
+                    bad |= !isfinite(fvv);
+                    nadd(s[0], fvv);
+                    nadd(s[1], __dmul_rn(vx, fvv));
+                    nadd(s[2], __dmul_rn(vy, fvv));
+                    nadd(s[3], __dmul_rn(__dadd_rn(__dmul_rn(vx, vx), __dmul_rn(vy, vy)), fvv));
+                }
+            }
+            const double m0 = nval(s[0]);
+            if (rho) rho[c] = m0 * dv * dv;
+            if (mv) {
+                mv[c] = m0 != 0.0 ? nval(s[1]) / m0 : 0.0;
+                mv[ncell + c] = m0 != 0.0 ? nval(s[2]) / m0 : 0.0;
+            }
+            if (mv2) mv2[c] = m0 != 0.0 ? nval(s[3]) / m0 : 0.0;
+            for (int q = 0; q < 4; ++q) nmerge(t[q], s[q]);
+        }
+        for (int q = 0; q < 4; ++q) warp_reduce(t[q]);
+        if (lane == 0)
+            for (int q = 0; q < 4; ++q) {
+                p[2 * q] = t[q].s;
+                p[2 * q + 1] = t[q].c;
+            }
+    } else {
+        FComp t[4];
+        for (long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x; c < ncell;
+             c += (long long)gridDim.x * blockDim.x) {
+            FComp s[4];
+            const float* sc_c = scales ? scales + c / nx : nullptr;  // this cell's x line
+            for (int jy = 0; jy < nv; ++jy) {
+                const float fy = (float)(jy - J);
+#pragma unroll 4
+                for (int jx = 0; jx < nv; ++jx) {
+                    const float fx = (float)(jx - J);
+                    const size_t plane = (size_t)jy * nv + jx;
+                    float fvv = (float)f[plane * ncell + c];
+                    if (sc_c) fvv = fvv * sc_c[plane * ny];  // exact: powers of two
+                    bad |= !isfinite(fvv);
+                    s[0].add(fvv);
+                    s[1].add(fx * fvv);
+                    s[2].add(fy * fvv);
+                    s[3].add((fx * fx + fy * fy) * fvv);
+                }
+            }
+            const double m0 = nval(s[0].to_comp(1.0));
+            if (rho) rho[c] = m0 * dv2;
+            if (mv) {
+                mv[c] = m0 != 0.0 ? nval(s[1].to_comp(dv)) / m0 : 0.0;
+                mv[ncell + c] = m0 != 0.0 ? nval(s[2].to_comp(dv)) / m0 : 0.0;
+            }
+            if (mv2) mv2[c] = m0 != 0.0 ? nval(s[3].to_comp(dv2)) / m0 : 0.0;
+            for (int q = 0; q < 4; ++q) t[q].merge(s[q]);
+        }
+        for (int q = 0; q < 4; ++q) warp_reduce(t[q]);
+        if (lane == 0) {
+            const double sc[4] = {1.0, dv, dv, dv2};
+            for (int q = 0; q < 4; ++q) {
+                const Comp cq = t[q].to_comp(sc[q]);
+                p[2 * q] = cq.s;
+                p[2 * q + 1] = cq.c;
             }
         }
-        const double m0 = nval(s[0]);
-        if (rho) rho[c] = m0 * dv * dv;
-        if (mv) {
-            mv[c] = m0 != 0.0 ? nval(s[1]) / m0 : 0.0;
-            mv[ncell + c] = m0 != 0.0 ? nval(s[2]) / m0 : 0.0;
-        }
-        if (mv2) mv2[c] = m0 != 0.0 ? nval(s[3]) / m0 : 0.0;
-        for (int q = 0; q < 4; ++q) nmerge(t[q], s[q]);
     }
     if (bad) atomicOr(&st->status, ST_NUMERIC);
-    for (int off = 16; off > 0; off >>= 1)
-        for (int q = 0; q < 4; ++q) {
-            Comp o{__shfl_down_sync(0xffffffffu, t[q].s, off),
-                   __shfl_down_sync(0xffffffffu, t[q].c, off)};
-            nmerge(t[q], o);
-        }
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    if (lane == 0)
-        for (int q = 0; q < 4; ++q) red[q][warp] = t[q];
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        Comp z[4] = {{0, 0}, {0, 0}, {0, 0}, {0, 0}};
-        for (int w = 0; w < (int)(blockDim.x >> 5); ++w)
-            for (int q = 0; q < 4; ++q) nmerge(z[q], red[q][w]);
-        for (int q = 0; q < 4; ++q) {
-            partials[(size_t)blockIdx.x * 8 + 2 * q] = z[q].s;
-            partials[(size_t)blockIdx.x * 8 + 2 * q + 1] = z[q].c;
-        }
-    }
 }
 
-__global__ void k_finalize2d(const double* partials, int nblocks, double w, double* glob) {
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+// One warp folds the per-warp partials: lane l takes partials l, l + 32, ..., then a butterfly.
+__global__ void k_finalize2d(const double* partials, int npart, double w, double* glob) {
+    if (blockIdx.x != 0 || threadIdx.x >= 32) return;
+    const int lane = threadIdx.x;
     Comp t[4] = {{0, 0}, {0, 0}, {0, 0}, {0, 0}};
-    for (int b = 0; b < nblocks; ++b)
+    for (int b = lane; b < npart; b += 32)
         for (int q = 0; q < 4; ++q) nmerge(t[q], Comp{partials[b * 8 + 2 * q], partials[b * 8 + 2 * q + 1]});
-    for (int q = 0; q < 4; ++q) glob[q] = nval(t[q]) * w;
+    for (int q = 0; q < 4; ++q) warp_reduce(t[q]);
+    if (lane == 0)
+        for (int q = 0; q < 4; ++q) glob[q] = nval(t[q]) * w;
 }
 
 __global__ void k_set_noise2d(DevState* st, long long base, long long rows) {
@@ -1149,8 +1177,8 @@ int ctx2d_create(Ctx2D** out, const lat_grid* g, DevState* st, int sm_count, cud
     c->chunks = chunks_supported(c->nv, 3) ? 3 : 1;
     c->pcv = c->ring && pc_supported(c->nv) ? 4 : 0;
     const long long ncell = (long long)c->nx * c->ny;
-    c->mom_blocks = (int)std::min<long long>((ncell + 255) / 256, 4LL * sm_count);
-    if (cudaMalloc(&c->d_partials, sizeof(double) * 8 * c->mom_blocks) != cudaSuccess ||
+    c->mom_blocks = (int)std::min<long long>((ncell + 255) / 256, 8LL * sm_count);
+    if (cudaMalloc(&c->d_partials, sizeof(double) * 8 * kMom2DWarps * c->mom_blocks) != cudaSuccess ||
         cudaMalloc(&c->d_glob, sizeof(double) * 4) != cudaSuccess ||
         cudaMallocHost(&c->h_glob, sizeof(double) * 4) != cudaSuccess) {
         ctx2d_destroy(c);
@@ -1282,14 +1310,14 @@ int ctx2d_step(Ctx2D* c, void* const f[2], int n, cudaStream_t s) {
 int ctx2d_moments(Ctx2D* c, const void* f, double* rho, double* mean_v, double* mean_v2,
                   double* globals, cudaStream_t s) {
     if (c->dtype == LAT_F64)
-        k_moments2d<double><<<c->mom_blocks, 256, 0, s>>>(f, nullptr, c->nv, c->nx, c->ny, c->dv,
+        k_moments2d<double><<<c->mom_blocks, 32 * kMom2DWarps, 0, s>>>(f, nullptr, c->nv, c->nx, c->ny, c->dv,
                                                          rho, mean_v, mean_v2, c->d_partials, c->st);
     else
-        k_moments2d<float><<<c->mom_blocks, 256, 0, s>>>(f, nullptr, c->nv, c->nx, c->ny, c->dv,
+        k_moments2d<float><<<c->mom_blocks, 32 * kMom2DWarps, 0, s>>>(f, nullptr, c->nv, c->nx, c->ny, c->dv,
                                                         rho, mean_v, mean_v2, c->d_partials, c->st);
     CK2(cudaGetLastError());
-    k_finalize2d<<<1, 32, 0, s>>>(c->d_partials, c->mom_blocks, c->dx * c->dx * c->dv * c->dv,
-                                  c->d_glob);
+    k_finalize2d<<<1, 32, 0, s>>>(c->d_partials, c->mom_blocks * kMom2DWarps,
+                                  c->dx * c->dx * c->dv * c->dv, c->d_glob);
     CK2(cudaGetLastError());
     if (globals) {
         CK2(cudaMemcpyAsync(c->h_glob, c->d_glob, sizeof(double) * 4, cudaMemcpyDeviceToHost, s));

@@ -55,6 +55,7 @@ def _load():
         "lat_step": (c_int, [P, c_int]),
         "lat_prepare": (c_int, [P, c_int]),
         "lat_moments": (c_int, [P, P, P, P, POINTER(c_double)]),
+        "lat_step_moments": (c_int, [P, c_int, P, P, P, POINTER(c_double)]),
         "lat_status": (c_int, [P]),
         "lat_current": (c_int, [P]),
         "lat_steps_done": (c_longlong, [P]),
@@ -266,6 +267,20 @@ class Ensemble(_Ctx):
         mv2 = torch.empty(ncell, dtype=torch.float64, device=dev) if per_cell else None
         glob = globals_out if globals_out is not None else np.zeros((self.n, 3))
         code = _lib.lat_moments(self._h, _ptr(rho), _ptr(mv), _ptr(mv2), _dptr(glob))
+        return code, rho, mv, mv2, glob
+
+    def step_moments(self, n: int = 1, per_cell: bool = False,
+                     globals_out: np.ndarray | None = None):
+        """n steps, then the moments of the new state (fused into the last step when the
+        producer/consumer kernel runs)."""
+        ncell = int(self.xoff[-1])
+        dev = self.f[0].device
+        rho = torch.empty(ncell, dtype=torch.float64, device=dev) if per_cell else None
+        mv = torch.empty(ncell, dtype=torch.float64, device=dev) if per_cell else None
+        mv2 = torch.empty(ncell, dtype=torch.float64, device=dev) if per_cell else None
+        glob = globals_out if globals_out is not None else np.zeros((self.n, 3))
+        code = _lib.lat_step_moments(self._h, int(n), _ptr(rho), _ptr(mv), _ptr(mv2),
+                                     _dptr(glob))
         return code, rho, mv, mv2, glob
 
 

@@ -159,3 +159,24 @@ def test_full_size_ensemble_sampled(lat):
     assert code == 0
     np.testing.assert_allclose(glob[:, 0], 1.0, rtol=1e-5)
     ens.close()
+
+
+@pytest.mark.parametrize("kernel", [5, 1])
+def test_step_moments_fused_matches_separate_calls(lat, kernel):
+    """lat_step_moments (moments fused into the last step of the producer/consumer kernel, or
+    the two calls otherwise) equals lat_step + lat_moments: per-cell moments bit for bit, the
+    globals to the rounding order of the compensated sums."""
+    nv, nsteps = 65, 6
+    tab = I.ensemble_table(40, 12, nv=nv, sizes=(1024, 2048, 4096))
+    fl = I.flow1d_inputs(83, nsteps, n_inst=40)
+    a, _ = build(lat, tab, nv, torch.float32, fl, launch=dict(kernel=kernel))
+    b, _ = build(lat, tab, nv, torch.float32, fl, launch=dict(kernel=kernel))
+    a.step(nsteps)
+    ca, ra, ma, m2a, ga = a.moments(per_cell=True)
+    cb, rb, mb, m2b, gb = b.step_moments(nsteps, per_cell=True)
+    assert ca == 0 and cb == 0
+    assert np.array_equal(a.state.cpu().numpy(), b.state.cpu().numpy())
+    assert torch.equal(ra, rb) and torch.equal(ma, mb) and torch.equal(m2a, m2b)
+    np.testing.assert_allclose(gb, ga, rtol=1e-14, atol=1e-18)
+    a.close()
+    b.close()
