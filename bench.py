@@ -48,7 +48,7 @@ def parse():
     p.add_argument("--no-autotune", action="store_true")
     p.add_argument("--no-per-instance", action="store_true")
     p.add_argument("--no-forms", action="store_true")
-    p.add_argument("--workload", default="ensemble", choices=["ensemble", "2d"])
+    p.add_argument("--workload", default="ensemble", choices=["ensemble", "2d", "2d_f16", "2d_bf16"])
     p.add_argument("--launch", default=None,
                    help="kernel,block,blocks_per_sm instead of autotuning (profiling runs)")
     return p.parse_args()
@@ -233,6 +233,9 @@ def run_reference(args):
 # ---------------------------------------------------------------------------------------------
 WORKLOAD_2D = ("2D FP32: periodic 512x512 grid, 33x33 velocity lattice (2.85e8 cells), St=1, "
                "kappa=1e-3, incompressible random-phase flow |k|<=8, k^-3 spectrum, OU phases")
+WORKLOAD_2D_16 = ("2D {fmt} storage (per x-line power-of-two scales, FP32 arithmetic): periodic "
+                  "{n}x{n} grid, {nv}x{nv} velocity lattice, St=1, kappa=1e-3, incompressible "
+                  "random-phase flow |k|<=8, k^-3 spectrum, OU phases")
 
 
 def build_ensemble(args, I, lat, torch, dev, rank, nsteps):
@@ -250,7 +253,9 @@ def build_ensemble(args, I, lat, torch, dev, rank, nsteps):
     return ens, cells, fl.noise[:1], np.zeros((n_inst, 3)), desc
 
 
-def build_2d(args, I, lat, torch, dev, rank, nsteps, n=512, nv=33):
+def build_2d(args, I, lat, torch, dev, rank, nsteps, n=512, nv=33, store="f32"):
+    """2D lattice, St = 1, kappa = 1e-3, Gaussian velocity start (sigma = 0.2 V_max), uniform in
+    space, random-phase flow; store = f32, or f16 / bf16 (encoded from the FP32 start)."""
     L = 2 * math.pi
     tau_p, kappa = L, 1e-3
     dt = I.choose_dt(2, n, L, nv, tau_p, kappa)
@@ -260,10 +265,19 @@ def build_2d(args, I, lat, torch, dev, rank, nsteps, n=512, nv=33):
     col2 = torch.tensor(np.outer(col, col) / (n * n), dtype=torch.float32, device=dev)
     f0 = col2[:, :, None, None].expand(nv, nv, n, n).contiguous()
     fl = I.flow2d_inputs(SEED + 11 + rank, nsteps, n, n, dx)
-    lt = lat.Lattice(f0, d=2, nx=n, ny=n, nv=nv, L=L, tau_p=tau_p, kappa=kappa, dt=dt)
+    if store == "f32":
+        lt = lat.Lattice(f0, d=2, nx=n, ny=n, nv=nv, L=L, tau_p=tau_p, kappa=kappa, dt=dt)
+        desc = WORKLOAD_2D
+    else:
+        tdt = torch.float16 if store == "f16" else torch.bfloat16
+        buf = torch.zeros(f0.shape, dtype=tdt, device=dev)
+        lt = lat.Lattice(buf, d=2, nx=n, ny=n, nv=nv, L=L, tau_p=tau_p, kappa=kappa, dt=dt)
+        lt.encode(f0)
+        desc = WORKLOAD_2D_16.format(fmt=store.upper(), n=n, nv=nv)
+    del f0
     lt.set_flow_modes_2d(fl.kvec, fl.a, fl.phi0, fl.tau_f)
     lt.set_noise(fl.noise)
-    return lt, n * n * nv * nv, fl.noise[:1], np.zeros(4), WORKLOAD_2D
+    return lt, n * n * nv * nv, fl.noise[:1], np.zeros(4), desc
 
 
 def timed(ctx, K, W, torch, dist, world, local, dev):
@@ -308,6 +322,10 @@ def end_to_end(ctx, noise_row, glob, steps, torch):
 
 def kernel_label(workload, best, nv):
     k = best["kernel"] if best else 0
+    if workload in ("2d_f16", "2d_bf16"):
+        t = "__half" if workload == "2d_f16" else "__nv_bfloat16"
+        return (f"k_step2d_pch<{t},{nv},{4 if k == 4 else 3}>" if k >= 4
+                else f"k_step2d_plain_h<{t},{nv}>")
     if workload == "2d":
         if k >= 3:
             return {3: f"k_step2d_pc<{nv},4,false>", 4: f"k_step2d_pc<{nv},4,true>",
@@ -341,10 +359,20 @@ def main():
     K, W = args.steps, args.warmup
     K_e2e = max(3, min(K, 50))
     nsteps = W + K + K_e2e + 2
+    bytes_per_cell, lines = 8, 0
     if args.workload == "2d":
         ctx, cells, noise_row, glob, desc = build_2d(args, I, lat, torch, dev, rank, nsteps)
         nv, prof, src = 33, "step2d_512_fp32_nv33.md", "paper_1508_02899_gb300/csrc/step2d.cu"
         launches_per_step = 2  # flow evaluation + fused step
+    elif args.workload in ("2d_f16", "2d_bf16"):
+        store = args.workload[3:]
+        ctx, cells, noise_row, glob, desc = build_2d(args, I, lat, torch, dev, rank, nsteps,
+                                                     n=1024, store=store)
+        nv = 33
+        prof = f"step2d_1024_{store}_nv33.md"
+        src = "paper_1508_02899_gb300/csrc/step2d_h.cu"
+        launches_per_step = 3  # flow evaluation + output scales + fused step
+        bytes_per_cell, lines = 4, nv * nv * 1024
     else:
         ctx, cells, noise_row, glob, desc = build_ensemble(args, I, lat, torch, dev, rank, nsteps)
         nv, prof, src = NV, "step1d_ensemble_fp32_nv65.md", "paper_1508_02899_gb300/csrc/step1d.cu"
@@ -377,7 +405,9 @@ def main():
     e2e_value = world * cells * K_e2e / e2e_s / 1e9
 
     peak, peak_src = measured_peaks()
-    bytes_per_launch = cells * 8  # one FP32 read and one FP32 write of every cell
+    # one read and one write of every cell; 16-bit storage adds per line its input scale, its
+    # output scale and its recorded maximum (4 bytes each)
+    bytes_per_launch = cells * bytes_per_cell + lines * 12
     achieved = bytes_per_launch / (ms_max / K / 1e3) / 1e9
     tr = profile_traffic(prof, src)
     traffic = None
@@ -400,6 +430,20 @@ def main():
         lt.close()
         del lt
         torch.cuda.empty_cache()
+        for store in ("f16", "bf16"):
+            lt, c2, *_ = build_2d(args, I, lat, torch, dev, rank, 2 * 40 + 4, n=1024,
+                                  store=store)
+            b2 = lt.autotune(reps=3)
+            ms2, _ = timed(lt, 40, 3, torch, dist, world, local, dev)
+            st2 = lt.status()
+            g2 = c2 * 40 / (ms2 / 1e3) / 1e9
+            forms[f"2d_{store}_1024x1024_33x33"] = {
+                "gcups": g2, "ms_per_step": ms2 / 40,
+                "hbm_frac": (g2 * 4 + g2 / 1024 * 12) / peak,
+                "kernel": kernel_label(f"2d_{store}", b2, 33), "steps": 40, "status": st2}
+            lt.close()
+            del lt
+            torch.cuda.empty_cache()
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -412,7 +456,10 @@ def main():
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K,
             "warmup": W, "ms_per_step": ms_max / K, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": {"2d_f16": "f16 storage, f32 math", "2d_bf16": "bf16 storage, f32 math"}.get(
+                args.workload, "f32"),
+            "data": "synthetic",
             "config": {"workload": desc, "nv": nv, "cells_per_step_per_gpu": cells,
                        "l2": "inputs larger than L2 (FP32 ping-pong buffers of GBs); no flush",
                        "launch": best, "status": status},

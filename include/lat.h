@@ -162,6 +162,27 @@ int lat_status(lat_ctx* c);
 
 /* 0 if f_a holds the current state, 1 if f_b does. */
 int lat_current(const lat_ctx* c);
+/*
+ * Reduced-precision storage (d = 2, dtype LAT_F16 or LAT_BF16).  The paper computes in double
+ * precision; this storage form is this library's own (it halves the bytes a step moves).
+ * Values are stored as 16-bit numbers h with one power-of-two scale S per x-line (velocity plane
+ * (jx, jy) and row y): f = h * S.  The context owns the scales (two sets, one per buffer).
+ * Each step decodes f*, computes in FP32 exactly like the FP32 path, and encodes with output
+ * scales chosen from a bound of the step's growth (at most 3 times the largest input on the
+ * 13-cell velocity diamond) so that encoded values stay below 2^15; the rounding residual of
+ * every value is carried into the next value of the same cell's velocity column, so the stored
+ * mass of a cell equals its FP32 mass up to one residual of the corner velocity cell.  A value
+ * that still leaves the format's range (the CFL condition broken) raises LAT_EOVERFLOW.
+ * The caller's f_a is taken at lat_init as 16-bit values with scale 1; lat_encode replaces the
+ * current state.  FIELD flows are float arrays.
+ */
+/* Encode the FP32 DEVICE array src (layout of f, N_v^2 N_y N_x floats, caller-owned) into the
+ * current buffer with fresh scales: S = 2^(ilogb(line max) - 12), residuals carried along each
+ * cell's velocity column in (jy, jx) order.  Synchronises; LAT_EINVAL for other contexts. */
+int lat_encode(lat_ctx* c, const float* src);
+/* Decode the current state into the FP32 DEVICE array dst (may be NULL) and copy its line
+ * scales, [jy][jx][y] floats, to the DEVICE array scales (may be NULL).  Synchronises. */
+int lat_decode(lat_ctx* c, float* dst, float* scales);
 
 /* Steps taken since init. */
 long long lat_steps_done(const lat_ctx* c);
@@ -176,6 +197,8 @@ long long lat_steps_done(const lat_ctx* c);
  *                 cell's jx range over C = 1..4 warp groups);
  *                 3..5 producer warp + consumer warps (3: vy-flux row in registers, 4 slots;
  *                 4: in shared memory, 4 slots; 5: in shared memory, 3 slots).
+ *          d = 2 with 16-bit storage: 1 plain loads (any size); 4 and 5 as above (N_x a
+ *                 multiple of 8 and >= 136, N_v >= 9).
  *  block:  threads per block (= x cells per tile) for kernel 1; the copy pipelines fix a 128-cell
  *          tile (2D kernel 2: 128 C threads); 0 keeps.
  *  blocks_per_sm: resident blocks per SM of the persistent grid; 0 keeps.

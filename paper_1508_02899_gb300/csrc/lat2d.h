@@ -13,8 +13,13 @@ int ctx2d_set_noise(Ctx2D* c, const double* noise, long long rows, long long ste
                     cudaStream_t s);
 int ctx2d_step(Ctx2D* c, void* const f[2], int n, cudaStream_t s);
 int ctx2d_prepare(Ctx2D* c, void* const f[2], int n);
-int ctx2d_moments(Ctx2D* c, const void* f, double* rho, double* mean_v, double* mean_v2,
-                  double* globals, cudaStream_t s);
+int ctx2d_moments(Ctx2D* c, const void* f, int cur, double* rho, double* mean_v,
+                  double* mean_v2, double* globals, cudaStream_t s);
+// 16-bit storage: line maxima of the caller's initial state (scales 1), encoding of an FP32
+// state into the current buffer, decoding of the current buffer (dst and/or its line scales).
+int ctx2d_init_state(Ctx2D* c, void* const f[2], int cur, cudaStream_t s);
+int ctx2d_encode(Ctx2D* c, const float* src, void* const f[2], int cur, cudaStream_t s);
+int ctx2d_decode(Ctx2D* c, void* const f[2], int cur, float* dst, float* scales, cudaStream_t s);
 int ctx2d_set_launch(Ctx2D* c, int kernel, int block, int bps, int mode);
 int ctx2d_autotune(Ctx2D* c, void* const f[2], int reps, double* best, cudaStream_t s);
 void ctx2d_destroy(Ctx2D* c);

@@ -333,6 +333,7 @@ int lat_init(lat_ctx** out, const lat_grid* g, void* f_a, void* f_b, void* strea
     c->f[1] = f_b;
     int rc = alloc_common(c);
     if (rc == LAT_OK) rc = ctx2d_create(&c->c2, g, c->d_state, c->sm_count, c->stream);
+    if (rc == LAT_OK) rc = ctx2d_init_state(c->c2, c->f, c->cur, c->stream);
     if (rc != LAT_OK) {
         lat_free(c);
         return rc;
@@ -505,7 +506,8 @@ int lat_status(lat_ctx* c) {
 int lat_moments(lat_ctx* c, double* rho, double* mean_v, double* mean_v2, double* globals) {
     if (!c) return LAT_EINVAL;
     if (c->d == 2) {
-        int rc = ctx2d_moments(c->c2, c->f[c->cur], rho, mean_v, mean_v2, globals, c->stream);
+        int rc = ctx2d_moments(c->c2, c->f[c->cur], c->cur, rho, mean_v, mean_v2, globals,
+                               c->stream);
         if (rc != LAT_OK) return rc;
         return lat_status(c);
     }
@@ -567,6 +569,22 @@ int lat_step_moments(lat_ctx* c, int n, double* rho, double* mean_v, double* mea
 }
 
 int lat_current(const lat_ctx* c) { return c ? c->cur : -1; }
+
+int lat_encode(lat_ctx* c, const float* src) {
+    if (!c || !src || c->d != 2 || (c->dtype != LAT_F16 && c->dtype != LAT_BF16))
+        return LAT_EINVAL;
+    int rc = ctx2d_encode(c->c2, src, c->f, c->cur, c->stream);
+    if (rc != LAT_OK) return rc;
+    return lat_status(c);
+}
+
+int lat_decode(lat_ctx* c, float* dst, float* scales) {
+    if (!c || (!dst && !scales) || c->d != 2 || (c->dtype != LAT_F16 && c->dtype != LAT_BF16))
+        return LAT_EINVAL;
+    int rc = ctx2d_decode(c->c2, c->f, c->cur, dst, scales, c->stream);
+    if (rc != LAT_OK) return rc;
+    return lat_status(c);
+}
 
 long long lat_steps_done(const lat_ctx* c) { return c ? c->h_step : -1; }
 

@@ -13,6 +13,8 @@
 // the copy's source address (x window rounded down to 16 bytes, split in two at the periodic
 // wrap; y wraps by choosing the source row).  A plain-load variant with the same arithmetic
 // serves FP64 and grids the copy path does not cover (N_x not a multiple of 4, or < 132).
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <math.h>
 #include <stdint.h>
 #include <stdio.h>
@@ -24,28 +26,22 @@
 #include <map>
 
 #include "lat2d.h"
+#include "step2d_dev.h"
+#include "step2d_h.h"
 #include "lat_reduce.h"
 
 namespace lat {
 
 namespace {
 
-constexpr int TW = 128;       // cells per tile (= threads per block)
+using namespace k2d;
+
 constexpr int WIN = TW + 4;   // floats copied per plane row (x window rounded to 16 bytes)
 #ifndef LAT_RING2D_SLOTS
 #define LAT_RING2D_SLOTS 4
 #endif
 constexpr int NSLOT = LAT_RING2D_SLOTS;  // ring slots of f* rows
 constexpr int LOOK = NSLOT - 2;          // rows in flight ahead of the one being waited for
-
-struct Step2DArgs {
-    void* f[2];
-    int nx, ny;
-    double g, r, inv_dv;
-    const void* u;            // [2][ny][nx] of T, or null for u = 0
-    DevState* st;
-    int ntx, ntiles;
-};
 
 struct Flow2DArgs {
     const int2* k;            // [M] (kx, ky)
@@ -62,182 +58,6 @@ struct Flow2DArgs {
     DevState* st;
     int frozen, dry;
 };
-
-// ---- PTX helpers (mbarrier + bulk async copy) ----------------------------------------------
-__device__ __forceinline__ unsigned smem_u32(const void* p) {
-    return (unsigned)__cvta_generic_to_shared(p);
-}
-__device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count)
-                 : "memory");
-}
-__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, unsigned bytes) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
-                 "r"(bytes)
-                 : "memory");
-}
-__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, unsigned parity) {
-    unsigned ok;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}"
-        : "=r"(ok)
-        : "r"(smem_u32(bar)), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
-__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned bytes,
-                                         uint64_t* bar) {
-    asm volatile(
-        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
-        ::"r"(smem_u32(dst)), "l"(src), "r"(bytes), "r"(smem_u32(bar))
-        : "memory");
-}
-__device__ __forceinline__ unsigned long long globaltimer() {
-    unsigned long long t;
-    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-    return t;
-}
-// Bounded wait on an mbarrier phase: gives up after ~1 s (then the caller raises ST_TIMEOUT).
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, unsigned parity) {
-    if (mbar_try_wait(bar, parity)) return true;
-    const unsigned long long t0 = globaltimer();
-    for (long long it = 0; it < (1ll << 26); ++it) {
-        if (mbar_try_wait(bar, parity)) return true;
-        if ((it & 255) == 0 && globaltimer() - t0 > 1000000000ull) break;
-    }
-    return false;
-}
-
-__device__ __forceinline__ int wrap(int v, int n) {
-    v %= n;
-    return v < 0 ? v + n : v;
-}
-
-// ---- the row sweep shared by both kernels ---------------------------------------------------
-// Processes velocity row index r (0..NV): computes f** of row r-1 (needs f* rows r-1 and r, the
-// latter absent when r == NV) and, for r >= 2, writes the output row r-2.
-// Column arithmetic with explicit rounding, so that every variant gives the same bits.
-template <typename T>
-struct Ops;
-template <>
-struct Ops<float> {
-    static __device__ __forceinline__ float mul(float a, float b) { return __fmul_rn(a, b); }
-    static __device__ __forceinline__ float sub(float a, float b) { return __fsub_rn(a, b); }
-    static __device__ __forceinline__ float add(float a, float b) { return __fadd_rn(a, b); }
-    static __device__ __forceinline__ float fma(float a, float b, float c) { return __fmaf_rn(a, b, c); }
-};
-template <>
-struct Ops<double> {
-    static __device__ __forceinline__ double mul(double a, double b) { return __dmul_rn(a, b); }
-    static __device__ __forceinline__ double sub(double a, double b) { return __dsub_rn(a, b); }
-    static __device__ __forceinline__ double add(double a, double b) { return __dadd_rn(a, b); }
-    static __device__ __forceinline__ double fma(double a, double b, double c) { return __fma_rn(a, b, c); }
-};
-// c a_j = g (w - j);  c F_{j+1/2} = (c a_j)^+ f_j + (c a_{j+1})^- f_{j+1}
-template <typename T>
-__device__ __forceinline__ T cacc(T g, T w, int j) { return Ops<T>::mul(g, Ops<T>::sub(w, T(j))); }
-template <typename T>
-__device__ __forceinline__ T dflux(T caj, T can, T fj, T fn) {
-    return Ops<T>::fma(fmax(caj, T(0)), fj, Ops<T>::mul(fmin(can, T(0)), fn));
-}
-
-// Processes velocity row index r (1..NV): computes f** of row rb = r-1 from f* rows rb (cur) and
-// r (nxt, absent when r == NV) and, for r >= 2, writes output row r-2.
-//   f**_{jx} = f*_{jx} - (cFx_{jx+1/2} - cFx_{jx-1/2}) - (cFy_{rb+1/2} - cFy_{rb-1/2})
-//   out      = f** + (Dx_{jx+1/2} - Dx_{jx-1/2}) + (Dy_{+1/2} - Dy_{-1/2}),  D = r (f**_+ - f**)
-// Opaque copy: keeps the compiler from hoisting per-jx invariants (drag coefficients, store
-// offsets) out of the row loop into NV live registers each.
-__device__ __forceinline__ float opaque(float v) {
-    float r;
-    asm volatile("mov.b32 %0, %1;" : "=f"(r) : "f"(v));
-    return r;
-}
-__device__ __forceinline__ double opaque(double v) {
-    double r;
-    asm volatile("mov.b64 %0, %1;" : "=d"(r) : "d"(v));
-    return r;
-}
-
-template <typename T, int NV, class Row, class GArr>
-__device__ __forceinline__ void sweep_row(T (&A)[NV], GArr& G, T (&H)[NV], int r,
-                                          const Row& cur, const Row& nxt_row, T g_in, T wx_in,
-                                          T wy, T rr, T* __restrict__ out, size_t pstride,
-                                          bool active) {
-    using O = Ops<T>;
-    constexpr int J = (NV - 1) / 2;
-    const int rb = r - 1;
-    const bool nxt = r < NV;
-    const T g = opaque(g_in), wx = opaque(wx_in);
-    const T ayp = fmax(cacc<T>(g, wy, rb - J), T(0));
-    const T aym = nxt ? fmin(cacc<T>(g, wy, r - J), T(0)) : T(0);
-    T Fprev = T(0), Dprev = T(0);
-    T sc = cur.get(0);
-    T* o_ptr = out + (size_t)(r >= 2 ? r - 2 : 0) * NV * pstride;
-#pragma unroll
-    for (int jx = 0; jx < NV; ++jx) {
-        T sn = T(0), Fnext = T(0);
-        if (jx < NV - 1) {
-            sn = cur.get(jx + 1);
-            Fnext = dflux<T>(cacc<T>(g, wx, jx - J), cacc<T>(g, wx, jx + 1 - J), sc, sn);
-        }
-        const T Gn = nxt ? O::fma(ayp, sc, O::mul(aym, nxt_row.get(jx))) : T(0);
-        const T b = O::sub(O::sub(sc, O::sub(Fnext, Fprev)), O::sub(Gn, G[jx]));
-        G[jx] = Gn;
-        Fprev = Fnext;
-        sc = sn;
-        if (r >= 2) {
-            const T a = A[jx];
-            const T Dn = (jx < NV - 1) ? O::mul(rr, O::sub(A[jx + 1], a)) : T(0);
-            const T Hn = O::mul(rr, O::sub(b, a));
-            const T o = O::add(O::add(a, O::sub(Dn, Dprev)), O::sub(Hn, H[jx]));
-            H[jx] = Hn;
-            Dprev = Dn;
-            if (active) *o_ptr = o;
-            o_ptr += pstride;
-        }
-        A[jx] = b;
-    }
-}
-
-// Last output row (jy = J): no f** row above it, so the vy-diffusion flux there is zero.
-template <typename T, int NV>
-__device__ __forceinline__ void final_row(T (&A)[NV], T (&H)[NV], T rr, T* __restrict__ out,
-                                          size_t pstride, bool active) {
-    using O = Ops<T>;
-    T Dprev = T(0);
-    T* o_ptr = out + (size_t)(NV - 1) * NV * pstride;
-#pragma unroll
-    for (int jx = 0; jx < NV; ++jx) {
-        const T a = A[jx];
-        const T Dn = (jx < NV - 1) ? O::mul(rr, O::sub(A[jx + 1], a)) : T(0);
-        const T o = O::add(O::add(a, O::sub(Dn, Dprev)), O::sub(T(0), H[jx]));
-        Dprev = Dn;
-        if (active) *o_ptr = o;
-        o_ptr += pstride;
-    }
-}
-
-template <typename T>
-__device__ __forceinline__ void load_w(const Step2DArgs& a, int x, int y, T& wx, T& wy) {
-    if (a.u) {
-        const T* u = static_cast<const T*>(a.u);
-        const size_t c = (size_t)y * a.nx + x;
-        wx = u[c] * T(a.inv_dv);
-        wy = u[(size_t)a.nx * a.ny + c] * T(a.inv_dv);
-    } else {
-        wx = T(0);
-        wy = T(0);
-    }
-}
-
-template <typename T, int NV>
-__device__ __forceinline__ void cfl_check(const Step2DArgs& a, T g, T wx, T wy, bool active) {
-    constexpr int J = (NV - 1) / 2;
-    if (active && g * (T(J) + fabs(wx)) + g * (T(J) + fabs(wy)) > T(1))
-        atomicOr(&a.st->status, ST_CFL);
-}
 
 // ---- plain-load kernel (any N_x, N_y; FP32 or FP64) -----------------------------------------
 // Row jy of f* at one cell, read straight from global memory (periodic wrap in x and y).
@@ -281,13 +101,13 @@ __global__ void __launch_bounds__(TW) k_step2d_plain(const Step2DArgs a, int kst
             G[j] = T(0);
             H[j] = T(0);
         }
-        T* out = fout + (size_t)y * a.nx + x;
+        StorePut<T, NV> put(fout + (size_t)y * a.nx + x, ps, active);
         for (int r = 1; r <= NV; ++r) {
             const GlobalRow<T, NV> cur(fin, r - 1, x, y, a.nx, a.ny);
             const GlobalRow<T, NV> nxt(fin, r < NV ? r : r - 1, x, y, a.nx, a.ny);
-            sweep_row<T, NV>(A, G, H, r, cur, nxt, g, wx, wy, rr, out, ps, active);
+            sweep_row<T, NV>(A, G, H, r, cur, nxt, g, wx, wy, rr, put);
         }
-        final_row<T, NV>(A, H, rr, out, ps, active);
+        final_row<T, NV>(A, H, rr, put);
     }
 }
 
@@ -555,15 +375,6 @@ __global__ void __launch_bounds__(RingShape<NV, C>::threads, RingShape<NV, C>::m
 // per-slot "full" mbarrier the bulk copies complete.  Warps drift freely within the ring's slack.
 // With GSM the vy-drag flux row G lives in shared memory (private per thread) instead of
 // registers, which lowers register pressure and raises occupancy.
-__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
-    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
-}
-
-struct SmemCol {  // one thread's column in a [NV][TW] shared array
-    float* p;
-    __device__ __forceinline__ float& operator[](int j) const { return p[j * TW]; }
-};
-
 template <int NV, int NS, bool GSM>
 struct PCShape {
     static constexpr int consumers = TW / 32;
@@ -641,7 +452,7 @@ __global__ void __launch_bounds__(PCShape<NV, NS, GSM>::threads, PCShape<NV, NS,
             if (GSM) Gs[j] = 0.f;
             else Greg[j] = 0.f;
         }
-        float* out = fout + (size_t)y * a.nx + x;
+        StorePut<float, NV> put(fout + (size_t)y * a.nx + x, ps, active);
         const long long s0 = (long long)lt * NV;
         for (int r = 0; r <= NV; ++r) {
             const long long s = s0 + r;
@@ -652,13 +463,13 @@ __global__ void __launch_bounds__(PCShape<NV, NS, GSM>::threads, PCShape<NV, NS,
             if (r >= 1) {
                 const RingRow<NV> cur{ring + (size_t)((s - 1) % NS) * NV * WIN + cell};
                 const RingRow<NV> nxt{ring + (size_t)(s % NS) * NV * WIN + cell};
-                if (GSM) sweep_row<float, NV>(A, Gs, H, r, cur, nxt, g, wx, wy, rr, out, ps, active);
-                else sweep_row<float, NV>(A, Greg, H, r, cur, nxt, g, wx, wy, rr, out, ps, active);
+                if (GSM) sweep_row<float, NV>(A, Gs, H, r, cur, nxt, g, wx, wy, rr, put);
+                else sweep_row<float, NV>(A, Greg, H, r, cur, nxt, g, wx, wy, rr, put);
                 __syncwarp();
                 if (lane == 0) mbar_arrive(&empty[(s - 1) % NS]);  // row s - 1 is done
             }
         }
-        if (!failed) final_row<float, NV>(A, H, rr, out, ps, active);
+        if (!failed) final_row<float, NV>(A, H, rr, put);
     }
     if (failed && lane == 0) atomicOr(&a.st->status, ST_TIMEOUT);
 }
@@ -724,7 +535,7 @@ __device__ __forceinline__ double to_d(T v) { return (double)v; }
 constexpr int kMom2DWarps = 8;  // warps per moment block (256 threads)
 
 // Per cell: sums over the N_v^2 velocity cells of f, jx f, jy f, (jx^2 + jy^2) f; per-cell moments
-// and one compensated partial per warp: partials[block][warp][4][2].
+// and one compensated partial per block: partials[block][4][2] (warps fold in warp order).
 //   FP64 storage: Neumaier FP64 throughout.
 //   FP32 / FP16 / BF16 storage: FP32 Kahan sums per cell and across a thread's cells and the
 //   warp (exact integer weights); FP64 from the warp partials on (FP64 is slow on this GPU).
@@ -738,9 +549,9 @@ __global__ void __launch_bounds__(256) k_moments2d(const void* fv, const float* 
     const long long ncell = (long long)nx * ny;
     const double dv2 = __dmul_rn(dv, dv);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    double* p = partials + ((size_t)blockIdx.x * (blockDim.x >> 5) + warp) * 8;
+    double* p = partials + (size_t)blockIdx.x * 8;  // one partial per block
     bool bad = false;
-    if (sizeof(T) == sizeof(double)) {
+    if constexpr (sizeof(T) == sizeof(double)) {
         Comp t[4] = {{0, 0}, {0, 0}, {0, 0}, {0, 0}};
         for (long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x; c < ncell;
              c += (long long)gridDim.x * blockDim.x) {
@@ -768,17 +579,24 @@ __global__ void __launch_bounds__(256) k_moments2d(const void* fv, const float* 
             for (int q = 0; q < 4; ++q) nmerge(t[q], s[q]);
         }
         for (int q = 0; q < 4; ++q) warp_reduce(t[q]);
+        __shared__ Comp wsum[kMom2DWarps][4];
         if (lane == 0)
+            for (int q = 0; q < 4; ++q) wsum[warp][q] = t[q];
+        __syncthreads();
+        if (threadIdx.x == 0)
             for (int q = 0; q < 4; ++q) {
-                p[2 * q] = t[q].s;
-                p[2 * q + 1] = t[q].c;
+                Comp z = wsum[0][q];
+                for (int w = 1; w < kMom2DWarps; ++w) nmerge(z, wsum[w][q]);
+                p[2 * q] = z.s;
+                p[2 * q + 1] = z.c;
             }
     } else {
         FComp t[4];
         for (long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x; c < ncell;
              c += (long long)gridDim.x * blockDim.x) {
             FComp s[4];
-            const float* sc_c = scales ? scales + c / nx : nullptr;  // this cell's x line
+            // scales of this cell's row: [jy][jx padded]
+            const float* sc_c = scales ? scales + (size_t)(c / nx) * nv * nv_padded(nv) : nullptr;
             for (int jy = 0; jy < nv; ++jy) {
                 const float fy = (float)(jy - J);
 #pragma unroll 4
@@ -786,7 +604,7 @@ __global__ void __launch_bounds__(256) k_moments2d(const void* fv, const float* 
                     const float fx = (float)(jx - J);
                     const size_t plane = (size_t)jy * nv + jx;
                     float fvv = (float)f[plane * ncell + c];
-                    if (sc_c) fvv = fvv * sc_c[plane * ny];  // exact: powers of two
+                    if (sc_c) fvv = fvv * sc_c[jy * nv_padded(nv) + jx];  // exact: powers of two
                     bad |= !isfinite(fvv);
                     s[0].add(fvv);
                     s[1].add(fx * fvv);
@@ -804,10 +622,16 @@ __global__ void __launch_bounds__(256) k_moments2d(const void* fv, const float* 
             for (int q = 0; q < 4; ++q) t[q].merge(s[q]);
         }
         for (int q = 0; q < 4; ++q) warp_reduce(t[q]);
-        if (lane == 0) {
+        __shared__ FComp wsum[kMom2DWarps][4];
+        if (lane == 0)
+            for (int q = 0; q < 4; ++q) wsum[warp][q] = t[q];
+        __syncthreads();
+        if (threadIdx.x == 0) {
             const double sc[4] = {1.0, dv, dv, dv2};
             for (int q = 0; q < 4; ++q) {
-                const Comp cq = t[q].to_comp(sc[q]);
+                FComp z = wsum[0][q];
+                for (int w = 1; w < kMom2DWarps; ++w) z.merge(wsum[w][q]);
+                const Comp cq = z.to_comp(sc[q]);
                 p[2 * q] = cq.s;
                 p[2 * q + 1] = cq.c;
             }
@@ -816,16 +640,26 @@ __global__ void __launch_bounds__(256) k_moments2d(const void* fv, const float* 
     if (bad) atomicOr(&st->status, ST_NUMERIC);
 }
 
-// One warp folds the per-warp partials: lane l takes partials l, l + 32, ..., then a butterfly.
-__global__ void k_finalize2d(const double* partials, int npart, double w, double* glob) {
-    if (blockIdx.x != 0 || threadIdx.x >= 32) return;
-    const int lane = threadIdx.x;
+// One block of kFin2DThreads folds the block partials: thread i takes partials i, i + 256, ...,
+// then warp butterflies and warp 0 folds the warps in order.
+constexpr int kFin2DThreads = 256;
+__global__ void __launch_bounds__(kFin2DThreads)
+    k_finalize2d(const double* partials, int npart, double w, double* glob) {
+    __shared__ Comp wsum[kFin2DThreads / 32][4];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     Comp t[4] = {{0, 0}, {0, 0}, {0, 0}, {0, 0}};
-    for (int b = lane; b < npart; b += 32)
+    for (int b = threadIdx.x; b < npart; b += kFin2DThreads)
         for (int q = 0; q < 4; ++q) nmerge(t[q], Comp{partials[b * 8 + 2 * q], partials[b * 8 + 2 * q + 1]});
     for (int q = 0; q < 4; ++q) warp_reduce(t[q]);
     if (lane == 0)
-        for (int q = 0; q < 4; ++q) glob[q] = nval(t[q]) * w;
+        for (int q = 0; q < 4; ++q) wsum[warp][q] = t[q];
+    __syncthreads();
+    if (threadIdx.x == 0)
+        for (int q = 0; q < 4; ++q) {
+            Comp z = wsum[0][q];
+            for (int v = 1; v < kFin2DThreads / 32; ++v) nmerge(z, wsum[v][q]);
+            glob[q] = nval(z) * w;
+        }
 }
 
 __global__ void k_set_noise2d(DevState* st, long long base, long long rows) {
@@ -1026,6 +860,11 @@ struct Ctx2D {
     int pcv = 0;       // 0: ring kernel; 3..5: producer/consumer variant
     int bps = 0;       // 0 = occupancy limit
     int mode = 0;      // 0 graph, 2 direct launches
+    // reduced-precision storage: per-line scales and maxima, [2][N_v^2 N_y] each
+    bool half = false;
+    long long nlines = 0;  // scales (or maxima) per buffer, padded layout
+    float* d_sc = nullptr;
+    unsigned* d_mx = nullptr;
     // moments
     double* d_partials = nullptr;
     double* d_glob = nullptr;
@@ -1052,7 +891,20 @@ void drop(Ctx2D* c) {
 }
 
 bool ring_ok(const Ctx2D* c) {
+    if (c->half) return h2d_ring_ok(c->nx);
     return c->dtype == LAT_F32 && c->nx % 4 == 0 && c->nx >= WIN;
+}
+
+bool pc_ok(const Ctx2D* c) { return c->half ? c->nv >= 9 : pc_supported(c->nv); }
+
+Step2DHArgs half_args(const Ctx2D* c, const Step2DArgs& a) {
+    Step2DHArgs h;
+    h.b = a;
+    h.sc[0] = c->d_sc;
+    h.sc[1] = c->d_sc + c->nlines;
+    h.mx[0] = c->d_mx;
+    h.mx[1] = c->d_mx + c->nlines;
+    return h;
 }
 
 Step2DArgs step_args(const Ctx2D* c, void* const f[2]) {
@@ -1075,7 +927,8 @@ Step2DArgs step_args(const Ctx2D* c, void* const f[2]) {
 int grid_of(const Ctx2D* c, int ntiles) {
     int per_sm = c->bps;
     if (c->ring) {
-        const int occ = occupancy_ring(c->nv, c->chunks, c->pcv);
+        const int occ = c->half ? occupancy_step2d_h(c->dtype, c->nv, c->pcv)
+                                : occupancy_ring(c->nv, c->chunks, c->pcv);
         if (per_sm <= 0 || per_sm > occ) per_sm = std::max(1, occ);
     } else if (per_sm <= 0) {
         per_sm = 8;
@@ -1115,7 +968,13 @@ int enqueue2d(Ctx2D* c, void* const f[2], int n, cudaStream_t s, int dry) {
             else k_flow2d<float><<<fg, 256, sh, s>>>(fa, k);
             CK2(cudaGetLastError());
         }
-        CK2(launch_step2d(c->dtype, c->nv, c->ring, c->chunks, c->pcv, grid, a, k, s));
+        if (c->half) {
+            const Step2DHArgs ha = half_args(c, a);
+            CK2(launch_scale2d(c->nv, c->ny, ha, k, s));
+            CK2(launch_step2d_h(c->dtype, c->nv, c->ring ? c->pcv : 0, grid, ha, k, s));
+        } else {
+            CK2(launch_step2d(c->dtype, c->nv, c->ring, c->chunks, c->pcv, grid, a, k, s));
+        }
     }
     if (!dry) {
         k_advance2d<<<1, 1, 0, s>>>(c->st, n);
@@ -1159,8 +1018,11 @@ int graph2d(Ctx2D* c, void* const f[2], int n, cudaGraphExec_t* out) {
 int ctx2d_create(Ctx2D** out, const lat_grid* g, DevState* st, int sm_count, cudaStream_t s) {
     *out = nullptr;
     if (!nv2d_supported(g->nv)) return LAT_EINVAL;
-    if (g->dtype != LAT_F32 && g->dtype != LAT_F64) return LAT_EINVAL;
+    const bool half = g->dtype == LAT_F16 || g->dtype == LAT_BF16;
+    if (g->dtype != LAT_F32 && g->dtype != LAT_F64 && !half) return LAT_EINVAL;
+    if (half && !h2d_supported(g->nv)) return LAT_EINVAL;
     Ctx2D* c = new Ctx2D();
+    c->half = half;
     c->nx = g->nx;
     c->ny = g->ny;
     c->nv = g->nv;
@@ -1175,16 +1037,30 @@ int ctx2d_create(Ctx2D** out, const lat_grid* g, DevState* st, int sm_count, cud
     c->sm_count = sm_count;
     c->ring = ring_ok(c);
     c->chunks = chunks_supported(c->nv, 3) ? 3 : 1;
-    c->pcv = c->ring && pc_supported(c->nv) ? 4 : 0;
+    c->pcv = c->ring && pc_ok(c) ? (half ? 5 : 4) : 0;
+    if (half && !c->pcv) c->ring = false;
     const long long ncell = (long long)c->nx * c->ny;
     c->mom_blocks = (int)std::min<long long>((ncell + 255) / 256, 8LL * sm_count);
-    if (cudaMalloc(&c->d_partials, sizeof(double) * 8 * kMom2DWarps * c->mom_blocks) != cudaSuccess ||
+    if (cudaMalloc(&c->d_partials, sizeof(double) * 8 * c->mom_blocks) != cudaSuccess ||
         cudaMalloc(&c->d_glob, sizeof(double) * 4) != cudaSuccess ||
         cudaMallocHost(&c->h_glob, sizeof(double) * 4) != cudaSuccess) {
         ctx2d_destroy(c);
         return LAT_ENOMEM;
     }
-    (void)s;
+    if (half) {
+        c->nlines = scale_count(c->nv, c->ny);
+        if (cudaMalloc(&c->d_sc, sizeof(float) * 2 * c->nlines) != cudaSuccess ||
+            cudaMalloc(&c->d_mx, sizeof(unsigned) * 2 * c->nlines) != cudaSuccess) {
+            ctx2d_destroy(c);
+            return LAT_ENOMEM;
+        }
+        cudaError_t e = launch_fill_scales(c->d_sc, 2 * c->nlines, s);
+        if (e == cudaSuccess) e = cudaMemsetAsync(c->d_mx, 0, sizeof(unsigned) * 2 * c->nlines, s);
+        if (e != cudaSuccess) {
+            ctx2d_destroy(c);
+            return cuda_err(e, "scale initialisation");
+        }
+    }
     *out = c;
     return LAT_OK;
 }
@@ -1307,17 +1183,24 @@ int ctx2d_step(Ctx2D* c, void* const f[2], int n, cudaStream_t s) {
     return LAT_OK;
 }
 
-int ctx2d_moments(Ctx2D* c, const void* f, double* rho, double* mean_v, double* mean_v2,
-                  double* globals, cudaStream_t s) {
-    if (c->dtype == LAT_F64)
+int ctx2d_moments(Ctx2D* c, const void* f, int cur, double* rho, double* mean_v,
+                  double* mean_v2, double* globals, cudaStream_t s) {
+    const float* sc = c->half ? c->d_sc + (size_t)cur * c->nlines : nullptr;
+    if (c->dtype == LAT_F16)
+        k_moments2d<__half><<<c->mom_blocks, 32 * kMom2DWarps, 0, s>>>(f, sc, c->nv, c->nx, c->ny, c->dv,
+                                                         rho, mean_v, mean_v2, c->d_partials, c->st);
+    else if (c->dtype == LAT_BF16)
+        k_moments2d<__nv_bfloat16><<<c->mom_blocks, 32 * kMom2DWarps, 0, s>>>(f, sc, c->nv, c->nx, c->ny, c->dv,
+                                                         rho, mean_v, mean_v2, c->d_partials, c->st);
+    else if (c->dtype == LAT_F64)
         k_moments2d<double><<<c->mom_blocks, 32 * kMom2DWarps, 0, s>>>(f, nullptr, c->nv, c->nx, c->ny, c->dv,
                                                          rho, mean_v, mean_v2, c->d_partials, c->st);
     else
         k_moments2d<float><<<c->mom_blocks, 32 * kMom2DWarps, 0, s>>>(f, nullptr, c->nv, c->nx, c->ny, c->dv,
                                                         rho, mean_v, mean_v2, c->d_partials, c->st);
     CK2(cudaGetLastError());
-    k_finalize2d<<<1, 32, 0, s>>>(c->d_partials, c->mom_blocks * kMom2DWarps,
-                                  c->dx * c->dx * c->dv * c->dv, c->d_glob);
+    k_finalize2d<<<1, kFin2DThreads, 0, s>>>(c->d_partials, c->mom_blocks,
+                                             c->dx * c->dx * c->dv * c->dv, c->d_glob);
     CK2(cudaGetLastError());
     if (globals) {
         CK2(cudaMemcpyAsync(c->h_glob, c->d_glob, sizeof(double) * 4, cudaMemcpyDeviceToHost, s));
@@ -1332,7 +1215,9 @@ int ctx2d_set_launch(Ctx2D* c, int kernel, int block, int bps, int mode) {
     // 128 C threads splits every cell's jx range over C warp groups (C = 1..4)
     // kernel 3..5: producer/consumer variants (block fixed at 160 threads)
     if (kernel < 0 || kernel > 5) return LAT_EINVAL;
+    if (c->half && (kernel == 2 || kernel == 3)) return LAT_EINVAL;
     if (kernel >= 2 && !ring_ok(c)) return LAT_EINVAL;
+    if (c->half && kernel >= 4 && !pc_ok(c)) return LAT_EINVAL;
     if (kernel >= 3 && !pc_supported(c->nv)) return LAT_EINVAL;
     const bool ring = kernel == 0 ? c->ring : kernel >= 2;
     const int pcv = kernel == 0 ? c->pcv : (kernel >= 3 ? kernel : 0);
@@ -1364,13 +1249,16 @@ int ctx2d_autotune(Ctx2D* c, void* const f[2], int reps, double* best, cudaStrea
     for (int variant = 0; variant <= 7; ++variant) {
         if (variant > 0 && !ring_ok(c)) continue;
         if (variant >= 1 && variant <= 4 && !chunks_supported(c->nv, variant)) continue;
-        if (variant >= 5 && !pc_supported(c->nv)) continue;
+        if (variant >= 5 && !pc_ok(c)) continue;
+        if (c->half && (variant >= 1 && variant <= 5)) continue;  // 16-bit: plain, pc 4, pc 5
         for (int bps : {1, 2, 3, 4, 6, 8}) {
             c->ring = variant > 0;
             c->chunks = (variant >= 1 && variant <= 4) ? variant : 1;
             c->pcv = variant >= 5 ? variant - 2 : 0;
             c->bps = bps;
-            if (c->ring && bps > occupancy_ring(c->nv, c->chunks, c->pcv)) continue;
+            const int occ = c->half ? occupancy_step2d_h(c->dtype, c->nv, c->pcv)
+                                    : occupancy_ring(c->nv, c->chunks, c->pcv);
+            if (c->ring && bps > occ) continue;
             int rc = enqueue2d(c, f, 1, s, 1);
             if (rc != LAT_OK) return rc;
             CK2(cudaEventRecord(e0, s));
@@ -1406,6 +1294,30 @@ int ctx2d_autotune(Ctx2D* c, void* const f[2], int reps, double* best, cudaStrea
     return LAT_OK;
 }
 
+int ctx2d_init_state(Ctx2D* c, void* const f[2], int cur, cudaStream_t s) {
+    if (!c->half) return LAT_OK;
+    // the caller's initial 16-bit values are taken with scale 1
+    CK2(launch_linemax_h(c->dtype, f[cur], c->d_sc + (size_t)cur * c->nlines,
+                         c->d_mx + (size_t)cur * c->nlines, c->nv, c->nx, c->ny, s));
+    return LAT_OK;
+}
+
+int ctx2d_encode(Ctx2D* c, const float* src, void* const f[2], int cur, cudaStream_t s) {
+    if (!c->half || !src) return LAT_EINVAL;
+    CK2(launch_encode_h(c->dtype, src, f[cur], c->d_sc + (size_t)cur * c->nlines,
+                        c->d_mx + (size_t)cur * c->nlines, c->nv, c->nx, c->ny, c->st, s));
+    return LAT_OK;
+}
+
+int ctx2d_decode(Ctx2D* c, void* const f[2], int cur, float* dst, float* scales,
+                 cudaStream_t s) {
+    if (!c->half) return LAT_EINVAL;
+    const float* sc = c->d_sc + (size_t)cur * c->nlines;
+    if (dst) CK2(launch_decode_h(c->dtype, f[cur], sc, dst, c->nv, c->nx, c->ny, s));
+    if (scales) CK2(launch_scales_dense(sc, scales, c->nv, c->ny, s));
+    return LAT_OK;
+}
+
 void ctx2d_destroy(Ctx2D* c) {
     if (!c) return;
     drop(c);
@@ -1418,6 +1330,8 @@ void ctx2d_destroy(Ctx2D* c) {
     cudaFree(c->d_noise);
     cudaFree(c->d_u);
     cudaFree(c->d_partials);
+    cudaFree(c->d_sc);
+    cudaFree(c->d_mx);
     cudaFree(c->d_glob);
     if (c->h_glob) cudaFreeHost(c->h_glob);
     delete c;

@@ -64,6 +64,8 @@ def _load():
         "lat_strerror": (ctypes.c_char_p, [c_int]),
         "lat_free": (None, [P]),
         "lat_moments1d_noalloc": (c_int, [P, c_int, c_int, c_double, c_double, P, P]),
+        "lat_encode": (c_int, [P, P]),
+        "lat_decode": (c_int, [P, P, P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -214,6 +216,22 @@ class Lattice(_Ctx):
     def set_flow_modes_2d(self, kvec, a, phi0, tau_f: float):
         self._set_flow(FLOW_MODES, k=np.asarray(kvec, dtype=np.int32).reshape(-1, 2), amp0=a,
                        phase0=phi0, tau_f=tau_f)
+
+    def encode(self, src: torch.Tensor):
+        """16-bit storage: replace the state by the encoding of the FP32 tensor src."""
+        if src.dtype != torch.float32 or not src.is_cuda or not src.is_contiguous():
+            raise ValueError("src must be a contiguous CUDA float32 tensor")
+        if src.numel() != self.f[0].numel():
+            raise ValueError("src must have the state's size")
+        _check(_lib.lat_encode(self._h, _ptr(src)), "lat_encode")
+
+    def decode(self):
+        """16-bit storage: the current state as FP32 and its line scales [N_v^2 N_y]."""
+        dst = torch.empty(self.f[0].shape, dtype=torch.float32, device=self.f[0].device)
+        sc = torch.empty(self.nv * self.nv * self.ny, dtype=torch.float32,
+                         device=self.f[0].device)
+        _check(_lib.lat_decode(self._h, _ptr(dst), _ptr(sc)), "lat_decode")
+        return dst, sc
 
     def moments(self, per_cell: bool = True):
         ncell = self.nx * self.ny
