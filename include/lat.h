@@ -183,6 +183,37 @@ int lat_encode(lat_ctx* c, const float* src);
 /* Decode the current state into the FP32 DEVICE array dst (may be NULL) and copy its line
  * scales, [jy][jx][y] floats, to the DEVICE array scales (may be NULL).  Synchronises. */
 int lat_decode(lat_ctx* c, float* dst, float* scales);
+/*
+ * Learned flux closure on a coarse 2D lattice (d = 2, LAT_F32, N_v in {3, 5, 9, 13, 17}).  The
+ * paper proposes large-eddy closures for the lattice (Section 5); this library's closure adds
+ * learned fluxes to the upwind drag fluxes of every interior velocity face, so mass is kept
+ * exactly.  Per phase-space cell (x, j) after streaming, 16 features: f*(x, j + d)/rho*(x) for
+ * the 3 x 3 velocity neighbourhood d = (dy, dx) (row-major, 0 outside the box; rho* the streamed
+ * density), dt du_x/dx, dt du_x/dy, dt du_y/dx, dt du_y/dy (centred differences), the Courant
+ * numbers g (u_x/dv - jx + J) and g (u_y/dv - jy + J), and 1; then h1 = relu(X W1 + b1),
+ * h2 = relu(h1 W2 + b2), y = tanh(h2 W3 + b3) / 4, and y_0 (f*_{jx+1} - f*_{jx}) and
+ * y_1 (f*_{jy+1} - f*_{jy}) join the drag fluxes through faces jx + 1/2 and jy + 1/2 (a learned
+ * face diffusivity in lattice units).
+ * params: HOST array of LAT_LEARN_NPARAM floats, W1 [16][64], b1 [64], W2 [64][64], b2 [64],
+ *         W3 [64][2], b3 [2] (row-major, copied).
+ * mode:   0 off (plain step), 1 FP32 network on CUDA cores, 2 BF16 network on the tensor cores
+ *         (FP32 accumulation).  Every lat_step then runs the learned step.
+ */
+#define LAT_LEARN_NPARAM 5378
+int lat_learn(lat_ctx* c, const float* params, int mode);
+/* Mean square difference between the state after nsteps learned steps (FP32 network) from the
+ * current state and the DEVICE array target (layout of f), and its exact gradient with respect
+ * to the parameters (HOST array grad of LAT_LEARN_NPARAM floats); loss: HOST double.  The state,
+ * the flow and the step count are left as they were (the flow's noise rows of the following
+ * nsteps steps are read).  Needs lat_learn with mode 1 or 2 and a flow; nsteps <= 64.
+ * Synchronises. */
+int lat_learn_grad(lat_ctx* c, int nsteps, const float* target, double* loss, float* grad);
+/* Restriction of a fine 2D FP32 state (N_v = nv_fine = 4 m + 1 >= 5, layout of f, DEVICE) to the
+ * coarse lattice of N_v = m + 1 velocities per axis with four times the velocity step (same dx and
+ * V_max, so dt four times smaller): coarse cell k collects fine cells 4k - 2 .. 4k + 2 with weights
+ * (1/2, 1, 1, 1, 1/2) per axis, divided by 16, which keeps the mass sum f dx^2 dv^2.  coarse:
+ * DEVICE array of (m + 1)^2 ny nx floats.  Asynchronous on `stream`. */
+int lat_restrict(const float* fine, int nv_fine, int nx, int ny, float* coarse, void* stream);
 
 /* Steps taken since init. */
 long long lat_steps_done(const lat_ctx* c);

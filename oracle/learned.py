@@ -18,11 +18,15 @@ closure the library implements, in plain numpy:
   streamed density sum_j f*), dt_c times the four velocity gradients (du_x/dx, du_x/dy, du_y/dx,
   du_y/dy, centred differences on the grid), the two drag Courant numbers c a_x, c a_y of the
   cell, and the constant 1.  Every feature is dimensionless.
-* Network (reading R-L3): 16 -> 64 -> 64 -> 2, ReLU on both hidden layers, biases on all three.
-* Correction (flux form): the drag fluxes of Section 2 (reading R3) get
-  c F_{jx+1/2} += rho* y_0(jx, jy) and c F_{jy+1/2} += rho* y_1(jx, jy) on every interior face;
-  faces on the walls of the velocity box stay at zero flux.  Mass is therefore kept exactly, and
-  a network with zero output gives back the plain coarse step.
+* Network (reading R-L3): 16 -> 64 -> 64 -> 2, ReLU on both hidden layers, biases on all three,
+  outputs bounded by y = Y_MAX tanh(z), Y_MAX = 1/4.
+* Correction (flux form, reading R-L5): the drag fluxes of Section 2 (reading R3) get
+  c F_{jx+1/2} += y_0(jx, jy) (f*_{jx+1} - f*_{jx}) and c F_{jy+1/2} += y_1 (f*_{jy+1} - f*_{jy})
+  on every interior face: a learned face diffusivity in lattice units (y > 0 moves mass up the
+  gradient, i.e. takes back numerical diffusion); faces on the walls stay at zero flux.  Mass is
+  kept exactly, a network with zero output gives back the plain coarse step, and the correction
+  of a face is proportional to the densities next to it, so the sparse tails of f are not
+  flooded by corrections sized for the bulk.
 * Training loss (reading R-L4): mean square difference between the coarse state after n_c
   coarse steps and the target (the restricted fine state at the same time).  ``rollout_grad``
   is its exact gradient with respect to the weights, by the adjoint of every step.
@@ -38,6 +42,7 @@ from . import lattice as _lat
 NF = 16       # features
 NH = 64       # hidden units per layer
 NO = 2        # outputs
+Y_MAX = 0.25  # bound of the outputs
 
 
 # --------------------------------------------------------------------------------------------
@@ -128,19 +133,19 @@ def zero_weights():
 
 
 def mlp_forward(X: np.ndarray, W):
-    """y = relu(relu(X W1 + b1) W2 + b2) W3 + b3 (reading R-L3); returns y and the cache."""
+    """y = Y_MAX tanh(relu(relu(X W1 + b1) W2 + b2) W3 + b3) (reading R-L3); y and the cache."""
     z1 = X @ W["W1"] + W["b1"]
     h1 = np.maximum(z1, 0.0)
     z2 = h1 @ W["W2"] + W["b2"]
     h2 = np.maximum(z2, 0.0)
-    y = h2 @ W["W3"] + W["b3"]
-    return y, (X, z1, h1, z2, h2)
+    t = np.tanh(h2 @ W["W3"] + W["b3"])
+    return Y_MAX * t, (X, z1, h1, z2, h2, t)
 
 
 def mlp_backward(dy: np.ndarray, W, cache):
     """Gradients of sum(dy * y) with respect to the weights and to X (chain rule by hand)."""
-    X, z1, h1, z2, h2 = cache
-    rows = dy.reshape(-1, NO)
+    X, z1, h1, z2, h2, t = cache
+    rows = (dy * Y_MAX * (1.0 - t * t)).reshape(-1, NO)   # through the tanh
     g = {"W3": h2.reshape(-1, NH).T @ rows, "b3": rows.sum(axis=0)}
     dz2 = (rows @ W["W3"].T) * (z2.reshape(-1, NH) > 0)
     g["W2"] = h1.reshape(-1, NH).T @ dz2
@@ -167,11 +172,11 @@ def learned_step_2d(f, ux, uy, W, *, tau_p, kappa, dt, dv, dx, keep=False):
     y, cache = mlp_forward(X, W)
     axp, axm, ayp, aym = _drag_parts(fs, ux, uy, tau_p, dt, dv)
     shp = fs.shape
-    # correction fluxes rho* y on the interior faces, added to the plain upwind drag step
+    # correction fluxes y (f*_{j+1} - f*_j) on the interior faces, added to the plain drag step
     Gx = np.zeros((shp[0], shp[1] + 1) + shp[2:])
-    Gx[:, 1:-1] = rho * y[:, :-1, ..., 0]
+    Gx[:, 1:-1] = y[:, :-1, ..., 0] * (fs[:, 1:] - fs[:, :-1])
     Gy = np.zeros((shp[0] + 1,) + shp[1:])
-    Gy[1:-1] = rho * y[:-1, :, ..., 1]
+    Gy[1:-1] = y[:-1, :, ..., 1] * (fs[1:] - fs[:-1])
     fss = _lat.drag_2d(fs, ux, uy, tau_p, dt, dv) - (Gx[:, 1:] - Gx[:, :-1]) - (Gy[1:] - Gy[:-1])
     out = _lat.diffuse_2d(fss, kappa, dt, dv)
     if keep:
@@ -206,10 +211,16 @@ def learned_step_adjoint(lam_out, W, saved, *, kappa, dt, dv):
     lfs[:, 1:] += axm[:, 1:] * lFx
     lfs[:-1] += ayp[:-1] * lFy
     lfs[1:] += aym[1:] * lFy
+    # correction G_{j+1/2} = y_j (f*_{j+1} - f*_j)
+    yx, yy = y[:, :-1, ..., 0], y[:-1, :, ..., 1]
+    lfs[:, 1:] += yx * lFx
+    lfs[:, :-1] -= yx * lFx
+    lfs[1:] += yy * lFy
+    lfs[:-1] -= yy * lFy
     dy = np.zeros_like(y)
-    dy[:, :-1, ..., 0] = rho * lFx
-    dy[:-1, :, ..., 1] = rho * lFy
-    lrho = (y[:, :-1, ..., 0] * lFx).sum(axis=(0, 1)) + (y[:-1, :, ..., 1] * lFy).sum(axis=(0, 1))
+    dy[:, :-1, ..., 0] = (fs[:, 1:] - fs[:, :-1]) * lFx
+    dy[:-1, :, ..., 1] = (fs[1:] - fs[:-1]) * lFy
+    lrho = np.zeros(fs.shape[2:])
     g, dX = mlp_backward(dy, W, cache)
     # neighbour features f*(v + d) / rho*
     nv = fs.shape[0]

@@ -12,6 +12,7 @@
 
 #include "lat_internal.h"
 #include "lat2d.h"
+#include "learn.h"
 
 using namespace lat;
 
@@ -569,6 +570,28 @@ int lat_step_moments(lat_ctx* c, int n, double* rho, double* mean_v, double* mea
 }
 
 int lat_current(const lat_ctx* c) { return c ? c->cur : -1; }
+
+int lat_restrict(const float* fine, int nv_fine, int nx, int ny, float* coarse, void* stream) {
+    if (!fine || !coarse || nx < 1 || ny < 1 || nv_fine < 5 || (nv_fine - 1) % 4 != 0)
+        return LAT_EINVAL;
+    if (launch_restrict(fine, nv_fine, nx, ny, coarse, (cudaStream_t)stream) != cudaSuccess)
+        return LAT_ECUDA;
+    return LAT_OK;
+}
+
+int lat_learn(lat_ctx* c, const float* params, int mode) {
+    if (!c || c->d != 2) return LAT_EINVAL;
+    int rc = ctx2d_learn_set(c->c2, params, mode, c->stream);
+    if (rc == LAT_OK) drop_graphs(c);
+    return rc;
+}
+
+int lat_learn_grad(lat_ctx* c, int nsteps, const float* target, double* loss, float* grad) {
+    if (!c || c->d != 2 || !target || !loss || !grad) return LAT_EINVAL;
+    int rc = ctx2d_learn_grad(c->c2, c->f, c->cur, nsteps, target, loss, grad, c->stream);
+    if (rc != LAT_OK) return rc;
+    return lat_status(c);
+}
 
 int lat_encode(lat_ctx* c, const float* src) {
     if (!c || !src || c->d != 2 || (c->dtype != LAT_F16 && c->dtype != LAT_BF16))

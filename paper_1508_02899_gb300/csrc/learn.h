@@ -1,0 +1,80 @@
+// Internal interface of the learned flux closure on a coarse 2D lattice (learn.cu, learn_tc.cu),
+// used by the 2D context in step2d.cu.
+//
+// One learned step: the streamed density rho* of every spatial cell; per phase-space cell the
+// 16 features, the 16-64-64-2 ReLU network with tanh-bounded outputs y, and the correction
+// fluxes y (f*_{j+1} - f*_j) on the interior velocity faces (G[0]: face jx + 1/2, G[1]: face
+// jy + 1/2, zero on the walls); then the plain step with G added to the upwind drag fluxes.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "step2d_dev.h"
+
+namespace lat {
+
+constexpr int kLNF = 16, kLNH = 64, kLNO = 2;
+// parameter vector: W1 [16][64], b1 [64], W2 [64][64], b2 [64], W3 [64][2], b3 [2] (x W + b)
+constexpr int kOffW1 = 0;
+constexpr int kOffB1 = kOffW1 + kLNF * kLNH;
+constexpr int kOffW2 = kOffB1 + kLNH;
+constexpr int kOffB2 = kOffW2 + kLNH * kLNH;
+constexpr int kOffW3 = kOffB2 + kLNH;
+constexpr int kOffB3 = kOffW3 + kLNH * kLNO;
+constexpr int kLNParam = kOffB3 + kLNO;
+constexpr float kYMax = 0.25f;  // outputs y = kYMax tanh(z)
+
+struct LearnArgs {
+    const float* f[2];     // state buffers; the step reads parity (st->step + k) & 1
+    const float* u;        // flow [2][ny][nx]
+    float* rho;            // streamed density [ny][nx]
+    const float* params;   // FP32 parameters [kLNParam]
+    float* G;              // corrections [2][N_v^2][ny][nx]
+    const DevState* st;
+    int nx, ny;
+    float g;               // dt / tau_p
+    float inv_dv;          // 1 / dv
+    float dt_2dx;          // dt / (2 dx): centred differences of u times dt
+};
+
+bool learn_nv_supported(int nv);
+cudaError_t launch_rho_star(int nv, const LearnArgs& a, int k, cudaStream_t s);
+cudaError_t launch_mlp_f32(int nv, const LearnArgs& a, int k, cudaStream_t s);
+// The same network in BF16 on the tensor cores (tcgen05, FP32 accumulation in TMEM), from the
+// parameter tiles that launch_learn_tc_pack builds from the FP32 parameters.
+bool learn_tc_supported(int nv);
+size_t learn_tc_bytes();
+cudaError_t launch_learn_tc_pack(const float* params, void* wtc, cudaStream_t s);
+cudaError_t launch_mlp_tc(int nv, const LearnArgs& a, const void* wtc, int sm_count, int k,
+                          cudaStream_t s);
+// The plain 2D FP32 step (Step2DArgs) with the corrections G added to the drag fluxes.
+cudaError_t launch_step2d_corr(int nv, int grid, const k2d::Step2DArgs& a, const float* G, int k,
+                               cudaStream_t s);
+
+// ---- gradient of a rollout (FP32, CUDA cores) ---------------------------------------------
+// Buffers of one backward step: lam_out = dL/df^{n+1} (in), lam_in = dL/df^n (out); f = f^n;
+// work arrays: lss (dL/df**), lrho [ny][nx], dX9 [9][N_v^2][ny][nx]; grad [kLNParam] accumulates.
+struct LearnBwdArgs {
+    LearnArgs fw;          // f[0] = f[1] = f^n, u = u^n, rho = rho*^n (recomputed)
+    const float* lam_out;
+    float* lss;
+    float* lrho;
+    float* dX9;
+    float* cxy;            // [2][N_v^2][ny][nx]: y lambda_F of faces jx + 1/2, jy + 1/2
+    float* lfs;            // dL/df* without the neighbour-feature and density terms
+    float* lam_in;
+    float* grad;
+    float r;               // kappa dt / dv^2
+};
+cudaError_t launch_diffuse_adjoint(int nv, const float* lam, float* out, float r, int nx, int ny,
+                                   cudaStream_t s);
+cudaError_t launch_mlp_bwd(int nv, const LearnBwdArgs& a, int sm_count, cudaStream_t s);
+cudaError_t launch_gather_adjoint(int nv, const LearnBwdArgs& a, cudaStream_t s);
+// Fine 2D state (N_v = nvf, 4 k + 1) -> coarse state (N_v = (nvf - 1)/4 + 1), per velocity axis.
+cudaError_t launch_restrict(const float* fine, int nvf, int nx, int ny, float* coarse,
+                            cudaStream_t s);
+// loss = mean (f - target)^2 over n values (FP64 partial sums), lam = 2 (f - target) / n
+cudaError_t launch_loss(const float* f, const float* target, long long n, float* lam,
+                        double* partials, int nblocks, double* loss, cudaStream_t s);
+
+}  // namespace lat

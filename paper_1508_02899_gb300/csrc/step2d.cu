@@ -28,6 +28,7 @@
 #include "lat2d.h"
 #include "step2d_dev.h"
 #include "step2d_h.h"
+#include "learn.h"
 #include "lat_reduce.h"
 
 namespace lat {
@@ -60,24 +61,6 @@ struct Flow2DArgs {
 };
 
 // ---- plain-load kernel (any N_x, N_y; FP32 or FP64) -----------------------------------------
-// Row jy of f* at one cell, read straight from global memory (periodic wrap in x and y).
-template <typename T, int NV>
-struct GlobalRow {
-    const T* base;  // f + (jy NV ny + ys) nx: plane (jy, 0), source row ys = (y - jy) mod ny
-    size_t pstride;
-    int x, nx;
-    __device__ __forceinline__ GlobalRow(const T* f, int row, int x_, int y, int nx_, int ny)
-        : x(x_), nx(nx_) {
-        constexpr int J = (NV - 1) / 2;
-        pstride = (size_t)nx_ * ny;
-        base = f + (size_t)row * NV * pstride + (size_t)wrap(y - (row - J), ny) * nx_;
-    }
-    __device__ __forceinline__ T get(int jx) const {
-        constexpr int J = (NV - 1) / 2;
-        return __ldg(base + jx * pstride + wrap(x - (jx - J), nx));
-    }
-};
-
 template <typename T, int NV>
 __global__ void __launch_bounds__(TW) k_step2d_plain(const Step2DArgs a, int kstep) {
     const long long step = a.st->step + kstep;
@@ -865,6 +848,13 @@ struct Ctx2D {
     long long nlines = 0;  // scales (or maxima) per buffer, padded layout
     float* d_sc = nullptr;
     unsigned* d_mx = nullptr;
+    // learned flux closure: 0 off, 1 FP32 network on CUDA cores, 2 BF16 network on tensor cores
+    int learn = 0;
+    float* d_params = nullptr;   // [kLNParam] FP32
+    void* d_wtc = nullptr;       // tensor-core weight tiles (BF16) and biases
+    float* d_rho = nullptr;      // [ny][nx]
+    float* d_G = nullptr;        // [2][N_v^2][ny][nx]
+    DevState* d_st0 = nullptr;   // step 0, no flags: explicit-buffer rollouts
     // moments
     double* d_partials = nullptr;
     double* d_glob = nullptr;
@@ -938,37 +928,76 @@ int grid_of(const Ctx2D* c, int ntiles) {
 
 // Enqueue n steps.  Dry runs (autotuning) repeat step 0 n times: every repetition reads the
 // current buffer and writes the other one, so the state and the flow are left as they were.
+// Flow of step st->step + k into d_u (modal flow only); the phases of the following step are
+// written unless dry.
+int launch_flow(Ctx2D* c, int k, int dry, cudaStream_t s) {
+    Flow2DArgs fa;
+            fa.k = c->d_k;
+    fa.cx = c->d_cx;
+    fa.cy = c->d_cy;
+    fa.phase = c->d_phase;
+    fa.noise = c->d_noise;
+    fa.walk = c->walk;
+    fa.xtab = c->d_xtab;
+    fa.ytab = c->d_ytab;
+    fa.kmax = c->kmax;
+    fa.nmodes = c->nmodes;
+    fa.nx = c->nx;
+    fa.ny = c->ny;
+    fa.u = c->d_u;
+    fa.st = c->st;
+    fa.frozen = c->frozen ? 1 : 0;
+    fa.dry = dry;
+    const long long ncell = (long long)c->nx * c->ny;
+    const int fg = (int)std::min<long long>((ncell + 255) / 256, 8LL * c->sm_count);
+    const size_t sh = 4 * sizeof(double) * c->nmodes;
+    if (c->dtype == LAT_F64) k_flow2d<double><<<fg, 256, sh, s>>>(fa, k);
+    else k_flow2d<float><<<fg, 256, sh, s>>>(fa, k);
+    CK2(cudaGetLastError());
+    return LAT_OK;
+}
+
+LearnArgs learn_args(const Ctx2D* c, const void* f0, const void* f1, const DevState* st) {
+    LearnArgs la;
+    la.f[0] = static_cast<const float*>(f0);
+    la.f[1] = static_cast<const float*>(f1);
+    la.u = c->flow_kind == LAT_FLOW_FIELD ? static_cast<const float*>(c->field)
+                                          : static_cast<const float*>(c->d_u);
+    la.rho = c->d_rho;
+    la.params = c->d_params;
+    la.G = c->d_G;
+    la.st = st;
+    la.nx = c->nx;
+    la.ny = c->ny;
+    la.g = (float)c->g;
+    la.inv_dv = (float)(1.0 / c->dv);
+    la.dt_2dx = (float)(c->dt / (2.0 * c->dx));
+    return la;
+}
+
+// One learned step from the buffers of a (parity from a.st): flow, density, network, step.
+int enqueue_learned(Ctx2D* c, const Step2DArgs& a, int grid, int k, cudaStream_t s) {
+    const LearnArgs la = learn_args(c, a.f[0], a.f[1], a.st);
+    CK2(launch_rho_star(c->nv, la, k, s));
+    if (c->learn == 2) CK2(launch_mlp_tc(c->nv, la, c->d_wtc, c->sm_count, k, s));
+    else CK2(launch_mlp_f32(c->nv, la, k, s));
+    CK2(launch_step2d_corr(c->nv, grid, a, c->d_G, k, s));
+    return LAT_OK;
+}
+
 int enqueue2d(Ctx2D* c, void* const f[2], int n, cudaStream_t s, int dry) {
     const Step2DArgs a = step_args(c, f);
     const int grid = grid_of(c, a.ntiles);
     for (int kk = 0; kk < n; ++kk) {
         const int k = dry ? 0 : kk;
         if (c->flow_kind == LAT_FLOW_MODES) {
-            Flow2DArgs fa;
-            fa.k = c->d_k;
-            fa.cx = c->d_cx;
-            fa.cy = c->d_cy;
-            fa.phase = c->d_phase;
-            fa.noise = c->d_noise;
-            fa.walk = c->walk;
-            fa.xtab = c->d_xtab;
-            fa.ytab = c->d_ytab;
-            fa.kmax = c->kmax;
-            fa.nmodes = c->nmodes;
-            fa.nx = c->nx;
-            fa.ny = c->ny;
-            fa.u = c->d_u;
-            fa.st = c->st;
-            fa.frozen = c->frozen ? 1 : 0;
-            fa.dry = dry;
-            const long long ncell = (long long)c->nx * c->ny;
-            const int fg = (int)std::min<long long>((ncell + 255) / 256, 8LL * c->sm_count);
-            const size_t sh = 4 * sizeof(double) * c->nmodes;
-            if (c->dtype == LAT_F64) k_flow2d<double><<<fg, 256, sh, s>>>(fa, k);
-            else k_flow2d<float><<<fg, 256, sh, s>>>(fa, k);
-            CK2(cudaGetLastError());
+            const int rc = launch_flow(c, k, dry, s);
+            if (rc != LAT_OK) return rc;
         }
-        if (c->half) {
+        if (c->learn) {
+            const int rc = enqueue_learned(c, a, grid, k, s);
+            if (rc != LAT_OK) return rc;
+        } else if (c->half) {
             const Step2DHArgs ha = half_args(c, a);
             CK2(launch_scale2d(c->nv, c->ny, ha, k, s));
             CK2(launch_step2d_h(c->dtype, c->nv, c->ring ? c->pcv : 0, grid, ha, k, s));
@@ -1239,6 +1268,15 @@ int ctx2d_set_launch(Ctx2D* c, int kernel, int block, int bps, int mode) {
 }
 
 int ctx2d_autotune(Ctx2D* c, void* const f[2], int reps, double* best, cudaStream_t s) {
+    if (c->learn) {  // the learned step has one launch shape
+        if (best) {
+            best[0] = 1;
+            best[1] = TW;
+            best[2] = 0;
+            best[3] = 0;
+        }
+        return LAT_OK;
+    }
     cudaEvent_t e0, e1;
     CK2(cudaEventCreate(&e0));
     CK2(cudaEventCreate(&e1));
@@ -1318,6 +1356,153 @@ int ctx2d_decode(Ctx2D* c, void* const f[2], int cur, float* dst, float* scales,
     return LAT_OK;
 }
 
+int ctx2d_learn_set(Ctx2D* c, const float* params, int mode, cudaStream_t s) {
+    if (mode == 0) {
+        c->learn = 0;
+        drop(c);
+        return LAT_OK;
+    }
+    if ((mode != 1 && mode != 2) || !params || c->dtype != LAT_F32 || !learn_nv_supported(c->nv))
+        return LAT_EINVAL;
+    if (mode == 2 && !learn_tc_supported(c->nv)) return LAT_EINVAL;
+    const long long ncell = (long long)c->nx * c->ny;
+    if (!c->d_params) {
+        if (cudaMalloc(&c->d_params, sizeof(float) * kLNParam) != cudaSuccess ||
+            cudaMalloc(&c->d_rho, sizeof(float) * ncell) != cudaSuccess ||
+            cudaMalloc(&c->d_G, sizeof(float) * 2 * c->nv * c->nv * ncell) != cudaSuccess ||
+            cudaMalloc(&c->d_wtc, learn_tc_bytes()) != cudaSuccess ||
+            cudaMalloc(&c->d_st0, sizeof(DevState)) != cudaSuccess)
+            return LAT_ENOMEM;
+        CK2(cudaMemsetAsync(c->d_st0, 0, sizeof(DevState), s));
+    }
+    CK2(cudaMemcpyAsync(c->d_params, params, sizeof(float) * kLNParam, cudaMemcpyHostToDevice, s));
+    CK2(launch_learn_tc_pack(c->d_params, c->d_wtc, s));
+    CK2(cudaStreamSynchronize(s));
+    c->learn = mode;
+    drop(c);
+    return LAT_OK;
+}
+
+// Loss of an n-step rollout of the learned step (FP32 network) from the current state against
+// target, and its gradient with respect to the parameters.  The state, the flow phases and the
+// step counter are left as they were.
+int ctx2d_learn_grad(Ctx2D* c, void* const f[2], int cur, int n, const float* target,
+                     double* loss, float* grad, cudaStream_t s) {
+    if (!c->learn || n < 1 || n > 64 || !target || c->flow_kind == LAT_FLOW_NONE) return LAT_EINVAL;
+    const long long ncell = (long long)c->nx * c->ny;
+    const long long nst = ncell * c->nv * c->nv;
+    float* buf = nullptr;
+    // F[0..n], U[0..n-1], lam x2, lss, lfs, lrho, dX9, cxy, grad; loss partials
+    const size_t nfl = (size_t)(n + 1) * nst + (size_t)n * 2 * ncell + 4 * (size_t)nst + ncell +
+                       11 * (size_t)nst + kLNParam;
+    const int nb = 256;
+    double* dpart = nullptr;
+    if (cudaMalloc(&buf, sizeof(float) * nfl) != cudaSuccess) return LAT_ENOMEM;
+    if (cudaMalloc(&dpart, sizeof(double) * (nb + 1)) != cudaSuccess) {
+        cudaFree(buf);
+        return LAT_ENOMEM;
+    }
+    double* dphase = nullptr;
+    const bool modes = c->flow_kind == LAT_FLOW_MODES;
+    int rc = LAT_OK;
+    auto fail = [&](int code) {
+        rc = code;
+        return code;
+    };
+    do {
+        float* F = buf;
+        float* U = F + (size_t)(n + 1) * nst;
+        float* lamA = U + (size_t)n * 2 * ncell;
+        float* lamB = lamA + nst;
+        float* lss = lamB + nst;
+        float* lfs = lss + nst;
+        float* lrho = lfs + nst;
+        float* dX9 = lrho + ncell;
+        float* cxy = dX9 + 9 * nst;
+        float* g = cxy + 2 * nst;
+        if (modes) {
+            if (cudaMalloc(&dphase, sizeof(double) * 2 * c->nmodes) != cudaSuccess) {
+                fail(LAT_ENOMEM);
+                break;
+            }
+            if (cudaMemcpyAsync(dphase, c->d_phase, sizeof(double) * 2 * c->nmodes,
+                                cudaMemcpyDeviceToDevice, s) != cudaSuccess) {
+                fail(LAT_ECUDA);
+                break;
+            }
+        }
+        if (cudaMemcpyAsync(F, f[cur], sizeof(float) * nst, cudaMemcpyDeviceToDevice, s) !=
+            cudaSuccess) {
+            fail(LAT_ECUDA);
+            break;
+        }
+        // forward rollout on explicit buffers F[k] -> F[k+1] (zero step counter: parity 0)
+        Step2DArgs a = step_args(c, f);
+        a.st = c->d_st0;
+        const int grid = grid_of(c, a.ntiles);
+        for (int k = 0; k < n && rc == LAT_OK; ++k) {
+            if (modes && launch_flow(c, k, 0, s) != LAT_OK) fail(LAT_ECUDA);
+            const float* u = c->flow_kind == LAT_FLOW_FIELD ? static_cast<const float*>(c->field)
+                                                            : static_cast<const float*>(c->d_u);
+            if (cudaMemcpyAsync(U + (size_t)k * 2 * ncell, u, sizeof(float) * 2 * ncell,
+                                cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+                fail(LAT_ECUDA);
+            a.f[0] = F + (size_t)k * nst;
+            a.f[1] = F + (size_t)(k + 1) * nst;
+            LearnArgs la = learn_args(c, a.f[0], a.f[1], c->d_st0);
+            la.u = U + (size_t)k * 2 * ncell;
+            a.u = la.u;
+            if (launch_rho_star(c->nv, la, 0, s) != cudaSuccess ||
+                launch_mlp_f32(c->nv, la, 0, s) != cudaSuccess ||
+                launch_step2d_corr(c->nv, grid, a, c->d_G, 0, s) != cudaSuccess)
+                fail(LAT_ECUDA);
+        }
+        if (rc != LAT_OK) break;
+        if (launch_loss(F + (size_t)n * nst, target, nst, lamA, dpart, nb, dpart + nb, s) !=
+                cudaSuccess ||
+            cudaMemsetAsync(g, 0, sizeof(float) * kLNParam, s) != cudaSuccess) {
+            fail(LAT_ECUDA);
+            break;
+        }
+        for (int k = n - 1; k >= 0 && rc == LAT_OK; --k) {
+            LearnBwdArgs b;
+            b.fw = learn_args(c, F + (size_t)k * nst, F + (size_t)k * nst, c->d_st0);
+            b.fw.u = U + (size_t)k * 2 * ncell;
+            b.lam_out = lamA;
+            b.lss = lss;
+            b.lrho = lrho;
+            b.dX9 = dX9;
+            b.cxy = cxy;
+            b.lfs = lfs;
+            b.lam_in = lamB;
+            b.grad = g;
+            b.r = (float)c->r;
+            if (launch_diffuse_adjoint(c->nv, lamA, lss, (float)c->r, c->nx, c->ny, s) != cudaSuccess ||
+                cudaMemsetAsync(lrho, 0, sizeof(float) * ncell, s) != cudaSuccess ||
+                launch_rho_star(c->nv, b.fw, 0, s) != cudaSuccess ||
+                launch_mlp_bwd(c->nv, b, c->sm_count, s) != cudaSuccess ||
+                launch_gather_adjoint(c->nv, b, s) != cudaSuccess)
+                fail(LAT_ECUDA);
+            std::swap(lamA, lamB);
+        }
+        if (rc != LAT_OK) break;
+        if (cudaMemcpyAsync(grad, g, sizeof(float) * kLNParam, cudaMemcpyDeviceToHost, s) !=
+                cudaSuccess ||
+            cudaMemcpyAsync(loss, dpart + nb, sizeof(double), cudaMemcpyDeviceToHost, s) !=
+                cudaSuccess)
+            fail(LAT_ECUDA);
+    } while (false);
+    if (dphase) {
+        cudaMemcpyAsync(c->d_phase, dphase, sizeof(double) * 2 * c->nmodes,
+                        cudaMemcpyDeviceToDevice, s);
+    }
+    if (cudaStreamSynchronize(s) != cudaSuccess && rc == LAT_OK) rc = LAT_ECUDA;
+    cudaFree(dphase);
+    cudaFree(dpart);
+    cudaFree(buf);
+    return rc;
+}
+
 void ctx2d_destroy(Ctx2D* c) {
     if (!c) return;
     drop(c);
@@ -1332,6 +1517,11 @@ void ctx2d_destroy(Ctx2D* c) {
     cudaFree(c->d_partials);
     cudaFree(c->d_sc);
     cudaFree(c->d_mx);
+    cudaFree(c->d_params);
+    cudaFree(c->d_wtc);
+    cudaFree(c->d_rho);
+    cudaFree(c->d_G);
+    cudaFree(c->d_st0);
     cudaFree(c->d_glob);
     if (c->h_glob) cudaFreeHost(c->h_glob);
     delete c;

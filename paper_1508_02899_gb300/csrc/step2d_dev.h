@@ -121,12 +121,23 @@ __device__ __forceinline__ double opaque(double v) {
     return r;
 }
 
+// Extra drag flux on the interior velocity faces (the learned closure); NoCorr adds nothing.
+// Corr::gx(rb, jx): flux through face jx + 1/2 of velocity row rb; Corr::gy(rb, jx): flux
+// through face rb + 1/2 of column jx.
+struct NoCorr {
+    static constexpr bool active = false;
+    template <typename T>
+    __device__ __forceinline__ T gx(int, int) const { return T(0); }
+    template <typename T>
+    __device__ __forceinline__ T gy(int, int) const { return T(0); }
+};
+
 // The output goes through `put`: put.begin(row) before output row `row`, then put(o) for
 // jx = 0..NV-1 in order (StorePut for FP32/FP64 storage).
-template <typename T, int NV, class Row, class GArr, class Put>
+template <typename T, int NV, class Row, class GArr, class Put, class Corr = NoCorr>
 __device__ __forceinline__ void sweep_row(T (&A)[NV], GArr& G, T (&H)[NV], int r,
                                           const Row& cur, const Row& nxt_row, T g_in, T wx_in,
-                                          T wy, T rr, Put& put) {
+                                          T wy, T rr, Put& put, const Corr& corr = Corr()) {
     using O = Ops<T>;
     constexpr int J = (NV - 1) / 2;
     const int rb = r - 1;
@@ -143,8 +154,12 @@ __device__ __forceinline__ void sweep_row(T (&A)[NV], GArr& G, T (&H)[NV], int r
         if (jx < NV - 1) {
             sn = cur.get(jx + 1);
             Fnext = dflux<T>(cacc<T>(g, wx, jx - J), cacc<T>(g, wx, jx + 1 - J), sc, sn);
+            if constexpr (Corr::active) Fnext = O::add(Fnext, corr.template gx<T>(rb, jx));
         }
-        const T Gn = nxt ? O::fma(ayp, sc, O::mul(aym, nxt_row.get(jx))) : T(0);
+        T Gn = nxt ? O::fma(ayp, sc, O::mul(aym, nxt_row.get(jx))) : T(0);
+        if constexpr (Corr::active) {
+            if (nxt) Gn = O::add(Gn, corr.template gy<T>(rb, jx));
+        }
         const T b = O::sub(O::sub(sc, O::sub(Fnext, Fprev)), O::sub(Gn, G[jx]));
         G[jx] = Gn;
         Fprev = Fnext;
@@ -213,6 +228,24 @@ __device__ __forceinline__ void cfl_check(const Step2DArgs& a, T g, T wx, T wy, 
     if (active && g * (T(J) + fabs(wx)) + g * (T(J) + fabs(wy)) > T(1))
         atomicOr(&a.st->status, ST_CFL);
 }
+
+// Row jy of f* at one cell, read straight from global memory (periodic wrap in x and y).
+template <typename T, int NV>
+struct GlobalRow {
+    const T* base;  // f + (jy NV ny + ys) nx: plane (jy, 0), source row ys = (y - jy) mod ny
+    size_t pstride;
+    int x, nx;
+    __device__ __forceinline__ GlobalRow(const T* f, int row, int x_, int y, int nx_, int ny)
+        : x(x_), nx(nx_) {
+        constexpr int J = (NV - 1) / 2;
+        pstride = (size_t)nx_ * ny;
+        base = f + (size_t)row * NV * pstride + (size_t)wrap(y - (row - J), ny) * nx_;
+    }
+    __device__ __forceinline__ T get(int jx) const {
+        constexpr int J = (NV - 1) / 2;
+        return __ldg(base + jx * pstride + wrap(x - (jx - J), nx));
+    }
+};
 
 struct SmemCol {  // one thread's column in a [NV][TW] shared array
     float* p;

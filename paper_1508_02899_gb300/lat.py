@@ -20,6 +20,7 @@ LAT_OK, LAT_EINVAL, LAT_ECFL, LAT_ENOMEM, LAT_ECUDA = 0, 1, 2, 3, 4
 LAT_ENUMERIC, LAT_ETIMEOUT, LAT_EOVERFLOW, LAT_ENOISE = 5, 6, 7, 8
 LAT_F64, LAT_F32, LAT_F16, LAT_BF16 = 0, 1, 2, 3
 FLOW_NONE, FLOW_FIELD, FLOW_MODES = 0, 1, 2
+LEARN_NPARAM = 5378
 
 _DTYPES = {torch.float64: LAT_F64, torch.float32: LAT_F32, torch.float16: LAT_F16,
            torch.bfloat16: LAT_BF16}
@@ -65,6 +66,9 @@ def _load():
         "lat_free": (None, [P]),
         "lat_moments1d_noalloc": (c_int, [P, c_int, c_int, c_double, c_double, P, P]),
         "lat_encode": (c_int, [P, P]),
+        "lat_learn": (c_int, [P, POINTER(ctypes.c_float), c_int]),
+        "lat_restrict": (c_int, [P, c_int, c_int, c_int, P, P]),
+        "lat_learn_grad": (c_int, [P, c_int, P, POINTER(c_double), POINTER(ctypes.c_float)]),
         "lat_decode": (c_int, [P, P, P]),
     }
     for name, (res, args) in sig.items():
@@ -225,6 +229,25 @@ class Lattice(_Ctx):
             raise ValueError("src must have the state's size")
         _check(_lib.lat_encode(self._h, _ptr(src)), "lat_encode")
 
+    def learn(self, params, mode: int = 1):
+        """Learned flux closure (2D FP32): params = the LAT_LEARN_NPARAM parameters (numpy);
+        mode 0 off, 1 FP32 network, 2 BF16 tensor-core network."""
+        p = np.ascontiguousarray(np.asarray(params, dtype=np.float32).reshape(-1))
+        if p.size != LEARN_NPARAM:
+            raise ValueError(f"expected {LEARN_NPARAM} parameters")
+        _check(_lib.lat_learn(self._h, p.ctypes.data_as(POINTER(ctypes.c_float)), mode),
+               "lat_learn")
+
+    def learn_grad(self, nsteps: int, target: torch.Tensor):
+        """Loss of an nsteps rollout against target (device FP32) and its gradient (numpy)."""
+        if target.dtype != torch.float32 or not target.is_cuda or not target.is_contiguous():
+            raise ValueError("target must be a contiguous CUDA float32 tensor")
+        loss = np.zeros(1)
+        grad = np.zeros(LEARN_NPARAM, dtype=np.float32)
+        _check(_lib.lat_learn_grad(self._h, nsteps, _ptr(target), _dptr(loss),
+                                   grad.ctypes.data_as(POINTER(ctypes.c_float))), "lat_learn_grad")
+        return float(loss[0]), grad
+
     def decode(self):
         """16-bit storage: the current state as FP32 and its line scales [N_v^2 N_y]."""
         dst = torch.empty(self.f[0].shape, dtype=torch.float32, device=self.f[0].device)
@@ -304,3 +327,12 @@ class Ensemble(_Ctx):
 
 def exported_symbols():
     return [n for n in dir(_lib) if n.startswith("lat_")]
+
+
+def restrict(fine: torch.Tensor, nx: int, ny: int, stream=None) -> torch.Tensor:
+    """Fine 2D FP32 state (N_v = 4 m + 1) -> coarse state (N_v = m + 1), on the device."""
+    nvf = fine.shape[0]
+    nvc = (nvf - 1) // 4 + 1
+    out = torch.empty((nvc, nvc, ny, nx), dtype=torch.float32, device=fine.device)
+    _check(_lib.lat_restrict(_ptr(fine), nvf, nx, ny, _ptr(out), _stream(stream)), "lat_restrict")
+    return out
