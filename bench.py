@@ -48,19 +48,23 @@ def parse():
     p.add_argument("--no-autotune", action="store_true")
     p.add_argument("--no-per-instance", action="store_true")
     p.add_argument("--no-forms", action="store_true")
-    p.add_argument("--workload", default="ensemble", choices=["ensemble", "2d", "2d_f16", "2d_bf16"])
+    p.add_argument("--workload", default="ensemble",
+                   choices=["ensemble", "2d", "2d_f16", "2d_bf16", "2d_learned"])
     p.add_argument("--launch", default=None,
                    help="kernel,block,blocks_per_sm instead of autotuning (profiling runs)")
     return p.parse_args()
 
 
-def measured_peaks():
+def measured_peaks(key: str = "hbm_gbs"):
+    """A measured peak of the GB300s (HBM copy GB/s, or dense BF16 TFLOP/s as a burst),
+    else the fallback figures of the profiling recipe."""
+    fallback = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
             pk = json.load(fh)
-        return float(pk["hbm_gbs"]), "measured"
+        return float(pk[key]), "measured"
     except Exception:
-        return 6800.0, "fallback"
+        return fallback[key], "fallback"
 
 
 def rank_seeds(rank: int):
@@ -233,6 +237,10 @@ def run_reference(args):
 # ---------------------------------------------------------------------------------------------
 WORKLOAD_2D = ("2D FP32: periodic 512x512 grid, 33x33 velocity lattice (2.85e8 cells), St=1, "
                "kappa=1e-3, incompressible random-phase flow |k|<=8, k^-3 spectrum, OU phases")
+WORKLOAD_LEARNED = ("2D learned coarse lattice: periodic {n}x{n} grid, 9x9 velocities (the 33x33 "
+                    "lattice restricted: dv x4, dt / 4), St=1, kappa=1e-3, random-phase flow; "
+                    "16-64-64-2 network in BF16 on tcgen05 tensor cores, random-init weights")
+LEARN_FLOP_PER_CELL = 2 * (16 * 64 + 64 * 64 + 64 * 2)  # useful multiply-adds x 2
 WORKLOAD_2D_16 = ("2D {fmt} storage (per x-line power-of-two scales, FP32 arithmetic): periodic "
                   "{n}x{n} grid, {nv}x{nv} velocity lattice, St=1, kappa=1e-3, incompressible "
                   "random-phase flow |k|<=8, k^-3 spectrum, OU phases")
@@ -278,6 +286,42 @@ def build_2d(args, I, lat, torch, dev, rank, nsteps, n=512, nv=33, store="f32"):
     lt.set_flow_modes_2d(fl.kvec, fl.a, fl.phi0, fl.tau_f)
     lt.set_noise(fl.noise)
     return lt, n * n * nv * nv, fl.noise[:1], np.zeros(4), desc
+
+
+def build_learned(args, I, lat, torch, dev, rank, nsteps, n=2048):
+    """Coarse 9x9 lattice of the n^2 x 33^2 FP32 problem with the learned closure (mode 2)."""
+    from paper_1508_02899_gb300 import train as T
+    L = 2 * math.pi
+    tau_p, kappa = L, 1e-3
+    dt = I.choose_dt(2, n, L, 33, tau_p, kappa) / T.COARSE_PER_FINE
+    dx = L / n
+    dv = dx / dt
+    nv = 9
+    col = I.gaussian_column(1, nv, dx, dv, 0.2 * ((nv - 1) // 2) * dv)
+    col2 = torch.tensor(np.outer(col, col) / (n * n), dtype=torch.float32, device=dev)
+    f0 = col2[:, :, None, None].expand(nv, nv, n, n).contiguous()
+    fl = I.flow2d_inputs(SEED + 13 + rank, nsteps, n, n, dx)
+    lt = lat.Lattice(f0, d=2, nx=n, ny=n, nv=nv, L=L, tau_p=tau_p, kappa=kappa, dt=dt)
+    lt.set_flow_modes_2d(fl.kvec, fl.a, fl.phi0, fl.tau_f)
+    lt.set_noise(fl.noise)
+    lt.learn(T.init_params(SEED + 17, scale=0.5), 2)
+    return lt, n * n * nv * nv, fl.noise[:1], np.zeros(4), WORKLOAD_LEARNED.format(n=n)
+
+
+def time_network(lt, reps, torch):
+    """CUDA-event time of the tensor-core network alone (lat_learn_corrections reusing the flow
+    and the streamed density of a first call), on the current stream."""
+    lt.learn_corrections()
+    for _ in range(2):
+        lt.learn_corrections(reuse_inputs=True)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(reps):
+        lt.learn_corrections(reuse_inputs=True)
+    e1.record()
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / reps
 
 
 def timed(ctx, K, W, torch, dist, world, local, dev):
@@ -360,7 +404,11 @@ def main():
     K_e2e = max(3, min(K, 50))
     nsteps = W + K + K_e2e + 2
     bytes_per_cell, lines = 8, 0
-    if args.workload == "2d":
+    if args.workload == "2d_learned":
+        ctx, cells, noise_row, glob, desc = build_learned(args, I, lat, torch, dev, rank, nsteps)
+        nv, prof, src = 9, "learn_tc_2048_nv9.md", "paper_1508_02899_gb300/csrc/learn_tc.cu"
+        launches_per_step = 4  # flow, streamed density, network, corrected step
+    elif args.workload == "2d":
         ctx, cells, noise_row, glob, desc = build_2d(args, I, lat, torch, dev, rank, nsteps)
         nv, prof, src = 33, "step2d_512_fp32_nv33.md", "paper_1508_02899_gb300/csrc/step2d.cu"
         launches_per_step = 2  # flow evaluation + fused step
@@ -409,6 +457,16 @@ def main():
     # output scale and its recorded maximum (4 bytes each)
     bytes_per_launch = cells * bytes_per_cell + lines * 12
     achieved = bytes_per_launch / (ms_max / K / 1e3) / 1e9
+    roof = None
+    if args.workload == "2d_learned":
+        # dominant kernel: the tensor-core network, timed alone with CUDA events
+        net_ms = time_network(ctx, max(5, min(K, 50)), torch)
+        flops = cells * LEARN_FLOP_PER_CELL
+        tpeak, tsrc = measured_peaks(key="bf16_tflops")
+        tf = flops / (net_ms / 1e3) / 1e12
+        roof = {"bound": "tensor", "achieved": tf, "peak": tpeak, "unit": "TFLOP/s",
+                "frac": tf / tpeak, "traffic": None, "peak_source": tsrc,
+                "kernel": "k_mlp_tc<9>", "flop_per_launch": flops, "ms_per_launch": net_ms}
     tr = profile_traffic(prof, src)
     traffic = None
     if tr is not None:
@@ -444,6 +502,19 @@ def main():
             lt.close()
             del lt
             torch.cuda.empty_cache()
+        lt, c2, *_ = build_learned(args, I, lat, torch, dev, rank, 2 * 20 + 4)
+        ms2, _ = timed(lt, 20, 3, torch, dist, world, local, dev)
+        st2 = lt.status()
+        net_ms = time_network(lt, 10, torch)
+        tpeak, _ = measured_peaks(key="bf16_tflops")
+        tf = c2 * LEARN_FLOP_PER_CELL / (net_ms / 1e3) / 1e12
+        forms["2d_learned_2048x2048_9x9"] = {
+            "gcups": c2 * 20 / (ms2 / 1e3) / 1e9, "ms_per_step": ms2 / 20,
+            "network_ms": net_ms, "network_tflops": tf, "network_frac_bf16": tf / tpeak,
+            "kernel": "k_mlp_tc<9> + k_step2d_corr<9>", "steps": 20, "status": st2}
+        lt.close()
+        del lt
+        torch.cuda.empty_cache()
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -457,16 +528,18 @@ def main():
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K,
             "warmup": W, "ms_per_step": ms_max / K, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None,
-            "dtype": {"2d_f16": "f16 storage, f32 math", "2d_bf16": "bf16 storage, f32 math"}.get(
+            "dtype": {"2d_f16": "f16 storage, f32 math", "2d_bf16": "bf16 storage, f32 math",
+                      "2d_learned": "f32 state, bf16 network (f32 accumulation)"}.get(
                 args.workload, "f32"),
             "data": "synthetic",
             "config": {"workload": desc, "nv": nv, "cells_per_step_per_gpu": cells,
                        "l2": "inputs larger than L2 (FP32 ping-pong buffers of GBs); no flush",
                        "launch": best, "status": status},
-            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                         "frac": achieved / peak, "traffic": traffic,
-                         "peak_source": peak_src, "kernel": kernel_label(args.workload, best, nv),
-                         "bytes_per_launch": bytes_per_launch},
+            "roofline": roof or {"bound": "hbm", "achieved": achieved, "peak": peak,
+                                 "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,
+                                 "peak_source": peak_src,
+                                 "kernel": kernel_label(args.workload, best, nv),
+                                 "bytes_per_launch": bytes_per_launch},
             "cpu_baseline": cpu,
             "e2e": {"value": e2e_value, "unit": UNIT, "steps": K_e2e,
                     "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},

@@ -191,9 +191,11 @@ int lat_decode(lat_ctx* c, float* dst, float* scales);
  * the 3 x 3 velocity neighbourhood d = (dy, dx) (row-major, 0 outside the box; rho* the streamed
  * density), dt du_x/dx, dt du_x/dy, dt du_y/dx, dt du_y/dy (centred differences), the Courant
  * numbers g (u_x/dv - jx + J) and g (u_y/dv - jy + J), and 1; then h1 = relu(X W1 + b1),
- * h2 = relu(h1 W2 + b2), y = tanh(h2 W3 + b3) / 4, and y_0 (f*_{jx+1} - f*_{jx}) and
- * y_1 (f*_{jy+1} - f*_{jy}) join the drag fluxes through faces jx + 1/2 and jy + 1/2 (a learned
- * face diffusivity in lattice units).
+ * h2 = relu(h1 W2 + b2), y = b tanh(z), z = h2 W3 + b3, with b = 1/4 for z <= 0 (extra
+ * diffusion) and b = 0.9 |ca| (1 - |ca|) / 2 for z > 0 (anti-diffusion: at most 0.9 of the
+ * upwind flux's numerical diffusivity; ca = the cell's drag Courant number - g/2).  Then
+ * y_0 (f*_{jx+1} - f*_{jx}) and y_1 (f*_{jy+1} - f*_{jy}) join the drag fluxes through faces
+ * jx + 1/2 and jy + 1/2 (a learned face diffusivity in lattice units).
  * params: HOST array of LAT_LEARN_NPARAM floats, W1 [16][64], b1 [64], W2 [64][64], b2 [64],
  *         W3 [64][2], b3 [2] (row-major, copied).
  * mode:   0 off (plain step), 1 FP32 network on CUDA cores, 2 BF16 network on the tensor cores
@@ -201,13 +203,23 @@ int lat_decode(lat_ctx* c, float* dst, float* scales);
  */
 #define LAT_LEARN_NPARAM 5378
 int lat_learn(lat_ctx* c, const float* params, int mode);
-/* Mean square difference between the state after nsteps learned steps (FP32 network) from the
- * current state and the DEVICE array target (layout of f), and its exact gradient with respect
- * to the parameters (HOST array grad of LAT_LEARN_NPARAM floats); loss: HOST double.  The state,
- * the flow and the step count are left as they were (the flow's noise rows of the following
- * nsteps steps are read).  Needs lat_learn with mode 1 or 2 and a flow; nsteps <= 64.
- * Synchronises. */
-int lat_learn_grad(lat_ctx* c, int nsteps, const float* target, double* loss, float* grad);
+/* Enqueue the learned correction fluxes of the current state at the current step (the flow, the
+ * streamed density, the network and G; the state and the flow do not advance) and, when G is not
+ * NULL, copy them to the DEVICE array G of 2 N_v^2 N_y N_x floats: G[0] through faces jx + 1/2,
+ * G[1] through faces jy + 1/2, zero on the walls.  reuse_inputs != 0 keeps the flow and the
+ * streamed density of the previous call and runs the network alone (same state and step).
+ * Asynchronous; LAT_EINVAL without lat_learn. */
+int lat_learn_corrections(lat_ctx* c, float* G, int reuse_inputs);
+/* Training loss after nsteps learned steps (FP32 network) from the current state against the
+ * DEVICE array target (layout of f):
+ *     loss = mean over all values of (f - target)^2 + rho_weight * mean over the spatial cells
+ *            of (sum_j (f - target))^2,
+ * and its exact gradient with respect to the parameters (HOST array grad of LAT_LEARN_NPARAM
+ * floats), by the adjoint of every step; loss: HOST double.  The state, the flow and the step
+ * count are left as they were (the flow's noise rows of the following nsteps steps are read).
+ * Needs lat_learn with mode 1 or 2, a flow, nsteps <= 64 and rho_weight >= 0.  Synchronises. */
+int lat_learn_grad(lat_ctx* c, int nsteps, const float* target, double rho_weight, double* loss,
+                   float* grad);
 /* Restriction of a fine 2D FP32 state (N_v = nv_fine = 4 m + 1 >= 5, layout of f, DEVICE) to the
  * coarse lattice of N_v = m + 1 velocities per axis with four times the velocity step (same dx and
  * V_max, so dt four times smaller): coarse cell k collects fine cells 4k - 2 .. 4k + 2 with weights

@@ -19,7 +19,10 @@ closure the library implements, in plain numpy:
   du_y/dy, centred differences on the grid), the two drag Courant numbers c a_x, c a_y of the
   cell, and the constant 1.  Every feature is dimensionless.
 * Network (reading R-L3): 16 -> 64 -> 64 -> 2, ReLU on both hidden layers, biases on all three,
-  outputs bounded by y = Y_MAX tanh(z), Y_MAX = 1/4.
+  outputs bounded by y = b tanh(z) with b = Y_MAX = 1/4 for z <= 0 (extra diffusion) and
+  b = THETA D_num for z > 0 (anti-diffusion), D_num = |ca| (1 - |ca|) / 2 the numerical
+  diffusivity of the upwind flux at the face (ca the face's drag Courant number, the mean of the
+  two cells'), THETA = 0.9: the learned flux never takes back all of the scheme's own diffusion.
 * Correction (flux form, reading R-L5): the drag fluxes of Section 2 (reading R3) get
   c F_{jx+1/2} += y_0(jx, jy) (f*_{jx+1} - f*_{jx}) and c F_{jy+1/2} += y_1 (f*_{jy+1} - f*_{jy})
   on every interior face: a learned face diffusivity in lattice units (y > 0 moves mass up the
@@ -28,8 +31,10 @@ closure the library implements, in plain numpy:
   of a face is proportional to the densities next to it, so the sparse tails of f are not
   flooded by corrections sized for the bulk.
 * Training loss (reading R-L4): mean square difference between the coarse state after n_c
-  coarse steps and the target (the restricted fine state at the same time).  ``rollout_grad``
-  is its exact gradient with respect to the weights, by the adjoint of every step.
+  coarse steps and the target (the restricted fine state at the same time), plus rho_weight
+  times the mean square of the density difference sum_j (f - target) per spatial cell.
+  ``rollout_grad`` is its exact gradient with respect to the weights, by the adjoint of every
+  step.
 """
 from __future__ import annotations
 
@@ -42,7 +47,8 @@ from . import lattice as _lat
 NF = 16       # features
 NH = 64       # hidden units per layer
 NO = 2        # outputs
-Y_MAX = 0.25  # bound of the outputs
+Y_MAX = 0.25  # bound of the outputs towards extra diffusion
+THETA = 0.9   # share of the upwind numerical diffusivity the outputs may take back
 
 
 # --------------------------------------------------------------------------------------------
@@ -132,20 +138,34 @@ def zero_weights():
     return {k: np.zeros_like(v) for k, v in init_weights(0).items()}
 
 
-def mlp_forward(X: np.ndarray, W):
-    """y = Y_MAX tanh(relu(relu(X W1 + b1) W2 + b2) W3 + b3) (reading R-L3); y and the cache."""
+def output_bounds(X: np.ndarray, g: float):
+    """Bounds b of the two outputs for z > 0: THETA |ca| (1 - |ca|) / 2 at the +jx and +jy faces,
+    with ca = c a_j - g / 2 the face value of the drag Courant numbers (features 13 and 14)."""
+    out = []
+    for q in (13, 14):
+        ca = np.abs(X[..., q] - 0.5 * g)
+        out.append(THETA * np.maximum(ca * (1.0 - ca), 0.0) * 0.5)
+    return np.stack(out, axis=-1)
+
+
+def mlp_forward(X: np.ndarray, W, g: float = 0.0):
+    """y = b tanh(relu(relu(X W1 + b1) W2 + b2) W3 + b3), b from output_bounds for z > 0 and
+    Y_MAX otherwise (reading R-L3); returns y and the cache.  g = dt / tau_p."""
     z1 = X @ W["W1"] + W["b1"]
     h1 = np.maximum(z1, 0.0)
     z2 = h1 @ W["W2"] + W["b2"]
     h2 = np.maximum(z2, 0.0)
-    t = np.tanh(h2 @ W["W3"] + W["b3"])
-    return Y_MAX * t, (X, z1, h1, z2, h2, t)
+    z3 = h2 @ W["W3"] + W["b3"]
+    t = np.tanh(z3)
+    b = np.where(z3 > 0.0, output_bounds(X, g), Y_MAX)
+    return b * t, (X, z1, h1, z2, h2, t, b)
 
 
 def mlp_backward(dy: np.ndarray, W, cache):
-    """Gradients of sum(dy * y) with respect to the weights and to X (chain rule by hand)."""
-    X, z1, h1, z2, h2, t = cache
-    rows = (dy * Y_MAX * (1.0 - t * t)).reshape(-1, NO)   # through the tanh
+    """Gradients of sum(dy * y) with respect to the weights and to X (chain rule by hand).
+    The bounds depend on the flow features only, which no weight and no density moves."""
+    X, z1, h1, z2, h2, t, b = cache
+    rows = (dy * b * (1.0 - t * t)).reshape(-1, NO)   # through the bounded tanh
     g = {"W3": h2.reshape(-1, NH).T @ rows, "b3": rows.sum(axis=0)}
     dz2 = (rows @ W["W3"].T) * (z2.reshape(-1, NH) > 0)
     g["W2"] = h1.reshape(-1, NH).T @ dz2
@@ -165,11 +185,24 @@ def _drag_parts(fs, ux, uy, tau_p, dt, dv):
     return np.maximum(cax, 0.0), np.minimum(cax, 0.0), np.maximum(cay, 0.0), np.minimum(cay, 0.0)
 
 
+def corrections(f, ux, uy, W, *, tau_p, dt, dv, dx):
+    """Correction fluxes of one step from state f: Gx[jy, jx] through face jx + 1/2 and
+    Gy[jy, jx] through face jy + 1/2 (zero on the walls), at every spatial cell."""
+    fs = _lat.stream_2d(f)
+    X, _ = features(fs, ux, uy, tau_p=tau_p, dt=dt, dv=dv, dx=dx)
+    y, _ = mlp_forward(X, W, dt / tau_p)
+    Gx = np.zeros_like(fs)
+    Gx[:, :-1] = y[:, :-1, ..., 0] * (fs[:, 1:] - fs[:, :-1])
+    Gy = np.zeros_like(fs)
+    Gy[:-1] = y[:-1, :, ..., 1] * (fs[1:] - fs[:-1])
+    return Gx, Gy
+
+
 def learned_step_2d(f, ux, uy, W, *, tau_p, kappa, dt, dv, dx, keep=False):
     """Stream, corrected upwind drag, diffusion (Section 2 with the learned flux correction)."""
     fs = _lat.stream_2d(f)
     X, rho = features(fs, ux, uy, tau_p=tau_p, dt=dt, dv=dv, dx=dx)
-    y, cache = mlp_forward(X, W)
+    y, cache = mlp_forward(X, W, dt / tau_p)
     axp, axm, ayp, aym = _drag_parts(fs, ux, uy, tau_p, dt, dv)
     shp = fs.shape
     # correction fluxes y (f*_{j+1} - f*_j) on the interior faces, added to the plain drag step
@@ -252,18 +285,26 @@ def rollout(f0, W, nsteps, flows, *, tau_p, kappa, dt, dv, dx, keep=False):
     return (f, saved) if keep else f
 
 
-def loss(f0, W, nsteps, flows, target, **kw):
-    """Mean square difference to the target after nsteps (reading R-L4)."""
-    f = rollout(f0, W, nsteps, flows, **kw)
-    return float(np.mean((f - target) ** 2))
+def loss_value(f, target, rho_weight=0.0):
+    """mean (f - target)^2 + rho_weight mean_x (sum_j (f - target))^2 (reading R-L4)."""
+    d = f - target
+    r = d.sum(axis=(0, 1))
+    return float(np.mean(d * d) + rho_weight * np.mean(r * r))
 
 
-def rollout_grad(f0, W, nsteps, flows, target, *, tau_p, kappa, dt, dv, dx):
+def loss(f0, W, nsteps, flows, target, rho_weight=0.0, **kw):
+    """The training loss after nsteps learned steps."""
+    return loss_value(rollout(f0, W, nsteps, flows, **kw), target, rho_weight)
+
+
+def rollout_grad(f0, W, nsteps, flows, target, *, tau_p, kappa, dt, dv, dx, rho_weight=0.0):
     """Loss and its exact gradient with respect to every weight (adjoint of every step)."""
     f, saved = rollout(f0, W, nsteps, flows, tau_p=tau_p, kappa=kappa, dt=dt, dv=dv, dx=dx,
                        keep=True)
-    L = float(np.mean((f - target) ** 2))
-    lam = 2.0 * (f - target) / f.size
+    L = loss_value(f, target, rho_weight)
+    d = f - target
+    r = d.sum(axis=(0, 1))
+    lam = 2.0 * d / f.size + rho_weight * 2.0 * r / r.size
     grads = {k: np.zeros_like(v) for k, v in W.items()}
     for n in reversed(range(nsteps)):
         lam, g = learned_step_adjoint(lam, W, saved[n], kappa=kappa, dt=dt, dv=dv)

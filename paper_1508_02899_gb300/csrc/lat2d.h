@@ -23,8 +23,10 @@ int ctx2d_decode(Ctx2D* c, void* const f[2], int cur, float* dst, float* scales,
 // Learned flux closure (FP32 contexts): parameters from host memory, mode 0 off, 1 FP32 network,
 // 2 BF16 tensor-core network; the loss and gradient of an n-step rollout (FP32 network).
 int ctx2d_learn_set(Ctx2D* c, const float* params, int mode, cudaStream_t s);
+int ctx2d_learn_corr(Ctx2D* c, void* const f[2], int cur, float* G_out, int reuse,
+                     cudaStream_t s);
 int ctx2d_learn_grad(Ctx2D* c, void* const f[2], int cur, int n, const float* target,
-                     double* loss, float* grad, cudaStream_t s);
+                     double rho_weight, double* loss, float* grad, cudaStream_t s);
 int ctx2d_set_launch(Ctx2D* c, int kernel, int block, int bps, int mode);
 int ctx2d_autotune(Ctx2D* c, void* const f[2], int reps, double* best, cudaStream_t s);
 void ctx2d_destroy(Ctx2D* c);

@@ -586,9 +586,16 @@ int lat_learn(lat_ctx* c, const float* params, int mode) {
     return rc;
 }
 
-int lat_learn_grad(lat_ctx* c, int nsteps, const float* target, double* loss, float* grad) {
-    if (!c || c->d != 2 || !target || !loss || !grad) return LAT_EINVAL;
-    int rc = ctx2d_learn_grad(c->c2, c->f, c->cur, nsteps, target, loss, grad, c->stream);
+int lat_learn_corrections(lat_ctx* c, float* G, int reuse_inputs) {
+    if (!c || c->d != 2) return LAT_EINVAL;
+    return ctx2d_learn_corr(c->c2, c->f, c->cur, G, reuse_inputs ? 1 : 0, c->stream);
+}
+
+int lat_learn_grad(lat_ctx* c, int nsteps, const float* target, double rho_weight, double* loss,
+                   float* grad) {
+    if (!c || c->d != 2 || !target || !loss || !grad || !(rho_weight >= 0)) return LAT_EINVAL;
+    int rc = ctx2d_learn_grad(c->c2, c->f, c->cur, nsteps, target, rho_weight, loss, grad,
+                              c->stream);
     if (rc != LAT_OK) return rc;
     return lat_status(c);
 }

@@ -6,7 +6,9 @@
 // d = (dy, dx) in {-1, 0, 1}^2 row-major (0 outside the velocity box), dt du_x/dx, dt du_x/dy,
 // dt du_y/dx, dt du_y/dy (centred differences on the periodic grid), the drag Courant numbers
 // c a_x = g (w_x - (jx - J)) and c a_y = g (w_y - (jy - J)), and 1.  Network: 16 -> 64 -> 64 -> 2
-// with ReLU, outputs y = kYMax tanh(z); correction fluxes y_0 (f*_{jx+1} - f*_{jx}) through face
+// with ReLU, outputs y = b tanh(z) (b = kYMax towards extra diffusion, at most kTheta times the
+// face's upwind numerical diffusivity towards anti-diffusion); correction fluxes
+// y_0 (f*_{jx+1} - f*_{jx}) through face
 // jx + 1/2 and y_1 (f*_{jy+1} - f*_{jy}) through face jy + 1/2 on interior faces only (a learned
 // face diffusivity), so mass is kept exactly.  The paper suggests large-eddy closures for the
 // lattice (Section 5); this is one, trained against a restricted fine lattice.
@@ -117,9 +119,13 @@ __device__ __forceinline__ void layer2(const float* P, const float (&h1)[kLNH], 
     }
 }
 
-// y = kYMax tanh(h2 W3 + b3); t = tanh(.) kept for the backward
-__device__ __forceinline__ void layer3(const float* P, const float (&z2)[kLNH], float& y0, float& y1,
-                                       float& t0, float& t1) {
+// y = b tanh(h2 W3 + b3), b = anti_bound(.) for z > 0 and kYMax otherwise; t = tanh(.) and the
+// bounds kept for the backward
+struct Out3 {
+    float y0, y1, t0, t1, b0, b1;
+};
+__device__ __forceinline__ Out3 layer3(const float* P, const float (&z2)[kLNH],
+                                       const float (&X)[kLNF], float g) {
     float z0 = P[kOffB3], z1 = P[kOffB3 + 1];
 #pragma unroll
     for (int k = 0; k < kLNH; ++k) {
@@ -127,10 +133,14 @@ __device__ __forceinline__ void layer3(const float* P, const float (&z2)[kLNH], 
         z0 = __fmaf_rn(hk, P[kOffW3 + 2 * k], z0);
         z1 = __fmaf_rn(hk, P[kOffW3 + 2 * k + 1], z1);
     }
-    t0 = tanhf(z0);
-    t1 = tanhf(z1);
-    y0 = __fmul_rn(kYMax, t0);
-    y1 = __fmul_rn(kYMax, t1);
+    Out3 o;
+    o.t0 = tanhf(z0);
+    o.t1 = tanhf(z1);
+    o.b0 = z0 > 0.f ? anti_bound(X[13], g) : kYMax;
+    o.b1 = z1 > 0.f ? anti_bound(X[14], g) : kYMax;
+    o.y0 = __fmul_rn(o.b0, o.t0);
+    o.y1 = __fmul_rn(o.b1, o.t1);
+    return o;
 }
 
 template <int NV>
@@ -146,14 +156,14 @@ __global__ void __launch_bounds__(128) k_mlp_f32(const LearnArgs a, int kstep) {
         const long long c = i % ncell;
         const int jy = p / NV, jx = p % NV;
         const int y = (int)(c / a.nx), x = (int)(c % a.nx);
-        float X[kLNF], h1[kLNH], z2[kLNH], y0, y1, t0, t1;
+        float X[kLNF], h1[kLNH], z2[kLNH];
         Nbr nb;
         features<NV>(a, f, jx, jy, x, y, X, nb);
         layer1(P, X, h1);
         layer2(P, h1, z2);
-        layer3(P, z2, y0, y1, t0, t1);
-        a.G[i] = jx < NV - 1 ? __fmul_rn(y0, __fsub_rn(nb.xp, nb.c)) : 0.f;
-        a.G[n + i] = jy < NV - 1 ? __fmul_rn(y1, __fsub_rn(nb.yp, nb.c)) : 0.f;
+        const Out3 o = layer3(P, z2, X, a.g);
+        a.G[i] = jx < NV - 1 ? __fmul_rn(o.y0, __fsub_rn(nb.xp, nb.c)) : 0.f;
+        a.G[n + i] = jy < NV - 1 ? __fmul_rn(o.y1, __fsub_rn(nb.yp, nb.c)) : 0.f;
     }
 }
 
@@ -265,7 +275,7 @@ __global__ void __launch_bounds__(kBT, 1) k_mlp_bwd(const LearnBwdArgs b) {
             const float inv = features<NV>(a, f, jx, jy, x, y, X, nb);
 #pragma unroll
             for (int q = 0; q < kLNF; ++q) v(kRX + q) = X[q];
-            float y0, y1, t0, t1;
+            Out3 o;
             {
                 float h1[kLNH];
                 layer1(P, X, h1);
@@ -283,7 +293,7 @@ __global__ void __launch_bounds__(kBT, 1) k_mlp_bwd(const LearnBwdArgs b) {
                 }
 #pragma unroll
                 for (int k = 0; k < kLNH; ++k) v(kRH2 + k) = fmaxf(z2[k], 0.f);
-                layer3(P, z2, y0, y1, t0, t1);
+                o = layer3(P, z2, X, a.g);
             }
             // adjoint of f** = f* - (F_{j+1/2} - F_{j-1/2}) in x and y, F = upwind + correction
             const float* L = b.lss;
@@ -300,15 +310,15 @@ __global__ void __launch_bounds__(kBT, 1) k_mlp_bwd(const LearnBwdArgs b) {
             lf = __fmaf_rn(fminf(cay, 0.f), lym, lf);
             // correction G_{j+1/2} = y (f*_{j+1} - f*_j): -y lambda_F to this cell, +y lambda_F
             // to the +jx / +jy neighbour (gathered there), dL/dy = lambda_F (f*_{j+1} - f*_j)
-            const float cx = __fmul_rn(y0, lxp), cy = __fmul_rn(y1, lyp);
+            const float cx = __fmul_rn(o.y0, lxp), cy = __fmul_rn(o.y1, lyp);
             lf = __fsub_rn(__fsub_rn(lf, cx), cy);
             b.cxy[i] = cx;
             b.cxy[n + i] = cy;
             const float dy0 = __fmul_rn(lxp, __fsub_rn(nb.xp, nb.c));
             const float dy1 = __fmul_rn(lyp, __fsub_rn(nb.yp, nb.c));
-            // through y = kYMax tanh(z3)
-            const float dz30 = __fmul_rn(dy0, __fmul_rn(kYMax, __fsub_rn(1.f, __fmul_rn(t0, t0))));
-            const float dz31 = __fmul_rn(dy1, __fmul_rn(kYMax, __fsub_rn(1.f, __fmul_rn(t1, t1))));
+            // through y = b tanh(z3)
+            const float dz30 = __fmul_rn(dy0, __fmul_rn(o.b0, __fsub_rn(1.f, __fmul_rn(o.t0, o.t0))));
+            const float dz31 = __fmul_rn(dy1, __fmul_rn(o.b1, __fsub_rn(1.f, __fmul_rn(o.t1, o.t1))));
             v(kRDY) = dz30;
             v(kRDY + 1) = dz31;
             float lr = 0.f;
@@ -438,16 +448,17 @@ __global__ void __launch_bounds__(256) k_restrict(const float* fine, int nvf, in
     }
 }
 
-__global__ void __launch_bounds__(256) k_loss(const float* f, const float* target, long long n,
-                                              float* lam, double* partials) {
+// Density error per spatial cell r(x) = sum_j (f - target), and sums of r^2 per block.
+__global__ void __launch_bounds__(256) k_rho_err(const float* f, const float* target, int np,
+                                                 long long ncell, float* r, double* partials) {
     __shared__ double red[8];
     double s = 0.0;
-    const double w = 2.0 / (double)n;
-    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
-         i += (long long)gridDim.x * blockDim.x) {
-        const double d = (double)f[i] - (double)target[i];
+    for (long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x; c < ncell;
+         c += (long long)gridDim.x * blockDim.x) {
+        double d = 0.0;
+        for (int p = 0; p < np; ++p) d += (double)f[p * ncell + c] - (double)target[p * ncell + c];
+        r[c] = (float)d;
         s += d * d;
-        lam[i] = (float)(w * d);
     }
     for (int off = 16; off > 0; off >>= 1) s += __shfl_down_sync(0xffffffffu, s, off);
     if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
@@ -459,11 +470,38 @@ __global__ void __launch_bounds__(256) k_loss(const float* f, const float* targe
     }
 }
 
-__global__ void k_loss_final(const double* partials, int nb, long long n, double* loss) {
+// lam = 2 (f - target) / n + rho_weight 2 r(x) / ncell, and sums of (f - target)^2 per block.
+__global__ void __launch_bounds__(256) k_loss(const float* f, const float* target, long long n,
+                                              long long ncell, const float* r, double rho_weight,
+                                              float* lam, double* partials) {
+    __shared__ double red[8];
+    double s = 0.0;
+    const double w = 2.0 / (double)n, wr = 2.0 * rho_weight / (double)ncell;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        const double d = (double)f[i] - (double)target[i];
+        s += d * d;
+        lam[i] = (float)(w * d + wr * (double)r[i % ncell]);
+    }
+    for (int off = 16; off > 0; off >>= 1) s += __shfl_down_sync(0xffffffffu, s, off);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double z = 0.0;
+        for (int q = 0; q < (int)(blockDim.x >> 5); ++q) z += red[q];
+        partials[blockIdx.x] = z;
+    }
+}
+
+__global__ void k_loss_final(const double* partials, const double* partials_r, int nb, long long n,
+                             long long ncell, double rho_weight, double* loss) {
     if (threadIdx.x != 0 || blockIdx.x != 0) return;
-    double z = 0.0;
-    for (int q = 0; q < nb; ++q) z += partials[q];
-    *loss = z / (double)n;
+    double z = 0.0, zr = 0.0;
+    for (int q = 0; q < nb; ++q) {
+        z += partials[q];
+        zr += partials_r[q];
+    }
+    *loss = z / (double)n + rho_weight * zr / (double)ncell;
 }
 
 int grid_n(long long n, int block) {
@@ -561,12 +599,18 @@ cudaError_t launch_restrict(const float* fine, int nvf, int nx, int ny, float* c
     return cudaGetLastError();
 }
 
-cudaError_t launch_loss(const float* f, const float* target, long long n, float* lam,
-                        double* partials, int nblocks, double* loss, cudaStream_t s) {
-    k_loss<<<nblocks, 256, 0, s>>>(f, target, n, lam, partials);
+cudaError_t launch_loss(const float* f, const float* target, int np, long long ncell,
+                        double rho_weight, float* r, float* lam, double* partials, int nblocks,
+                        double* loss, cudaStream_t s) {
+    const long long n = ncell * np;
+    k_rho_err<<<nblocks, 256, 0, s>>>(f, target, np, ncell, r, partials + nblocks);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    k_loss_final<<<1, 32, 0, s>>>(partials, nblocks, n, loss);
+    k_loss<<<nblocks, 256, 0, s>>>(f, target, n, ncell, r, rho_weight, lam, partials);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    k_loss_final<<<1, 32, 0, s>>>(partials, partials + nblocks, nblocks, n, ncell, rho_weight,
+                                  loss);
     return cudaGetLastError();
 }
 

@@ -22,7 +22,15 @@ constexpr int kOffB2 = kOffW2 + kLNH * kLNH;
 constexpr int kOffW3 = kOffB2 + kLNH;
 constexpr int kOffB3 = kOffW3 + kLNH * kLNO;
 constexpr int kLNParam = kOffB3 + kLNO;
-constexpr float kYMax = 0.25f;  // outputs y = kYMax tanh(z)
+constexpr float kYMax = 0.25f;   // output bound towards extra diffusion
+constexpr float kTheta = 0.9f;   // share of the upwind numerical diffusivity y may take back
+
+// Bound of an output for z > 0: kTheta |ca| (1 - |ca|) / 2, ca = c a_cell - g / 2 the face
+// value of the cell's drag Courant number (the numerical diffusivity of the upwind flux).
+__host__ __device__ __forceinline__ float anti_bound(float ca_cell, float g) {
+    const float ca = fabsf(ca_cell - 0.5f * g);
+    return kTheta * 0.5f * fmaxf(ca * (1.f - ca), 0.f);
+}
 
 struct LearnArgs {
     const float* f[2];     // state buffers; the step reads parity (st->step + k) & 1
@@ -73,8 +81,10 @@ cudaError_t launch_gather_adjoint(int nv, const LearnBwdArgs& a, cudaStream_t s)
 // Fine 2D state (N_v = nvf, 4 k + 1) -> coarse state (N_v = (nvf - 1)/4 + 1), per velocity axis.
 cudaError_t launch_restrict(const float* fine, int nvf, int nx, int ny, float* coarse,
                             cudaStream_t s);
-// loss = mean (f - target)^2 over n values (FP64 partial sums), lam = 2 (f - target) / n
-cudaError_t launch_loss(const float* f, const float* target, long long n, float* lam,
-                        double* partials, int nblocks, double* loss, cudaStream_t s);
+// loss = mean (f - target)^2 + rho_weight mean_x r(x)^2, r = sum over the np velocity planes of
+// (f - target) (FP64 sums); lam = dloss/df.  partials: 2 nblocks doubles; r: ncell floats.
+cudaError_t launch_loss(const float* f, const float* target, int np, long long ncell,
+                        double rho_weight, float* r, float* lam, double* partials, int nblocks,
+                        double* loss, cudaStream_t s);
 
 }  // namespace lat

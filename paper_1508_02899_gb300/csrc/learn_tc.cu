@@ -308,8 +308,9 @@ __global__ void __launch_bounds__(128) k_mlp_tc(const LearnArgs a, const unsigne
             float y0, y1;
             tmem_ld2(trow, y0, y1);
             if (on) {
-                y0 = __fmul_rn(kYMax, tanhf(y0 + b3[0]));
-                y1 = __fmul_rn(kYMax, tanhf(y1 + b3[1]));
+                const float z0 = y0 + b3[0], z1 = y1 + b3[1];
+                y0 = __fmul_rn(z0 > 0.f ? anti_bound(X[13], a.g) : kYMax, tanhf(z0));
+                y1 = __fmul_rn(z1 > 0.f ? anti_bound(X[14], a.g) : kYMax, tanhf(z1));
                 a.G[i] = jx < NV - 1 ? __fmul_rn(y0, __fsub_rn(fxp, fc)) : 0.f;
                 a.G[n + i] = jy < NV - 1 ? __fmul_rn(y1, __fsub_rn(fyp, fc)) : 0.f;
             }

@@ -1383,11 +1383,31 @@ int ctx2d_learn_set(Ctx2D* c, const float* params, int mode, cudaStream_t s) {
     return LAT_OK;
 }
 
+// Correction fluxes of the current state (flow of the current step, not advanced): rho*, the
+// network, G; copied to G_out ([2][N_v^2][ny][nx] floats, device) when given.
+int ctx2d_learn_corr(Ctx2D* c, void* const f[2], int cur, float* G_out, int reuse,
+                     cudaStream_t s) {
+    if (!c->learn) return LAT_EINVAL;
+    if (c->flow_kind == LAT_FLOW_MODES && !reuse) {
+        const int rc = launch_flow(c, 0, 1, s);
+        if (rc != LAT_OK) return rc;
+    }
+    const LearnArgs la = learn_args(c, f[cur], f[cur], c->d_st0);
+    if (!reuse) CK2(launch_rho_star(c->nv, la, 0, s));
+    if (c->learn == 2) CK2(launch_mlp_tc(c->nv, la, c->d_wtc, c->sm_count, 0, s));
+    else CK2(launch_mlp_f32(c->nv, la, 0, s));
+    if (G_out) {
+        const size_t n = (size_t)2 * c->nv * c->nv * c->nx * c->ny;
+        CK2(cudaMemcpyAsync(G_out, c->d_G, sizeof(float) * n, cudaMemcpyDeviceToDevice, s));
+    }
+    return LAT_OK;
+}
+
 // Loss of an n-step rollout of the learned step (FP32 network) from the current state against
 // target, and its gradient with respect to the parameters.  The state, the flow phases and the
 // step counter are left as they were.
 int ctx2d_learn_grad(Ctx2D* c, void* const f[2], int cur, int n, const float* target,
-                     double* loss, float* grad, cudaStream_t s) {
+                     double rho_weight, double* loss, float* grad, cudaStream_t s) {
     if (!c->learn || n < 1 || n > 64 || !target || c->flow_kind == LAT_FLOW_NONE) return LAT_EINVAL;
     const long long ncell = (long long)c->nx * c->ny;
     const long long nst = ncell * c->nv * c->nv;
@@ -1398,7 +1418,7 @@ int ctx2d_learn_grad(Ctx2D* c, void* const f[2], int cur, int n, const float* ta
     const int nb = 256;
     double* dpart = nullptr;
     if (cudaMalloc(&buf, sizeof(float) * nfl) != cudaSuccess) return LAT_ENOMEM;
-    if (cudaMalloc(&dpart, sizeof(double) * (nb + 1)) != cudaSuccess) {
+    if (cudaMalloc(&dpart, sizeof(double) * (2 * nb + 1)) != cudaSuccess) {
         cudaFree(buf);
         return LAT_ENOMEM;
     }
@@ -1458,8 +1478,9 @@ int ctx2d_learn_grad(Ctx2D* c, void* const f[2], int cur, int n, const float* ta
                 fail(LAT_ECUDA);
         }
         if (rc != LAT_OK) break;
-        if (launch_loss(F + (size_t)n * nst, target, nst, lamA, dpart, nb, dpart + nb, s) !=
-                cudaSuccess ||
+        // lrho holds the density error r(x) until the backward steps reuse it
+        if (launch_loss(F + (size_t)n * nst, target, c->nv * c->nv, ncell, rho_weight, lrho, lamA,
+                        dpart, nb, dpart + 2 * nb, s) != cudaSuccess ||
             cudaMemsetAsync(g, 0, sizeof(float) * kLNParam, s) != cudaSuccess) {
             fail(LAT_ECUDA);
             break;
@@ -1488,7 +1509,7 @@ int ctx2d_learn_grad(Ctx2D* c, void* const f[2], int cur, int n, const float* ta
         if (rc != LAT_OK) break;
         if (cudaMemcpyAsync(grad, g, sizeof(float) * kLNParam, cudaMemcpyDeviceToHost, s) !=
                 cudaSuccess ||
-            cudaMemcpyAsync(loss, dpart + nb, sizeof(double), cudaMemcpyDeviceToHost, s) !=
+            cudaMemcpyAsync(loss, dpart + 2 * nb, sizeof(double), cudaMemcpyDeviceToHost, s) !=
                 cudaSuccess)
             fail(LAT_ECUDA);
     } while (false);

@@ -68,7 +68,9 @@ def _load():
         "lat_encode": (c_int, [P, P]),
         "lat_learn": (c_int, [P, POINTER(ctypes.c_float), c_int]),
         "lat_restrict": (c_int, [P, c_int, c_int, c_int, P, P]),
-        "lat_learn_grad": (c_int, [P, c_int, P, POINTER(c_double), POINTER(ctypes.c_float)]),
+        "lat_learn_corrections": (c_int, [P, P, c_int]),
+        "lat_learn_grad": (c_int, [P, c_int, P, c_double, POINTER(c_double),
+                                   POINTER(ctypes.c_float)]),
         "lat_decode": (c_int, [P, P, P]),
     }
     for name, (res, args) in sig.items():
@@ -238,13 +240,20 @@ class Lattice(_Ctx):
         _check(_lib.lat_learn(self._h, p.ctypes.data_as(POINTER(ctypes.c_float)), mode),
                "lat_learn")
 
-    def learn_grad(self, nsteps: int, target: torch.Tensor):
+    def learn_corrections(self, out: torch.Tensor | None = None, reuse_inputs: bool = False):
+        """Correction fluxes of the current state (enqueued; copied into out when given);
+        reuse_inputs runs the network alone on the previous call's flow and density."""
+        _check(_lib.lat_learn_corrections(self._h, _ptr(out), int(reuse_inputs)),
+               "lat_learn_corrections")
+        return out
+
+    def learn_grad(self, nsteps: int, target: torch.Tensor, rho_weight: float = 0.0):
         """Loss of an nsteps rollout against target (device FP32) and its gradient (numpy)."""
         if target.dtype != torch.float32 or not target.is_cuda or not target.is_contiguous():
             raise ValueError("target must be a contiguous CUDA float32 tensor")
         loss = np.zeros(1)
         grad = np.zeros(LEARN_NPARAM, dtype=np.float32)
-        _check(_lib.lat_learn_grad(self._h, nsteps, _ptr(target), _dptr(loss),
+        _check(_lib.lat_learn_grad(self._h, nsteps, _ptr(target), float(rho_weight), _dptr(loss),
                                    grad.ctypes.data_as(POINTER(ctypes.c_float))), "lat_learn_grad")
         return float(loss[0]), grad
 

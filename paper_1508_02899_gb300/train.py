@@ -97,7 +97,7 @@ def restricted_trajectory(p: Pair, nsteps: int):
 
 
 def train(pairs, trajectories, iters: int, lr: float = 1e-3, seed: int = 0, scale: float = 0.1,
-          fine_steps: int = 1, log=None) -> np.ndarray:
+          fine_steps: int = 1, rho_weight: float = 0.0, log=None) -> np.ndarray:
     """Adam on the loss of 4 * fine_steps coarse steps from a restricted state at a random fine
     step k of a random trajectory against the restricted state at k + fine_steps, normalised by
     the target's mean square so that every sample weighs alike."""
@@ -113,7 +113,7 @@ def train(pairs, trajectories, iters: int, lr: float = 1e-3, seed: int = 0, scal
         c = p.coarse
         c.f[c.current_index].copy_(states[k])
         target = states[k + fine_steps]
-        loss, g = c.learn_grad(COARSE_PER_FINE * fine_steps, target)
+        loss, g = c.learn_grad(COARSE_PER_FINE * fine_steps, target, rho_weight)
         w = 1.0 / float((target.double() ** 2).mean())
         params = opt.step(params, g.astype(np.float64) * w)
         for pp in pairs:

@@ -142,11 +142,12 @@ def test_rollout_gradient_matches_oracle(lat):
     rng = np.random.default_rng(4)
     target = Lr.rollout(c["f0"], Lr.zero_weights(), 3, c["flows"], **c["kw"])
     target = (target * (1 + 0.02 * rng.standard_normal(target.shape))).astype(np.float32)
-    loss_o, g_o = Lr.rollout_grad(c["f0"], W, 3, c["flows"], target.astype(np.float64), **c["kw"])
+    loss_o, g_o = Lr.rollout_grad(c["f0"], W, 3, c["flows"], target.astype(np.float64),
+                                  rho_weight=0.7, **c["kw"])
     lt = lattice(lat, c)
     lt.learn(pack(W), 1)
     state0 = lt.state.clone()
-    loss, g = lt.learn_grad(3, torch.tensor(target, device="cuda"))
+    loss, g = lt.learn_grad(3, torch.tensor(target, device="cuda"), 0.7)
     # the state and the step count are untouched
     assert torch.equal(lt.state, state0) and lt.steps_done == 0
     assert loss == pytest.approx(loss_o, rel=1e-5)
@@ -154,7 +155,27 @@ def test_rollout_gradient_matches_oracle(lat):
     assert np.linalg.norm(g - go) <= 1e-5 * np.linalg.norm(go), np.linalg.norm(g - go) / np.linalg.norm(go)
     # a second call gives the same numbers (the flow state was restored), up to the order of
     # the FP32 atomic additions that sum the parameter gradients over the cells
-    loss2, g2 = lt.learn_grad(3, torch.tensor(target, device="cuda"))
+    loss2, g2 = lt.learn_grad(3, torch.tensor(target, device="cuda"), 0.7)
     assert loss2 == loss
     assert np.linalg.norm(g2 - g) <= 1e-6 * np.linalg.norm(g)
+    lt.close()
+
+
+@pytest.mark.parametrize("mode,tol", [(1, 1e-5), (2, 0.03)])
+def test_corrections_match_oracle(lat, mode, tol):
+    """Correction fluxes of one state (128-cell tiles, ragged end): FP32 network to 1e-5 of their
+    norm, BF16 tensor-core network to 3 % (inputs, weights, activations rounded to 2^-8)."""
+    c = case(72, 30, 9, 1, 17)
+    W = quantised_weights(7, 0.5)
+    gx, gy = Lr.corrections(c["f0"], *c["flows"][0], W,
+                            **{k: c["kw"][k] for k in ("tau_p", "dt", "dv", "dx")})
+    want = np.stack([gx, gy])
+    lt = lattice(lat, c)
+    lt.learn(pack(W), mode)
+    out = torch.empty(want.shape, dtype=torch.float32, device="cuda")
+    lt.learn_corrections(out)
+    assert lt.status() == 0
+    got = out.double().cpu().numpy()
+    assert np.linalg.norm(got - want) <= tol * np.linalg.norm(want), (
+        np.linalg.norm(got - want) / np.linalg.norm(want))
     lt.close()

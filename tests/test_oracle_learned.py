@@ -98,7 +98,7 @@ def test_mlp_backward_matches_finite_differences():
     for k in W:
         W[k] = W[k] + 0.1 * rng.standard_normal(W[k].shape)
     dy = rng.standard_normal((11, Lr.NO))
-    y, cache = Lr.mlp_forward(X, W)
+    y, cache = Lr.mlp_forward(X, W, 0.05)
     g, dX = Lr.mlp_backward(dy, W, cache)
     h = 1e-6
     for k in ("W1", "b2", "W3"):
@@ -107,12 +107,12 @@ def test_mlp_backward_matches_finite_differences():
         Wm = {q: v.copy() for q, v in W.items()}
         Wp[k][idx] += h
         Wm[k][idx] -= h
-        fd = ((Lr.mlp_forward(X, Wp)[0] - Lr.mlp_forward(X, Wm)[0]) * dy).sum() / (2 * h)
+        fd = ((Lr.mlp_forward(X, Wp, 0.05)[0] - Lr.mlp_forward(X, Wm, 0.05)[0]) * dy).sum() / (2 * h)
         assert fd == pytest.approx(g[k][idx], rel=1e-6, abs=1e-9)
     Xp, Xm = X.copy(), X.copy()
     Xp[2, 5] += h
     Xm[2, 5] -= h
-    fd = ((Lr.mlp_forward(Xp, W)[0] - Lr.mlp_forward(Xm, W)[0]) * dy).sum() / (2 * h)
+    fd = ((Lr.mlp_forward(Xp, W, 0.05)[0] - Lr.mlp_forward(Xm, W, 0.05)[0]) * dy).sum() / (2 * h)
     assert fd == pytest.approx(dX[2, 5], rel=1e-6, abs=1e-9)
 
 
@@ -121,7 +121,8 @@ def test_rollout_gradient_matches_finite_differences():
     W = Lr.init_weights(9, scale=0.5)
     rng = np.random.default_rng(1)
     target = Lr.rollout(f0, Lr.zero_weights(), 3, flows, **kw) * (1 + 0.01 * rng.standard_normal(f0.shape))
-    L0, g = Lr.rollout_grad(f0, W, 3, flows, target, **kw)
+    beta = 0.5
+    L0, g = Lr.rollout_grad(f0, W, 3, flows, target, rho_weight=beta, **kw)
     h = 1e-6
     checked = 0
     for k, idxs in (("W1", [(0, 3), (4, 10), (13, 60), (15, 1)]), ("b1", [(5,), (40,)]),
@@ -132,8 +133,42 @@ def test_rollout_gradient_matches_finite_differences():
             Wm = {q: v.copy() for q, v in W.items()}
             Wp[k][idx] += h
             Wm[k][idx] -= h
-            fd = (Lr.loss(f0, Wp, 3, flows, target, **kw) - Lr.loss(f0, Wm, 3, flows, target, **kw)) / (2 * h)
+            fd = (Lr.loss(f0, Wp, 3, flows, target, beta, **kw)
+                  - Lr.loss(f0, Wm, 3, flows, target, beta, **kw)) / (2 * h)
             scale = max(abs(fd), 1e-3 * np.abs(g[k]).max())
             assert abs(fd - g[k][idx]) <= 1e-5 * scale, (k, idx, fd, g[k][idx])
             checked += 1
     assert checked == 13
+
+
+def test_corrections_are_the_step_difference_on_each_face():
+    # the step with corrections minus the plain step is minus the divergence of (Gx, Gy),
+    # diffused: check it against the corrections computed on their own
+    f0, flows, kw = _case(seed=12)
+    W = Lr.init_weights(4, scale=0.5)
+    Gx, Gy = Lr.corrections(f0, *flows[0], W, **{k: kw[k] for k in ("tau_p", "dt", "dv", "dx")})
+    assert np.all(Gx[:, -1] == 0) and np.all(Gy[-1] == 0)
+    fs = O.stream_2d(f0)
+    div = np.zeros_like(fs)
+    div[:, :] += Gx
+    div[:, 1:] -= Gx[:, :-1]
+    div[:, :] += Gy
+    div[1:] -= Gy[:-1]
+    want = O.diffuse_2d(O.drag_2d(fs, *flows[0], kw["tau_p"], kw["dt"], kw["dv"]) - div,
+                        kw["kappa"], kw["dt"], kw["dv"])
+    got = Lr.learned_step_2d(f0, *flows[0], W, **kw)
+    np.testing.assert_allclose(got, want, rtol=1e-13, atol=1e-15 * np.abs(want).max())
+
+
+def test_outputs_stay_inside_their_bounds():
+    # large random weights drive the outputs to their bounds: never more anti-diffusion than
+    # THETA times the face's upwind numerical diffusivity, never more diffusion than Y_MAX
+    rng = np.random.default_rng(8)
+    X = rng.standard_normal((4000, Lr.NF))
+    X[:, 13:15] = rng.uniform(-0.6, 0.6, (4000, 2))
+    W = Lr.init_weights(2, scale=20.0)
+    y, _ = Lr.mlp_forward(X, W, 0.05)
+    ca = np.abs(X[:, 13:15] - 0.025)
+    assert np.all(y <= Lr.THETA * ca * (1 - ca) / 2 + 1e-15)
+    assert np.all(y >= -Lr.Y_MAX)
+    assert y.max() > 0.5 * (Lr.THETA * ca * (1 - ca) / 2).max() and y.min() < -0.2
