@@ -50,6 +50,9 @@ def parse():
     p.add_argument("--no-forms", action="store_true")
     p.add_argument("--workload", default="ensemble",
                    choices=["ensemble", "2d", "2d_f16", "2d_bf16", "2d_learned"])
+    p.add_argument("--size", type=int, default=0,
+                   help="grid size N (N x N) of a 2D workload instead of its default "
+                        "(profiling a smaller case)")
     p.add_argument("--launch", default=None,
                    help="kernel,block,blocks_per_sm instead of autotuning (profiling runs)")
     return p.parse_args()
@@ -86,6 +89,18 @@ def job_throughput(cells_per_rank: int, steps: int, world: int, ms_max: float) -
     return world * cells_per_rank * steps / (ms_max / 1e3) / 1e9
 
 
+def parse_profile(txt: str) -> dict:
+    """The roofline inputs of an ncu summary: its `- key: value` lines."""
+    vals = {}
+    for line in txt.splitlines():
+        line = line.strip().lstrip("- ")
+        if ":" in line and line.startswith(("traffic_bytes_per_launch", "source_sha256",
+                                            "units_per_launch")):
+            k, v = line.split(":", 1)
+            vals[k.strip()] = v.strip().strip("`")
+    return vals
+
+
 def profile_traffic(kernel_file: str, src: str):
     """DRAM bytes per launch from the committed ncu summary, if it was taken on this source."""
     import hashlib
@@ -95,12 +110,7 @@ def profile_traffic(kernel_file: str, src: str):
     except OSError:
         return None
     h = hashlib.sha256(open(os.path.join(ROOT, src), "rb").read()).hexdigest()[:16]
-    vals = {}
-    for line in txt.splitlines():
-        if ":" in line and line.strip().startswith(("traffic_bytes_per_launch", "source_sha256",
-                                                    "units_per_launch")):
-            k, v = line.split(":", 1)
-            vals[k.strip().lstrip("- ")] = v.strip().strip("`")
+    vals = parse_profile(txt)
     if vals.get("source_sha256") != h or "traffic_bytes_per_launch" not in vals:
         return None
     return float(vals["traffic_bytes_per_launch"]), float(vals.get("units_per_launch", "nan"))
@@ -405,22 +415,24 @@ def main():
     nsteps = W + K + K_e2e + 2
     bytes_per_cell, lines = 8, 0
     if args.workload == "2d_learned":
-        ctx, cells, noise_row, glob, desc = build_learned(args, I, lat, torch, dev, rank, nsteps)
+        ctx, cells, noise_row, glob, desc = build_learned(args, I, lat, torch, dev, rank, nsteps,
+                                                          n=args.size or 2048)
         nv, prof, src = 9, "learn_tc_2048_nv9.md", "paper_1508_02899_gb300/csrc/learn_tc.cu"
         launches_per_step = 4  # flow, streamed density, network, corrected step
     elif args.workload == "2d":
-        ctx, cells, noise_row, glob, desc = build_2d(args, I, lat, torch, dev, rank, nsteps)
+        ctx, cells, noise_row, glob, desc = build_2d(args, I, lat, torch, dev, rank, nsteps,
+                                                     n=args.size or 512)
         nv, prof, src = 33, "step2d_512_fp32_nv33.md", "paper_1508_02899_gb300/csrc/step2d.cu"
         launches_per_step = 2  # flow evaluation + fused step
     elif args.workload in ("2d_f16", "2d_bf16"):
         store = args.workload[3:]
         ctx, cells, noise_row, glob, desc = build_2d(args, I, lat, torch, dev, rank, nsteps,
-                                                     n=1024, store=store)
+                                                     n=args.size or 1024, store=store)
         nv = 33
         prof = f"step2d_1024_{store}_nv33.md"
         src = "paper_1508_02899_gb300/csrc/step2d_h.cu"
         launches_per_step = 3  # flow evaluation + output scales + fused step
-        bytes_per_cell, lines = 4, nv * nv * 1024
+        bytes_per_cell, lines = 4, nv * nv * (args.size or 1024)
     else:
         ctx, cells, noise_row, glob, desc = build_ensemble(args, I, lat, torch, dev, rank, nsteps)
         nv, prof, src = NV, "step1d_ensemble_fp32_nv65.md", "paper_1508_02899_gb300/csrc/step1d.cu"

@@ -184,7 +184,8 @@ int lat_encode(lat_ctx* c, const float* src);
  * scales, [jy][jx][y] floats, to the DEVICE array scales (may be NULL).  Synchronises. */
 int lat_decode(lat_ctx* c, float* dst, float* scales);
 /*
- * Learned flux closure on a coarse 2D lattice (d = 2, LAT_F32, N_v in {3, 5, 9, 13, 17}).  The
+ * Learned flux closure on a coarse 2D lattice (d = 2, LAT_F32, N_v in {3, 5, 9, 13, 17},
+ * N_x and N_y > (N_v + 1)/2, N_v^2 N_x N_y < 2^32; LAT_EINVAL otherwise).  The
  * paper proposes large-eddy closures for the lattice (Section 5); this library's closure adds
  * learned fluxes to the upwind drag fluxes of every interior velocity face, so mass is kept
  * exactly.  Per phase-space cell (x, j) after streaming, 16 features: f*(x, j + d)/rho*(x) for

@@ -24,10 +24,7 @@ namespace {
 
 using namespace k2d;
 
-__device__ __forceinline__ int vwrap(int v, int n) {
-    v %= n;
-    return v < 0 ? v + n : v;
-}
+__device__ __forceinline__ int vwrap(int v, int n) { return wrap_near(v, n); }
 
 // f*(x, y, jx, jy) of buffer f = f(x - (jx - J), y - (jy - J), jx, jy)
 template <int NV>
@@ -45,7 +42,7 @@ __global__ void __launch_bounds__(256) k_rho_star(const LearnArgs a, int kstep) 
     const long long ncell = (long long)a.nx * a.ny;
     for (long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x; c < ncell;
          c += (long long)gridDim.x * blockDim.x) {
-        const int y = (int)(c / a.nx), x = (int)(c % a.nx);
+        const int y = (int)((unsigned)c / (unsigned)a.nx), x = (int)((unsigned)c - (unsigned)y * a.nx);
         float s = 0.f;
         for (int jy = 0; jy < NV; ++jy)
             for (int jx = 0; jx < NV; ++jx) s = __fadd_rn(s, fstar<NV>(f, jx, jy, x, y, a.nx, a.ny));
@@ -152,10 +149,9 @@ __global__ void __launch_bounds__(128) k_mlp_f32(const LearnArgs a, int kstep) {
     const long long n = ncell * NV * NV;
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
          i += (long long)gridDim.x * blockDim.x) {
-        const int p = (int)(i / ncell);
-        const long long c = i % ncell;
+        int p, x, y;
+        split_index((unsigned)i, (unsigned)ncell, (unsigned)a.nx, p, x, y);
         const int jy = p / NV, jx = p % NV;
-        const int y = (int)(c / a.nx), x = (int)(c % a.nx);
         float X[kLNF], h1[kLNH], z2[kLNH];
         Nbr nb;
         features<NV>(a, f, jx, jy, x, y, X, nb);
@@ -266,10 +262,10 @@ __global__ void __launch_bounds__(kBT, 1) k_mlp_bwd(const LearnBwdArgs b) {
     for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
         const long long i = tile * kBT + t;
         if (i < n) {
-            const int p = (int)(i / ncell);
-            const long long c = i % ncell;
+            int p, x, y;
+            split_index((unsigned)i, (unsigned)ncell, (unsigned)a.nx, p, x, y);
+            const long long c = (long long)y * a.nx + x;
             const int jy = p / NV, jx = p % NV;
-            const int y = (int)(c / a.nx), x = (int)(c % a.nx);
             float X[kLNF];
             Nbr nb;
             const float inv = features<NV>(a, f, jx, jy, x, y, X, nb);
@@ -395,10 +391,9 @@ __global__ void __launch_bounds__(256) k_gather_adjoint(const LearnBwdArgs b) {
     const long long n = ncell * NV * NV;
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
          i += (long long)gridDim.x * blockDim.x) {
-        const int p = (int)(i / ncell);
-        const long long c = i % ncell;
+        int p, x, y;
+        split_index((unsigned)i, (unsigned)ncell, (unsigned)nx, p, x, y);
         const int jy = p / NV, jx = p % NV;
-        const int y = (int)(c / nx), x = (int)(c % nx);
         // f^n at (x, y) of plane p streams to (x + jx - J, y + jy - J)
         const long long cs = (long long)vwrap(y + (jy - J), ny) * nx + vwrap(x + (jx - J), nx);
         const long long is = (long long)p * ncell + cs;

@@ -45,6 +45,21 @@ struct LearnArgs {
     float dt_2dx;          // dt / (2 dx): centred differences of u times dt
 };
 
+// Periodic wrap of v = i + d with |d| < n (the learned step needs N_x, N_y > J).
+__device__ __forceinline__ int wrap_near(int v, int n) {
+    v += v < 0 ? n : 0;
+    return v >= n ? v - n : v;
+}
+
+// Phase-cell index i (< 2^32) -> plane p and spatial cell (x, y), 32-bit divisions.
+__device__ __forceinline__ void split_index(unsigned i, unsigned ncell, unsigned nx, int& p, int& x,
+                                            int& y) {
+    p = (int)(i / ncell);
+    const unsigned c = i - (unsigned)p * ncell;
+    y = (int)(c / nx);
+    x = (int)(c - (unsigned)y * nx);
+}
+
 bool learn_nv_supported(int nv);
 cudaError_t launch_rho_star(int nv, const LearnArgs& a, int k, cudaStream_t s);
 cudaError_t launch_mlp_f32(int nv, const LearnArgs& a, int k, cudaStream_t s);

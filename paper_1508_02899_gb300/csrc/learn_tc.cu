@@ -4,10 +4,15 @@
 // A CTA of 128 threads takes tiles of 128 phase-space cells (one cell per thread = one row of
 // the M = 128 MMA tile).  Per tile: every thread builds its row of features (FP32 -> BF16) in
 // shared memory; one thread issues layer 1 (K = 16, N = 64), the CTA waits on the commit's
-// mbarrier, reads its accumulator rows (tcgen05.ld), adds the bias, applies ReLU and writes the
-// BF16 activations back as the next A operand; layer 2 (K = 64, N = 64) and layer 3 (K = 64,
-// N = 16 with two live outputs) the same way; the outputs y = kYMax tanh(z) times the density
-// differences across the +jx and +jy faces are the corrections.
+// mbarrier, reads its accumulator row (tcgen05.ld) and writes relu(.) as BF16 (one
+// cvt.rn.relu.bf16x2 per pair) back as the next A operand; layer 2 (K = 80, N = 64) and layer 3
+// (K = 80, N = 16 with two live outputs) the same way; the bounded outputs y = b tanh(z) times
+// the density differences across the +jx and +jy faces are the corrections.
+//
+// Biases ride in the products: feature 15 is the constant 1, so b1 joins row 15 of W1; the
+// activation tiles carry a constant 1 in column 64 (columns 65..79 zero, K padded to a multiple
+// of 16), so b2 and b3 join row 64 of W2 and W3.  The three layers share one 64-column TMEM
+// accumulator (each is read before the next MMA writes), so five CTAs fit an SM.
 //
 // Operand layout (no swizzle, K-major): a tile of R rows by K columns is stored as 8 x 8 core
 // matrices of 128 contiguous bytes (8 rows of 8 BF16); the stride between core matrices along
@@ -27,19 +32,21 @@ namespace {
 using namespace k2d;
 
 // byte offsets inside the packed parameter image (global memory and shared memory alike)
-constexpr int kW1T = 0;                       // B of layer 1: N 64 x K 16 (2 KB)
-constexpr int kW2T = kW1T + 64 * 16 * 2;      // B of layer 2: N 64 x K 64 (8 KB)
-constexpr int kW3T = kW2T + 64 * 64 * 2;      // B of layer 3: N 16 x K 64 (2 KB), rows >= 2 zero
-constexpr int kBias = kW3T + 16 * 64 * 2;     // FP32 b1 [64], b2 [64], b3 [2] (+2 pad)
-constexpr int kImage = kBias + (64 + 64 + 4) * 4;
-// shared memory of the kernel: image, A1 (128 x 16), A2 (128 x 64), barrier, TMEM address
+constexpr int kK2 = 80;                       // K of layers 2 and 3: 64 activations, 1, zeros
+constexpr int kW1T = 0;                       // B of layer 1: N 64 x K 16 (2 KB), b1 in k = 15
+constexpr int kW2T = kW1T + 64 * 16 * 2;      // B of layer 2: N 64 x K 80 (10 KB), b2 in k = 64
+constexpr int kW3T = kW2T + 64 * kK2 * 2;     // B of layer 3: N 16 x K 80 (2.5 KB), b3 in k = 64
+constexpr int kImage = kW3T + 16 * kK2 * 2;
+// shared memory of the kernel: image, A1 (128 x 16), A2 (128 x 80), barrier, TMEM address
 constexpr int kSA1 = (kImage + 1023) / 1024 * 1024;
 constexpr int kSA2 = kSA1 + 128 * 16 * 2;
-constexpr int kSBar = kSA2 + 128 * 64 * 2;
+constexpr int kSBar = kSA2 + 128 * kK2 * 2;
 constexpr int kSmem = kSBar + 16;
-// Requested per CTA: at most 4 CTAs per SM, so that their TMEM (4 x 128 columns) always fits.
-constexpr int kSmemReq = kSmem > 48 * 1024 ? kSmem : 48 * 1024;
-constexpr int kTmemCols = 128;                // D1 / D3 at columns 0.., D2 at 64..
+constexpr int kSmemReq = kSmem;
+constexpr int kTmemCols = 64;                 // D1, D2, D3 in turn (D3: columns 0..15)
+static_assert(kImage % 16 == 0, "image copied in 16-byte pieces");
+static_assert((228 * 1024) / (kSmemReq + 1024) * kTmemCols <= 512,
+              "the CTAs that fit an SM by shared memory must also fit its TMEM");
 
 __host__ __device__ constexpr unsigned tile_off(int r, int k, int rows) {
     // element (r, k) of a K-major no-swizzle tile with `rows` rows: SBO 128, LBO rows/8 * 128
@@ -99,9 +106,8 @@ __device__ __forceinline__ bool wait_parity(uint64_t* bar, unsigned parity) {
     return false;
 }
 
-// 16 consecutive accumulator columns of this thread's row
-__device__ __forceinline__ void tmem_ld16(unsigned taddr, float (&v)[16]) {
-    unsigned r[16];
+// 16 consecutive accumulator columns of this thread's row (completion: tmem_wait)
+__device__ __forceinline__ void tmem_ld16(unsigned taddr, unsigned (&r)[16]) {
     asm volatile(
         "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,"
         "%15}, [%16];"
@@ -109,9 +115,9 @@ __device__ __forceinline__ void tmem_ld16(unsigned taddr, float (&v)[16]) {
           "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
           "=r"(r[14]), "=r"(r[15])
         : "r"(taddr));
+}
+__device__ __forceinline__ void tmem_wait() {
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
 
 __device__ __forceinline__ void tmem_ld2(unsigned taddr, float& a, float& b) {
@@ -129,67 +135,107 @@ __device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
     return *reinterpret_cast<const uint32_t*>(&h);
 }
 
-// bias + ReLU of 64 accumulator columns of this thread's row into row r of a 128 x 64 A tile
-__device__ __forceinline__ void epilogue64(unsigned taddr, const float* bias, unsigned char* A,
-                                           int r) {
+// relu(lo), relu(hi) rounded to BF16 and packed (lo in the low half)
+__device__ __forceinline__ uint32_t pack_relu_bf16(float lo, float hi) {
+    uint32_t d;
+    asm("cvt.rn.relu.bf16x2.f32 %0, %1, %2;" : "=r"(d) : "f"(hi), "f"(lo));
+    return d;
+}
+
+// ReLU of 64 accumulator columns of this thread's row into row r of a 128-row A tile; the
+// columns come in two groups of 32 (two loads in flight per wait)
+__device__ __forceinline__ void epilogue64(unsigned taddr, unsigned char* A, int r) {
 #pragma unroll
-    for (int c0 = 0; c0 < 64; c0 += 16) {
-        float v[16];
-        tmem_ld16(taddr + c0, v);
+    for (int c0 = 0; c0 < 64; c0 += 32) {
+        unsigned v[2][16];
+        tmem_ld16(taddr + c0, v[0]);
+        tmem_ld16(taddr + c0 + 16, v[1]);
+        tmem_wait();
 #pragma unroll
-        for (int h = 0; h < 2; ++h) {  // two 8-column core-matrix chunks
+        for (int g = 0; g < 4; ++g) {  // four 8-column core-matrix chunks
+            const unsigned* u = v[g >> 1] + 8 * (g & 1);
             uint4 w;
-            const int k = c0 + 8 * h;
-            w.x = pack_bf16(fmaxf(v[8 * h + 0] + bias[k + 0], 0.f), fmaxf(v[8 * h + 1] + bias[k + 1], 0.f));
-            w.y = pack_bf16(fmaxf(v[8 * h + 2] + bias[k + 2], 0.f), fmaxf(v[8 * h + 3] + bias[k + 3], 0.f));
-            w.z = pack_bf16(fmaxf(v[8 * h + 4] + bias[k + 4], 0.f), fmaxf(v[8 * h + 5] + bias[k + 5], 0.f));
-            w.w = pack_bf16(fmaxf(v[8 * h + 6] + bias[k + 6], 0.f), fmaxf(v[8 * h + 7] + bias[k + 7], 0.f));
-            *reinterpret_cast<uint4*>(A + tile_off(r, k, 128)) = w;
+            w.x = pack_relu_bf16(__uint_as_float(u[0]), __uint_as_float(u[1]));
+            w.y = pack_relu_bf16(__uint_as_float(u[2]), __uint_as_float(u[3]));
+            w.z = pack_relu_bf16(__uint_as_float(u[4]), __uint_as_float(u[5]));
+            w.w = pack_relu_bf16(__uint_as_float(u[6]), __uint_as_float(u[7]));
+            *reinterpret_cast<uint4*>(A + tile_off(r, c0 + 8 * g, 128)) = w;
         }
     }
 }
 
-__device__ __forceinline__ int vwrap(int v, int n) {
-    v %= n;
-    return v < 0 ? v + n : v;
+// tanh on the special-function unit (tanh.approx.f32: relative error about 2^-11, far below the
+// BF16 rounding the network already carries)
+__device__ __forceinline__ float tanh_fast(float x) {
+    float y;
+    asm("tanh.approx.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
 }
 
-// Features of phase cell (jx, jy, x, y), as in learn.cu.
+__device__ __forceinline__ int vwrap(int v, int n) { return wrap_near(v, n); }
+
+// Raw inputs of one phase cell's features (learn.cu's features, split so that the global loads
+// can be issued early and consumed after other work): f* over the 3 x 3 velocity neighbourhood,
+// rho*, and u at the cell and at its four spatial neighbours.  Element indices are 32-bit (the
+// learned step keeps N_v^2 N_x N_y below 2^32) and periodic wraps are one conditional add.
+struct Raw {
+    float fs[9];
+    float rho;
+    float uxc, uyc, uxe, uxw, uxn, uxs, uye, uyw, uyn, uys;
+};
+
 template <int NV>
-__device__ __forceinline__ void features_tc(const LearnArgs& a, const float* f, int jx, int jy,
-                                            int x, int y, float (&X)[kLNF], float& fc,
-                                            float& fxp, float& fyp) {
+__device__ __forceinline__ void load_raw(const LearnArgs& a, const float* f, int jx, int jy, int x,
+                                         int y, Raw& r) {
     constexpr int J = (NV - 1) / 2;
-    const size_t ncell = (size_t)a.nx * a.ny;
-    const float rho = a.rho[(size_t)y * a.nx + x];
-    const float inv = rho != 0.f ? __frcp_rn(rho) : 0.f;
+    const unsigned nx = (unsigned)a.nx, ncell = (unsigned)a.nx * (unsigned)a.ny;
+    const unsigned c = (unsigned)y * nx + (unsigned)x;
+    r.rho = a.rho[c];
     int q = 0;
 #pragma unroll
-    for (int dy = -1; dy <= 1; ++dy)
+    for (int dy = -1; dy <= 1; ++dy) {
+        const int jy2 = jy + dy;
+        const bool iny = jy2 >= 0 && jy2 < NV;
+        const unsigned row = (unsigned)vwrap(y - (jy2 - J), a.ny) * nx;  // source row of plane row jy2
 #pragma unroll
         for (int dx = -1; dx <= 1; ++dx) {
-            const int jx2 = jx + dx, jy2 = jy + dy;
-            const bool in = jx2 >= 0 && jx2 < NV && jy2 >= 0 && jy2 < NV;
-            float v = 0.f;
-            if (in)
-                v = f[(size_t)(jy2 * NV + jx2) * ncell + (size_t)vwrap(y - (jy2 - J), a.ny) * a.nx +
-                      vwrap(x - (jx2 - J), a.nx)];
-            if (dy == 0 && dx == 0) fc = v;
-            if (dy == 0 && dx == 1) fxp = v;
-            if (dy == 1 && dx == 0) fyp = v;
-            X[q++] = __fmul_rn(v, inv);
+            const int jx2 = jx + dx;
+            const bool in = iny && jx2 >= 0 && jx2 < NV;
+            r.fs[q++] = in ? f[(unsigned)(jy2 * NV + jx2) * ncell + row +
+                               (unsigned)vwrap(x - (jx2 - J), a.nx)]
+                           : 0.f;
         }
+    }
     const float* ux = a.u;
     const float* uy = a.u + ncell;
-    const size_t c = (size_t)y * a.nx + x;
-    const int xp = x + 1 == a.nx ? 0 : x + 1, xm = x == 0 ? a.nx - 1 : x - 1;
-    const int yp = y + 1 == a.ny ? 0 : y + 1, ym = y == 0 ? a.ny - 1 : y - 1;
-    X[9] = __fmul_rn(__fsub_rn(ux[(size_t)y * a.nx + xp], ux[(size_t)y * a.nx + xm]), a.dt_2dx);
-    X[10] = __fmul_rn(__fsub_rn(ux[(size_t)yp * a.nx + x], ux[(size_t)ym * a.nx + x]), a.dt_2dx);
-    X[11] = __fmul_rn(__fsub_rn(uy[(size_t)y * a.nx + xp], uy[(size_t)y * a.nx + xm]), a.dt_2dx);
-    X[12] = __fmul_rn(__fsub_rn(uy[(size_t)yp * a.nx + x], uy[(size_t)ym * a.nx + x]), a.dt_2dx);
-    X[13] = __fmul_rn(a.g, __fsub_rn(__fmul_rn(ux[c], a.inv_dv), (float)(jx - J)));
-    X[14] = __fmul_rn(a.g, __fsub_rn(__fmul_rn(uy[c], a.inv_dv), (float)(jy - J)));
+    const unsigned xp = x + 1 == a.nx ? 0u : (unsigned)x + 1, xm = x == 0 ? nx - 1 : (unsigned)x - 1;
+    const unsigned yp = y + 1 == a.ny ? 0u : (unsigned)y + 1, ym = y == 0 ? (unsigned)a.ny - 1 : (unsigned)y - 1;
+    const unsigned yr = (unsigned)y * nx;
+    r.uxc = ux[c];
+    r.uyc = uy[c];
+    r.uxe = ux[yr + xp];
+    r.uxw = ux[yr + xm];
+    r.uxn = ux[yp * nx + x];
+    r.uxs = ux[ym * nx + x];
+    r.uye = uy[yr + xp];
+    r.uyw = uy[yr + xm];
+    r.uyn = uy[yp * nx + x];
+    r.uys = uy[ym * nx + x];
+}
+
+template <int NV>
+__device__ __forceinline__ void features_of(const LearnArgs& a, const Raw& r, int jx, int jy,
+                                            float (&X)[kLNF]) {
+    constexpr int J = (NV - 1) / 2;
+    const float inv = r.rho != 0.f ? __frcp_rn(r.rho) : 0.f;
+#pragma unroll
+    for (int q = 0; q < 9; ++q) X[q] = __fmul_rn(r.fs[q], inv);
+    X[9] = __fmul_rn(__fsub_rn(r.uxe, r.uxw), a.dt_2dx);
+    X[10] = __fmul_rn(__fsub_rn(r.uxn, r.uxs), a.dt_2dx);
+    X[11] = __fmul_rn(__fsub_rn(r.uye, r.uyw), a.dt_2dx);
+    X[12] = __fmul_rn(__fsub_rn(r.uyn, r.uys), a.dt_2dx);
+    X[13] = __fmul_rn(a.g, __fsub_rn(__fmul_rn(r.uxc, a.inv_dv), (float)(jx - J)));
+    X[14] = __fmul_rn(a.g, __fsub_rn(__fmul_rn(r.uyc, a.inv_dv), (float)(jy - J)));
     X[15] = 1.f;
 }
 
@@ -205,6 +251,13 @@ __global__ void __launch_bounds__(128) k_mlp_tc(const LearnArgs a, const unsigne
     const int t = threadIdx.x, warp = t >> 5;
     for (int i = t; i < kImage / 16; i += blockDim.x)
         reinterpret_cast<uint4*>(W)[i] = reinterpret_cast<const uint4*>(image)[i];
+    {   // the constant columns 64..79 of this thread's activation row: 1, then zeros
+        uint4 one;
+        one.x = pack_bf16(1.f, 0.f);
+        one.y = one.z = one.w = 0u;
+        *reinterpret_cast<uint4*>(A2 + tile_off(t, 64, 128)) = one;
+        *reinterpret_cast<uint4*>(A2 + tile_off(t, 72, 128)) = make_uint4(0u, 0u, 0u, 0u);
+    }
     if (t == 0) {
         asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(su32(bar)) : "memory");
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -222,9 +275,6 @@ __global__ void __launch_bounds__(128) k_mlp_tc(const LearnArgs a, const unsigne
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const unsigned tmem = *tslot;
     const unsigned trow = tmem + ((unsigned)(warp * 32) << 16);  // this warp's lanes
-    const float* b1 = reinterpret_cast<const float*>(W + kBias);
-    const float* b2 = b1 + 64;
-    const float* b3 = b2 + 64;
     const unsigned wbase = su32(W), a1 = su32(A1), a2 = su32(A2);
     const float* f = a.f[(int)((a.st->step + kstep) & 1)];
     const long long ncell = (long long)a.nx * a.ny;
@@ -232,20 +282,39 @@ __global__ void __launch_bounds__(128) k_mlp_tc(const LearnArgs a, const unsigne
     const long long ntiles = (n + 127) / 128;
     unsigned phase = 0;
     bool failed = false;
-    for (long long tile = blockIdx.x; tile < ntiles && !failed; tile += gridDim.x) {
-        const long long i = tile * 128 + t;
-        const bool on = i < n;
-        float X[kLNF], fc = 0.f, fxp = 0.f, fyp = 0.f;
-        int jx = 0, jy = 0;
-        if (on) {
-            const int p = (int)(i / ncell);
-            const long long c = i % ncell;
-            jy = p / NV;
-            jx = p % NV;
-            features_tc<NV>(a, f, jx, jy, (int)(c % a.nx), (int)(c / a.nx), X, fc, fxp, fyp);
+    const bool row_tiles = a.nx % 128 == 0;
+    // One tile's cell for this thread: raw inputs loaded early, features formed late.
+    struct Cell {
+        Raw r;
+        int jx, jy;
+        long long i;
+        bool on;
+    };
+    auto load = [&](long long tile, Cell& q) {
+        q.i = tile * 128 + t;
+        q.on = tile < ntiles && q.i < n;
+        q.jx = q.jy = 0;
+        if (q.on) {
+            int p, x, y;
+            if (row_tiles) {  // the tile is 128 consecutive x of one row of one plane
+                split_index((unsigned)(tile * 128), (unsigned)ncell, (unsigned)a.nx, p, x, y);
+                x += t;
+            } else {
+                split_index((unsigned)q.i, (unsigned)ncell, (unsigned)a.nx, p, x, y);
+            }
+            q.jy = p / NV;
+            q.jx = p % NV;
+            load_raw<NV>(a, f, q.jx, q.jy, x, y, q.r);
+        }
+    };
+    // features of q into A1 (zeros past the end); X kept for the output bounds
+    float Xc[kLNF];
+    auto store_a1 = [&](const Cell& q, float (&X)[kLNF]) {
+        if (q.on) {
+            features_of<NV>(a, q.r, q.jx, q.jy, X);
         } else {
 #pragma unroll
-            for (int q = 0; q < kLNF; ++q) X[q] = 0.f;
+            for (int k = 0; k < kLNF; ++k) X[k] = 0.f;
         }
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
@@ -256,72 +325,84 @@ __global__ void __launch_bounds__(128) k_mlp_tc(const LearnArgs a, const unsigne
             w.w = pack_bf16(X[8 * h + 6], X[8 * h + 7]);
             *reinterpret_cast<uint4*>(A1 + tile_off(t, 8 * h, 128)) = w;
         }
-        // layer 1: D[0..63] = A1 (128 x 16) W1^T
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    };
+    // Wait for the MMAs committed last: warp 0 polls the mbarrier, the others block in the CTA
+    // barrier (no issue slots spent spinning); false on a timeout, for every thread.
+    auto wait_mma = [&]() -> bool {
+        bool ok = true;
+        if (warp == 0) ok = wait_parity(bar, phase);
+        phase ^= 1;
+        const bool bad = __syncthreads_or(!ok);
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        return !bad;
+    };
+    auto sync_for_mma = [&]() {
         asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
         __syncthreads();
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    };
+    Cell cur, nxt;
+    long long tile = blockIdx.x;
+    load(tile, cur);
+    store_a1(cur, Xc);
+    for (; tile < ntiles; tile += gridDim.x) {
+        // layer 1: D = A1 (128 x 16) W1^T, while the next tile's features load
+        sync_for_mma();
         if (t == 0) {
             mma(tmem, sdesc(a1, 2048, 128), sdesc(wbase + kW1T, 1024, 128), idesc_n(64), 0);
             commit(bar);
         }
-        bool ok = wait_parity(bar, phase);
-        phase ^= 1;
-        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        if (ok) epilogue64(trow, b1, A2, t);
-        // layer 2: D[64..127] = H1 (128 x 64) W2^T
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-        if (__syncthreads_or(!ok)) {
+        load(tile + gridDim.x, nxt);
+        if (!wait_mma()) {
             failed = true;
             break;
         }
-        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        epilogue64(trow, A2, t);
+        // layer 2: D = [H1 1 0] (128 x 80) W2^T; A1 is free again: stage the next features
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        sync_for_mma();
         if (t == 0) {
-            for (int kk = 0; kk < 4; ++kk)
-                mma(tmem + 64, sdesc(a2 + kk * 2 * 2048, 2048, 128),
+            for (int kk = 0; kk < kK2 / 16; ++kk)
+                mma(tmem, sdesc(a2 + kk * 2 * 2048, 2048, 128),
                     sdesc(wbase + kW2T + kk * 2 * 1024, 1024, 128), idesc_n(64), kk);
             commit(bar);
         }
-        ok = wait_parity(bar, phase);
-        phase ^= 1;
-        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        if (ok) epilogue64(trow + 64, b2, A2, t);  // MMA 2 is done with A2: overwrite with H2
-        // layer 3: D[0..15] = H2 (128 x 64) W3^T
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-        if (__syncthreads_or(!ok)) {
+        float Xn[kLNF];
+        store_a1(nxt, Xn);
+        if (!wait_mma()) {
             failed = true;
             break;
         }
-        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        epilogue64(trow, A2, t);  // MMA 2 is done with A2: overwrite with H2
+        // layer 3: D[0..15] = [H2 1 0] (128 x 80) W3^T
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        sync_for_mma();
         if (t == 0) {
-            for (int kk = 0; kk < 4; ++kk)
+            for (int kk = 0; kk < kK2 / 16; ++kk)
                 mma(tmem, sdesc(a2 + kk * 2 * 2048, 2048, 128),
                     sdesc(wbase + kW3T + kk * 2 * 256, 256, 128), idesc_n(16), kk);
             commit(bar);
         }
-        ok = wait_parity(bar, phase);
-        phase ^= 1;
-        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        if (ok) {
-            float y0, y1;
-            tmem_ld2(trow, y0, y1);
-            if (on) {
-                const float z0 = y0 + b3[0], z1 = y1 + b3[1];
-                y0 = __fmul_rn(z0 > 0.f ? anti_bound(X[13], a.g) : kYMax, tanhf(z0));
-                y1 = __fmul_rn(z1 > 0.f ? anti_bound(X[14], a.g) : kYMax, tanhf(z1));
-                a.G[i] = jx < NV - 1 ? __fmul_rn(y0, __fsub_rn(fxp, fc)) : 0.f;
-                a.G[n + i] = jy < NV - 1 ? __fmul_rn(y1, __fsub_rn(fyp, fc)) : 0.f;
-            }
-        }
-        // every thread is done with the accumulators and A2 before the next tile's MMAs
-        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-        if (__syncthreads_or(!ok)) {
+        if (!wait_mma()) {
             failed = true;
             break;
         }
-        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        float z0, z1;
+        tmem_ld2(trow, z0, z1);
+        if (cur.on) {
+            const float y0 = __fmul_rn(z0 > 0.f ? anti_bound(Xc[13], a.g) : kYMax, tanh_fast(z0));
+            const float y1 = __fmul_rn(z1 > 0.f ? anti_bound(Xc[14], a.g) : kYMax, tanh_fast(z1));
+            const unsigned gi = (unsigned)cur.i;
+            // f* of the cell and of its +jx, +jy neighbours: entries 4, 5 and 7 of the 3 x 3 block
+            a.G[gi] = cur.jx < NV - 1 ? __fmul_rn(y0, __fsub_rn(cur.r.fs[5], cur.r.fs[4])) : 0.f;
+            a.G[(size_t)n + gi] =
+                cur.jy < NV - 1 ? __fmul_rn(y1, __fsub_rn(cur.r.fs[7], cur.r.fs[4])) : 0.f;
+        }
+        cur = nxt;
+#pragma unroll
+        for (int k = 0; k < kLNF; ++k) Xc[k] = Xn[k];
+        // the next layer-1 MMA (after sync_for_mma) overwrites D only once every thread has read it
     }
     if (failed && t == 0) atomicOr(const_cast<unsigned*>(&a.st->status), ST_TIMEOUT);
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -332,27 +413,29 @@ __global__ void __launch_bounds__(128) k_mlp_tc(const LearnArgs a, const unsigne
                      : "memory");
 }
 
-// Parameter image: BF16 B operands of the three layers and the FP32 biases.
+// Parameter image: the BF16 B operands of the three layers, biases folded in (b1 into row 15 of
+// W1, which meets the constant feature 1; b2 and b3 into row 64 of W2 and W3, which meets the
+// constant activation column).
 __global__ void k_pack(const float* P, unsigned char* img) {
-    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < 64 * 16 + 64 * 64 + 16 * 64;
+    const int n1 = 64 * 16, n2 = 64 * kK2, n3 = 16 * kK2;
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n1 + n2 + n3;
          e += gridDim.x * blockDim.x) {
-        if (e < 64 * 16) {  // W1T [n][k] = W1[k][n]
+        if (e < n1) {  // W1T [n][k] = W1[k][n] (+ b1[n] at k = 15)
             const int nn = e / 16, k = e % 16;
-            *reinterpret_cast<__nv_bfloat16*>(img + kW1T + tile_off(nn, k, 64)) =
-                __float2bfloat16_rn(P[kOffW1 + k * kLNH + nn]);
-        } else if (e < 64 * 16 + 64 * 64) {
-            const int q = e - 64 * 16, nn = q / 64, k = q % 64;
-            *reinterpret_cast<__nv_bfloat16*>(img + kW2T + tile_off(nn, k, 64)) =
-                __float2bfloat16_rn(P[kOffW2 + k * kLNH + nn]);
+            float w = P[kOffW1 + k * kLNH + nn];
+            if (k == 15) w += P[kOffB1 + nn];
+            *reinterpret_cast<__nv_bfloat16*>(img + kW1T + tile_off(nn, k, 64)) = __float2bfloat16_rn(w);
+        } else if (e < n1 + n2) {
+            const int q = e - n1, nn = q / kK2, k = q % kK2;
+            const float w = k < 64 ? P[kOffW2 + k * kLNH + nn] : (k == 64 ? P[kOffB2 + nn] : 0.f);
+            *reinterpret_cast<__nv_bfloat16*>(img + kW2T + tile_off(nn, k, 64)) = __float2bfloat16_rn(w);
         } else {
-            const int q = e - 64 * 16 - 64 * 64, nn = q / 64, k = q % 64;
-            *reinterpret_cast<__nv_bfloat16*>(img + kW3T + tile_off(nn, k, 16)) =
-                __float2bfloat16_rn(nn < kLNO ? P[kOffW3 + k * kLNO + nn] : 0.f);
+            const int q = e - n1 - n2, nn = q / kK2, k = q % kK2;
+            float w = 0.f;
+            if (nn < kLNO) w = k < 64 ? P[kOffW3 + k * kLNO + nn] : (k == 64 ? P[kOffB3 + nn] : 0.f);
+            *reinterpret_cast<__nv_bfloat16*>(img + kW3T + tile_off(nn, k, 16)) = __float2bfloat16_rn(w);
         }
     }
-    float* bias = reinterpret_cast<float*>(img + kBias);
-    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < 64 + 64 + 4; e += gridDim.x * blockDim.x)
-        bias[e] = e < 64 ? P[kOffB1 + e] : (e < 128 ? P[kOffB2 + e - 64] : (e < 130 ? P[kOffB3 + e - 128] : 0.f));
 }
 
 }  // namespace

@@ -1364,6 +1364,11 @@ int ctx2d_learn_set(Ctx2D* c, const float* params, int mode, cudaStream_t s) {
     }
     if ((mode != 1 && mode != 2) || !params || c->dtype != LAT_F32 || !learn_nv_supported(c->nv))
         return LAT_EINVAL;
+    const int J = (c->nv - 1) / 2;
+    // the kernels wrap streamed indices with one conditional add; nv^2 nx ny indexes in 32 bits
+    if (c->nx <= J + 1 || c->ny <= J + 1 ||
+        (long long)c->nx * c->ny * c->nv * c->nv >= (1ll << 32) - 256)
+        return LAT_EINVAL;
     if (mode == 2 && !learn_tc_supported(c->nv)) return LAT_EINVAL;
     const long long ncell = (long long)c->nx * c->ny;
     if (!c->d_params) {

@@ -54,3 +54,19 @@ def test_binding_marshals_structs_like_the_header():
     assert ctypes.sizeof(lat.LatInstance) == 40
     assert lat.LatFlow.field.offset == 8 and lat.LatFlow.k.offset == 24
     assert ctypes.sizeof(lat.LatFlow) == 64
+
+
+def test_committed_profiles_carry_their_roofline_inputs():
+    """Every ncu summary that states a traffic figure also states the units it covers and the
+    source hash it was taken on, in the form bench.py reads."""
+    import bench
+    prof = os.path.join(bench.ROOT, "profiles")
+    found = 0
+    for name in sorted(os.listdir(prof)):
+        vals = bench.parse_profile(open(os.path.join(prof, name)).read())
+        if "traffic_bytes_per_launch" in vals:
+            found += 1
+            assert float(vals["traffic_bytes_per_launch"]) > 0
+            assert float(vals["units_per_launch"]) > 0
+            assert re.fullmatch(r"[0-9a-f]{16}", vals["source_sha256"])
+    assert found >= 3
