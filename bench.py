@@ -378,12 +378,15 @@ def kernel_label(workload, best, nv):
     k = best["kernel"] if best else 0
     if workload in ("2d_f16", "2d_bf16"):
         t = "__half" if workload == "2d_f16" else "__nv_bfloat16"
-        return (f"k_step2d_pch<{t},{nv},{4 if k == 4 else 3}>" if k >= 4
-                else f"k_step2d_plain_h<{t},{nv}>")
+        if k >= 4:
+            return {4: f"k_step2d_pch<{t},{nv},4,false>", 5: f"k_step2d_pch<{t},{nv},3,false>",
+                    6: f"k_step2d_pch<{t},{nv},3,true>", 7: f"k_step2d_pch<{t},{nv},2,true>"}[k]
+        return f"k_step2d_plain_h<{t},{nv}>"
     if workload == "2d":
         if k >= 3:
-            return {3: f"k_step2d_pc<{nv},4,false>", 4: f"k_step2d_pc<{nv},4,true>",
-                    5: f"k_step2d_pc<{nv},3,true>"}[k]
+            return {3: f"k_step2d_pc<{nv},4,false,false>", 4: f"k_step2d_pc<{nv},4,true,false>",
+                    5: f"k_step2d_pc<{nv},3,true,false>", 6: f"k_step2d_pc<{nv},3,true,true>",
+                    7: f"k_step2d_pc<{nv},2,true,true>"}[k]
         return f"k_step2d_{'ring' if k == 2 else 'plain'}<{nv}>"
     if k >= 5:
         return f"k_step1d_pc<{nv},{k - 3}>"

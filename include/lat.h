@@ -239,9 +239,10 @@ long long lat_steps_done(const lat_ctx* c);
  *                 5..7 producer warp + consumer warps on a ring of 2..4 slots (no barrier).
  *          d = 2: 2 ring refilled after a block barrier (block = 128 C threads splits each
  *                 cell's jx range over C = 1..4 warp groups);
- *                 3..5 producer warp + consumer warps (3: vy-flux row in registers, 4 slots;
- *                 4: in shared memory, 4 slots; 5: in shared memory, 3 slots).
- *          d = 2 with 16-bit storage: 1 plain loads (any size); 4 and 5 as above (N_x a
+ *                 3..7 producer warp + consumer warps (3: vy-drag flux row in registers,
+ *                 4 slots; 4: in shared memory, 4 slots; 5: in shared memory, 3 slots; 6: the
+ *                 vy-diffusion flux row in shared memory too, 3 slots; 7: as 6, 2 slots).
+ *          d = 2 with 16-bit storage: 1 plain loads (any size); 4..7 as above (N_x a
  *                 multiple of 8 and >= 136, N_v >= 9).
  *  block:  threads per block (= x cells per tile) for kernel 1; the copy pipelines fix a 128-cell
  *          tile (2D kernel 2: 128 C threads); 0 keeps.

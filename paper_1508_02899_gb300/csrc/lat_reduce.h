@@ -37,6 +37,16 @@ struct FComp {
         c = __fsub_rn(__fsub_rn(t, s), y);
         s = t;
     }
+    // s + x by Knuth's branch-free TwoSum (t + e = s + x exactly), e folded into c: unlike add(),
+    // no rounding of x is lost, so s - c keeps the sum to the roundings of c (about n u^2 of the
+    // sum after n terms) where Kahan's add() can lose up to about 2u.
+    __device__ __forceinline__ void add_exact(float x) {
+        const float t = __fadd_rn(s, x);
+        const float bb = __fsub_rn(t, s);
+        const float e = __fadd_rn(__fsub_rn(s, __fsub_rn(t, bb)), __fsub_rn(x, bb));
+        s = t;
+        c = __fsub_rn(c, e);
+    }
     // (s - c) + (o.s - o.c): s + o.s by Knuth's branch-free TwoSum (t + e exactly, whatever the
     // magnitudes), then both error terms and e fold into c.  Only the rounding of c is lost,
     // about u^2 of the partial sums per merge (u = 2^-24).
@@ -67,20 +77,27 @@ __device__ __forceinline__ void warp_reduce(Comp& t) {
     for (int off = 16; off > 0; off >>= 1) nmerge(t, shfl_down(t, off));
 }
 
-// Column sums of one 1D column [sum f, sum j f, sum j^2 f] accumulated in FP32 (Kahan) and
-// returned as FP64 compensated values scaled to [M0, M1 = sum v f, M2 = sum v^2 f] / dv.
+// Column sums of one 1D column [sum f, sum j f, sum j^2 f] in FP32, returned as FP64
+// compensated values scaled to [M0, M1 = sum v f, M2 = sum v^2 f] / dv.  The mass sum is exact
+// up to the roundings of its compensation term (TwoSum, add_exact).  The two weighted sums take
+// one FMA per value (the product j f or j^2 f exact inside it, one rounding of the running
+// sum): error at most (N_v - 1) u of sum |j^k f| (u = 2^-24), the accuracy of the FP32 state
+// itself, at far fewer instructions than compensating them too.
 struct ColumnSums {
-    FComp a0, a1, a2;
+    FComp a0;
+    float b1 = 0.f, b2 = 0.f;
     __device__ __forceinline__ void add(float j, float fv) {
-        a0.add(fv);
-        a1.add(j * fv);
-        a2.add(j * j * fv);
+        a0.add_exact(fv);
+        b1 = __fmaf_rn(j, fv, b1);
+        b2 = __fmaf_rn(j * j, fv, b2);
     }
+    __device__ __forceinline__ FComp a1() const { return FComp{b1, 0.f}; }
+    __device__ __forceinline__ FComp a2() const { return FComp{b2, 0.f}; }
     __device__ __forceinline__ void result(double dv, Comp& s0, Comp& s1, Comp& s2) const {
         const double dv2 = __dmul_rn(dv, dv);
         s0 = Comp{(double)a0.s, -(double)a0.c};
-        s1 = Comp{__dmul_rn((double)a1.s, dv), -__dmul_rn((double)a1.c, dv)};
-        s2 = Comp{__dmul_rn((double)a2.s, dv2), -__dmul_rn((double)a2.c, dv2)};
+        s1 = Comp{__dmul_rn((double)b1, dv), 0.0};
+        s2 = Comp{__dmul_rn((double)b2, dv2), 0.0};
     }
 };
 
@@ -94,11 +111,11 @@ __device__ __forceinline__ void warp_reduce3(Comp& t0, Comp& t1, Comp& t2) {
     }
 }
 
-// Per-warp partial of the 1D moments of FP32 columns: every lane holds the Kahan column sums of
-// its column (zero for an inactive lane); lane 0 writes [M, P, E] (sum, compensation) scaled to
+// Per-warp partial of the 1D moments of FP32 columns: every lane holds the column sums of its
+// column (zero for an inactive lane); lane 0 writes [M, P, E] (sum, compensation) scaled to
 // [1, dv, dv^2] at p.  The cross-column part stays in FP32 Kahan form (FP64 is slow here).
 __device__ __forceinline__ void warp_partial_1d(const ColumnSums& cs_, double dv, double* p) {
-    FComp a0 = cs_.a0, a1 = cs_.a1, a2 = cs_.a2;
+    FComp a0 = cs_.a0, a1 = cs_.a1(), a2 = cs_.a2();
     warp_reduce(a0);
     warp_reduce(a1);
     warp_reduce(a2);

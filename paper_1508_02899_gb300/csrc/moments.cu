@@ -20,8 +20,9 @@ using namespace cs;
 
 // One block (one thread per column of a work item's tile, blockDim = tile width) per item,
 // grid-stride over items.  Every warp writes one partial per item: partials[item][warp][6].
-//  FP32 storage: column sums in FP32 Kahan form (exact integer weights j, j^2), cross-column
-//    sums per warp in FP32 Kahan form, FP64 from the warp partials on (FP64 is slow here).
+//  FP32 storage: column sums in FP32 (ColumnSums: mass compensated, weights j, j^2 by FMA),
+//    cross-column sums per warp in FP32 compensated form, FP64 from the warp partials on (FP64
+//    is slow here).
 //  FP64 storage: Neumaier FP64 throughout.
 template <typename T>
 __global__ void __launch_bounds__(1024) k_moments1d(const Mom1DArgs a, const int xpt) {
@@ -69,13 +70,15 @@ __global__ void __launch_bounds__(1024) k_moments1d(const Mom1DArgs a, const int
                     bad |= !isfinite(fv);
                     sums.add((float)(jj - J), fv);
                 }
-                Comp s0, s1, s2;
-                sums.result(in.dv, s0, s1, s2);
-                const double m0 = nval(s0), m1 = nval(s1), m2 = nval(s2);
-                const long long cell = in.xoff + x;
-                if (a.rho) a.rho[cell] = m0 * in.dv;
-                if (a.mean_v) a.mean_v[cell] = (m0 != 0.0) ? m1 / m0 : 0.0;
-                if (a.mean_v2) a.mean_v2[cell] = (m0 != 0.0) ? m2 / m0 : 0.0;
+                if (a.rho || a.mean_v || a.mean_v2) {  // FP64 per cell only when asked for
+                    Comp s0, s1, s2;
+                    sums.result(in.dv, s0, s1, s2);
+                    const double m0 = nval(s0), m1 = nval(s1), m2 = nval(s2);
+                    const long long cell = in.xoff + x;
+                    if (a.rho) a.rho[cell] = m0 * in.dv;
+                    if (a.mean_v) a.mean_v[cell] = (m0 != 0.0) ? m1 / m0 : 0.0;
+                    if (a.mean_v2) a.mean_v2[cell] = (m0 != 0.0) ? m2 / m0 : 0.0;
+                }
             }
             warp_partial_1d(sums, in.dv, p);
         }
@@ -114,7 +117,7 @@ constexpr int kNoAllocTile = 128;
 // Every GPU that loads this library holds this array until the process exits.
 static __device__ __align__(256) double g_noalloc_partials[LAT_NOALLOC_MAX_TILES * 6];
 
-// One block per 128-column tile: FP32 Kahan column sums, Neumaier over the tile's columns.
+// One block per 128-column tile: FP32 column sums (ColumnSums), Neumaier over the tile's columns.
 __global__ void __launch_bounds__(kNoAllocTile)
     k_moments1d_noalloc(const float* f, int nv, int nx, double dv, double* partials) {
     __shared__ Comp red[3][kNoAllocTile / 32];
@@ -122,18 +125,9 @@ __global__ void __launch_bounds__(kNoAllocTile)
     const int x = blockIdx.x * kNoAllocTile + threadIdx.x;
     Comp t0{0, 0}, t1{0, 0}, t2{0, 0};
     if (x < nx) {
-        FComp a0, a1, a2;
-        for (int jj = 0; jj < nv; ++jj) {
-            const float fv = f[(size_t)jj * nx + x];
-            const float j = (float)(jj - J);
-            a0.add(fv);
-            a1.add(j * fv);
-            a2.add(j * j * fv);
-        }
-        const double dv2 = __dmul_rn(dv, dv);
-        t0 = Comp{(double)a0.s, -(double)a0.c};
-        t1 = Comp{__dmul_rn((double)a1.s, dv), -__dmul_rn((double)a1.c, dv)};
-        t2 = Comp{__dmul_rn((double)a2.s, dv2), -__dmul_rn((double)a2.c, dv2)};
+        ColumnSums sums;
+        for (int jj = 0; jj < nv; ++jj) sums.add((float)(jj - J), f[(size_t)jj * nx + x]);
+        sums.result(dv, t0, t1, t2);
     }
     for (int off = 16; off > 0; off >>= 1) {
         Comp o0 = shfl_down(t0, off), o1 = shfl_down(t1, off), o2 = shfl_down(t2, off);

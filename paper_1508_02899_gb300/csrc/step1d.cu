@@ -424,7 +424,7 @@ size_t pc1d_smem() {
 }
 
 // With MOM the consumers also reduce the moments of the columns they write (the same FP32
-// Kahan column sums, in the same order, as the moment kernel; compensated FP64 across cells).
+// column sums, in the same order, as the moment kernel; compensated across cells).
 template <int NV, int NS, bool MOM = false>
 __global__ void __launch_bounds__(PC1_THREADS) k_step1d_pc(const Step1DArgs a, const int kstep) {
     constexpr int J = (NV - 1) / 2;
@@ -493,14 +493,18 @@ __global__ void __launch_bounds__(PC1_THREADS) k_step1d_pc(const Step1DArgs a, c
         if (lane == 0) mbar_arrive(&empty[k % NS]);
         if constexpr (MOM) {  // same per-warp partials as the moment kernel with 128 columns
             if (x < in.nx) {
-                cs::Comp t0, t1, t2;
-                sums.result(in.dv, t0, t1, t2);
-                const double m0 = cs::nval(t0), m1 = cs::nval(t1), m2 = cs::nval(t2);
-                if (!isfinite(m0) || !isfinite(m2)) atomicOr(&a.st->status, ST_NUMERIC);
-                const long long cell = in.xoff + x;
-                if (a.m_rho) a.m_rho[cell] = m0 * in.dv;
-                if (a.m_mv) a.m_mv[cell] = (m0 != 0.0) ? m1 / m0 : 0.0;
-                if (a.m_mv2) a.m_mv2[cell] = (m0 != 0.0) ? m2 / m0 : 0.0;
+                if (!isfinite(sums.a0.s) || !isfinite(sums.b2))
+                    atomicOr(&a.st->status, ST_NUMERIC);
+                // per-cell moments in FP64 only when asked for (FP64 is slow here)
+                if (a.m_rho || a.m_mv || a.m_mv2) {
+                    cs::Comp t0, t1, t2;
+                    sums.result(in.dv, t0, t1, t2);
+                    const double m0 = cs::nval(t0), m1 = cs::nval(t1), m2 = cs::nval(t2);
+                    const long long cell = in.xoff + x;
+                    if (a.m_rho) a.m_rho[cell] = m0 * in.dv;
+                    if (a.m_mv) a.m_mv[cell] = (m0 != 0.0) ? m1 / m0 : 0.0;
+                    if (a.m_mv2) a.m_mv2[cell] = (m0 != 0.0) ? m2 / m0 : 0.0;
+                }
             }
             cs::warp_partial_1d(sums, in.dv,
                                 a.m_partials + ((size_t)it * PC1_CONSUMERS + warp) * 6);

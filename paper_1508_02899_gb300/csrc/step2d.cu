@@ -358,27 +358,51 @@ __global__ void __launch_bounds__(RingShape<NV, C>::threads, RingShape<NV, C>::m
 // per-slot "full" mbarrier the bulk copies complete.  Warps drift freely within the ring's slack.
 // With GSM the vy-drag flux row G lives in shared memory (private per thread) instead of
 // registers, which lowers register pressure and raises occupancy.
-template <int NV, int NS, bool GSM>
+// Producer warp of the producer/consumer kernels: fill f (row f % NV of the block's tile f / NV)
+// goes to slot f % NS once the consumers released that slot's previous content (fill f - NS).
+template <int NV, int NS, class TileOf>
+__device__ __forceinline__ void produce_rows(const Step2DArgs& a, const float* fin, float* ring,
+                                             uint64_t* full, uint64_t* empty, long long total,
+                                             const TileOf& tile_of) {
+    const int lane = threadIdx.x & 31;
+    long long f = 0;
+    for (; f < total; ++f) {
+        const int q = (int)(f % NS);
+        if (f >= NS && !mbar_wait_bounded(&empty[q], (unsigned)(((f / NS) + 1) & 1))) {
+            if (lane == 0) atomicOr(&a.st->status, ST_TIMEOUT);
+            break;
+        }
+        issue_row<NV>(a, fin, ring, full, q, tile_of(f), (int)(f % NV));
+    }
+    // the copies issued last must land before this warp leaves (the block may finish early)
+    for (long long d = std::max(0ll, f - NS); d < f; ++d)
+        mbar_wait_bounded(&full[d % NS], (unsigned)((d / NS) & 1));
+}
+
+template <int NV, int NS, bool GSM, bool HSM = false>
 struct PCShape {
     static constexpr int consumers = TW / 32;
     static constexpr int threads = 32 * (consumers + 1);
-    static constexpr int min_blocks = (GSM && NS == 3) ? 3 : 2;
+    static constexpr int min_blocks = HSM ? (NS == 2 ? 3 : 2) : ((GSM && NS == 3) ? 3 : 2);
 };
 
-template <int NV, int NS, bool GSM>
+template <int NV, int NS, bool GSM, bool HSM = false>
 size_t pc_smem() {
     return (size_t)NS * NV * WIN * sizeof(float) + (GSM ? (size_t)NV * TW * sizeof(float) : 0) +
-           2 * NS * sizeof(uint64_t);
+           (HSM ? (size_t)NV * TW * sizeof(float) : 0) + 2 * NS * sizeof(uint64_t);
 }
 
-template <int NV, int NS, bool GSM>
-__global__ void __launch_bounds__(PCShape<NV, NS, GSM>::threads, PCShape<NV, NS, GSM>::min_blocks)
+// HSM: the vy-diffusion flux row H in shared memory too (fewer registers, no spills).
+template <int NV, int NS, bool GSM, bool HSM>
+__global__ void __launch_bounds__(PCShape<NV, NS, GSM, HSM>::threads,
+                                  PCShape<NV, NS, GSM, HSM>::min_blocks)
     k_step2d_pc(const Step2DArgs a, int kstep) {
-    constexpr int NC = PCShape<NV, NS, GSM>::consumers;
+    constexpr int NC = PCShape<NV, NS, GSM, HSM>::consumers;
     extern __shared__ __align__(128) unsigned char smem[];
     float* ring = reinterpret_cast<float*>(smem);
     float* gsm = ring + (size_t)NS * NV * WIN;
-    uint64_t* full = reinterpret_cast<uint64_t*>(gsm + (GSM ? NV * TW : 0));
+    float* hsm = gsm + (GSM ? NV * TW : 0);
+    uint64_t* full = reinterpret_cast<uint64_t*>(hsm + (HSM ? NV * TW : 0));
     uint64_t* empty = full + NS;
     const long long step = a.st->step + kstep;
     const int par = (int)(step & 1);
@@ -399,20 +423,7 @@ __global__ void __launch_bounds__(PCShape<NV, NS, GSM>::threads, PCShape<NV, NS,
     }
     __syncthreads();
     if (warp == NC) {
-        // producer: fill f goes to slot f % NS once the consumers released that slot's previous
-        // content (fill f - NS)
-        long long f = 0;
-        for (; f < total; ++f) {
-            const int q = (int)(f % NS);
-            if (f >= NS && !mbar_wait_bounded(&empty[q], (unsigned)(((f / NS) + 1) & 1))) {
-                if (lane == 0) atomicOr(&a.st->status, ST_TIMEOUT);
-                break;
-            }
-            issue_row<NV>(a, fin, ring, full, q, tile_of(f), (int)(f % NV));
-        }
-        // the copies issued last must land before this warp leaves (the block may finish early)
-        for (long long d = std::max(0ll, f - NS); d < f; ++d)
-            mbar_wait_bounded(&full[d % NS], (unsigned)((d / NS) & 1));
+        produce_rows<NV, NS>(a, fin, ring, full, empty, total, tile_of);
         return;
     }
     const int cell = threadIdx.x;
@@ -426,12 +437,13 @@ __global__ void __launch_bounds__(PCShape<NV, NS, GSM>::threads, PCShape<NV, NS,
         float wx, wy;
         load_w<float>(a, x, y, wx, wy);
         cfl_check<float, NV>(a, g, wx, wy, active);
-        float A[NV], H[NV], Greg[NV];
-        SmemCol Gs{gsm + cell};
+        float A[NV], Hreg[NV], Greg[NV];
+        SmemCol Gs{gsm + cell}, Hs{hsm + cell};
 #pragma unroll
         for (int j = 0; j < NV; ++j) {
             A[j] = 0.f;
-            H[j] = 0.f;
+            if (HSM) Hs[j] = 0.f;
+            else Hreg[j] = 0.f;
             if (GSM) Gs[j] = 0.f;
             else Greg[j] = 0.f;
         }
@@ -446,13 +458,17 @@ __global__ void __launch_bounds__(PCShape<NV, NS, GSM>::threads, PCShape<NV, NS,
             if (r >= 1) {
                 const RingRow<NV> cur{ring + (size_t)((s - 1) % NS) * NV * WIN + cell};
                 const RingRow<NV> nxt{ring + (size_t)(s % NS) * NV * WIN + cell};
-                if (GSM) sweep_row<float, NV>(A, Gs, H, r, cur, nxt, g, wx, wy, rr, put);
-                else sweep_row<float, NV>(A, Greg, H, r, cur, nxt, g, wx, wy, rr, put);
+                if constexpr (HSM) sweep_row<float, NV>(A, Gs, Hs, r, cur, nxt, g, wx, wy, rr, put);
+                else if constexpr (GSM) sweep_row<float, NV>(A, Gs, Hreg, r, cur, nxt, g, wx, wy, rr, put);
+                else sweep_row<float, NV>(A, Greg, Hreg, r, cur, nxt, g, wx, wy, rr, put);
                 __syncwarp();
                 if (lane == 0) mbar_arrive(&empty[(s - 1) % NS]);  // row s - 1 is done
             }
         }
-        if (!failed) final_row<float, NV>(A, H, rr, put);
+        if (!failed) {
+            if constexpr (HSM) final_row<float, NV>(A, Hs, rr, put);
+            else final_row<float, NV>(A, Hreg, rr, put);
+        }
     }
     if (failed && lane == 0) atomicOr(&a.st->status, ST_TIMEOUT);
 }
@@ -574,35 +590,50 @@ __global__ void __launch_bounds__(256) k_moments2d(const void* fv, const float* 
                 p[2 * q + 1] = z.c;
             }
     } else {
+        // per cell: the mass exact up to the roundings of its compensation (TwoSum per velocity
+        // row, rows merged); the weighted sums one FMA per value (the integer weights exact, the
+        // product exact inside the FMA), error at most (N_v^2 - 1) u of the sum of
+        // |weight f|, u = 2^-24
         FComp t[4];
         for (long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x; c < ncell;
              c += (long long)gridDim.x * blockDim.x) {
-            FComp s[4];
+            FComp s0;
+            float s1 = 0.f, s2 = 0.f, s3 = 0.f;
             // scales of this cell's row: [jy][jx padded]
             const float* sc_c = scales ? scales + (size_t)(c / nx) * nv * nv_padded(nv) : nullptr;
             for (int jy = 0; jy < nv; ++jy) {
                 const float fy = (float)(jy - J);
+                const float fy2 = fy * fy;
+                FComp ey;         // sum f of the velocity row
+                float ex = 0.f;   // sum jx f of the velocity row
 #pragma unroll 4
                 for (int jx = 0; jx < nv; ++jx) {
                     const float fx = (float)(jx - J);
                     const size_t plane = (size_t)jy * nv + jx;
                     float fvv = (float)f[plane * ncell + c];
                     if (sc_c) fvv = fvv * sc_c[jy * nv_padded(nv) + jx];  // exact: powers of two
-                    bad |= !isfinite(fvv);
-                    s[0].add(fvv);
-                    s[1].add(fx * fvv);
-                    s[2].add(fy * fvv);
-                    s[3].add((fx * fx + fy * fy) * fvv);
+                    ey.add_exact(fvv);
+                    ex = __fmaf_rn(fx, fvv, ex);
+                    s3 = __fmaf_rn(__fmaf_rn(fx, fx, fy2), fvv, s3);
                 }
+                s0.merge(ey);
+                s1 = __fadd_rn(s1, ex);
+                s2 = __fmaf_rn(fy, __fsub_rn(ey.s, ey.c), s2);
             }
-            const double m0 = nval(s[0].to_comp(1.0));
-            if (rho) rho[c] = m0 * dv2;
-            if (mv) {
-                mv[c] = m0 != 0.0 ? nval(s[1].to_comp(dv)) / m0 : 0.0;
-                mv[ncell + c] = m0 != 0.0 ? nval(s[2].to_comp(dv)) / m0 : 0.0;
+            bad |= !isfinite(s0.s) || !isfinite(s3);
+            if (rho || mv || mv2) {  // FP64 per cell only when asked for (FP64 is slow here)
+                const double m0 = nval(s0.to_comp(1.0));
+                if (rho) rho[c] = m0 * dv2;
+                if (mv) {
+                    mv[c] = m0 != 0.0 ? __dmul_rn((double)s1, dv) / m0 : 0.0;
+                    mv[ncell + c] = m0 != 0.0 ? __dmul_rn((double)s2, dv) / m0 : 0.0;
+                }
+                if (mv2) mv2[c] = m0 != 0.0 ? __dmul_rn((double)s3, dv2) / m0 : 0.0;
             }
-            if (mv2) mv2[c] = m0 != 0.0 ? nval(s[3].to_comp(dv2)) / m0 : 0.0;
-            for (int q = 0; q < 4; ++q) t[q].merge(s[q]);
+            t[0].merge(s0);
+            t[1].merge(FComp{s1, 0.f});
+            t[2].merge(FComp{s2, 0.f});
+            t[3].merge(FComp{s3, 0.f});
         }
         for (int q = 0; q < 4; ++q) warp_reduce(t[q]);
         __shared__ FComp wsum[kMom2DWarps][4];
@@ -730,31 +761,32 @@ int occupancy_ring_c(int chunks) {
 }
 
 // Producer/consumer variants: 3 = G in registers, 4-slot ring; 4 = G in shared memory, 4 slots;
-// 5 = G in shared memory, 3 slots.
+// 5 = G in shared memory, 3 slots; 6 = G and H in shared memory, 3 slots; 7 = the same, 2 slots.
 #define LAT2D_PC(n) ((n) >= 9)
 
-template <int NV, int NS, bool GSM>
+template <int NV, int NS, bool GSM, bool HSM = false>
 cudaError_t launch_pc(int grid, const Step2DArgs& a, int k, cudaStream_t s) {
     static bool attr = false;
+    const size_t bytes = pc_smem<NV, NS, GSM, HSM>();
     if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute(k_step2d_pc<NV, NS, GSM>,
+        cudaError_t e = cudaFuncSetAttribute(k_step2d_pc<NV, NS, GSM, HSM>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)pc_smem<NV, NS, GSM>());
+                                             (int)bytes);
         if (e != cudaSuccess) return e;
         attr = true;
     }
-    k_step2d_pc<NV, NS, GSM><<<grid, PCShape<NV, NS, GSM>::threads, pc_smem<NV, NS, GSM>(), s>>>(a, k);
+    k_step2d_pc<NV, NS, GSM, HSM><<<grid, PCShape<NV, NS, GSM, HSM>::threads, bytes, s>>>(a, k);
     return cudaGetLastError();
 }
 
-template <int NV, int NS, bool GSM>
+template <int NV, int NS, bool GSM, bool HSM = false>
 int occupancy_pc_t() {
     int nb = 0;
-    cudaFuncSetAttribute(k_step2d_pc<NV, NS, GSM>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)pc_smem<NV, NS, GSM>());
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_step2d_pc<NV, NS, GSM>,
-                                                  PCShape<NV, NS, GSM>::threads,
-                                                  pc_smem<NV, NS, GSM>());
+    const size_t bytes = pc_smem<NV, NS, GSM, HSM>();
+    cudaFuncSetAttribute(k_step2d_pc<NV, NS, GSM, HSM>,
+                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_step2d_pc<NV, NS, GSM, HSM>,
+                                                  PCShape<NV, NS, GSM, HSM>::threads, bytes);
     return nb;
 }
 
@@ -764,6 +796,8 @@ cudaError_t launch_pc_v(int v, int grid, const Step2DArgs& a, int k, cudaStream_
         if (v == 3) return launch_pc<NV, 4, false>(grid, a, k, s);
         if (v == 4) return launch_pc<NV, 4, true>(grid, a, k, s);
         if (v == 5) return launch_pc<NV, 3, true>(grid, a, k, s);
+        if (v == 6) return launch_pc<NV, 3, true, true>(grid, a, k, s);
+        if (v == 7) return launch_pc<NV, 2, true, true>(grid, a, k, s);
     }
     return cudaErrorInvalidValue;
 }
@@ -774,6 +808,8 @@ int occupancy_pc_v(int v) {
         if (v == 3) return occupancy_pc_t<NV, 4, false>();
         if (v == 4) return occupancy_pc_t<NV, 4, true>();
         if (v == 5) return occupancy_pc_t<NV, 3, true>();
+        if (v == 6) return occupancy_pc_t<NV, 3, true, true>();
+        if (v == 7) return occupancy_pc_t<NV, 2, true, true>();
     }
     return 0;
 }
@@ -840,7 +876,7 @@ struct Ctx2D {
     // launch
     bool ring = false;
     int chunks = 1;    // warp groups per cell column in the ring kernel
-    int pcv = 0;       // 0: ring kernel; 3..5: producer/consumer variant
+    int pcv = 0;       // 0: ring kernel; 3..7: producer/consumer variant
     int bps = 0;       // 0 = occupancy limit
     int mode = 0;      // 0 graph, 2 direct launches
     // reduced-precision storage: per-line scales and maxima, [2][N_v^2 N_y] each
@@ -1242,8 +1278,8 @@ int ctx2d_moments(Ctx2D* c, const void* f, int cur, double* rho, double* mean_v,
 int ctx2d_set_launch(Ctx2D* c, int kernel, int block, int bps, int mode) {
     // kernel: 0 keep, 1 plain loads (128 threads), >= 2 bulk-copy ring; for the ring, block =
     // 128 C threads splits every cell's jx range over C warp groups (C = 1..4)
-    // kernel 3..5: producer/consumer variants (block fixed at 160 threads)
-    if (kernel < 0 || kernel > 5) return LAT_EINVAL;
+    // kernel 3..7: producer/consumer variants (block fixed at 160 threads)
+    if (kernel < 0 || kernel > 7) return LAT_EINVAL;
     if (c->half && (kernel == 2 || kernel == 3)) return LAT_EINVAL;
     if (kernel >= 2 && !ring_ok(c)) return LAT_EINVAL;
     if (c->half && kernel >= 4 && !pc_ok(c)) return LAT_EINVAL;
@@ -1283,12 +1319,12 @@ int ctx2d_autotune(Ctx2D* c, void* const f[2], int reps, double* best, cudaStrea
     double best_us = 1e300;
     bool best_ring = c->ring;
     int best_bps = c->bps, best_chunks = c->chunks, best_pcv = c->pcv;
-    // variant 0: plain loads; 1..4: ring with that many chunks; 5..7: producer/consumer 3..5
-    for (int variant = 0; variant <= 7; ++variant) {
+    // variant 0: plain loads; 1..4: ring with that many chunks; 5..9: producer/consumer 3..7
+    for (int variant = 0; variant <= 9; ++variant) {
         if (variant > 0 && !ring_ok(c)) continue;
         if (variant >= 1 && variant <= 4 && !chunks_supported(c->nv, variant)) continue;
         if (variant >= 5 && !pc_ok(c)) continue;
-        if (c->half && (variant >= 1 && variant <= 5)) continue;  // 16-bit: plain, pc 4, pc 5
+        if (c->half && (variant >= 1 && variant <= 5)) continue;  // 16-bit: plain, pc 4..7
         for (int bps : {1, 2, 3, 4, 6, 8}) {
             c->ring = variant > 0;
             c->chunks = (variant >= 1 && variant <= 4) ? variant : 1;

@@ -133,9 +133,10 @@ struct NoCorr {
 };
 
 // The output goes through `put`: put.begin(row) before output row `row`, then put(o) for
-// jx = 0..NV-1 in order (StorePut for FP32/FP64 storage).
-template <typename T, int NV, class Row, class GArr, class Put, class Corr = NoCorr>
-__device__ __forceinline__ void sweep_row(T (&A)[NV], GArr& G, T (&H)[NV], int r,
+// jx = 0..NV-1 in order (StorePut for FP32/FP64 storage).  G (vy-drag flux row) and H
+// (vy-diffusion flux row) are register arrays or per-thread shared-memory columns (SmemCol).
+template <typename T, int NV, class Row, class GArr, class HArr, class Put, class Corr = NoCorr>
+__device__ __forceinline__ void sweep_row(T (&A)[NV], GArr& G, HArr& H, int r,
                                           const Row& cur, const Row& nxt_row, T g_in, T wx_in,
                                           T wy, T rr, Put& put, const Corr& corr = Corr()) {
     using O = Ops<T>;
@@ -178,8 +179,8 @@ __device__ __forceinline__ void sweep_row(T (&A)[NV], GArr& G, T (&H)[NV], int r
 }
 
 // Last output row (jy = J): no f** row above it, so the vy-diffusion flux there is zero.
-template <typename T, int NV, class Put>
-__device__ __forceinline__ void final_row(T (&A)[NV], T (&H)[NV], T rr, Put& put) {
+template <typename T, int NV, class HArr, class Put>
+__device__ __forceinline__ void final_row(T (&A)[NV], HArr& H, T rr, Put& put) {
     using O = Ops<T>;
     T Dprev = T(0);
     put.begin(NV - 1);

@@ -248,12 +248,13 @@ struct PCHShape {
     static constexpr int min_blocks = 3;
 };
 
-template <typename S, int NV, int NS>
+// HSM: the vy-diffusion flux row H in shared memory as well, right after G.
+template <typename S, int NV, int NS, bool HSM = false>
 struct PCHLayout {
     static constexpr int NVP = nv_padded(NV);
     static constexpr int NLP = NV * NVP;  // padded output lines of a tile
     static constexpr size_t ring = (size_t)NS * NV * kWinH * sizeof(S);
-    static constexpr size_t gsm = (size_t)NV * TW * sizeof(float);
+    static constexpr size_t gsm = (size_t)(HSM ? 2 : 1) * NV * TW * sizeof(float);
     static constexpr size_t dsc = (size_t)NS * NVP * sizeof(float);
     static constexpr size_t enc = (size_t)2 * NLP * sizeof(float);
     static constexpr size_t mxs = (size_t)2 * NLP * sizeof(unsigned);
@@ -346,10 +347,61 @@ __device__ __forceinline__ void issue_row_h(const Step2DArgs& a, const S* fin, S
     }
 }
 
-template <typename S, int NV, int NS>
+// Producer warp of the 16-bit producer/consumer kernels (NT threads per block): fills the ring,
+// copies the scales, and flushes the tiles' line maxima (tile t - 2 when tile t starts, the last
+// two after every consumer is done).
+template <typename S, int NV, int NS, int NT, class TileOf>
+__device__ __forceinline__ void produce_rows_h(const Step2DArgs& a, const S* fin, S* ring,
+                                               uint64_t* full, uint64_t* empty, float* dsc,
+                                               const float* s_in, const float* s_out, float* enc,
+                                               unsigned* mxs, unsigned* m_out, int ntl,
+                                               const TileOf& tile_of) {
+    constexpr int NLP = NV * nv_padded(NV);
+    const int lane = threadIdx.x & 31;
+    const long long total = (long long)ntl * NV;
+    auto flush = [&](int t) {  // tile t's maxima to global memory; clear the buffer
+        const int yt = tile_of((long long)t * NV) / a.ntx;
+        unsigned* m = mxs + (t & 1) * NLP;
+        unsigned* g_row = m_out + (size_t)yt * NLP;
+        for (int i = lane; i < NLP; i += 32) {
+            const unsigned v = m[i];
+            if (v) atomicMax(&g_row[i], v);
+            m[i] = 0u;
+        }
+        __syncwarp();
+    };
+    int flushed = 0;  // tiles below this one are flushed
+    long long f = 0;
+    for (; f < total; ++f) {
+        const int q = (int)(f % NS);
+        if (f >= NS && !mbar_wait_bounded(&empty[q], (unsigned)(((f / NS) + 1) & 1))) {
+            if (lane == 0) atomicOr(&a.st->status, ST_TIMEOUT);
+            break;
+        }
+        const int t = (int)(f / NV);
+        if (f % NV == 0 && t >= 2) {
+            // every consumer warp has released fill f - NS (a row of tile t - 1, NS <= NV), so
+            // all of them are past tile t - 2, the previous user of these buffers; the
+            // generic-proxy writes of the flush and the async copies below touch disjoint
+            // buffers (maxima vs scales)
+            flush(t - 2);
+            flushed = t - 1;
+        }
+        issue_row_h<S, NV>(a, fin, ring, full, dsc, s_in, s_out, enc + (t & 1) * NLP, q,
+                           tile_of(f), (int)(f % NV));
+    }
+    for (long long d = std::max(0ll, f - NS); d < f; ++d)
+        mbar_wait_bounded(&full[d % NS], (unsigned)((d / NS) & 1));
+    // wait for the consumers, then flush the tiles not flushed yet
+    asm volatile("bar.sync 1, %0;" ::"r"(NT) : "memory");
+    for (int t = flushed; t < ntl; ++t)
+        if (t >= ntl - 2) flush(t);
+}
+
+template <typename S, int NV, int NS, bool HSM>
 __global__ void __launch_bounds__(PCHShape<NV, NS>::threads, PCHShape<NV, NS>::min_blocks)
     k_step2d_pch(const Step2DHArgs ha, int kstep) {
-    using Lay = PCHLayout<S, NV, NS>;
+    using Lay = PCHLayout<S, NV, NS, HSM>;
     constexpr int NC = PCHShape<NV, NS>::consumers;
     constexpr int NVP = Lay::NVP;
     constexpr int NLP = Lay::NLP;
@@ -373,7 +425,6 @@ __global__ void __launch_bounds__(PCHShape<NV, NS>::threads, PCHShape<NV, NS>::m
     const size_t ps = (size_t)a.nx * a.ny;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int ntl = a.ntiles > (int)blockIdx.x ? (a.ntiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
-    const long long total = (long long)ntl * NV;
     auto tile_of = [&](long long s) { return (int)(blockIdx.x + (s / NV) * gridDim.x); };
     for (int i = threadIdx.x; i < 2 * NLP; i += blockDim.x) mxs[i] = 0u;
     if (threadIdx.x == 0) {
@@ -385,44 +436,9 @@ __global__ void __launch_bounds__(PCHShape<NV, NS>::threads, PCHShape<NV, NS>::m
     }
     __syncthreads();
     if (warp == NC) {
-        // producer
-        auto flush = [&](int t) {  // tile t's maxima to global memory; clear the buffer
-            const int yt = tile_of((long long)t * NV) / a.ntx;
-            unsigned* m = mxs + (t & 1) * NLP;
-            unsigned* g_row = m_out + (size_t)yt * NLP;
-            for (int i = lane; i < NLP; i += 32) {
-                const unsigned v = m[i];
-                if (v) atomicMax(&g_row[i], v);
-                m[i] = 0u;
-            }
-            __syncwarp();
-        };
-        int flushed = 0;  // tiles below this one are flushed
-        long long f = 0;
-        for (; f < total; ++f) {
-            const int q = (int)(f % NS);
-            if (f >= NS && !mbar_wait_bounded(&empty[q], (unsigned)(((f / NS) + 1) & 1))) {
-                if (lane == 0) atomicOr(&a.st->status, ST_TIMEOUT);
-                break;
-            }
-            const int t = (int)(f / NV);
-            if (f % NV == 0 && t >= 2) {
-                // every consumer warp has released fill f - NS (a row of tile t - 1, NS <= NV),
-                // so all of them are past tile t - 2, the previous user of these buffers; the
-                // generic-proxy writes of the flush and the async copies below touch disjoint
-                // buffers (maxima vs scales)
-                flush(t - 2);
-                flushed = t - 1;
-            }
-            issue_row_h<S, NV>(a, fin, ring, full, dsc, s_in, s_out, enc + (t & 1) * NLP, q,
-                               tile_of(f), (int)(f % NV));
-        }
-        for (long long d = std::max(0ll, f - NS); d < f; ++d)
-            mbar_wait_bounded(&full[d % NS], (unsigned)((d / NS) & 1));
-        // wait for the consumers, then flush the tiles not flushed yet
-        asm volatile("bar.sync 1, %0;" ::"r"(PCHShape<NV, NS>::threads) : "memory");
-        for (int t = flushed; t < ntl; ++t)
-            if (t >= ntl - 2) flush(t);
+        produce_rows_h<S, NV, NS, PCHShape<NV, NS>::threads>(a, fin, ring, full, empty, dsc, s_in,
+                                                              s_out, enc, mxs, m_out, ntl,
+                                                              tile_of);
         return;
     }
     const int cell = threadIdx.x;
@@ -436,12 +452,13 @@ __global__ void __launch_bounds__(PCHShape<NV, NS>::threads, PCHShape<NV, NS>::m
         float wx, wy;
         load_w<float>(a, x, y, wx, wy);
         cfl_check<float, NV>(a, g, wx, wy, active);
-        float A[NV], H[NV];
-        SmemCol Gs{gsm + cell};
+        float A[NV], Hreg[NV];
+        SmemCol Gs{gsm + cell}, Hs{gsm + NV * TW + cell};
 #pragma unroll
         for (int j = 0; j < NV; ++j) {
             A[j] = 0.f;
-            H[j] = 0.f;
+            if constexpr (HSM) Hs[j] = 0.f;
+            else Hreg[j] = 0.f;
             Gs[j] = 0.f;
         }
         HalfPutS<S, NV> put(fout + (size_t)y * a.nx + x, ps, active, enc + (lt & 1) * NLP,
@@ -457,12 +474,16 @@ __global__ void __launch_bounds__(PCHShape<NV, NS>::threads, PCHShape<NV, NS>::m
                 const int qc = (int)((s - 1) % NS), qn = (int)(s % NS);
                 const RingRowH<S, NV> cur{ring + (size_t)qc * NV * kWinH + cell, dsc + qc * NVP};
                 const RingRowH<S, NV> nxt{ring + (size_t)qn * NV * kWinH + cell, dsc + qn * NVP};
-                sweep_row<float, NV>(A, Gs, H, r, cur, nxt, g, wx, wy, rr, put);
+                if constexpr (HSM) sweep_row<float, NV>(A, Gs, Hs, r, cur, nxt, g, wx, wy, rr, put);
+                else sweep_row<float, NV>(A, Gs, Hreg, r, cur, nxt, g, wx, wy, rr, put);
                 __syncwarp();
                 if (lane == 0) mbar_arrive(&empty[qc]);  // row s - 1 is done
             }
         }
-        if (!failed) final_row<float, NV>(A, H, rr, put);
+        if (!failed) {
+            if constexpr (HSM) final_row<float, NV>(A, Hs, rr, put);
+            else final_row<float, NV>(A, Hreg, rr, put);
+        }
         bad |= put.enc.bad && active;
     }
     if (failed && lane == 0) atomicOr(&a.st->status, ST_TIMEOUT);
@@ -555,28 +576,28 @@ int grid_for(long long n, int per_block) {
 #define LATH_NV_LIST(X) X(1) X(3) X(5) X(9) X(13) X(17) X(21) X(33)
 #define LATH_PC(n) ((n) >= 9)
 
-template <typename S, int NV, int NS>
+template <typename S, int NV, int NS, bool HSM = false>
 cudaError_t launch_pch(int grid, const Step2DHArgs& a, int k, cudaStream_t s) {
-    using Lay = PCHLayout<S, NV, NS>;
+    using Lay = PCHLayout<S, NV, NS, HSM>;
     static bool attr = false;
     if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute(k_step2d_pch<S, NV, NS>,
+        cudaError_t e = cudaFuncSetAttribute(k_step2d_pch<S, NV, NS, HSM>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)Lay::total);
         if (e != cudaSuccess) return e;
         attr = true;
     }
-    k_step2d_pch<S, NV, NS><<<grid, PCHShape<NV, NS>::threads, Lay::total, s>>>(a, k);
+    k_step2d_pch<S, NV, NS, HSM><<<grid, PCHShape<NV, NS>::threads, Lay::total, s>>>(a, k);
     return cudaGetLastError();
 }
 
-template <typename S, int NV, int NS>
+template <typename S, int NV, int NS, bool HSM = false>
 int occupancy_pch() {
-    using Lay = PCHLayout<S, NV, NS>;
+    using Lay = PCHLayout<S, NV, NS, HSM>;
     int nb = 0;
-    cudaFuncSetAttribute(k_step2d_pch<S, NV, NS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)Lay::total);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_step2d_pch<S, NV, NS>,
+    cudaFuncSetAttribute(k_step2d_pch<S, NV, NS, HSM>,
+                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Lay::total);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_step2d_pch<S, NV, NS, HSM>,
                                                   PCHShape<NV, NS>::threads, Lay::total);
     return nb;
 }
@@ -586,6 +607,8 @@ cudaError_t launch_h_t(int pcv, int grid, const Step2DHArgs& a, int k, cudaStrea
     if constexpr (LATH_PC(NV)) {
         if (pcv == 4) return launch_pch<S, NV, 4>(grid, a, k, s);
         if (pcv == 5) return launch_pch<S, NV, 3>(grid, a, k, s);
+        if (pcv == 6) return launch_pch<S, NV, 3, true>(grid, a, k, s);
+        if (pcv == 7) return launch_pch<S, NV, 2, true>(grid, a, k, s);
     }
     if (pcv == 0) {
         k_step2d_plain_h<S, NV><<<grid, TW, 0, s>>>(a, k);
@@ -599,6 +622,8 @@ int occupancy_h_t(int pcv) {
     if constexpr (LATH_PC(NV)) {
         if (pcv == 4) return occupancy_pch<S, NV, 4>();
         if (pcv == 5) return occupancy_pch<S, NV, 3>();
+        if (pcv == 6) return occupancy_pch<S, NV, 3, true>();
+        if (pcv == 7) return occupancy_pch<S, NV, 2, true>();
     }
     return 0;
 }

@@ -144,6 +144,31 @@ def test_moments_match_oracle(lat):
     lt.close()
 
 
+def test_fp32_moments_within_their_bound(lat):
+    """FP32 state: the mass sums are exact up to the roundings of their compensation terms
+    (about N_v u^2 per column); the momentum and energy column sums take one FMA per value, so
+    their error is at most (N_v - 1) u of the sum of |v^k f| (u = 2^-24), plus the compensated
+    cross-column part."""
+    c = make_case(300, 33, 1.0, 1e-3, 30, 6, init="random")
+    got, lt = run_gpu(lat, c, torch.float32)
+    code, rho, mv, mv2, glob = lt.moments()
+    assert code == 0
+    f = got.astype(np.float64)
+    rho_o, mv_o, mv2_o, glob_o = O.moments_1d(f, c["dx"], c["dv"])
+    nv = f.shape[0]
+    v = (np.arange(nv) - (nv - 1) // 2) * c["dv"]
+    u = 2.0**-24
+    assert abs(glob[0] - glob_o[0]) <= 1e-12 * glob_o[0]
+    for k in (1, 2):
+        bound = (nv - 1) * u * math.fsum((np.abs(v[:, None]) ** k * np.abs(f)).ravel())
+        bound *= c["dx"] * c["dv"]
+        assert abs(glob[k] - glob_o[k]) <= bound + 1e-14 * abs(glob_o[k]), k
+    np.testing.assert_allclose(rho.cpu().numpy(), rho_o, rtol=1e-12)
+    col = (nv - 1) * u * (np.abs(v[:, None]) ** 2 * f).sum(axis=0) / f.sum(axis=0)
+    assert np.all(np.abs(mv2.cpu().numpy() - mv2_o) <= col + 1e-13 * np.abs(mv2_o))
+    lt.close()
+
+
 def test_mass_is_conserved_over_1000_steps(lat):
     c, _ = config0()
     got, lt = run_gpu(lat, c, torch.float32)

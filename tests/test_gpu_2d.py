@@ -100,7 +100,7 @@ def test_gaussian_start_with_flow_1000_steps(lat):
         lt.close()
 
 
-@pytest.mark.parametrize("kernel", [1, 2, 3, 4, 5])
+@pytest.mark.parametrize("kernel", [1, 2, 3, 4, 5, 6, 7])
 def test_free_streaming_is_exact(lat, kernel):
     nx, ny, nv = 136, 12, 9
     rng = np.random.default_rng(3)
@@ -168,7 +168,7 @@ def _one_cell_oracle(f0, x, y, ux, uy, tau_p, kappa, dt, dv, gathered=False):
     return O.diffuse_2d(g, kappa, dt, dv)[:, :, 0, 0]
 
 
-@pytest.mark.parametrize("kernel", [1, 2, 3, 4, 5])
+@pytest.mark.parametrize("kernel", [1, 2, 3, 4, 5, 6, 7])
 def test_many_tiles_per_block_match_oracle(lat, kernel):
     """136 x 200 x 9^2 with one resident block per SM: 400 tiles on at most 152 blocks, so every
     block carries its pipeline across several tiles."""
@@ -197,8 +197,8 @@ def test_ring_equals_plain_at_full_size(lat):
     dt = I.choose_dt(2, nx, L, nv, L, 1e-3)
     fl = I.flow2d_inputs(10, 3, nx, ny, L / nx)
     outs = []
-    # plain loads; ring with 1 and 3 chunks; the three producer/consumer variants
-    for kernel, block in ((1, 0), (2, 128), (2, 384), (3, 0), (4, 0), (5, 0)):
+    # plain loads; ring with 1 and 3 chunks; the five producer/consumer variants
+    for kernel, block in ((1, 0), (2, 128), (2, 384), (3, 0), (4, 0), (5, 0), (6, 0), (7, 0)):
         lt = lat.Lattice(f0.clone(), d=2, nx=nx, ny=ny, nv=nv, L=L, tau_p=L, kappa=1e-3, dt=dt)
         lt.set_launch(kernel=kernel, block=block)
         lt.set_flow_modes_2d(fl.kvec, fl.a, fl.phi0, fl.tau_f)

@@ -50,7 +50,8 @@ def test_noalloc_moments_match_context_moments(lat):
         assert _noalloc(lat, lt.state, nv, nx, dx, dv, out) == 0
         torch.cuda.synchronize()
         got = out.cpu().numpy()
-        # Both sides sum every column in the same FP32 Kahan order.  They differ in how columns
+        # Both sides sum every column in the same FP32 order (the mass by TwoSum, the weighted
+        # sums by FMA).  They differ in how columns
         # combine: FP64 Neumaier here; FP32 TwoSum merges (exact but for the rounding of the
         # error term, about u^2 = 2^-48 of a partial per merge, five merges per warp) then
         # FP64 in the context.  So |got - want| <= 1e-13 * sum|terms| of each moment.
