@@ -50,6 +50,9 @@ def parse():
     p.add_argument("--no-forms", action="store_true")
     p.add_argument("--workload", default="ensemble",
                    choices=["ensemble", "2d", "2d_f16", "2d_bf16", "2d_learned"])
+    p.add_argument("--scheme", default="upwind", choices=["upwind", "koren"],
+                   help="drag scheme of the 1D ensemble workload (koren: flux-limited, "
+                        "mu = 2/3, Heun's method)")
     p.add_argument("--size", type=int, default=0,
                    help="grid size N (N x N) of a 2D workload instead of its default "
                         "(profiling a smaller case)")
@@ -176,11 +179,15 @@ class OracleSample:
     """The FP64 oracle, as it stands, on the first instances of the benchmark ensemble
     (about `sample_cells` phase-space cells per step)."""
 
-    def __init__(self, sample_cells: int = 2_000_000):
+    def __init__(self, sample_cells: int = 2_000_000, scheme: str = "upwind"):
         from oracle import lattice as O
+        from oracle import limiter as K
         from paper_1508_02899_gb300 import inputs as I
         self.O = O
-        self.tab = I.ensemble_table(N_INST, SEED, nv=NV)
+        self.koren = scheme == "koren"
+        self.step_1d = ((lambda *a: K.step_1d(*a, mu=KOREN_MU)) if self.koren else O.step_1d)
+        self.tab = I.ensemble_table(N_INST, SEED, nv=NV,
+                                    cfl_factor=1 + KOREN_MU if self.koren else 1.0)
         self.idx, self.cells = [], 0
         while self.cells < sample_cells:
             self.idx.append(len(self.idx))
@@ -196,13 +203,13 @@ class OracleSample:
             nx = int(tab.nx[i])
             dv = (tab.L[i] / nx) / tab.dt[i]
             u = O.flow1d_u(amp, fl.k, nx)
-            f = O.step_1d(f, u, tab.tau_p[i], tab.kappa[i], tab.dt[i], dv)
+            f = self.step_1d(f, u, tab.tau_p[i], tab.kappa[i], tab.dt[i], dv)
             amp = O.ou_advance(amp, fl.noise[0, j], tab.dt[i], fl.tau_f, fl.sigma)
             self.state[i] = (f, amp)
 
     def describe(self, steps):
         return (f"first {len(self.idx)} of 4096 instances ({self.cells} cells per step), "
-                f"{steps} steps")
+                f"{steps} steps" + (", flux-limited drag" if self.koren else ""))
 
     def time_for(self, budget_s: float):
         steps, t0 = 0, time.perf_counter()
@@ -218,7 +225,7 @@ def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return 0
-    smp = OracleSample()
+    smp = OracleSample(scheme=args.scheme)
     for _ in range(args.warmup):
         smp.step()
     t0 = time.perf_counter()
@@ -256,18 +263,28 @@ WORKLOAD_2D_16 = ("2D {fmt} storage (per x-line power-of-two scales, FP32 arithm
                   "random-phase flow |k|<=8, k^-3 spectrum, OU phases")
 
 
-def build_ensemble(args, I, lat, torch, dev, rank, nsteps):
+KOREN_MU = 2.0 / 3.0
+
+
+def build_ensemble(args, I, lat, torch, dev, rank, nsteps, scheme="upwind"):
+    """The 1D ensemble; with scheme "koren" the flux-limited drag (mu = 2/3) and the time steps
+    its Courant bound asks for (choose_dt with factor 1 + mu)."""
     n_inst = args.instances
     seed_tab, seed_flow = rank_seeds(rank)
-    tab = I.ensemble_table(n_inst, seed_tab, nv=NV)
+    koren = scheme == "koren"
+    tab = I.ensemble_table(n_inst, seed_tab, nv=NV, cfl_factor=1 + KOREN_MU if koren else 1.0)
     fl = I.flow1d_inputs(seed_flow, nsteps, n_inst=n_inst)
     f0 = I.ensemble_initial(tab, NV, torch.float32, dev)
     ens = lat.Ensemble(f0, nv=NV, nx=tab.nx, L=tab.L, tau_p=tab.tau_p, kappa=tab.kappa,
                        dt=tab.dt)
+    if koren:
+        ens.set_scheme(lat.SCHEME_KOREN, KOREN_MU)
     ens.set_flow_modes(fl.k, fl.amp0, fl.tau_f, fl.sigma)
     ens.set_noise(fl.noise)
     cells = int(tab.nx.sum()) * NV
     desc = WORKLOAD if n_inst == N_INST else f"{WORKLOAD} (profiling case: {n_inst} instances)"
+    if koren:
+        desc += "; flux-limited drag (Koren limiter, mu = 2/3, Heun's method)"
     return ens, cells, fl.noise[:1], np.zeros((n_inst, 3)), desc
 
 
@@ -437,8 +454,11 @@ def main():
         launches_per_step = 3  # flow evaluation + output scales + fused step
         bytes_per_cell, lines = 4, nv * nv * (args.size or 1024)
     else:
-        ctx, cells, noise_row, glob, desc = build_ensemble(args, I, lat, torch, dev, rank, nsteps)
-        nv, prof, src = NV, "step1d_ensemble_fp32_nv65.md", "paper_1508_02899_gb300/csrc/step1d.cu"
+        ctx, cells, noise_row, glob, desc = build_ensemble(args, I, lat, torch, dev, rank, nsteps,
+                                                           scheme=args.scheme)
+        nv, src = NV, "paper_1508_02899_gb300/csrc/step1d.cu"
+        prof = ("step1d_ensemble_fp32_nv65.md" if args.scheme == "upwind"
+                else "step1d_ensemble_koren_fp32_nv65.md")
         launches_per_step = 1
     best = None
     if args.launch:
@@ -517,6 +537,19 @@ def main():
             lt.close()
             del lt
             torch.cuda.empty_cache()
+        if args.scheme == "upwind":
+            lt, c2, *_ = build_ensemble(args, I, lat, torch, dev, rank, 2 * 40 + 4,
+                                        scheme="koren")
+            b2 = lt.autotune(reps=3)
+            ms2, _ = timed(lt, 40, 3, torch, dist, world, local, dev)
+            st2 = lt.status()
+            g2 = c2 * 40 / (ms2 / 1e3) / 1e9
+            forms["ensemble_koren_fp32_nv65"] = {
+                "gcups": g2, "ms_per_step": ms2 / 40, "hbm_frac": g2 * 8 / peak,
+                "kernel": kernel_label("ensemble", b2, NV), "steps": 40, "status": st2}
+            lt.close()
+            del lt
+            torch.cuda.empty_cache()
         lt, c2, *_ = build_learned(args, I, lat, torch, dev, rank, 2 * 20 + 4)
         ms2, _ = timed(lt, 20, 3, torch, dist, world, local, dev)
         st2 = lt.status()
@@ -533,7 +566,7 @@ def main():
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        smp = OracleSample()
+        smp = OracleSample(scheme=args.scheme if args.workload == "ensemble" else "upwind")
         c_steps, c_el = smp.time_for(args.cpu_seconds)
         cpu = {"value": smp.cells * c_steps / c_el / 1e9, "unit": UNIT, "cores": 1,
                "kind": "oracle", "sample": smp.describe(c_steps)}

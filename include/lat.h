@@ -62,6 +62,10 @@ extern "C" {
 #define LAT_FLOW_FIELD 1  /* caller's device field, frozen until the next lat_set_flow */
 #define LAT_FLOW_MODES 2  /* synthetic random flow evolved on the device every step */
 
+/* ---- drag schemes (lat_set_scheme) ---- */
+#define LAT_SCHEME_UPWIND 0  /* first-order upwind flux, forward Euler (Sec. 2) */
+#define LAT_SCHEME_KOREN 1   /* flux-limited, Heun's method (Sec. 2, flux limiter) */
+
 typedef struct lat_ctx lat_ctx;
 
 /* One lattice (Section 2).  d = 1: ny must be 1.  d = 2: the domain is nx*dx by ny*dx. */
@@ -252,6 +256,23 @@ long long lat_steps_done(const lat_ctx* c);
  *          launches issued directly (no graph).
  * Returns LAT_EINVAL for a shape the lattice does not support. */
 int lat_set_launch(lat_ctx* c, int kernel, int block, int blocks_per_sm, int mode);
+
+/* Drag sub-step scheme (Section 2 offers the first-order upwind flux and a flux-limiter scheme
+ * after Hundsdorfer et al. with Koren's limiter, "parameter 2/3").
+ *  scheme: LAT_SCHEME_UPWIND (default) or LAT_SCHEME_KOREN.  KOREN: the flux through interface
+ *          j+1/2 is, for each split flux P = a^+ f and M = a^- f (cell-centre force) taken from
+ *          its upwind side, q_j + psi(theta_j)(q_{j+1} - q_j) with theta_j = (q_j - q_{j-1}) /
+ *          (q_{j+1} - q_j) and psi(theta) = max(0, min(1, 1/3 + theta/6, mu theta)); cells
+ *          beyond the walls count as empty and the wall fluxes stay zero.  The sub-step is
+ *          integrated by Heun's method: f1 = f + dt L(f), f_new = (f + f1 + dt L(f1)) / 2.
+ *  mu:     limiter bound, 0 < mu <= 2 (2/3 reads the paper's parameter; 1 is the limiter's
+ *          usual form); ignored for UPWIND.
+ * Each Heun stage keeps f >= 0 when (dt/dv) max|a| (1 + mu) <= 1; lat_set_scheme checks the
+ * at-rest bound (dt/tau_p) J (1 + mu) <= 1 of every instance (LAT_ECFL otherwise) and the step
+ * kernels flag the local bound at run time.  1D lattices and ensembles, FP32 or FP64, with N_v in
+ * {3, 5, 9, 17, 33, 65}; other contexts return LAT_EINVAL.  The 16-bit and learned 2D paths keep
+ * the upwind scheme. */
+int lat_set_scheme(lat_ctx* c, int scheme, double mu);
 
 /* Time candidate launch shapes on the current state without advancing it (reads the current
  * buffer, writes the other; the flow state is not advanced) and keep the fastest.  best[4]

@@ -66,6 +66,10 @@ struct lat_ctx {
     DevState* d_state = nullptr;
     DevState* h_state = nullptr;    // pinned
 
+    // drag scheme (1D)
+    int scheme = LAT_SCHEME_UPWIND;
+    double mu = 2.0 / 3.0;
+
     // launch shape: kernel variant (plain loads or bulk-copy ring), threads per block (= tile
     // width), ring slots, resident blocks per SM of the persistent grid, launch mode
     int variant = STEP1D_PLAIN, block = 256, slots = 3, bps = 4, mode = 0;
@@ -163,6 +167,8 @@ Step1DArgs step_args(const lat_ctx* c, int k, int dry) {
     a.st = c->d_state;
     a.dry = dry;
     a.frozen = c->frozen ? 1 : 0;
+    a.scheme = c->scheme;
+    a.mu = c->mu;
     return a;
 }
 
@@ -617,6 +623,24 @@ int lat_decode(lat_ctx* c, float* dst, float* scales) {
 }
 
 long long lat_steps_done(const lat_ctx* c) { return c ? c->h_step : -1; }
+
+int lat_set_scheme(lat_ctx* c, int scheme, double mu) {
+    if (!c) return LAT_EINVAL;
+    if (scheme != LAT_SCHEME_UPWIND && scheme != LAT_SCHEME_KOREN) return LAT_EINVAL;
+    if (scheme == LAT_SCHEME_KOREN) {
+        if (c->d != 1 || (c->dtype != LAT_F32 && c->dtype != LAT_F64)) return LAT_EINVAL;
+        if (!step1d_limiter_supported(c->nv)) return LAT_EINVAL;
+        if (!(mu > 0.0 && mu <= 2.0)) return LAT_EINVAL;
+        // each Heun stage is positive for nu (1 + mu) <= 1; at rest nu = (dt/tau_p) J
+        const int J = (c->nv - 1) / 2;
+        for (const Inst1D& in : c->h_inst)
+            if (in.g * J * (1.0 + mu) > 1.0) return LAT_ECFL;
+    }
+    c->scheme = scheme;
+    if (scheme == LAT_SCHEME_KOREN) c->mu = mu;
+    drop_graphs(c);
+    return LAT_OK;
+}
 
 int lat_set_launch(lat_ctx* c, int kernel, int block, int blocks_per_sm, int mode) {
     if (!c) return LAT_EINVAL;

@@ -78,6 +78,8 @@ struct Step1DArgs {
     DevState* st;
     int dry;                 // 1: do not advance the flow (autotuning)
     int frozen;              // 1: flow frozen (tau_f infinite)
+    int scheme;              // LAT_SCHEME_UPWIND or LAT_SCHEME_KOREN (drag sub-step)
+    double mu;               // limiter bound psi(theta) <= mu theta (KOREN)
     // moments of the new state, fused into the step (k_step1d_pc with moments); may be null
     double* m_rho;
     double* m_mv;
@@ -106,6 +108,7 @@ cudaError_t launch_step1d(int dtype, int nv, int variant, int block, int slots, 
                           const Step1DArgs& a, int kstep, cudaStream_t s);
 int step1d_max_block(int dtype, int nv, int variant);
 bool step1d_ring_supported(int dtype, int nv);
+bool step1d_limiter_supported(int nv);
 int step1d_ring_tile();
 int step1d_ring_min_nx();
 int step1d_ring_occupancy(int nv, int slots, int variant);

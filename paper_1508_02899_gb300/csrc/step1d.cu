@@ -88,6 +88,88 @@ __device__ __forceinline__ void sweep_column(T w, T g, T r, const Get& get, cons
     put(NV - 1, Ops<T>::add(dprev, Ops<T>::sub(T(0), Dprev)));
 }
 
+// ---- flux-limited drag (scheme KOREN) -----------------------------------------------------------
+// Limited increment psi(theta) dp of Koren's limiter in Hundsdorfer et al.'s form (Sec. 2, flux
+// limiter): psi(theta) = max(0, min(1, 1/3 + theta/6, mu theta)), theta = dm / dp, written
+// without the division: with s = sign(dp), psi(theta) dp = s max(0, min(|dp|, s (dp/3 + dm/6),
+// s mu dm)); zero when dp = 0.
+template <typename T>
+__device__ __forceinline__ T lim_inc(T dp, T dm, T mu) {
+    using O = Ops<T>;
+    const T s = copysign(T(1), dp);
+    const T b = O::mul(s, O::fma(dm, T(1.0 / 6.0), O::mul(dp, T(1.0 / 3.0))));
+    const T c = O::mul(s, O::mul(mu, dm));
+    return O::mul(s, fmax(T(0), fmin(fabs(dp), fmin(b, c))));
+}
+
+// Limited flux through interface i + 1/2 from the split fluxes P = (c a)^+ q, M = (c a)^- q of
+// cells i - 1 .. i + 2 (cells beyond the walls count as empty):
+//   F = P_i + psi(theta^P)(P_{i+1} - P_i) + M_{i+1} + psi(theta^M)(M_i - M_{i+1}).
+template <typename T, int NV>
+__device__ __forceinline__ T lim_face(const T (&P)[NV], const T (&M)[NV], int i, T mu) {
+    using O = Ops<T>;
+    const T Pm = i >= 1 ? P[i - 1] : T(0);
+    const T Mpp = i + 2 < NV ? M[i + 2] : T(0);
+    const T pos = O::add(P[i], lim_inc<T>(O::sub(P[i + 1], P[i]), O::sub(P[i], Pm), mu));
+    const T neg = O::add(M[i + 1], lim_inc<T>(O::sub(M[i], M[i + 1]), O::sub(M[i + 1], Mpp), mu));
+    return O::add(pos, neg);
+}
+
+// The limited drag sub-step by Heun's method, then the diffusion, for one column (scheme KOREN):
+//   y = x - (F(x)_{j+1/2} - F(x)_{j-1/2}),  h = (x + y - (F(y)_{j+1/2} - F(y)_{j-1/2})) / 2,
+//   out = h + (D_{j+1/2} - D_{j-1/2}),  D = r (h_{j+1} - h_j),  zero fluxes at the walls.
+// One unrolled pass over k: cell k is read, stage-1 face and cell k - 2, stage-2 face and cell
+// k - 4, output k - 5, so that every array element lives for a few iterations only.
+template <typename T, int NV, class Get, class Put>
+__device__ __forceinline__ void sweep_column_lim(T w, T g, T r, T mu, const Get& get,
+                                                 const Put& put) {
+    using O = Ops<T>;
+    constexpr int J = (NV - 1) / 2;
+    T x[NV], P0[NV], M0[NV], y[NV], P1[NV], M1[NV], h[NV], F0[NV + 1], F1[NV + 1];
+    T Dprev = T(0);
+#pragma unroll
+    for (int k = 0; k < NV + 5; ++k) {
+        if (k < NV) {
+            x[k] = get(k);
+            const T ca = cacc<T>(g, w, k - J);
+            P0[k] = O::mul(fmax(ca, T(0)), x[k]);
+            M0[k] = O::mul(fmin(ca, T(0)), x[k]);
+        }
+        if (k - 2 >= 0 && k - 2 <= NV - 2) F0[k - 1] = lim_face<T, NV>(P0, M0, k - 2, mu);
+        if (k - 2 >= 0 && k - 2 < NV) {
+            const int j = k - 2;
+            const T Fl = j == 0 ? T(0) : F0[j];
+            const T Fr = j == NV - 1 ? T(0) : F0[j + 1];
+            y[j] = O::sub(x[j], O::sub(Fr, Fl));
+            const T ca = cacc<T>(g, w, j - J);
+            P1[j] = O::mul(fmax(ca, T(0)), y[j]);
+            M1[j] = O::mul(fmin(ca, T(0)), y[j]);
+        }
+        if (k - 4 >= 0 && k - 4 <= NV - 2) F1[k - 3] = lim_face<T, NV>(P1, M1, k - 4, mu);
+        if (k - 4 >= 0 && k - 4 < NV) {
+            const int j = k - 4;
+            const T Fl = j == 0 ? T(0) : F1[j];
+            const T Fr = j == NV - 1 ? T(0) : F1[j + 1];
+            h[j] = O::mul(T(0.5), O::add(x[j], O::sub(y[j], O::sub(Fr, Fl))));
+        }
+        if (k - 5 >= 0 && k - 5 < NV) {
+            const int j = k - 5;
+            const T D = j < NV - 1 ? O::mul(r, O::sub(h[j + 1], h[j])) : T(0);
+            put(j, O::add(h[j], O::sub(D, Dprev)));
+            Dprev = D;
+        }
+    }
+}
+
+// Drag scheme of one column: upwind, or the limited scheme (LIM, a separate kernel instance,
+// so that the upwind kernels keep their own code and registers).
+template <typename T, int NV, bool LIM, class Get, class Put>
+__device__ __forceinline__ void sweep_scheme(const Step1DArgs& a, T w, T g, T r, const Get& get,
+                                             const Put& put) {
+    if constexpr (LIM) sweep_column_lim<T, NV>(w, g, r, T(a.mu), get, put);
+    else sweep_column<T, NV>(w, g, r, get, put);
+}
+
 // Runtime-N_v version of the same sweep (identical operation order).
 template <typename T, class Get, class Put>
 __device__ __forceinline__ void sweep_column_any(int NV, T w, T g, T r, const Get& get,
@@ -167,9 +249,11 @@ __device__ __forceinline__ void advance_amplitudes(const Step1DArgs& a, int inst
     if (!have && threadIdx.x == 0) atomicOr(&a.st->status, ST_NOISE);
 }
 
-template <typename T, int J>
+template <typename T, int J, bool LIM = false>
 __device__ __forceinline__ void cfl_flag(const Step1DArgs& a, T g, T w) {
-    if (g * (T(J) + fabs(w)) > T(1)) atomicOr(&a.st->status, ST_CFL);
+    // Eq. (cfl); each stage of the limited scheme (LIM) is positive for nu (1 + mu) <= 1
+    const T f = LIM ? T(1) + T(a.mu) : T(1);
+    if (g * (T(J) + fabs(w)) * f > T(1)) atomicOr(&a.st->status, ST_CFL);
 }
 
 // ---- reg / any variants (plain loads) ----------------------------------------------------------
@@ -179,7 +263,7 @@ struct MaxThreads {
     static constexpr int value = words > 56 ? 256 : (words > 20 ? 512 : 1024);
 };
 
-template <typename T, int NV>
+template <typename T, int NV, bool LIM>
 __global__ void __launch_bounds__(MaxThreads<T, NV>::value)
     k_step1d_reg(const Step1DArgs a, const int kstep) {
     constexpr int J = (NV - 1) / 2;
@@ -212,10 +296,10 @@ __global__ void __launch_bounds__(MaxThreads<T, NV>::value)
                     f[jj] = __ldg(src + (size_t)jj * nx + xs);
                 }
             }
-            sweep_column<T, NV>(
-                w, g, r, [&](int jj) { return f[jj]; },
+            sweep_scheme<T, NV, LIM>(
+                a, w, g, r, [&](int jj) { return f[jj]; },
                 [&](int jj, T v) { dst[(size_t)jj * nx] = v; });
-            cfl_flag<T, J>(a, g, w);
+            cfl_flag<T, J, LIM>(a, g, w);
         }
         if (!a.dry && !a.frozen && a.flow_kind == LAT_FLOW_MODES && item.y == 0)
             advance_amplitudes(a, item.x, in, step, par);
@@ -332,7 +416,7 @@ __device__ __forceinline__ void issue_item(const Step1DArgs& a, const float* fin
     }
 }
 
-template <int NV, int NS>
+template <int NV, int NS, bool LIM>
 __global__ void __launch_bounds__(TW1) k_step1d_ring(const Step1DArgs a, const int kstep) {
     constexpr int J = (NV - 1) / 2;
     extern __shared__ __align__(128) unsigned char smem[];
@@ -386,11 +470,11 @@ __global__ void __launch_bounds__(TW1) k_step1d_ring(const Step1DArgs a, const i
             const float* col = ring + (size_t)(k % NS) * NV * WIN1 + tid;
             float* dst = fout + in.off + x;
             const int nx = in.nx;
-            sweep_column<float, NV>(
-                w, g, r,
+            sweep_scheme<float, NV, LIM>(
+                a, w, g, r,
                 [&](int jj) { return col[jj * WIN1 + ((J - jj) % 4 + 4) % 4]; },
                 [&](int jj, float v) { dst[(size_t)jj * nx] = v; });
-            cfl_flag<float, J>(a, g, w);
+            cfl_flag<float, J, LIM>(a, g, w);
         }
         if (!a.dry && !a.frozen && a.flow_kind == LAT_FLOW_MODES && item.y == 0)
             advance_amplitudes(a, item.x, in, step, par);
@@ -425,7 +509,7 @@ size_t pc1d_smem() {
 
 // With MOM the consumers also reduce the moments of the columns they write (the same FP32
 // column sums, in the same order, as the moment kernel; compensated across cells).
-template <int NV, int NS, bool MOM = false>
+template <int NV, int NS, bool MOM, bool LIM>
 __global__ void __launch_bounds__(PC1_THREADS) k_step1d_pc(const Step1DArgs a, const int kstep) {
     constexpr int J = (NV - 1) / 2;
     extern __shared__ __align__(128) unsigned char smem[];
@@ -480,14 +564,14 @@ __global__ void __launch_bounds__(PC1_THREADS) k_step1d_pc(const Step1DArgs a, c
             const float* col = ring + (size_t)(k % NS) * NV * WIN1 + tid;
             float* dst = fout + in.off + x;
             const int nx = in.nx;
-            sweep_column<float, NV>(
-                w, g, r,
+            sweep_scheme<float, NV, LIM>(
+                a, w, g, r,
                 [&](int jj) { return col[jj * WIN1 + ((J - jj) % 4 + 4) % 4]; },
                 [&](int jj, float v) {
                     dst[(size_t)jj * nx] = v;
                     if constexpr (MOM) sums.add((float)(jj - J), v);
                 });
-            cfl_flag<float, J>(a, g, w);
+            cfl_flag<float, J, LIM>(a, g, w);
         }
         __syncwarp();
         if (lane == 0) mbar_arrive(&empty[k % NS]);
@@ -516,26 +600,35 @@ __global__ void __launch_bounds__(PC1_THREADS) k_step1d_pc(const Step1DArgs a, c
 
 __global__ void k_advance_step(DevState* st, long long n) { st->step += n; }
 
-template <int NV, int NS, bool MOM = false>
-cudaError_t launch_pc1(int grid, const Step1DArgs& a, int kstep, cudaStream_t s) {
+template <int NV, int NS, bool MOM, bool LIM>
+cudaError_t launch_pc1_t(int grid, const Step1DArgs& a, int kstep, cudaStream_t s) {
     static bool attr = false;
     if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute(k_step1d_pc<NV, NS, MOM>,
+        cudaError_t e = cudaFuncSetAttribute(k_step1d_pc<NV, NS, MOM, LIM>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)pc1d_smem<NV, NS>());
         if (e != cudaSuccess) return e;
         attr = true;
     }
-    k_step1d_pc<NV, NS, MOM><<<grid, PC1_THREADS, pc1d_smem<NV, NS>(), s>>>(a, kstep);
+    k_step1d_pc<NV, NS, MOM, LIM><<<grid, PC1_THREADS, pc1d_smem<NV, NS>(), s>>>(a, kstep);
     return cudaGetLastError();
 }
 
+// the scheme's instance of the kernel
+template <int NV, int NS, bool MOM = false>
+cudaError_t launch_pc1(int grid, const Step1DArgs& a, int kstep, cudaStream_t s) {
+    if (a.scheme == LAT_SCHEME_KOREN) return launch_pc1_t<NV, NS, MOM, true>(grid, a, kstep, s);
+    return launch_pc1_t<NV, NS, MOM, false>(grid, a, kstep, s);
+}
+
+// Occupancy of the upwind instance; the limited one holds the same shared memory, which is what
+// limits the resident blocks.
 template <int NV, int NS>
 int occupancy_pc1() {
     int nb = 0;
-    cudaFuncSetAttribute(k_step1d_pc<NV, NS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaFuncSetAttribute(k_step1d_pc<NV, NS, false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)pc1d_smem<NV, NS>());
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_step1d_pc<NV, NS>, PC1_THREADS,
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_step1d_pc<NV, NS, false, false>, PC1_THREADS,
                                                   pc1d_smem<NV, NS>());
     return nb;
 }
@@ -545,26 +638,32 @@ size_t ring1d_smem() {
     return (size_t)NS * NV * WIN1 * sizeof(float) + NS * sizeof(uint64_t);
 }
 
-template <int NV, int NS>
-cudaError_t launch_ring(int grid, const Step1DArgs& a, int kstep, cudaStream_t s) {
+template <int NV, int NS, bool LIM>
+cudaError_t launch_ring_t(int grid, const Step1DArgs& a, int kstep, cudaStream_t s) {
     static bool attr = false;
     if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute(k_step1d_ring<NV, NS>,
+        cudaError_t e = cudaFuncSetAttribute(k_step1d_ring<NV, NS, LIM>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)ring1d_smem<NV, NS>());
         if (e != cudaSuccess) return e;
         attr = true;
     }
-    k_step1d_ring<NV, NS><<<grid, TW1, ring1d_smem<NV, NS>(), s>>>(a, kstep);
+    k_step1d_ring<NV, NS, LIM><<<grid, TW1, ring1d_smem<NV, NS>(), s>>>(a, kstep);
     return cudaGetLastError();
+}
+
+template <int NV, int NS>
+cudaError_t launch_ring(int grid, const Step1DArgs& a, int kstep, cudaStream_t s) {
+    if (a.scheme == LAT_SCHEME_KOREN) return launch_ring_t<NV, NS, true>(grid, a, kstep, s);
+    return launch_ring_t<NV, NS, false>(grid, a, kstep, s);
 }
 
 template <int NV, int NS>
 int occupancy_ring() {
     int nb = 0;
-    cudaFuncSetAttribute(k_step1d_ring<NV, NS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaFuncSetAttribute(k_step1d_ring<NV, NS, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)ring1d_smem<NV, NS>());
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_step1d_ring<NV, NS>, TW1,
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_step1d_ring<NV, NS, false>, TW1,
                                                   ring1d_smem<NV, NS>());
     return nb;
 }
@@ -572,11 +671,13 @@ int occupancy_ring() {
 template <typename T, int NV>
 cudaError_t launch_reg(int block, int grid, const Step1DArgs& a, int kstep, cudaStream_t s) {
     if (block > MaxThreads<T, NV>::value) return cudaErrorInvalidValue;
-    k_step1d_reg<T, NV><<<grid, block, 0, s>>>(a, kstep);
+    if (a.scheme == LAT_SCHEME_KOREN) k_step1d_reg<T, NV, true><<<grid, block, 0, s>>>(a, kstep);
+    else k_step1d_reg<T, NV, false><<<grid, block, 0, s>>>(a, kstep);
     return cudaGetLastError();
 }
 
 #define LAT1D_NV_LIST(X) X(3) X(5) X(9) X(17) X(33) X(65)
+
 
 template <typename T>
 cudaError_t launch_plain(int nv, int block, int grid, const Step1DArgs& a, int kstep,
@@ -604,6 +705,17 @@ int step1d_max_block(int dtype, int nv, int variant) {
     if (!reg) return 512;
     const int words = nv * (dtype == LAT_F64 ? 2 : 1);
     return words > 56 ? 256 : (words > 20 ? 512 : 1024);
+}
+
+// The limited scheme runs in the compiled-N_v kernels only (not k_step1d_any).
+bool step1d_limiter_supported(int nv) {
+    switch (nv) {
+#define X(n) case n:
+        LAT1D_NV_LIST(X)
+#undef X
+        return true;
+        default: return false;
+    }
 }
 
 bool step1d_ring_supported(int dtype, int nv) {

@@ -149,11 +149,13 @@ def flow2d_inputs(seed: int, nsteps: int, nx: int, ny: int, dx: float, kmax: int
 # Parameter choices
 # --------------------------------------------------------------------------------------------
 def choose_dt(d: int, nx: int, L: float, nv: int, tau_p: float, kappa: float,
-              u_rms: float = 1.0) -> float:
+              u_rms: float = 1.0, cfl_factor: float = 1.0) -> float:
     """Largest dt (bisection) such that, with dv = dx / dt and V_max = J dv:
 
     (i)   V_max >= 3 u_rms                      (Section 2: Gaussian flows, V_max = 3 u_rms),
-    (ii)  d (dt/dv)(V_max + 5 u_rms)/tau_p <= 0.9 (Eq. cfl with |u| <= 5 u_rms, d components),
+    (ii)  d (dt/dv)(V_max + 5 u_rms)/tau_p * cfl_factor <= 0.9
+          (Eq. cfl with |u| <= 5 u_rms, d components; cfl_factor = 1 + mu for the limited
+          drag scheme, whose stages are positive for nu (1 + mu) <= 1),
     (iii) 2 d kappa dt / dv^2 <= 0.9               (Eq. stabLapl, d dimensions).
     """
     dx = L / nx
@@ -164,7 +166,7 @@ def choose_dt(d: int, nx: int, L: float, nv: int, tau_p: float, kappa: float,
         vmax = J * dv
         if J > 0 and vmax < 3.0 * u_rms * (1 - 1e-12):
             return False
-        if d * (dt / dv) * (vmax + 5.0 * u_rms) / tau_p > 0.9:
+        if d * (dt / dv) * (vmax + 5.0 * u_rms) / tau_p * cfl_factor > 0.9:
             return False
         if 2 * d * kappa * dt / (dv * dv) > 0.9:
             return False
@@ -195,10 +197,11 @@ class EnsembleTable:
 def ensemble_table(n_inst: int, seed: int, nv: int = 65,
                    sizes=(1024, 2048, 4096, 8192), stokes=(0.1, 1.0, 10.0),
                    kappa: float = 1e-3, L: float = 2 * math.pi,
-                   u_rms: float = 1.0) -> EnsembleTable:
+                   u_rms: float = 1.0, cfl_factor: float = 1.0) -> EnsembleTable:
     """Instances with N_x drawn uniformly from ``sizes`` and St cycling through ``stokes``.
 
-    St = tau_p u_rms / L (Sec. 3.1) fixes tau_p; dt follows ``choose_dt``.
+    St = tau_p u_rms / L (Sec. 3.1) fixes tau_p; dt follows ``choose_dt`` (with ``cfl_factor``
+    = 1 + mu for the limited drag scheme).
     """
     rng = np.random.default_rng(seed)
     nx = rng.choice(np.array(sizes, dtype=np.int64), size=n_inst)
@@ -209,7 +212,8 @@ def ensemble_table(n_inst: int, seed: int, nv: int = 65,
     for i in range(n_inst):
         key = (int(nx[i]), float(tau_p[i]))
         if key not in cache:
-            cache[key] = choose_dt(1, int(nx[i]), L, nv, float(tau_p[i]), kappa, u_rms)
+            cache[key] = choose_dt(1, int(nx[i]), L, nv, float(tau_p[i]), kappa, u_rms,
+                                   cfl_factor)
         dts[i] = cache[key]
     return EnsembleTable(nx=nx.astype(np.int64), L=np.full(n_inst, L), tau_p=tau_p,
                          kappa=np.full(n_inst, kappa), dt=dts, st=st)

@@ -21,6 +21,7 @@ LAT_ENUMERIC, LAT_ETIMEOUT, LAT_EOVERFLOW, LAT_ENOISE = 5, 6, 7, 8
 LAT_F64, LAT_F32, LAT_F16, LAT_BF16 = 0, 1, 2, 3
 FLOW_NONE, FLOW_FIELD, FLOW_MODES = 0, 1, 2
 LEARN_NPARAM = 5378
+SCHEME_UPWIND, SCHEME_KOREN = 0, 1
 
 _DTYPES = {torch.float64: LAT_F64, torch.float32: LAT_F32, torch.float16: LAT_F16,
            torch.bfloat16: LAT_BF16}
@@ -61,6 +62,7 @@ def _load():
         "lat_current": (c_int, [P]),
         "lat_steps_done": (c_longlong, [P]),
         "lat_set_launch": (c_int, [P, c_int, c_int, c_int, c_int]),
+        "lat_set_scheme": (c_int, [P, c_int, c_double]),
         "lat_autotune": (c_int, [P, c_int, POINTER(c_double)]),
         "lat_strerror": (ctypes.c_char_p, [c_int]),
         "lat_free": (None, [P]),
@@ -174,6 +176,10 @@ class _Ctx:
 
     def set_launch(self, kernel=0, block=0, blocks_per_sm=0, mode=-1):
         _check(_lib.lat_set_launch(self._h, kernel, block, blocks_per_sm, mode), "lat_set_launch")
+
+    def set_scheme(self, scheme: int, mu: float = 2.0 / 3.0):
+        """Drag sub-step scheme: SCHEME_UPWIND or SCHEME_KOREN (limiter bound mu)."""
+        _check(_lib.lat_set_scheme(self._h, scheme, mu), "lat_set_scheme")
 
     def autotune(self, reps: int = 5):
         best = np.zeros(4)

@@ -1,0 +1,188 @@
+"""Parity of the flux-limited drag scheme (LAT_SCHEME_KOREN, 1D) with the FP64 oracle of
+oracle/limiter.py: single lattices after 1000 steps (1e-12 FP64, 1e-5 FP32), every launch
+variant bit for bit, an ensemble with ragged sizes, the benchmark ensemble at full size on sampled
+instances, mass and positivity, and the host-side checks."""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+from oracle import limiter as K
+from paper_1508_02899_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+L = 2 * math.pi
+MU = 2.0 / 3.0
+TOL = {torch.float64: 1e-12, torch.float32: 1e-5}
+
+
+def rel_l1(got, want):
+    return np.abs(got - want).sum() / np.abs(want).sum()
+
+
+def case(nx, nv, st, kappa, nsteps, seed, mu=MU, init="gauss"):
+    tau_p = st * L
+    dt = I.choose_dt(1, nx, L, nv, tau_p, kappa, cfl_factor=1 + mu)
+    dx = L / nx
+    dv = dx / dt
+    J = (nv - 1) // 2
+    if init == "gauss":
+        f0 = I.gaussian_initial_1d(nx, nv, dx, dv, 0.2 * J * dv)
+    else:
+        f0 = I.random_initial((nv, nx), seed)
+    fl = I.flow1d_inputs(seed, nsteps)
+    return dict(nx=nx, nv=nv, tau_p=tau_p, kappa=kappa, dt=dt, dv=dv, f0=f0, fl=fl,
+                nsteps=nsteps, mu=mu)
+
+
+def run_gpu(lat, c, dtype, launch=None, nsteps=None):
+    nsteps = c["nsteps"] if nsteps is None else nsteps
+    t = torch.tensor(c["f0"], dtype=dtype, device="cuda")
+    lt = lat.Lattice(t, d=1, nx=c["nx"], nv=c["nv"], L=L, tau_p=c["tau_p"], kappa=c["kappa"],
+                     dt=c["dt"])
+    lt.set_scheme(lat.SCHEME_KOREN, c["mu"])
+    if launch:
+        lt.set_launch(**launch)
+    fl = c["fl"]
+    lt.set_flow_modes_1d(fl.k, fl.amp0[0], fl.tau_f, fl.sigma)
+    lt.set_noise(fl.noise[:, 0, :])
+    lt.step(nsteps)
+    assert lt.status() == 0
+    return lt.state.double().cpu().numpy(), lt
+
+
+def run_oracle(c, nsteps=None):
+    nsteps = c["nsteps"] if nsteps is None else nsteps
+    fl = c["fl"]
+    f, _ = K.run_1d(c["f0"], nsteps, tau_p=c["tau_p"], kappa=c["kappa"], dt=c["dt"], dv=c["dv"],
+                    k=fl.k, amp0=fl.amp0[0], tau_f=fl.tau_f, sigma=fl.sigma,
+                    noise=fl.noise[:, 0, :], mu=c["mu"])
+    return f
+
+
+@pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
+def test_1000_steps_match_oracle(lat, dtype):
+    c = case(256, 33, 1.0, 1e-3, 1000, 11)
+    want = run_oracle(c)
+    got, lt = run_gpu(lat, c, dtype)
+    assert rel_l1(got, want) <= TOL[dtype], rel_l1(got, want)
+    lt.close()
+
+
+@pytest.mark.parametrize("nv,nx,mu", [(3, 40, MU), (9, 137, 1.0), (17, 300, MU), (65, 520, 1.0)])
+def test_shapes_and_limiter_bounds_match_oracle(lat, nv, nx, mu):
+    c = case(nx, nv, 0.3, 2e-3, 40, nv + nx, mu=mu, init="random")
+    want = run_oracle(c)
+    got, lt = run_gpu(lat, c, torch.float64)
+    assert rel_l1(got, want) <= 1e-12, rel_l1(got, want)
+    lt.close()
+
+
+def test_launch_variants_give_the_same_bits(lat):
+    c = case(1000, 33, 1.0, 1e-3, 30, 5, init="random")
+    outs = []
+    for kernel in (1, 2, 3, 4, 5, 6, 7):
+        got, lt = run_gpu(lat, c, torch.float32, launch=dict(kernel=kernel))
+        outs.append(got)
+        lt.close()
+    for k, o in enumerate(outs[1:], start=2):
+        assert np.array_equal(outs[0], o), k
+
+
+def test_ensemble_matches_oracle(lat):
+    nv, nsteps = 33, 60
+    tab = I.ensemble_table(6, 5, nv=nv, sizes=(100, 256, 37, 512, 8, 300), cfl_factor=1 + MU)
+    fl = I.flow1d_inputs(78, nsteps, n_inst=len(tab.nx))
+    parts = [I.random_initial((nv, int(n)), 30 + i) for i, n in enumerate(tab.nx)]
+    t = torch.tensor(np.concatenate([p.ravel() for p in parts]), dtype=torch.float64,
+                     device="cuda")
+    ens = lat.Ensemble(t, nv=nv, nx=tab.nx, L=tab.L, tau_p=tab.tau_p, kappa=tab.kappa, dt=tab.dt)
+    ens.set_scheme(lat.SCHEME_KOREN, MU)
+    ens.set_flow_modes(fl.k, fl.amp0, fl.tau_f, fl.sigma)
+    ens.set_noise(fl.noise)
+    ens.step(nsteps)
+    assert ens.status() == 0
+    for i in range(len(tab.nx)):
+        nx = int(tab.nx[i])
+        dv = (tab.L[i] / nx) / tab.dt[i]
+        want, _ = K.run_1d(parts[i], nsteps, tau_p=tab.tau_p[i], kappa=tab.kappa[i],
+                           dt=tab.dt[i], dv=dv, k=fl.k, amp0=fl.amp0[i], tau_f=fl.tau_f,
+                           sigma=fl.sigma, noise=fl.noise[:, i, :], mu=MU)
+        got = ens.instance_view(i).cpu().numpy()
+        assert rel_l1(got, want) <= 1e-12, (i, rel_l1(got, want))
+    ens.close()
+
+
+def test_full_size_ensemble_sampled(lat):
+    """The benchmark ensemble (4096 instances, N_v = 65, FP32) with the limited scheme, autotuned
+    launch shape: eight sampled instances against the oracle after 10 steps; mass and
+    positivity of the whole ensemble."""
+    nv, nsteps, n = 65, 10, 4096
+    tab = I.ensemble_table(n, 2024, nv=nv, cfl_factor=1 + MU)
+    fl = I.flow1d_inputs(2025, nsteps, n_inst=n)
+    f0 = I.ensemble_initial(tab, nv, torch.float32, "cuda")
+    ens = lat.Ensemble(f0, nv=nv, nx=tab.nx, L=tab.L, tau_p=tab.tau_p, kappa=tab.kappa,
+                       dt=tab.dt)
+    ens.set_scheme(lat.SCHEME_KOREN, MU)
+    ens.set_flow_modes(fl.k, fl.amp0, fl.tau_f, fl.sigma)
+    ens.set_noise(fl.noise)
+    ens.autotune(reps=2)
+    ens.step(nsteps)
+    assert ens.status() == 0
+    rng = np.random.default_rng(1)
+    sample = sorted(int(i) for i in rng.choice(n, 8, replace=False))
+    parts = I.ensemble_initial(tab, nv, None, None, instances=sample)
+    for i in sample:
+        nx = int(tab.nx[i])
+        dv = (tab.L[i] / nx) / tab.dt[i]
+        want, _ = K.run_1d(parts[i], nsteps, tau_p=tab.tau_p[i], kappa=tab.kappa[i],
+                           dt=tab.dt[i], dv=dv, k=fl.k, amp0=fl.amp0[i], tau_f=fl.tau_f,
+                           sigma=fl.sigma, noise=fl.noise[:, i, :], mu=MU)
+        got = ens.instance_view(i).double().cpu().numpy()
+        assert rel_l1(got, want) <= 1e-5, (i, rel_l1(got, want))
+    code, _, _, _, glob = ens.moments()
+    assert code == 0
+    np.testing.assert_allclose(glob[:, 0], 1.0, rtol=1e-5)
+    assert float(ens.state.min()) >= -1e-6 * float(ens.state.max())
+    ens.close()
+
+
+def test_mass_and_positivity_over_many_steps(lat):
+    c = case(512, 65, 0.1, 1e-3, 500, 21)
+    got, lt = run_gpu(lat, c, torch.float32)
+    code, _, _, _, glob = lt.moments(per_cell=False)
+    assert code == 0
+    m0 = c["f0"].sum() * (L / c["nx"]) * c["dv"]
+    assert abs(glob[0] - m0) <= 1e-5 * m0
+    assert got.min() >= -1e-6 * got.max()
+    lt.close()
+
+
+def test_host_checks(lat):
+    c = case(64, 33, 1.0, 1e-3, 1, 1)
+    t = torch.tensor(c["f0"], dtype=torch.float32, device="cuda")
+    # (dt / tau_p) J = 0.8: fine for the upwind step, too long for the limited one (x 5/3)
+    dt = 0.1
+    lt = lat.Lattice(t.clone(), d=1, nx=64, nv=33, L=L, tau_p=dt * 16 / 0.8, kappa=1e-3, dt=dt)
+    with pytest.raises(lat.LatError) as e:
+        lt.set_scheme(lat.SCHEME_KOREN, MU)
+    assert e.value.code == lat.LAT_ECFL
+    with pytest.raises(lat.LatError) as e:
+        lt.set_scheme(lat.SCHEME_KOREN, 0.0)
+    assert e.value.code == lat.LAT_EINVAL
+    lt.set_scheme(lat.SCHEME_UPWIND)
+    lt.close()
+    f7 = torch.zeros((7, 64), device="cuda")  # N_v = 7 runs in the runtime-N_v kernel only
+    lt = lat.Lattice(f7, d=1, nx=64, nv=7, L=L, tau_p=L, kappa=1e-3, dt=c["dt"])
+    with pytest.raises(lat.LatError) as e:
+        lt.set_scheme(lat.SCHEME_KOREN, MU)
+    assert e.value.code == lat.LAT_EINVAL
+    lt.close()
+    f2 = torch.zeros((9, 9, 8, 8), device="cuda")
+    lt = lat.Lattice(f2, d=2, nx=8, ny=8, nv=9, L=L, tau_p=L, kappa=1e-3, dt=0.05)
+    with pytest.raises(lat.LatError) as e:
+        lt.set_scheme(lat.SCHEME_KOREN, MU)
+    assert e.value.code == lat.LAT_EINVAL
+    lt.close()

@@ -70,3 +70,14 @@ def test_committed_profiles_carry_their_roofline_inputs():
             assert float(vals["units_per_launch"]) > 0
             assert re.fullmatch(r"[0-9a-f]{16}", vals["source_sha256"])
     assert found >= 3
+
+
+def test_library_leaves_no_internal_symbol_undefined(libpath):
+    """Every function of the library's own namespace that one translation unit calls is defined
+    in another (a shared library links with undefined symbols and would fail only when loaded
+    on the GPU machine)."""
+    import subprocess
+    out = subprocess.run(["nm", "-D", "--undefined-only", "-C", libpath], capture_output=True,
+                         text=True, check=True).stdout
+    bad = [l for l in out.splitlines() if "lat::" in l or " lat_" in l]
+    assert not bad, bad
