@@ -315,6 +315,26 @@ def build_2d(args, I, lat, torch, dev, rank, nsteps, n=512, nv=33, store="f32"):
     return lt, n * n * nv * nv, fl.noise[:1], np.zeros(4), desc
 
 
+def build_cellular(args, I, lat, torch, dev, rank, n=1024, nv=19):
+    """The tilted cellular flow of Sec. 4.1 (U = 1, L = 2 pi) frozen on an n^2 x 19^2 FP32
+    lattice, St = 1/(2 pi), kappa = 8 pi 1e-3, Gaussian velocity start."""
+    L = 2 * math.pi
+    tau_p, kappa = L / (2 * math.pi), 8 * math.pi * 1e-3
+    dt = I.choose_dt(2, n, L, nv, tau_p, kappa, u_rms=0.1)  # max |u| = 0.5 = 5 u_rms
+    dx = L / n
+    dv = dx / dt
+    col = I.gaussian_column(1, nv, dx, dv, 0.3 * ((nv - 1) // 2) * dv)
+    col2 = torch.tensor(np.outer(col, col) / (n * n), dtype=torch.float32, device=dev)
+    f0 = col2[:, :, None, None].expand(nv, nv, n, n).contiguous()
+    lt = lat.Lattice(f0, d=2, nx=n, ny=n, nv=nv, L=L, tau_p=tau_p, kappa=kappa, dt=dt)
+    del f0
+    ux, uy = I.cellular_flow(n, n, L, 1.0)
+    u = torch.tensor(np.stack([ux, uy]), dtype=torch.float32, device=dev)
+    lt.set_flow_field(u)
+    lt._keep_field = u
+    return lt, n * n * nv * nv
+
+
 def build_learned(args, I, lat, torch, dev, rank, nsteps, n=2048):
     """Coarse 9x9 lattice of the n^2 x 33^2 FP32 problem with the learned closure (mode 2)."""
     from paper_1508_02899_gb300 import train as T
@@ -550,6 +570,40 @@ def main():
             lt.close()
             del lt
             torch.cuda.empty_cache()
+        lt, c2 = build_cellular(args, I, lat, torch, dev, rank)
+        b2 = lt.autotune(reps=3)
+        ms2, _ = timed(lt, 40, 3, torch, dist, world, local, dev)
+        st2 = lt.status()
+        g2 = c2 * 40 / (ms2 / 1e3) / 1e9
+        forms["2d_cellular_fp32_1024x1024_19x19"] = {
+            "gcups": g2, "ms_per_step": ms2 / 40, "hbm_frac": g2 * 8 / peak,
+            "kernel": kernel_label("2d", b2, 19), "steps": 40, "status": st2,
+            "flow": "tilted cellular flow (Sec. 4.1), frozen field, St = 1/(2 pi), "
+                    "kappa = 8 pi 1e-3"}
+        lt.close()
+        del lt
+        torch.cuda.empty_cache()
+        # observables of the ensemble state (Eqs. def_coarse, def_eulS1): one call each
+        lt, c2, *_ = build_ensemble(args, I, lat, torch, dev, rank, 8)
+        lt.step(4)
+        widths = [1, 2, 4, 8, 16, 32, 64, 128, 256, 512]
+        seps = [0, 1, 2, 4, 8, 16, 32, 64]
+        lt.coarse_moment(widths)
+        lt.s1(seps)
+        t0 = time.perf_counter()
+        lt.coarse_moment(widths)
+        t1 = time.perf_counter()
+        lt.s1(seps)
+        t2 = time.perf_counter()
+        forms["observables_ensemble_fp32_nv65"] = {
+            "coarse_moment_ms": 1e3 * (t1 - t0), "widths": len(widths),
+            "s1_ms": 1e3 * (t2 - t1), "separations": len(seps),
+            "s1_pair_gcups": c2 * len(seps) / (t2 - t1) / 1e9,
+            "note": "host-timed calls (each synchronises), per-cell moments included",
+            "status": lt.status()}
+        lt.close()
+        del lt
+        torch.cuda.empty_cache()
         lt, c2, *_ = build_learned(args, I, lat, torch, dev, rank, 2 * 20 + 4)
         ms2, _ = timed(lt, 20, 3, torch, dist, world, local, dev)
         st2 = lt.status()

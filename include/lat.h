@@ -274,6 +274,29 @@ int lat_set_launch(lat_ctx* c, int kernel, int block, int blocks_per_sm, int mod
  * the upwind scheme. */
 int lat_set_scheme(lat_ctx* c, int scheme, double mu);
 
+/* ---- observables (Section 3.2, Eqs. def_coarse and def_eulS1) ---- */
+
+/* Second moment of the coarse-grained density.  rho_r(x) is the mass in a window of width r
+ * around x (Eq. def_coarse); here r = w dx for whole numbers w of cells, the window of cell i
+ * covering cells i .. i + w - 1, periodic (2D: the w x w square of cells from (y, x)).
+ *   widths: host array of nw window widths in cells, 1 <= w <= N_x (2D: min(N_x, N_y)).
+ *   out:    host array, out[k nw + q] = (1 / N_x) sum_i rho_r(x_i)^2 for instance k and width
+ *           widths[q] (one instance for a single lattice or a 2D lattice; 2D divides by
+ *           N_x N_y).  rho = sum_j f dv (dv^2 in 2D); rho_r in units of mass.
+ * Window sums come from compensated FP64 prefix sums (a summed-area table in 2D) of the per-cell
+ * density, the average from a compensated FP64 sum.  Synchronises; returns the pending device
+ * status, LAT_EINVAL for nw outside 1..256 or a width out of range. */
+int lat_coarse_moment(lat_ctx* c, int nw, const int* widths, double* out);
+
+/* Eulerian first-order velocity structure function of 1D lattices (Eq. def_eulS1):
+ *   num[k ns + q] = (1 / N_x) sum_i sum_j sum_j' f_j(x_i) f_j'(x_{i+s}) |v_j - v_j'| dv^2,
+ *   den[k ns + q] = (1 / N_x) sum_i rho(x_i) rho(x_{i+s}),   S1(s dx) = num / den,
+ * for instance k and separation s = seps[q] in cells (0 <= s < N_x, periodic).  The velocity
+ * double sum runs in the state's precision by two running sums without cancellation (about
+ * N_v u of its positive terms); sums over cells are compensated FP64.  FP32 or FP64 state.
+ * Synchronises; LAT_EINVAL for 2D, ns outside 1..256 or a separation out of range. */
+int lat_s1(lat_ctx* c, int ns, const int* seps, double* num, double* den);
+
 /* Time candidate launch shapes on the current state without advancing it (reads the current
  * buffer, writes the other; the flow state is not advanced) and keep the fastest.  best[4]
  * (host, may be NULL) receives {kernel, block, blocks_per_sm, microseconds per step}. */

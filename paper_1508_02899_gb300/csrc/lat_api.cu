@@ -78,6 +78,10 @@ struct lat_ctx {
     // cached graphs keyed by the number of steps (buffers are picked by the device step parity)
     std::map<int, cudaGraphExec_t> graphs;
 
+    // observables scratch (FP64): per-cell rho, prefix sums or summed-area table, outputs
+    double* d_obs = nullptr;
+    size_t obs_cap = 0;
+
     // 2D
     Ctx2D* c2 = nullptr;
 };
@@ -624,6 +628,87 @@ int lat_decode(lat_ctx* c, float* dst, float* scales) {
 
 long long lat_steps_done(const lat_ctx* c) { return c ? c->h_step : -1; }
 
+namespace {
+
+// Grows the observables scratch to n doubles (device).
+int obs_scratch(lat_ctx* c, size_t n) {
+    if (c->obs_cap >= n) return LAT_OK;
+    if (c->d_obs) cudaFree(c->d_obs);
+    c->d_obs = nullptr;
+    c->obs_cap = 0;
+    if (cudaMalloc(&c->d_obs, sizeof(double) * n) != cudaSuccess) return LAT_ENOMEM;
+    c->obs_cap = n;
+    return LAT_OK;
+}
+
+}  // namespace
+
+int lat_coarse_moment(lat_ctx* c, int nw, const int* widths, double* out) {
+    if (!c || nw < 1 || nw > 256 || !widths || !out) return LAT_EINVAL;
+    int nx = 0, ny = 1, nv = 0;
+    double dx = 0, dv = 0;
+    long long ncell;
+    int nmin;
+    if (c->d == 2) {
+        ctx2d_geometry(c->c2, &nx, &ny, &nv, &dx, &dv);
+        ncell = (long long)nx * ny;
+        nmin = std::min(nx, ny);
+    } else {
+        ncell = c->total_x;
+        nmin = c->h_inst.empty() ? 0 : c->h_inst[0].nx;
+        for (const Inst1D& in : c->h_inst) nmin = std::min(nmin, in.nx);
+    }
+    for (int q = 0; q < nw; ++q)
+        if (widths[q] < 1 || widths[q] > nmin) return LAT_EINVAL;
+    const int nout = (c->d == 2 ? 1 : c->n_inst) * nw;
+    const size_t table = c->d == 2 ? 2 * (size_t)(ny + 1) * (nx + 1)
+                                   : 2 * (size_t)(c->total_x + c->n_inst);
+    const size_t ints = (nw + 1) / 2;  // widths, two per double
+    int rc = obs_scratch(c, (size_t)ncell + table + nout + ints);
+    if (rc != LAT_OK) return rc;
+    double* rho = c->d_obs;
+    double* tab = rho + ncell;
+    double* d_out = tab + table;
+    int* d_w = reinterpret_cast<int*>(d_out + nout);
+    // per-cell rho (also raises the pending status)
+    rc = lat_moments(c, rho, nullptr, nullptr, nullptr);
+    if (rc != LAT_OK) return rc;
+    CK(cudaMemcpyAsync(d_w, widths, sizeof(int) * nw, cudaMemcpyHostToDevice, c->stream));
+    if (c->d == 2)
+        CK(launch_coarse2d(rho, nx, ny, dx, d_w, nw, tab, d_out, c->sm_count, c->stream));
+    else
+        CK(launch_coarse1d(rho, c->d_inst, c->n_inst, c->total_x, d_w, nw, tab, d_out,
+                           c->sm_count, c->stream));
+    CK(cudaMemcpyAsync(out, d_out, sizeof(double) * nout, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    return LAT_OK;
+}
+
+int lat_s1(lat_ctx* c, int ns, const int* seps, double* num, double* den) {
+    if (!c || c->d != 1 || ns < 1 || ns > 256 || !seps || !num || !den) return LAT_EINVAL;
+    if (c->dtype != LAT_F32 && c->dtype != LAT_F64) return LAT_EINVAL;
+    int nmin = c->h_inst.empty() ? 0 : c->h_inst[0].nx;
+    for (const Inst1D& in : c->h_inst) nmin = std::min(nmin, in.nx);
+    for (int q = 0; q < ns; ++q)
+        if (seps[q] < 0 || seps[q] >= nmin) return LAT_EINVAL;
+    const int nout = c->n_inst * ns;
+    int rc = obs_scratch(c, (size_t)c->total_x + 2 * (size_t)nout + (ns + 1) / 2);
+    if (rc != LAT_OK) return rc;
+    double* rho = c->d_obs;
+    double* d_num = rho + c->total_x;
+    double* d_den = d_num + nout;
+    int* d_s = reinterpret_cast<int*>(d_den + nout);
+    rc = lat_moments(c, rho, nullptr, nullptr, nullptr);
+    if (rc != LAT_OK) return rc;
+    CK(cudaMemcpyAsync(d_s, seps, sizeof(int) * ns, cudaMemcpyHostToDevice, c->stream));
+    CK(launch_s1_1d(c->dtype, c->f[c->cur], c->d_inst, c->n_inst, c->nv, rho, d_s, ns, d_num,
+                    d_den, c->sm_count, c->stream));
+    CK(cudaMemcpyAsync(num, d_num, sizeof(double) * nout, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaMemcpyAsync(den, d_den, sizeof(double) * nout, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    return LAT_OK;
+}
+
 int lat_set_scheme(lat_ctx* c, int scheme, double mu) {
     if (!c) return LAT_EINVAL;
     if (scheme != LAT_SCHEME_UPWIND && scheme != LAT_SCHEME_KOREN) return LAT_EINVAL;
@@ -755,6 +840,7 @@ void lat_free(lat_ctx* c) {
     cudaFree(c->d_ampf);
     cudaFree(c->d_noise);
     cudaFree(c->d_state);
+    cudaFree(c->d_obs);
     if (c->h_glob) cudaFreeHost(c->h_glob);
     if (c->h_state) cudaFreeHost(c->h_state);
     if (c->cap) cudaStreamDestroy(c->cap);

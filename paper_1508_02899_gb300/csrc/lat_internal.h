@@ -118,6 +118,16 @@ bool step1d_moments_supported(int dtype, int nv);
 cudaError_t launch_moments1d(int dtype, int block, int tile_xpt, int grid, const Mom1DArgs& a,
                              cudaStream_t s);
 // Fold per-instance partials: instance i owns partials [per_item begin[i], per_item begin[i+1]).
+// Observables (observables.cu): <rho_r^2> and the Eulerian S1 from per-cell rho (FP64).
+cudaError_t launch_coarse1d(const double* rho, const Inst1D* inst, int n_inst, long long total_x,
+                            const int* widths, int nw, double* P, double* out, int sm_count,
+                            cudaStream_t s);
+cudaError_t launch_coarse2d(const double* rho, int nx, int ny, double dx, const int* widths,
+                            int nw, double* S, double* out, int sm_count, cudaStream_t s);
+cudaError_t launch_s1_1d(int dtype, const void* f, const Inst1D* inst, int n_inst, int nv,
+                         const double* rho, const int* seps, int ns, double* num, double* den,
+                         int sm_count, cudaStream_t s);
+
 cudaError_t launch_finalize1d(const double* partials, const int* inst_item_begin,
                               const Inst1D* inst, int n_inst, double* glob, int per_item,
                               cudaStream_t s);

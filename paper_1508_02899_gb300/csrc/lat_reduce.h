@@ -27,6 +27,9 @@ __device__ __forceinline__ double nval(const Comp& a) { return __dadd_rn(a.s, a.
 __device__ __forceinline__ Comp shfl_down(const Comp& a, int off) {
     return Comp{__shfl_down_sync(0xffffffffu, a.s, off), __shfl_down_sync(0xffffffffu, a.c, off)};
 }
+__device__ __forceinline__ Comp shfl_up(const Comp& a, int off) {
+    return Comp{__shfl_up_sync(0xffffffffu, a.s, off), __shfl_up_sync(0xffffffffu, a.c, off)};
+}
 
 // Kahan-compensated FP32 accumulator (c holds the negated running error: the sum is s - c).
 struct FComp {

@@ -720,7 +720,7 @@ int occupancy_ring_t() {
     return nb;
 }
 
-#define LAT2D_NV_LIST(X) X(1) X(3) X(5) X(9) X(13) X(17) X(21) X(33)
+#define LAT2D_NV_LIST(X) X(1) X(3) X(5) X(9) X(13) X(17) X(19) X(21) X(33)
 // velocity lattices whose columns may be split over several warp groups
 #define LAT2D_SPLIT(n) ((n) >= 17)
 
@@ -1246,6 +1246,14 @@ int ctx2d_step(Ctx2D* c, void* const f[2], int n, cudaStream_t s) {
     if (rc != LAT_OK) return rc;
     CK2(cudaGraphLaunch(ge, s));
     return LAT_OK;
+}
+
+void ctx2d_geometry(const Ctx2D* c, int* nx, int* ny, int* nv, double* dx, double* dv) {
+    *nx = c->nx;
+    *ny = c->ny;
+    *nv = c->nv;
+    *dx = c->dx;
+    *dv = c->dv;
 }
 
 int ctx2d_moments(Ctx2D* c, const void* f, int cur, double* rho, double* mean_v,

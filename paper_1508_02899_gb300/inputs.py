@@ -145,6 +145,23 @@ def flow2d_inputs(seed: int, nsteps: int, nx: int, ny: int, dx: float, kmax: int
     return Flow2D(kvec=kvec, a=a, phi0=phi0, noise=noise, tau_f=tau_f)
 
 
+def cellular_flow(nx: int, ny: int, L: float, U: float = 1.0):
+    """The tilted cellular flow of Sec. 4.1: u = (d_y psi, -d_x psi) of the stationary stream
+    function psi = U sin(pi (x + y) / L) sin(pi (x - y) / L), at the cell positions x_i = i dx,
+    y_k = k dx (dx = L / nx, ny dx = L).  Returns (ux, uy), each (ny, nx), FP64."""
+    dx = L / nx
+    x = np.arange(nx) * dx
+    y = np.arange(ny) * dx
+    X, Y = np.meshgrid(x, y)
+    a = math.pi * (X + Y) / L
+    b = math.pi * (X - Y) / L
+    k = math.pi / L
+    # d_x psi = U k (cos a sin b + sin a cos b),  d_y psi = U k (cos a sin b - sin a cos b)
+    dpsi_dx = U * k * (np.cos(a) * np.sin(b) + np.sin(a) * np.cos(b))
+    dpsi_dy = U * k * (np.cos(a) * np.sin(b) - np.sin(a) * np.cos(b))
+    return dpsi_dy, -dpsi_dx
+
+
 # --------------------------------------------------------------------------------------------
 # Parameter choices
 # --------------------------------------------------------------------------------------------

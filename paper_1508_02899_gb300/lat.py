@@ -63,6 +63,8 @@ def _load():
         "lat_steps_done": (c_longlong, [P]),
         "lat_set_launch": (c_int, [P, c_int, c_int, c_int, c_int]),
         "lat_set_scheme": (c_int, [P, c_int, c_double]),
+        "lat_coarse_moment": (c_int, [P, c_int, P, P]),
+        "lat_s1": (c_int, [P, c_int, P, P, P]),
         "lat_autotune": (c_int, [P, c_int, POINTER(c_double)]),
         "lat_strerror": (ctypes.c_char_p, [c_int]),
         "lat_free": (None, [P]),
@@ -180,6 +182,28 @@ class _Ctx:
     def set_scheme(self, scheme: int, mu: float = 2.0 / 3.0):
         """Drag sub-step scheme: SCHEME_UPWIND or SCHEME_KOREN (limiter bound mu)."""
         _check(_lib.lat_set_scheme(self._h, scheme, mu), "lat_set_scheme")
+
+    def coarse_moment(self, widths):
+        """<rho_r^2> for window widths in cells: array [instances, len(widths)]."""
+        w = np.ascontiguousarray(widths, dtype=np.int32)
+        out = np.zeros((self._n_out(), len(w)))
+        _check(_lib.lat_coarse_moment(self._h, len(w), w.ctypes.data_as(POINTER(c_int)),
+                                       _dptr(out)),
+               "lat_coarse_moment")
+        return out
+
+    def s1(self, seps):
+        """Eulerian S1 terms for separations in cells: (num, den), each [instances, len(seps)];
+        S1 = num / den."""
+        s = np.ascontiguousarray(seps, dtype=np.int32)
+        num = np.zeros((self._n_out(), len(s)))
+        den = np.zeros_like(num)
+        _check(_lib.lat_s1(self._h, len(s), s.ctypes.data_as(POINTER(c_int)), _dptr(num),
+                           _dptr(den)), "lat_s1")
+        return num, den
+
+    def _n_out(self):
+        return 1
 
     def autotune(self, reps: int = 5):
         best = np.zeros(4)
@@ -302,6 +326,9 @@ class Ensemble(_Ctx):
         _check(_lib.lat_ensemble_init(byref(self._h), n, arr, nv, _DTYPES[f0.dtype],
                                       _ptr(self.f[0]), _ptr(self.f[1]), _stream(stream)),
                "lat_ensemble_init")
+
+    def _n_out(self):
+        return self.n
 
     @property
     def state(self) -> torch.Tensor:

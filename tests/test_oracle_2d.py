@@ -196,3 +196,25 @@ def test_phase_walk_decorrelates_like_exp():
     for _ in range(n_steps):
         phi = O.phase_advance(phi, rng.standard_normal(n_real), dt, tau_f)
     assert abs(np.mean(np.cos(phi)) - math.exp(-n_steps * dt / tau_f)) < 0.02
+
+
+def test_cellular_flow_is_the_orthogonal_gradient_of_its_stream_function():
+    """inputs.cellular_flow against centred differences of psi = U sin(pi(x+y)/L) sin(pi(x-y)/L)
+    (fourth-order stencil) and a spectral divergence of zero."""
+    import math
+    from paper_1508_02899_gb300 import inputs as I
+    L, n, U = 2 * math.pi, 128, 1.3
+    ux, uy = I.cellular_flow(n, n, L, U)
+    dx = L / n
+    x = np.arange(n) * dx
+    X, Y = np.meshgrid(x, x)
+    psi = U * np.sin(np.pi * (X + Y) / L) * np.sin(np.pi * (X - Y) / L)
+
+    def d(f, axis):
+        return (8 * (np.roll(f, -1, axis) - np.roll(f, 1, axis))
+                - (np.roll(f, -2, axis) - np.roll(f, 2, axis))) / (12 * dx)
+    np.testing.assert_allclose(ux, d(psi, 0), atol=1e-6)
+    np.testing.assert_allclose(uy, -d(psi, 1), atol=1e-6)
+    kx = np.fft.fftfreq(n, d=dx) * 2 * np.pi
+    div = np.fft.ifft2(1j * kx[None, :] * np.fft.fft2(ux) + 1j * kx[:, None] * np.fft.fft2(uy))
+    assert np.abs(div).max() < 1e-12
