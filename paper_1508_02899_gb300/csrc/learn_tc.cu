@@ -239,9 +239,31 @@ __device__ __forceinline__ void features_of(const LearnArgs& a, const Raw& r, in
     X[15] = 1.f;
 }
 
+// Division of 32-bit unsigned n by a divisor d fixed at launch, by one high multiply (Granlund and
+// Montgomery's round-up method): with l = ceil(log2 d) and m = floor(2^32 (2^l - d) / d) + 1,
+// n / d = (mulhi(m, n) + n) >> l, the sum formed in 64 bits.
+struct FastDiv {
+    unsigned m;
+    int l;
+    unsigned d;
+};
+FastDiv fast_div(unsigned d) {
+    int l = 0;
+    while ((1ull << l) < d) ++l;
+    const unsigned long long m = ((1ull << 32) * ((1ull << l) - d)) / d + 1;
+    return FastDiv{(unsigned)m, l, d};
+}
+__device__ __forceinline__ unsigned fdiv(unsigned n, const FastDiv& f) {
+    return (unsigned)(((unsigned long long)__umulhi(f.m, n) + n) >> f.l);
+}
+
+// Tiles: with N_x a multiple of 128, tile t covers 128 consecutive x of one spatial row in plane
+// t mod N_v^2 (planes fastest), so that the velocity neighbours a tile gathers were just loaded
+// by the tiles of the neighbouring planes; nbx = N_x / 128.  Otherwise tiles run through the
+// phase cells in their storage order.
 template <int NV>
 __global__ void __launch_bounds__(128) k_mlp_tc(const LearnArgs a, const unsigned char* image,
-                                                int kstep) {
+                                                int kstep, const FastDiv nbx) {
     extern __shared__ __align__(1024) unsigned char sm[];
     unsigned char* W = sm;
     unsigned char* A1 = sm + kSA1;
@@ -297,8 +319,13 @@ __global__ void __launch_bounds__(128) k_mlp_tc(const LearnArgs a, const unsigne
         if (q.on) {
             int p, x, y;
             if (row_tiles) {  // the tile is 128 consecutive x of one row of one plane
-                split_index((unsigned)(tile * 128), (unsigned)ncell, (unsigned)a.nx, p, x, y);
-                x += t;
+                constexpr unsigned NN = NV * NV;
+                p = (int)((unsigned)tile % NN);
+                const unsigned rb = (unsigned)tile / NN;
+                const unsigned yy = fdiv(rb, nbx);
+                y = (int)yy;
+                x = (int)((rb - yy * nbx.d) * 128u) + t;
+                q.i = (long long)p * ncell + (long long)y * a.nx + x;
             } else {
                 split_index((unsigned)q.i, (unsigned)ncell, (unsigned)a.nx, p, x, y);
             }
@@ -462,8 +489,10 @@ cudaError_t launch_learn_tc_pack(const float* params, void* wtc, cudaStream_t s)
 cudaError_t launch_mlp_tc(int nv, const LearnArgs& a, const void* wtc, int sm_count, int k,
                           cudaStream_t s) {
     const long long n = (long long)a.nx * a.ny * nv * nv;
-    const int grid = (int)std::max<long long>(1, std::min<long long>((n + 127) / 128, 4LL * sm_count));
+    // five resident CTAs per SM: 5 x 64 TMEM columns and 5 x 40 KB of shared memory
+    const int grid = (int)std::max<long long>(1, std::min<long long>((n + 127) / 128, 5LL * sm_count));
     const unsigned char* img = static_cast<const unsigned char*>(wtc);
+    const FastDiv nbx = fast_div((unsigned)std::max(1, a.nx / 128));
     switch (nv) {
 #define X(nn)                                                                                   \
     case nn: {                                                                                  \
@@ -475,7 +504,7 @@ cudaError_t launch_mlp_tc(int nv, const LearnArgs& a, const void* wtc, int sm_co
             if (e != cudaSuccess) return e;                                                     \
             attr = true;                                                                        \
         }                                                                                       \
-        k_mlp_tc<nn><<<grid, 128, kSmemReq, s>>>(a, img, k);                                    \
+        k_mlp_tc<nn><<<grid, 128, kSmemReq, s>>>(a, img, k, nbx);                               \
         return cudaGetLastError();                                                              \
     }
         LEARN_TC_NV_LIST(X)

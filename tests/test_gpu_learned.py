@@ -105,8 +105,11 @@ def test_fp32_network_matches_oracle(lat, nx, ny, nv):
     lt.close()
 
 
-@pytest.mark.parametrize("nx,ny,nv", [(32, 20, 9), (150, 6, 5), (48, 16, 17)])
+@pytest.mark.parametrize("nx,ny,nv", [(32, 20, 9), (150, 6, 5), (48, 16, 17), (256, 12, 9),
+                                     (128, 7, 5)])
 def test_tensor_core_network_matches_oracle(lat, nx, ny, nv):
+    """Ragged 128-cell tiles in storage order, and (N_x a multiple of 128) row tiles taken planes
+    first."""
     c = case(nx, ny, nv, 4, 11 + nx)
     W = quantised_weights(5, 0.4)
     want = Lr.rollout(c["f0"], W, 4, c["flows"], **c["kw"])
@@ -161,11 +164,13 @@ def test_rollout_gradient_matches_oracle(lat):
     lt.close()
 
 
+@pytest.mark.parametrize("nx", [72, 256])
 @pytest.mark.parametrize("mode,tol", [(1, 1e-5), (2, 0.03)])
-def test_corrections_match_oracle(lat, mode, tol):
-    """Correction fluxes of one state (128-cell tiles, ragged end): FP32 network to 1e-5 of their
-    norm, BF16 tensor-core network to 3 % (inputs, weights, activations rounded to 2^-8)."""
-    c = case(72, 30, 9, 1, 17)
+def test_corrections_match_oracle(lat, mode, tol, nx):
+    """Correction fluxes of one state (128-cell tiles with a ragged end, or row tiles): FP32
+    network to 1e-5 of their norm, BF16 tensor-core network to 3 % (inputs, weights, activations
+    rounded to 2^-8)."""
+    c = case(nx, 30, 9, 1, 17)
     W = quantised_weights(7, 0.5)
     gx, gy = Lr.corrections(c["f0"], *c["flows"][0], W,
                             **{k: c["kw"][k] for k in ("tau_p", "dt", "dv", "dx")})
