@@ -47,6 +47,26 @@ __global__ void __launch_bounds__(256) k_rho_star(const LearnArgs a, int kstep) 
         for (int jy = 0; jy < NV; ++jy)
             for (int jx = 0; jx < NV; ++jx) s = __fadd_rn(s, fstar<NV>(f, jx, jy, x, y, a.nx, a.ny));
         a.rho[c] = s;
+        if (a.feat) {
+            // the spatial parts of the features, formed once per cell with the same operations
+            // as features(): 1/rho*, dt times the centred velocity gradients, u / dv
+            const float* ux = a.u;
+            const float* uy = a.u + ncell;
+            const int xp = x + 1 == a.nx ? 0 : x + 1, xm = x == 0 ? a.nx - 1 : x - 1;
+            const int yp = y + 1 == a.ny ? 0 : y + 1, ym = y == 0 ? a.ny - 1 : y - 1;
+            const size_t yr = (size_t)y * a.nx;
+            float4 fa, fb;
+            fa.x = s != 0.f ? __frcp_rn(s) : 0.f;
+            fa.y = __fmul_rn(__fsub_rn(ux[yr + xp], ux[yr + xm]), a.dt_2dx);
+            fa.z = __fmul_rn(__fsub_rn(ux[(size_t)yp * a.nx + x], ux[(size_t)ym * a.nx + x]), a.dt_2dx);
+            fa.w = __fmul_rn(__fsub_rn(uy[yr + xp], uy[yr + xm]), a.dt_2dx);
+            fb.x = __fmul_rn(__fsub_rn(uy[(size_t)yp * a.nx + x], uy[(size_t)ym * a.nx + x]), a.dt_2dx);
+            fb.y = __fmul_rn(ux[c], a.inv_dv);
+            fb.z = __fmul_rn(uy[c], a.inv_dv);
+            fb.w = 0.f;
+            a.feat[2 * c] = fa;
+            a.feat[2 * c + 1] = fb;
+        }
     }
 }
 

@@ -36,6 +36,8 @@ struct LearnArgs {
     const float* f[2];     // state buffers; the step reads parity (st->step + k) & 1
     const float* u;        // flow [2][ny][nx]
     float* rho;            // streamed density [ny][nx]
+    float4* feat;          // per spatial cell, two float4 (or null): [1/rho*, dt du_x/dx,
+                           // dt du_x/dy, dt du_y/dx], [dt du_y/dy, u_x/dv, u_y/dv, 0]
     const float* params;   // FP32 parameters [kLNParam]
     float* G;              // corrections [2][N_v^2][ny][nx]
     const DevState* st;

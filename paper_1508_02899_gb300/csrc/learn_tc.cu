@@ -176,12 +176,12 @@ __device__ __forceinline__ int vwrap(int v, int n) { return wrap_near(v, n); }
 
 // Raw inputs of one phase cell's features (learn.cu's features, split so that the global loads
 // can be issued early and consumed after other work): f* over the 3 x 3 velocity neighbourhood,
-// rho*, and u at the cell and at its four spatial neighbours.  Element indices are 32-bit (the
+// and the spatial parts of the features, which the density kernel formed once per spatial cell
+// (1/rho*, the four velocity gradients times dt, u / dv).  Element indices are 32-bit (the
 // learned step keeps N_v^2 N_x N_y below 2^32) and periodic wraps are one conditional add.
 struct Raw {
     float fs[9];
-    float rho;
-    float uxc, uyc, uxe, uxw, uxn, uxs, uye, uyw, uyn, uys;
+    float4 fa, fb;
 };
 
 template <int NV>
@@ -190,7 +190,8 @@ __device__ __forceinline__ void load_raw(const LearnArgs& a, const float* f, int
     constexpr int J = (NV - 1) / 2;
     const unsigned nx = (unsigned)a.nx, ncell = (unsigned)a.nx * (unsigned)a.ny;
     const unsigned c = (unsigned)y * nx + (unsigned)x;
-    r.rho = a.rho[c];
+    r.fa = a.feat[2 * c];
+    r.fb = a.feat[2 * c + 1];
     int q = 0;
 #pragma unroll
     for (int dy = -1; dy <= 1; ++dy) {
@@ -206,36 +207,21 @@ __device__ __forceinline__ void load_raw(const LearnArgs& a, const float* f, int
                            : 0.f;
         }
     }
-    const float* ux = a.u;
-    const float* uy = a.u + ncell;
-    const unsigned xp = x + 1 == a.nx ? 0u : (unsigned)x + 1, xm = x == 0 ? nx - 1 : (unsigned)x - 1;
-    const unsigned yp = y + 1 == a.ny ? 0u : (unsigned)y + 1, ym = y == 0 ? (unsigned)a.ny - 1 : (unsigned)y - 1;
-    const unsigned yr = (unsigned)y * nx;
-    r.uxc = ux[c];
-    r.uyc = uy[c];
-    r.uxe = ux[yr + xp];
-    r.uxw = ux[yr + xm];
-    r.uxn = ux[yp * nx + x];
-    r.uxs = ux[ym * nx + x];
-    r.uye = uy[yr + xp];
-    r.uyw = uy[yr + xm];
-    r.uyn = uy[yp * nx + x];
-    r.uys = uy[ym * nx + x];
 }
 
 template <int NV>
 __device__ __forceinline__ void features_of(const LearnArgs& a, const Raw& r, int jx, int jy,
                                             float (&X)[kLNF]) {
     constexpr int J = (NV - 1) / 2;
-    const float inv = r.rho != 0.f ? __frcp_rn(r.rho) : 0.f;
+    const float inv = r.fa.x;
 #pragma unroll
     for (int q = 0; q < 9; ++q) X[q] = __fmul_rn(r.fs[q], inv);
-    X[9] = __fmul_rn(__fsub_rn(r.uxe, r.uxw), a.dt_2dx);
-    X[10] = __fmul_rn(__fsub_rn(r.uxn, r.uxs), a.dt_2dx);
-    X[11] = __fmul_rn(__fsub_rn(r.uye, r.uyw), a.dt_2dx);
-    X[12] = __fmul_rn(__fsub_rn(r.uyn, r.uys), a.dt_2dx);
-    X[13] = __fmul_rn(a.g, __fsub_rn(__fmul_rn(r.uxc, a.inv_dv), (float)(jx - J)));
-    X[14] = __fmul_rn(a.g, __fsub_rn(__fmul_rn(r.uyc, a.inv_dv), (float)(jy - J)));
+    X[9] = r.fa.y;
+    X[10] = r.fa.z;
+    X[11] = r.fa.w;
+    X[12] = r.fb.x;
+    X[13] = __fmul_rn(a.g, __fsub_rn(r.fb.y, (float)(jx - J)));
+    X[14] = __fmul_rn(a.g, __fsub_rn(r.fb.z, (float)(jy - J)));
     X[15] = 1.f;
 }
 
@@ -335,7 +321,6 @@ __global__ void __launch_bounds__(128) k_mlp_tc(const LearnArgs a, const unsigne
         }
     };
     // features of q into A1 (zeros past the end); X kept for the output bounds
-    float Xc[kLNF];
     auto store_a1 = [&](const Cell& q, float (&X)[kLNF]) {
         if (q.on) {
             features_of<NV>(a, q.r, q.jx, q.jy, X);
@@ -369,11 +354,10 @@ __global__ void __launch_bounds__(128) k_mlp_tc(const LearnArgs a, const unsigne
         __syncthreads();
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     };
-    Cell cur, nxt;
-    long long tile = blockIdx.x;
-    load(tile, cur);
-    store_a1(cur, Xc);
-    for (; tile < ntiles; tile += gridDim.x) {
+    // One tile: the MMAs of `cur` (features already in A1) while `nxt`, the block's next tile,
+    // is loaded and staged.  Two Cell/feature sets alternate, so nothing is copied per tile.
+    auto one_tile = [&](long long tile, const Cell& cur, const float (&Xc)[kLNF], Cell& nxt,
+                        float (&Xn)[kLNF]) -> bool {
         // layer 1: D = A1 (128 x 16) W1^T, while the next tile's features load
         sync_for_mma();
         if (t == 0) {
@@ -381,10 +365,7 @@ __global__ void __launch_bounds__(128) k_mlp_tc(const LearnArgs a, const unsigne
             commit(bar);
         }
         load(tile + gridDim.x, nxt);
-        if (!wait_mma()) {
-            failed = true;
-            break;
-        }
+        if (!wait_mma()) return false;
         epilogue64(trow, A2, t);
         // layer 2: D = [H1 1 0] (128 x 80) W2^T; A1 is free again: stage the next features
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -395,12 +376,8 @@ __global__ void __launch_bounds__(128) k_mlp_tc(const LearnArgs a, const unsigne
                     sdesc(wbase + kW2T + kk * 2 * 1024, 1024, 128), idesc_n(64), kk);
             commit(bar);
         }
-        float Xn[kLNF];
         store_a1(nxt, Xn);
-        if (!wait_mma()) {
-            failed = true;
-            break;
-        }
+        if (!wait_mma()) return false;
         epilogue64(trow, A2, t);  // MMA 2 is done with A2: overwrite with H2
         // layer 3: D[0..15] = [H2 1 0] (128 x 80) W3^T
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -411,10 +388,7 @@ __global__ void __launch_bounds__(128) k_mlp_tc(const LearnArgs a, const unsigne
                     sdesc(wbase + kW3T + kk * 2 * 256, 256, 128), idesc_n(16), kk);
             commit(bar);
         }
-        if (!wait_mma()) {
-            failed = true;
-            break;
-        }
+        if (!wait_mma()) return false;
         float z0, z1;
         tmem_ld2(trow, z0, z1);
         if (cur.on) {
@@ -426,10 +400,26 @@ __global__ void __launch_bounds__(128) k_mlp_tc(const LearnArgs a, const unsigne
             a.G[(size_t)n + gi] =
                 cur.jy < NV - 1 ? __fmul_rn(y1, __fsub_rn(cur.r.fs[7], cur.r.fs[4])) : 0.f;
         }
-        cur = nxt;
-#pragma unroll
-        for (int k = 0; k < kLNF; ++k) Xc[k] = Xn[k];
         // the next layer-1 MMA (after sync_for_mma) overwrites D only once every thread has read it
+        return true;
+    };
+    Cell c0, c1;
+    float X0[kLNF], X1[kLNF];
+    long long tile = blockIdx.x;
+    load(tile, c0);
+    store_a1(c0, X0);
+    while (tile < ntiles) {
+        if (!one_tile(tile, c0, X0, c1, X1)) {
+            failed = true;
+            break;
+        }
+        tile += gridDim.x;
+        if (tile >= ntiles) break;
+        if (!one_tile(tile, c1, X1, c0, X0)) {
+            failed = true;
+            break;
+        }
+        tile += gridDim.x;
     }
     if (failed && t == 0) atomicOr(const_cast<unsigned*>(&a.st->status), ST_TIMEOUT);
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");

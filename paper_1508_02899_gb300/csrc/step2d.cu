@@ -889,6 +889,7 @@ struct Ctx2D {
     float* d_params = nullptr;   // [kLNParam] FP32
     void* d_wtc = nullptr;       // tensor-core weight tiles (BF16) and biases
     float* d_rho = nullptr;      // [ny][nx]
+    float4* d_feat = nullptr;    // [ny][nx][2]: spatial parts of the features (BF16 network)
     float* d_G = nullptr;        // [2][N_v^2][ny][nx]
     DevState* d_st0 = nullptr;   // step 0, no flags: explicit-buffer rollouts
     // moments
@@ -1000,6 +1001,7 @@ LearnArgs learn_args(const Ctx2D* c, const void* f0, const void* f1, const DevSt
     la.u = c->flow_kind == LAT_FLOW_FIELD ? static_cast<const float*>(c->field)
                                           : static_cast<const float*>(c->d_u);
     la.rho = c->d_rho;
+    la.feat = c->d_feat;
     la.params = c->d_params;
     la.G = c->d_G;
     la.st = st;
@@ -1418,6 +1420,7 @@ int ctx2d_learn_set(Ctx2D* c, const float* params, int mode, cudaStream_t s) {
     if (!c->d_params) {
         if (cudaMalloc(&c->d_params, sizeof(float) * kLNParam) != cudaSuccess ||
             cudaMalloc(&c->d_rho, sizeof(float) * ncell) != cudaSuccess ||
+            cudaMalloc(&c->d_feat, sizeof(float4) * 2 * ncell) != cudaSuccess ||
             cudaMalloc(&c->d_G, sizeof(float) * 2 * c->nv * c->nv * ncell) != cudaSuccess ||
             cudaMalloc(&c->d_wtc, learn_tc_bytes()) != cudaSuccess ||
             cudaMalloc(&c->d_st0, sizeof(DevState)) != cudaSuccess)
@@ -1590,6 +1593,7 @@ void ctx2d_destroy(Ctx2D* c) {
     cudaFree(c->d_params);
     cudaFree(c->d_wtc);
     cudaFree(c->d_rho);
+    cudaFree(c->d_feat);
     cudaFree(c->d_G);
     cudaFree(c->d_st0);
     cudaFree(c->d_glob);
