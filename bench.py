@@ -315,12 +315,14 @@ def build_2d(args, I, lat, torch, dev, rank, nsteps, n=512, nv=33, store="f32"):
     return lt, n * n * nv * nv, fl.noise[:1], np.zeros(4), desc
 
 
-def build_cellular(args, I, lat, torch, dev, rank, n=1024, nv=19):
+def build_cellular(args, I, lat, torch, dev, rank, n=1024, nv=19, koren=False):
     """The tilted cellular flow of Sec. 4.1 (U = 1, L = 2 pi) frozen on an n^2 x 19^2 FP32
-    lattice, St = 1/(2 pi), kappa = 8 pi 1e-3, Gaussian velocity start."""
+    lattice, St = 1/(2 pi), kappa = 8 pi 1e-3, Gaussian velocity start; with `koren` the
+    flux-limited drag of the paper's 2D runs (mu = 2/3)."""
     L = 2 * math.pi
     tau_p, kappa = L / (2 * math.pi), 8 * math.pi * 1e-3
-    dt = I.choose_dt(2, n, L, nv, tau_p, kappa, u_rms=0.1)  # max |u| = 0.5 = 5 u_rms
+    dt = I.choose_dt(2, n, L, nv, tau_p, kappa, u_rms=0.1,  # max |u| = 0.5 = 5 u_rms
+                     cfl_factor=1 + KOREN_MU if koren else 1.0)
     dx = L / n
     dv = dx / dt
     col = I.gaussian_column(1, nv, dx, dv, 0.3 * ((nv - 1) // 2) * dv)
@@ -332,6 +334,8 @@ def build_cellular(args, I, lat, torch, dev, rank, n=1024, nv=19):
     u = torch.tensor(np.stack([ux, uy]), dtype=torch.float32, device=dev)
     lt.set_flow_field(u)
     lt._keep_field = u
+    if koren:
+        lt.set_scheme(lat.SCHEME_KOREN, KOREN_MU)
     return lt, n * n * nv * nv
 
 
@@ -580,6 +584,18 @@ def main():
             "kernel": kernel_label("2d", b2, 19), "steps": 40, "status": st2,
             "flow": "tilted cellular flow (Sec. 4.1), frozen field, St = 1/(2 pi), "
                     "kappa = 8 pi 1e-3"}
+        lt.close()
+        del lt
+        torch.cuda.empty_cache()
+        lt, c2 = build_cellular(args, I, lat, torch, dev, rank, koren=True)
+        ms2, _ = timed(lt, 20, 3, torch, dist, world, local, dev)
+        st2 = lt.status()
+        g2 = c2 * 20 / (ms2 / 1e3) / 1e9
+        forms["2d_cellular_koren_fp32_1024x1024_19x19"] = {
+            "gcups": g2, "ms_per_step": ms2 / 20, "hbm_frac_of_8B": g2 * 8 / peak,
+            "kernel": "k_lim2d_stage<float,1>, k_lim2d_stage<float,2>, k_lim2d_diffuse<float>",
+            "steps": 20, "status": st2,
+            "flow": "tilted cellular flow, flux-limited drag (Koren, mu = 2/3), Heun's method"}
         lt.close()
         del lt
         torch.cuda.empty_cache()

@@ -267,11 +267,14 @@ int lat_set_launch(lat_ctx* c, int kernel, int block, int blocks_per_sm, int mod
  *          integrated by Heun's method: f1 = f + dt L(f), f_new = (f + f1 + dt L(f1)) / 2.
  *  mu:     limiter bound, 0 < mu <= 2 (2/3 reads the paper's parameter; 1 is the limiter's
  *          usual form); ignored for UPWIND.
- * Each Heun stage keeps f >= 0 when (dt/dv) max|a| (1 + mu) <= 1; lat_set_scheme checks the
- * at-rest bound (dt/tau_p) J (1 + mu) <= 1 of every instance (LAT_ECFL otherwise) and the step
- * kernels flag the local bound at run time.  1D lattices and ensembles, FP32 or FP64, with N_v in
- * {3, 5, 9, 17, 33, 65}; other contexts return LAT_EINVAL.  The 16-bit and learned 2D paths keep
- * the upwind scheme. */
+ * Each Heun stage keeps f >= 0 when (dt/dv) max|a| (1 + mu) <= 1 (2D, unsplit: the sum of both
+ * axes' maxima); lat_set_scheme checks the at-rest bound (dt/tau_p) J d (1 + mu) <= 1 of every
+ * instance (LAT_ECFL otherwise) and the step kernels flag the local bound at run time.
+ * 1D lattices and ensembles, FP32 or FP64, with N_v in {3, 5, 9, 17, 33, 65}: the limited sweep
+ * runs inside every 1D step kernel.  2D lattices, FP32 or FP64, N_v^2 N_x N_y < 2^32 and
+ * N_x, N_y > (N_v - 1) / 2: three
+ * passes (two Heun stages, the diffusion) with a scratch copy of the state allocated here.  The
+ * 16-bit and learned 2D paths keep the upwind scheme (LAT_EINVAL). */
 int lat_set_scheme(lat_ctx* c, int scheme, double mu);
 
 /* ---- observables (Section 3.2, Eqs. def_coarse and def_eulS1) ---- */

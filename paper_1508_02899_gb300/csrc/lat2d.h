@@ -14,6 +14,7 @@ int ctx2d_set_noise(Ctx2D* c, const double* noise, long long rows, long long ste
 int ctx2d_step(Ctx2D* c, void* const f[2], int n, cudaStream_t s);
 int ctx2d_prepare(Ctx2D* c, void* const f[2], int n);
 void ctx2d_geometry(const Ctx2D* c, int* nx, int* ny, int* nv, double* dx, double* dv);
+int ctx2d_set_scheme(Ctx2D* c, int scheme, double mu);
 int ctx2d_moments(Ctx2D* c, const void* f, int cur, double* rho, double* mean_v,
                   double* mean_v2, double* globals, cudaStream_t s);
 // 16-bit storage: line maxima of the caller's initial state (scales 1), encoding of an FP32

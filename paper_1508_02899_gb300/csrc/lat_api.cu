@@ -712,8 +712,14 @@ int lat_s1(lat_ctx* c, int ns, const int* seps, double* num, double* den) {
 int lat_set_scheme(lat_ctx* c, int scheme, double mu) {
     if (!c) return LAT_EINVAL;
     if (scheme != LAT_SCHEME_UPWIND && scheme != LAT_SCHEME_KOREN) return LAT_EINVAL;
+    if (c->d == 2) {
+        if (scheme == LAT_SCHEME_KOREN && !(mu > 0.0 && mu <= 2.0)) return LAT_EINVAL;
+        const int rc = ctx2d_set_scheme(c->c2, scheme, mu);
+        if (rc == LAT_OK) drop_graphs(c);
+        return rc;
+    }
     if (scheme == LAT_SCHEME_KOREN) {
-        if (c->d != 1 || (c->dtype != LAT_F32 && c->dtype != LAT_F64)) return LAT_EINVAL;
+        if (c->dtype != LAT_F32 && c->dtype != LAT_F64) return LAT_EINVAL;
         if (!step1d_limiter_supported(c->nv)) return LAT_EINVAL;
         if (!(mu > 0.0 && mu <= 2.0)) return LAT_EINVAL;
         // each Heun stage is positive for nu (1 + mu) <= 1; at rest nu = (dt/tau_p) J

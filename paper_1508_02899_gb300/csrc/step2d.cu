@@ -890,6 +890,10 @@ struct Ctx2D {
     void* d_wtc = nullptr;       // tensor-core weight tiles (BF16) and biases
     float* d_rho = nullptr;      // [ny][nx]
     float4* d_feat = nullptr;    // [ny][nx][2]: spatial parts of the features (BF16 network)
+    // drag scheme: upwind (the fused kernels) or flux-limited (limiter2d.cu, scratch d_lim)
+    int scheme = LAT_SCHEME_UPWIND;
+    double mu = 2.0 / 3.0;
+    void* d_lim = nullptr;
     float* d_G = nullptr;        // [2][N_v^2][ny][nx]
     DevState* d_st0 = nullptr;   // step 0, no flags: explicit-buffer rollouts
     // moments
@@ -1035,6 +1039,8 @@ int enqueue2d(Ctx2D* c, void* const f[2], int n, cudaStream_t s, int dry) {
         if (c->learn) {
             const int rc = enqueue_learned(c, a, grid, k, s);
             if (rc != LAT_OK) return rc;
+        } else if (c->scheme == LAT_SCHEME_KOREN) {
+            CK2(launch_step2d_limited(c->dtype, a, c->nv, c->mu, c->d_lim, k, c->sm_count, s));
         } else if (c->half) {
             const Step2DHArgs ha = half_args(c, a);
             CK2(launch_scale2d(c->nv, c->ny, ha, k, s));
@@ -1250,6 +1256,32 @@ int ctx2d_step(Ctx2D* c, void* const f[2], int n, cudaStream_t s) {
     return LAT_OK;
 }
 
+int ctx2d_set_scheme(Ctx2D* c, int scheme, double mu) {
+    if (scheme == LAT_SCHEME_KOREN) {
+        if (c->half || c->learn || (c->dtype != LAT_F32 && c->dtype != LAT_F64)) return LAT_EINVAL;
+        const long long n = (long long)c->nx * c->ny * c->nv * c->nv;
+        const int Jv = (c->nv - 1) / 2;
+        // 32-bit indices, one-step periodic wraps of the streaming shifts, grid.y = plane
+        if (n >= (1ll << 32) || c->nx <= Jv || c->ny <= Jv)
+            return LAT_EINVAL;
+        // each Heun stage is positive for (dt/dv)(max|a_x| + max|a_y|)(1 + mu) <= 1; at rest
+        // that is 2 g J (1 + mu)
+        const int J = (c->nv - 1) / 2;
+        if (2.0 * c->g * J * (1.0 + mu) > 1.0) return LAT_ECFL;
+        if (!c->d_lim) {
+            const size_t bytes = (size_t)n * (c->dtype == LAT_F64 ? 8 : 4);
+            if (cudaMalloc(&c->d_lim, bytes) != cudaSuccess) return LAT_ENOMEM;
+        }
+        c->mu = mu;
+    } else {
+        cudaFree(c->d_lim);
+        c->d_lim = nullptr;
+    }
+    c->scheme = scheme;
+    drop(c);
+    return LAT_OK;
+}
+
 void ctx2d_geometry(const Ctx2D* c, int* nx, int* ny, int* nv, double* dx, double* dv) {
     *nx = c->nx;
     *ny = c->ny;
@@ -1314,7 +1346,7 @@ int ctx2d_set_launch(Ctx2D* c, int kernel, int block, int bps, int mode) {
 }
 
 int ctx2d_autotune(Ctx2D* c, void* const f[2], int reps, double* best, cudaStream_t s) {
-    if (c->learn) {  // the learned step has one launch shape
+    if (c->learn || c->scheme == LAT_SCHEME_KOREN) {  // one launch shape
         if (best) {
             best[0] = 1;
             best[1] = TW;
@@ -1594,6 +1626,7 @@ void ctx2d_destroy(Ctx2D* c) {
     cudaFree(c->d_wtc);
     cudaFree(c->d_rho);
     cudaFree(c->d_feat);
+    cudaFree(c->d_lim);
     cudaFree(c->d_G);
     cudaFree(c->d_st0);
     cudaFree(c->d_glob);

@@ -254,4 +254,10 @@ struct SmemCol {  // one thread's column in a [NV][TW] shared array
 };
 
 }  // namespace k2d
+
+// Flux-limited 2D step (limiter2d.cu): stage 1, stage 2 and the diffusion of step k of a batch;
+// scratch holds one state.
+cudaError_t launch_step2d_limited(int dtype, const k2d::Step2DArgs& s2, int nv, double mu,
+                                  void* scratch, int k, int sm_count, cudaStream_t s);
+
 }  // namespace lat

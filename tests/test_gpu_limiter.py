@@ -1,13 +1,15 @@
-"""Parity of the flux-limited drag scheme (LAT_SCHEME_KOREN, 1D) with the FP64 oracle of
-oracle/limiter.py: single lattices after 1000 steps (1e-12 FP64, 1e-5 FP32), every launch
+"""Parity of the flux-limited drag scheme (LAT_SCHEME_KOREN) with the FP64 oracle of
+oracle/limiter.py.  1D: single lattices after 1000 steps (1e-12 FP64, 1e-5 FP32), every launch
 variant bit for bit, an ensemble with ragged sizes, the benchmark ensemble at full size on sampled
-instances, mass and positivity, and the host-side checks."""
+instances, mass and positivity, and the host-side checks.  2D (the scheme of the paper's 2D runs):
+random-phase flows on three shapes, the tilted cellular flow, mass and positivity."""
 import math
 
 import numpy as np
 import pytest
 import torch
 
+from oracle import lattice as O
 from oracle import limiter as K
 from paper_1508_02899_gb300 import inputs as I
 
@@ -180,9 +182,92 @@ def test_host_checks(lat):
         lt.set_scheme(lat.SCHEME_KOREN, MU)
     assert e.value.code == lat.LAT_EINVAL
     lt.close()
-    f2 = torch.zeros((9, 9, 8, 8), device="cuda")
-    lt = lat.Lattice(f2, d=2, nx=8, ny=8, nv=9, L=L, tau_p=L, kappa=1e-3, dt=0.05)
-    with pytest.raises(lat.LatError) as e:
+    f2 = torch.zeros((9, 9, 16, 16), dtype=torch.float16, device="cuda")
+    lt = lat.Lattice(f2, d=2, nx=16, ny=16, nv=9, L=L, tau_p=L, kappa=1e-3, dt=0.05)
+    with pytest.raises(lat.LatError) as e:  # 16-bit storage keeps the upwind scheme
         lt.set_scheme(lat.SCHEME_KOREN, MU)
     assert e.value.code == lat.LAT_EINVAL
+    lt.close()
+
+
+# ---- 2D: the scheme of the paper's 2D runs ------------------------------------------------------
+def case2d(nx, ny, nv, st, kappa, nsteps, seed, mu=MU):
+    tau_p = st * L
+    dt = I.choose_dt(2, nx, L, nv, tau_p, kappa, cfl_factor=1 + mu)
+    dx = L / nx
+    dv = dx / dt
+    rng = np.random.default_rng(seed)
+    J = (nv - 1) // 2
+    f0 = I.gaussian_initial_2d(nx, ny, nv, dx, dv, 0.3 * J * dv)
+    f0 = f0 * (1 + 0.5 * rng.random((1, 1, ny, nx)))
+    fl = I.flow2d_inputs(seed, nsteps, nx, ny, dx, kmax=3)
+    return dict(nx=nx, ny=ny, nv=nv, tau_p=tau_p, kappa=kappa, dt=dt, dx=dx, dv=dv, f0=f0,
+                fl=fl, nsteps=nsteps, mu=mu)
+
+
+def oracle2d(c):
+    fl = c["fl"]
+    f = c["f0"].copy()
+    phi = fl.phi0.copy()
+    for n in range(c["nsteps"]):
+        ux, uy = O.flow2d_u(fl.a, fl.kvec, phi, c["nx"], c["ny"], c["dx"])
+        f = K.step_2d(f, ux, uy, c["tau_p"], c["kappa"], c["dt"], c["dv"], c["mu"])
+        phi = O.phase_advance(phi, fl.noise[n], c["dt"], fl.tau_f)
+    return f
+
+
+def gpu2d(lat, c, dtype):
+    t = torch.tensor(c["f0"], dtype=dtype, device="cuda")
+    lt = lat.Lattice(t, d=2, nx=c["nx"], ny=c["ny"], nv=c["nv"], L=L, tau_p=c["tau_p"],
+                     kappa=c["kappa"], dt=c["dt"])
+    lt.set_scheme(lat.SCHEME_KOREN, c["mu"])
+    fl = c["fl"]
+    lt.set_flow_modes_2d(fl.kvec, fl.a, fl.phi0, fl.tau_f)
+    lt.set_noise(fl.noise)
+    lt.step(c["nsteps"])
+    assert lt.status() == 0
+    return lt.state.double().cpu().numpy(), lt
+
+
+@pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
+@pytest.mark.parametrize("nx,ny,nv,mu", [(48, 40, 9, MU), (33, 20, 5, 1.0), (24, 24, 17, MU)])
+def test_2d_matches_oracle(lat, dtype, nx, ny, nv, mu):
+    c = case2d(nx, ny, nv, 1.0, 2e-3, 30, nx + nv, mu=mu)
+    want = oracle2d(c)
+    got, lt = gpu2d(lat, c, dtype)
+    assert rel_l1(got, want) <= TOL[dtype], rel_l1(got, want)
+    lt.close()
+
+
+def test_2d_mass_and_positivity(lat):
+    c = case2d(128, 96, 17, 0.5, 1e-3, 200, 3)
+    got, lt = gpu2d(lat, c, torch.float32)
+    code, *_, g = lt.moments(per_cell=False)
+    assert code == 0
+    m0 = c["f0"].sum() * c["dx"] ** 2 * c["dv"] ** 2
+    assert abs(g[0] - m0) <= 1e-5 * m0
+    assert got.min() >= -1e-6 * got.max()
+    lt.close()
+
+
+def test_2d_cellular_flow_limited_matches_oracle(lat):
+    """The paper's 2D set-up of Sec. 4.1: tilted cellular flow, 19^2 velocities, limited drag."""
+    n, nv = 40, 19
+    tau_p, kappa = 1.0, 8 * math.pi * 1e-3
+    dt = I.choose_dt(2, n, L, nv, tau_p, kappa, u_rms=0.1, cfl_factor=1 + MU)
+    dx = L / n
+    dv = dx / dt
+    f0 = I.gaussian_initial_2d(n, n, nv, dx, dv, 0.3 * ((nv - 1) // 2) * dv)
+    ux, uy = I.cellular_flow(n, n, L, 1.0)
+    want = f0.copy()
+    for _ in range(25):
+        want = K.step_2d(want, ux, uy, tau_p, kappa, dt, dv, MU)
+    lt = lat.Lattice(torch.tensor(f0, device="cuda"), d=2, nx=n, ny=n, nv=nv, L=L, tau_p=tau_p,
+                     kappa=kappa, dt=dt)
+    lt.set_scheme(lat.SCHEME_KOREN, MU)
+    u = torch.tensor(np.stack([ux, uy]), device="cuda")
+    lt.set_flow_field(u)
+    lt.step(25)
+    assert lt.status() == 0
+    assert rel_l1(lt.state.cpu().numpy(), want) <= 1e-12
     lt.close()
