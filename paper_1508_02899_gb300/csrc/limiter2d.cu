@@ -2,15 +2,15 @@
 // paper's 2D runs): Koren's limiter on the split fluxes P = (c a)^+ q and M = (c a)^- q of both
 // velocity axes, unsplit, integrated by Heun's method, then the five-point diffusion.
 //
-// Three passes over the state, one thread per phase cell (x fastest, so that every stencil load
+// Three passes over the state (x fastest within every thread block, so that every stencil load
 // is coalesced along x):
 //   1. y1 = q - dFx(q) - dFy(q),  q = f* gathered from the input buffer (streaming)  -> output buffer
 //   2. h = (q + y1 - dFx(y1) - dFy(y1)) / 2                                          -> scratch
 //   3. out = h + (Dx_{+} - Dx_{-}) + (Dy_{+} - Dy_{-}),  D = r (h_next - h)           -> output buffer
 // Each flux through face i + 1/2 needs the cells i - 1 .. i + 2 of its axis (cells beyond the
-// walls count as empty; the wall fluxes are zero), so a cell reads 9 values per stage.  The
-// passes trade the fused kernels' single read and write for simplicity: about three reads and
-// three writes of the state per step.
+// walls count as empty; the wall fluxes are zero).  The stages sweep velocity rows, so a cell
+// reads 5 values per stage.  The passes trade the fused kernels' single read and write for
+// simplicity: about three reads and three writes of the state per step.
 #include "lat_internal.h"
 #include "step2d_dev.h"
 
@@ -76,82 +76,103 @@ __device__ __forceinline__ int wrap1(int v, int n) {
     return v >= n ? v - n : v;
 }
 
-// f*(jx, jy, x, y) from the input buffer (streaming: j moves mass by j cells), or y1 values from
-// a post-streaming buffer; zero outside the velocity box.  32-bit indices (N_v^2 N_x N_y < 2^32).
-template <typename T, bool STREAMED>
-__device__ __forceinline__ T qval(const T* q, int jx, int jy, int x, int y, int nx, int ny,
-                                  int nv) {
-    if (jx < 0 || jx >= nv || jy < 0 || jy >= nv) return T(0);
-    const unsigned ncell = (unsigned)nx * (unsigned)ny;
-    if (STREAMED) {
-        const int J = (nv - 1) / 2;
-        return q[(unsigned)(jy * nv + jx) * ncell + (unsigned)wrap1(y - (jy - J), ny) * nx +
-                 (unsigned)wrap1(x - (jx - J), nx)];
-    }
-    return q[(unsigned)(jy * nv + jx) * ncell + (unsigned)y * nx + x];
-}
-
-// c a_j = g (w - j) along one axis at velocity index j (offset J), for the five stencil cells
-template <typename T>
-__device__ __forceinline__ void speeds(T g, T w, int j, int J, T (&ca)[5]) {
-#pragma unroll
-    for (int k = 0; k < 5; ++k) ca[k] = Ops<T>::mul(g, Ops<T>::sub(w, T(j - 2 + k - J)));
-}
-
-// Stage 1 (STAGE = 1): y1 = q - dFx - dFy with q = f* -> fout.  Stage 2: h = (q + y1 - dFx(y1) -
-// dFy(y1)) / 2 with y1 from fout -> scr.
+// Stage 1 (STAGE = 1): y1 = q - dFx - dFy with q = f* -> f[par ^ 1].  Stage 2: h = (q + y1 -
+// dFx(y1) - dFy(y1)) / 2 with y1 from f[par ^ 1] -> scratch.
+// A thread takes one spatial cell and one velocity row jy and sweeps jx = 0 .. N_v - 1: the
+// vx split fluxes and faces slide along the row (each face once), the vy faces jy -+ 1/2 come from
+// the column values jy - 2 .. jy + 2 at each jx.  grid.x = jy, grid.y over the spatial cells
+// (consecutive blocks take the same cells in every row, so the other rows are still in L2).
 template <typename T, int STAGE>
 __global__ void __launch_bounds__(kLimThreads) k_lim2d_stage(const Lim2DArgs a, int kstep) {
     using O = Ops<T>;
     const int nx = a.nx, ny = a.ny, nv = a.nv, J = (nv - 1) / 2;
-    const long long ncell = (long long)nx * ny;
-    const long long n = ncell * nv * nv;
+    const unsigned ncell = (unsigned)nx * (unsigned)ny;
     const T g = T(a.g), mu = T(a.mu);
     const int par = (int)((a.st->step + kstep) & 1);
     const T* fin = static_cast<const T*>(a.f[par]);
     const T* y1 = static_cast<const T*>(a.f[par ^ 1]);
     T* dst = STAGE == 1 ? static_cast<T*>(a.f[par ^ 1]) : static_cast<T*>(a.scr);
+    const T* src = STAGE == 1 ? fin : y1;  // the values the fluxes act on
     const T cflf = O::mul(g, O::add(T(1), mu));
     const T* ux = static_cast<const T*>(a.u);
+    const int jy = blockIdx.x;
     bool cfl = false;
-    // grid.x = velocity plane, grid.y over the plane's cells: consecutive blocks take the same
-    // cells in all planes, so that the stencil's other planes are still in L2.  N_v^2 N_x N_y
-    // < 2^32 (checked by lat_set_scheme): 32-bit index arithmetic
-    (void)n;
-    const int p = blockIdx.x;
-    const int jy = p / nv, jx = p - jy * nv;
-    for (unsigned cc = blockIdx.y * blockDim.x + threadIdx.x; cc < (unsigned)ncell;
+    for (unsigned cc = blockIdx.y * blockDim.x + threadIdx.x; cc < ncell;
          cc += gridDim.y * blockDim.x) {
-        const unsigned i = (unsigned)p * (unsigned)ncell + cc;
         const int y = (int)(cc / (unsigned)nx), x = (int)(cc - (unsigned)y * (unsigned)nx);
         T wx = T(0), wy = T(0);
         if (ux) {
             wx = O::mul(ux[cc], T(a.inv_dv));
             wy = O::mul(ux[ncell + cc], T(a.inv_dv));
         }
-        if (STAGE == 1 && cflf * (T(2 * J) + fabs(wx) + fabs(wy)) > T(1)) cfl = true;
-        T cax[5], cay[5], vx[5], vy[5];
-        speeds<T>(g, wx, jx, J, cax);
-        speeds<T>(g, wy, jy, J, cay);
+        if (STAGE == 1 && jy == 0 && cflf * (T(2 * J) + fabs(wx) + fabs(wy)) > T(1)) cfl = true;
+        // rows jy - 2 .. jy + 2: plane-row offsets (0 flags a row outside the box) and c a_y
+        unsigned rowoff[5];
+        bool rowin[5];
+        T cay[5];
 #pragma unroll
         for (int k = 0; k < 5; ++k) {
-            if (STAGE == 1) {
-                vx[k] = qval<T, true>(fin, jx - 2 + k, jy, x, y, nx, ny, nv);
-                vy[k] = qval<T, true>(fin, jx, jy - 2 + k, x, y, nx, ny, nv);
-            } else {
-                vx[k] = qval<T, false>(y1, jx - 2 + k, jy, x, y, nx, ny, nv);
-                vy[k] = qval<T, false>(y1, jx, jy - 2 + k, x, y, nx, ny, nv);
-            }
+            const int jr = jy - 2 + k;
+            rowin[k] = jr >= 0 && jr < nv;
+            const int yr = STAGE == 1 ? wrap1(y - (jr - J), ny) : y;
+            rowoff[k] = rowin[k] ? (unsigned)(jr * nv) * ncell + (unsigned)yr * nx : 0u;
+            cay[k] = O::mul(g, O::sub(wy, T(jr - J)));
         }
-        const T dfx = flux_diff<T>(vx, cax, jx, nv, mu);
-        const T dfy = flux_diff<T>(vy, cay, jy, nv, mu);
-        const T c = vx[2];  // the cell itself
-        const T stage = O::sub(O::sub(c, dfx), dfy);
-        if (STAGE == 1) {
-            dst[i] = stage;
-        } else {
-            const T q0 = qval<T, true>(fin, jx, jy, x, y, nx, ny, nv);
-            dst[i] = O::mul(T(0.5), O::add(q0, stage));
+        // value of (jx', row k) for the stencil (0 outside the box)
+        auto val = [&](int jxp, int k) -> T {
+            if (!rowin[k] || jxp < 0 || jxp >= nv) return T(0);
+            const int xc = STAGE == 1 ? wrap1(x - (jxp - J), nx) : x;
+            return src[rowoff[k] + (unsigned)jxp * ncell + (unsigned)xc];
+        };
+        auto cax = [&](int jxp) { return O::mul(g, O::sub(wx, T(jxp - J))); };
+        // stage 2 averages with f* of the cell, read streamed from the input buffer
+        const unsigned rowq =
+            (unsigned)(jy * nv) * ncell + (unsigned)wrap1(y - (jy - J), ny) * (unsigned)nx;
+        // x window: values and split fluxes of cells jx - 1 .. jx + 2 of row jy (index 0 .. 3)
+        T Vw[4], Pw[4], Mw[4];
+        Vw[0] = Pw[0] = Mw[0] = T(0);  // cell -1, beyond the wall
+#pragma unroll
+        for (int k = 1; k < 4; ++k) {
+            Vw[k] = val(k - 1, 2);
+            const T ca = cax(k - 1);
+            Pw[k] = O::mul(fmax(ca, T(0)), Vw[k]);
+            Mw[k] = O::mul(fmin(ca, T(0)), Vw[k]);
+        }
+        T Fxl = T(0);  // face jx - 1/2 (the wall face for jx = 0)
+        for (int jx = 0; jx < nv; ++jx) {
+            // face jx + 1/2 from cells jx - 1 .. jx + 2
+            T Fxr = T(0);
+            if (jx < nv - 1) {
+                const T P4[4] = {Pw[0], Pw[1], Pw[2], Pw[3]};
+                const T M4[4] = {Mw[0], Mw[1], Mw[2], Mw[3]};
+                Fxr = face_flux<T>(P4, M4, mu);
+            }
+            // the column jx: rows jy - 2 .. jy + 2
+            const T cval = Vw[1];
+            T vy[5];
+#pragma unroll
+            for (int k = 0; k < 5; ++k) vy[k] = k == 2 ? cval : val(jx, k);
+            const T dfy = flux_diff<T>(vy, cay, jy, nv, mu);
+            const T stage = O::sub(O::sub(cval, O::sub(Fxr, Fxl)), dfy);
+            const unsigned o = (unsigned)(jy * nv + jx) * ncell + cc;
+            if (STAGE == 1) {
+                dst[o] = stage;
+            } else {
+                const T q0 = fin[rowq + (unsigned)jx * ncell + (unsigned)wrap1(x - (jx - J), nx)];
+                dst[o] = O::mul(T(0.5), O::add(q0, stage));
+            }
+            // slide the window to cells jx .. jx + 3
+            Fxl = Fxr;
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                Vw[k] = Vw[k + 1];
+                Pw[k] = Pw[k + 1];
+                Mw[k] = Mw[k + 1];
+            }
+            Vw[3] = val(jx + 3, 2);
+            const T ca = cax(jx + 3);
+            Pw[3] = O::mul(fmax(ca, T(0)), Vw[3]);
+            Mw[3] = O::mul(fmin(ca, T(0)), Vw[3]);
         }
     }
     if (cfl) atomicOr(&a.st->status, ST_CFL);
@@ -187,15 +208,15 @@ template <typename T>
 cudaError_t launch_lim2d_t(const Lim2DArgs& a, int k, int sm_count, cudaStream_t s) {
     const long long ncell = (long long)a.nx * a.ny;
     (void)sm_count;
-    const dim3 grid((unsigned)(a.nv * a.nv),
-                    (unsigned)std::min((ncell + kLimThreads - 1) / kLimThreads, 65535ll));
-    k_lim2d_stage<T, 1><<<grid, kLimThreads, 0, s>>>(a, k);
+    const unsigned chunks = (unsigned)std::min((ncell + kLimThreads - 1) / kLimThreads, 65535ll);
+    const dim3 grow((unsigned)a.nv, chunks), gcell((unsigned)(a.nv * a.nv), chunks);
+    k_lim2d_stage<T, 1><<<grow, kLimThreads, 0, s>>>(a, k);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    k_lim2d_stage<T, 2><<<grid, kLimThreads, 0, s>>>(a, k);
+    k_lim2d_stage<T, 2><<<grow, kLimThreads, 0, s>>>(a, k);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    k_lim2d_diffuse<T><<<grid, kLimThreads, 0, s>>>(a, k);
+    k_lim2d_diffuse<T><<<gcell, kLimThreads, 0, s>>>(a, k);
     return cudaGetLastError();
 }
 
