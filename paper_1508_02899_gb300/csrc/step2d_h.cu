@@ -256,7 +256,7 @@ struct PCHLayout {
     static constexpr size_t ring = (size_t)NS * NV * kWinH * sizeof(S);
     static constexpr size_t gsm = (size_t)(HSM ? 2 : 1) * NV * TW * sizeof(float);
     static constexpr size_t dsc = (size_t)NS * NVP * sizeof(float);
-    static constexpr size_t enc = (size_t)2 * NLP * sizeof(float);
+    static constexpr size_t enc = ((size_t)2 * NLP + 15) / 16 * 16;  // exponent bytes
     static constexpr size_t mxs = (size_t)2 * NLP * sizeof(unsigned);
     static constexpr size_t bars = (size_t)2 * NS * sizeof(uint64_t);
     static constexpr size_t o_gsm = ring;
@@ -284,13 +284,15 @@ struct HalfPutS {
     S* out;
     size_t pstride;
     bool active;
-    const float* sc_tab;   // scales of the tile's output lines [NV][NVP] (shared memory)
-    unsigned* mxs;         // the tile's line maxima [NV][NVP] (shared memory)
+    const unsigned char* sc_tab;  // biased exponents of the tile's output scales [NV][NVP]
+                                  // (shared memory; the scales are powers of two)
+    unsigned* mxs;                // the tile's line maxima [NV][NVP] (shared memory)
     Encoder<S> enc;
     S* p;
-    const float* sp;
+    const unsigned char* sp;
     unsigned* mp;
-    __device__ __forceinline__ HalfPutS(S* out_, size_t ps, bool act, const float* e, unsigned* m)
+    __device__ __forceinline__ HalfPutS(S* out_, size_t ps, bool act, const unsigned char* e,
+                                        unsigned* m)
         : out(out_), pstride(ps), active(act), sc_tab(e), mxs(m), p(out_), sp(e), mp(m) {}
     __device__ __forceinline__ void begin(int row) {
         p = out + (size_t)row * NV * pstride;
@@ -299,7 +301,7 @@ struct HalfPutS {
     }
     __device__ __forceinline__ void operator()(float o) {
         float back;
-        const S h = enc(o, pow2_inv(*sp), &back);
+        const S h = enc(o, pow2_inv(__int_as_float((int)((unsigned)*sp << 23))), &back);
         ++sp;
         if (active) *p = h;
         p += pstride;
@@ -310,11 +312,13 @@ struct HalfPutS {
 };
 
 // Issue the copies of f* row `row` of tile `tile` into ring slot `slot` (producer warp): the
-// plane windows, the row's decode scales, and for row 0 the tile's output scales into enc_dst.
+// plane windows and the row's decode scales; with row 0 the warp first writes the biased
+// exponents of the tile's output scales (powers of two) into enc_dst, one byte per line, which
+// the row's mbarrier arrival releases to the consumers.
 template <typename S, int NV>
 __device__ __forceinline__ void issue_row_h(const Step2DArgs& a, const S* fin, S* ring,
                                             uint64_t* bar, float* dsc, const float* s_in,
-                                            const float* s_out, float* enc_dst, int slot,
+                                            const float* s_out, unsigned char* enc_dst, int slot,
                                             int tile, int row) {
     constexpr int J = (NV - 1) / 2;
     constexpr int NVP = nv_padded(NV);
@@ -323,15 +327,18 @@ __device__ __forceinline__ void issue_row_h(const Step2DArgs& a, const S* fin, S
     const int y = tile / a.ntx;
     const int x0 = (tile % a.ntx) * TW;
     const int ys = wrap(y - (row - J), a.ny);
-    unsigned bytes = (unsigned)(NV * kWinH * sizeof(S) + NVP * sizeof(float));
-    if (row == 0) bytes += (unsigned)(NV * NVP * sizeof(float));
-    if (lane == 0) mbar_expect_tx(&bar[slot], bytes);
+    const unsigned bytes = (unsigned)(NV * kWinH * sizeof(S) + NVP * sizeof(float));
+    if (row == 0) {
+        const float* so = s_out + (size_t)y * NV * NVP;
+        for (int i = lane; i < NV * NVP; i += 32)
+            enc_dst[i] = (unsigned char)(__float_as_uint(so[i]) >> 23);
+        __syncwarp();
+    }
+    if (lane == 0) mbar_expect_tx(&bar[slot], bytes);  // release: the exponents written above
     __syncwarp();
     if (lane == 0)
         bulk_g2s(dsc + slot * NVP, s_in + ((size_t)ys * NV + row) * NVP, NVP * sizeof(float),
                  &bar[slot]);
-    if (lane == 1 && row == 0)
-        bulk_g2s(enc_dst, s_out + (size_t)y * NV * NVP, NV * NVP * sizeof(float), &bar[slot]);
     for (int jx = lane; jx < NV; jx += 32) {
         const S* prow = fin + (((size_t)row * NV + jx) * a.ny + ys) * a.nx;
         const int s = x0 - (jx - J);
@@ -353,7 +360,8 @@ __device__ __forceinline__ void issue_row_h(const Step2DArgs& a, const S* fin, S
 template <typename S, int NV, int NS, int NT, class TileOf>
 __device__ __forceinline__ void produce_rows_h(const Step2DArgs& a, const S* fin, S* ring,
                                                uint64_t* full, uint64_t* empty, float* dsc,
-                                               const float* s_in, const float* s_out, float* enc,
+                                               const float* s_in, const float* s_out,
+                                               unsigned char* enc,
                                                unsigned* mxs, unsigned* m_out, int ntl,
                                                const TileOf& tile_of) {
     constexpr int NLP = NV * nv_padded(NV);
@@ -410,7 +418,7 @@ __global__ void __launch_bounds__(PCHShape<NV, NS>::threads, PCHShape<NV, NS>::m
     S* ring = reinterpret_cast<S*>(smem);
     float* gsm = reinterpret_cast<float*>(smem + Lay::o_gsm);
     float* dsc = reinterpret_cast<float*>(smem + Lay::o_dsc);
-    float* enc = reinterpret_cast<float*>(smem + Lay::o_enc);
+    unsigned char* enc = smem + Lay::o_enc;
     unsigned* mxs = reinterpret_cast<unsigned*>(smem + Lay::o_mxs);
     uint64_t* full = reinterpret_cast<uint64_t*>(smem + Lay::o_bar);
     uint64_t* empty = full + NS;
