@@ -1110,7 +1110,7 @@ int ctx2d_create(Ctx2D** out, const lat_grid* g, DevState* st, int sm_count, cud
     c->sm_count = sm_count;
     c->ring = ring_ok(c);
     c->chunks = chunks_supported(c->nv, 3) ? 3 : 1;
-    c->pcv = c->ring && pc_ok(c) ? (half ? 5 : 4) : 0;
+    c->pcv = c->ring && pc_ok(c) ? (half ? 6 : 4) : 0;
     if (half && !c->pcv) c->ring = false;
     const long long ncell = (long long)c->nx * c->ny;
     c->mom_blocks = (int)std::min<long long>((ncell + 255) / 256, 8LL * sm_count);
