@@ -43,6 +43,8 @@ def parse():
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--cpu-seconds", type=float, default=10.0)
+    p.add_argument("--no-cpu-pool", action="store_true",
+                   help="skip the all-cores oracle timing of the cpu_baseline leg")
     p.add_argument("--instances", type=int, default=N_INST,
                    help="ensemble size (smaller cases are for profiling only)")
     p.add_argument("--no-autotune", action="store_true")
@@ -179,7 +181,7 @@ class OracleSample:
     """The FP64 oracle, as it stands, on the first instances of the benchmark ensemble
     (about `sample_cells` phase-space cells per step)."""
 
-    def __init__(self, sample_cells: int = 2_000_000, scheme: str = "upwind"):
+    def __init__(self, sample_cells: int = 2_000_000, scheme: str = "upwind", start: int = 0):
         from oracle import lattice as O
         from oracle import limiter as K
         from paper_1508_02899_gb300 import inputs as I
@@ -190,7 +192,7 @@ class OracleSample:
                                     cfl_factor=1 + KOREN_MU if self.koren else 1.0)
         self.idx, self.cells = [], 0
         while self.cells < sample_cells:
-            self.idx.append(len(self.idx))
+            self.idx.append(start + len(self.idx))
             self.cells += int(self.tab.nx[self.idx[-1]]) * NV
         f0 = I.ensemble_initial(self.tab, NV, None, None, instances=self.idx)
         self.fl = I.flow1d_inputs(SEED, 1, n_inst=len(self.idx))
@@ -208,7 +210,7 @@ class OracleSample:
             self.state[i] = (f, amp)
 
     def describe(self, steps):
-        return (f"first {len(self.idx)} of 4096 instances ({self.cells} cells per step), "
+        return (f"instances {self.idx[0]}..{self.idx[-1]} of 4096 ({self.cells} cells per step), "
                 f"{steps} steps" + (", flux-limited drag" if self.koren else ""))
 
     def time_for(self, budget_s: float):
@@ -219,6 +221,25 @@ class OracleSample:
             el = time.perf_counter() - t0
             if el >= budget_s:
                 return steps, el
+
+
+def _oracle_worker(job):
+    """One process of the all-cores oracle timing: its own disjoint instances, timed for a budget
+    (a top-level function, so that a spawned process can import it)."""
+    start, budget, scheme = job
+    smp = OracleSample(scheme=scheme, start=start)
+    steps, el = smp.time_for(budget)
+    return smp.cells * steps / el / 1e9
+
+
+def oracle_all_cores(budget: float, scheme: str):
+    """The oracle, as it stands, in one process per host core on disjoint instances (spawned: no
+    process is forked from one that has touched the GPU).  Aggregate GCUPS and the core count."""
+    import multiprocessing as mp
+    n = os.cpu_count() or 1
+    with mp.get_context("spawn").Pool(n) as pool:
+        rates = pool.map(_oracle_worker, [(16 * w, budget, scheme) for w in range(n)])
+    return float(sum(rates)), n
 
 
 def run_reference(args):
@@ -636,10 +657,16 @@ def main():
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        smp = OracleSample(scheme=args.scheme if args.workload == "ensemble" else "upwind")
+        scheme = args.scheme if args.workload == "ensemble" else "upwind"
+        smp = OracleSample(scheme=scheme)
         c_steps, c_el = smp.time_for(args.cpu_seconds)
         cpu = {"value": smp.cells * c_steps / c_el / 1e9, "unit": UNIT, "cores": 1,
                "kind": "oracle", "sample": smp.describe(c_steps)}
+        if not args.no_cpu_pool:
+            v_all, n_all = oracle_all_cores(args.cpu_seconds, scheme)
+            cpu["all_cores"] = {"value": v_all, "unit": UNIT, "cores": n_all,
+                                "sample": f"{n_all} spawned processes, each on its own 2.3e6-cell "
+                                          f"sample of the ensemble for {args.cpu_seconds:g} s"}
 
     if rank == 0:
         line = {
