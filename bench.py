@@ -552,6 +552,8 @@ def main():
     if tr is not None:
         tb, units = tr
         traffic = tb * (cells / units) if units == units and units > 0 else tb
+    if roof is not None:
+        roof["traffic"] = traffic
     ctx.close()
     del ctx
     torch.cuda.empty_cache()
