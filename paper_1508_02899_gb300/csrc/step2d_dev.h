@@ -194,6 +194,16 @@ __device__ __forceinline__ void final_row(T (&A)[NV], HArr& H, T rr, Put& put) {
     }
 }
 
+// Steps an output pointer by one velocity plane.  The sum is opaque to the compiler, which
+// otherwise keeps all N_v per-plane store addresses live across the row loop (two registers
+// each) and spills the flux rows instead.
+template <typename T>
+__device__ __forceinline__ T* next_plane(T* p, size_t pstride) {
+    unsigned long long q = reinterpret_cast<unsigned long long>(p + pstride);
+    asm volatile("mov.b64 %0, %0;" : "+l"(q));
+    return reinterpret_cast<T*>(q);
+}
+
 // Plain store of every output value: out points at cell (x, y) of plane (0, 0).
 template <typename T, int NV>
 struct StorePut {
@@ -206,7 +216,7 @@ struct StorePut {
     __device__ __forceinline__ void begin(int row) { p = out + (size_t)row * NV * pstride; }
     __device__ __forceinline__ void operator()(T o) {
         if (active) *p = o;
-        p += pstride;
+        p = next_plane(p, pstride);
     }
 };
 

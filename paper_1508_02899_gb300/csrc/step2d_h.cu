@@ -185,7 +185,7 @@ struct HalfPutG {
         float back;
         const S h = enc(o, pow2_inv(*sp), &back);
         if (active) *p = h;
-        p += pstride;
+        p = next_plane(p, pstride);
         const unsigned m = warp_max_abs(back, active);
         if ((threadIdx.x & 31) == 0 && m) atomicMax(mp, m);
         ++sp;
@@ -304,7 +304,7 @@ struct HalfPutS {
         const S h = enc(o, pow2_inv(__int_as_float((int)((unsigned)*sp << 23))), &back);
         ++sp;
         if (active) *p = h;
-        p += pstride;
+        p = next_plane(p, pstride);
         const unsigned m = warp_max_abs(back, active);
         if ((threadIdx.x & 31) == 0 && m) atomicMax(mp, m);
         ++mp;
