@@ -106,15 +106,25 @@ def parse_profile(txt: str) -> dict:
     return vals
 
 
-def profile_traffic(kernel_file: str, src: str):
-    """DRAM bytes per launch from the committed ncu summary, if it was taken on this source."""
+def source_hash(src) -> str:
+    """First 16 hex digits of the SHA-256 of the kernel's source files, concatenated in order."""
     import hashlib
+    srcs = (src,) if isinstance(src, str) else tuple(src)
+    m = hashlib.sha256()
+    for f in srcs:
+        m.update(open(os.path.join(ROOT, f), "rb").read())
+    return m.hexdigest()[:16]
+
+
+def profile_traffic(kernel_file: str, src):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken on this source
+    (src: one file or the files the kernel is compiled from)."""
     path = os.path.join(ROOT, "profiles", kernel_file)
     try:
         txt = open(path).read()
     except OSError:
         return None
-    h = hashlib.sha256(open(os.path.join(ROOT, src), "rb").read()).hexdigest()[:16]
+    h = source_hash(src)
     vals = parse_profile(txt)
     if vals.get("source_sha256") != h or "traffic_bytes_per_launch" not in vals:
         return None
@@ -487,7 +497,8 @@ def main():
     elif args.workload == "2d":
         ctx, cells, noise_row, glob, desc = build_2d(args, I, lat, torch, dev, rank, nsteps,
                                                      n=args.size or 512)
-        nv, prof, src = 33, "step2d_512_fp32_nv33.md", "paper_1508_02899_gb300/csrc/step2d.cu"
+        nv, prof = 33, "step2d_512_fp32_nv33.md"
+        src = ("paper_1508_02899_gb300/csrc/step2d.cu", "paper_1508_02899_gb300/csrc/step2d_dev.h")
         launches_per_step = 2  # flow evaluation + fused step
     elif args.workload in ("2d_f16", "2d_bf16"):
         store = args.workload[3:]
@@ -495,7 +506,7 @@ def main():
                                                      n=args.size or 1024, store=store)
         nv = 33
         prof = f"step2d_1024_{store}_nv33.md"
-        src = "paper_1508_02899_gb300/csrc/step2d_h.cu"
+        src = ("paper_1508_02899_gb300/csrc/step2d_h.cu", "paper_1508_02899_gb300/csrc/step2d_dev.h")
         launches_per_step = 3  # flow evaluation + output scales + fused step
         bytes_per_cell, lines = 4, nv * nv * (args.size or 1024)
     else:
@@ -570,6 +581,17 @@ def main():
         lt.close()
         del lt
         torch.cuda.empty_cache()
+        # FP32 storage at the 16-bit forms' size: their speedup is taken against this
+        lt, c2, *_ = build_2d(args, I, lat, torch, dev, rank, 2 * 40 + 4, n=1024)
+        b2 = lt.autotune(reps=3)
+        ms32, _ = timed(lt, 40, 3, torch, dist, world, local, dev)
+        g2 = c2 * 40 / (ms32 / 1e3) / 1e9
+        forms["2d_fp32_1024x1024_33x33"] = {
+            "gcups": g2, "ms_per_step": ms32 / 40, "hbm_frac": g2 * 8 / peak,
+            "kernel": kernel_label("2d", b2, 33), "steps": 40, "status": lt.status()}
+        lt.close()
+        del lt
+        torch.cuda.empty_cache()
         for store in ("f16", "bf16"):
             lt, c2, *_ = build_2d(args, I, lat, torch, dev, rank, 2 * 40 + 4, n=1024,
                                   store=store)
@@ -580,6 +602,7 @@ def main():
             forms[f"2d_{store}_1024x1024_33x33"] = {
                 "gcups": g2, "ms_per_step": ms2 / 40,
                 "hbm_frac": (g2 * 4 + g2 / 1024 * 12) / peak,
+                "speedup_vs_fp32_storage": ms32 / ms2,
                 "kernel": kernel_label(f"2d_{store}", b2, 33), "steps": 40, "status": st2}
             lt.close()
             del lt
@@ -653,6 +676,21 @@ def main():
             "gcups": c2 * 20 / (ms2 / 1e3) / 1e9, "ms_per_step": ms2 / 20,
             "network_ms": net_ms, "network_tflops": tf, "network_frac_bf16": tf / tpeak,
             "kernel": "k_mlp_tc<9> + k_step2d_corr<9>", "steps": 20, "status": st2}
+        lt.close()
+        del lt
+        torch.cuda.empty_cache()
+        # the fine lattice the closure stands in for: plain FP32 33^2 at 2048^2 (2 x 18 GB);
+        # one fine step spans COARSE_PER_FINE coarse steps
+        from paper_1508_02899_gb300 import train as T
+        lt, c2, *_ = build_2d(args, I, lat, torch, dev, rank, 2 * 20 + 4, n=2048)
+        b2 = lt.autotune(reps=2)
+        msf, _ = timed(lt, 20, 3, torch, dist, world, local, dev)
+        forms["2d_fp32_2048x2048_33x33"] = {
+            "gcups": c2 * 20 / (msf / 1e3) / 1e9, "ms_per_step": msf / 20,
+            "kernel": kernel_label("2d", b2, 33), "steps": 20, "status": lt.status()}
+        forms["2d_learned_2048x2048_9x9"]["speedup_vs_fine_fp32"] = (
+            msf / (T.COARSE_PER_FINE * ms2))
+        forms["2d_learned_2048x2048_9x9"]["coarse_steps_per_fine_step"] = T.COARSE_PER_FINE
         lt.close()
         del lt
         torch.cuda.empty_cache()

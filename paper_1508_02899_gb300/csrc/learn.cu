@@ -221,7 +221,7 @@ __global__ void __launch_bounds__(TW) k_step2d_corr(const Step2DArgs a, const fl
         }
         const size_t c = (size_t)y * a.nx + x;
         const GlobCorr corr{G + c, G + (size_t)NV * NV * ps + c, ps, NV};
-        StorePut<float, NV> put(fout + c, ps, active);
+        StorePut<float, NV, false> put(fout + c, ps, active);  // global loads: plain steps
         for (int r = 1; r <= NV; ++r) {
             const GlobalRow<float, NV> cur(fin, r - 1, x, y, a.nx, a.ny);
             const GlobalRow<float, NV> nxt(fin, r < NV ? r : r - 1, x, y, a.nx, a.ny);
@@ -557,10 +557,28 @@ cudaError_t launch_mlp_f32(int nv, const LearnArgs& a, int k, cudaStream_t s) {
     }
 }
 
-cudaError_t launch_step2d_corr(int nv, int grid, const Step2DArgs& a, const float* G, int k,
+// Persistent grid of k_step2d_corr<NV>: its resident blocks on sm_count SMs.  A larger grid
+// would leave its last blocks to run their whole tile loops after the others finish.
+template <int NV>
+int corr_grid(int sm_count, int ntiles) {
+    static int occ = 0;
+    if (occ == 0) {
+        int nb = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_step2d_corr<NV>, TW, 0) !=
+            cudaSuccess)
+            nb = 1;
+        occ = nb > 0 ? nb : 1;
+    }
+    return std::max(1, std::min(ntiles, occ * sm_count));
+}
+
+cudaError_t launch_step2d_corr(int nv, int sm_count, const Step2DArgs& a, const float* G, int k,
                                cudaStream_t s) {
     switch (nv) {
-#define X(n) case n: k_step2d_corr<n><<<grid, TW, 0, s>>>(a, G, k); return cudaGetLastError();
+#define X(n)                                                                                 \
+    case n:                                                                                  \
+        k_step2d_corr<n><<<corr_grid<n>(sm_count, a.ntiles), TW, 0, s>>>(a, G, k);           \
+        return cudaGetLastError();
         LEARN_NV_LIST(X)
 #undef X
         default: return cudaErrorInvalidValue;

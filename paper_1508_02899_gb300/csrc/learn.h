@@ -72,9 +72,10 @@ size_t learn_tc_bytes();
 cudaError_t launch_learn_tc_pack(const float* params, void* wtc, cudaStream_t s);
 cudaError_t launch_mlp_tc(int nv, const LearnArgs& a, const void* wtc, int sm_count, int k,
                           cudaStream_t s);
-// The plain 2D FP32 step (Step2DArgs) with the corrections G added to the drag fluxes.
-cudaError_t launch_step2d_corr(int nv, int grid, const k2d::Step2DArgs& a, const float* G, int k,
-                               cudaStream_t s);
+// The plain 2D FP32 step (Step2DArgs) with the corrections G added to the drag fluxes, on a
+// persistent grid of as many blocks as are resident on sm_count SMs.
+cudaError_t launch_step2d_corr(int nv, int sm_count, const k2d::Step2DArgs& a, const float* G,
+                               int k, cudaStream_t s);
 
 // ---- gradient of a rollout (FP32, CUDA cores) ---------------------------------------------
 // Buffers of one backward step: lam_out = dL/df^{n+1} (in), lam_in = dL/df^n (out); f = f^n;

@@ -84,7 +84,7 @@ __global__ void __launch_bounds__(TW) k_step2d_plain(const Step2DArgs a, int kst
             G[j] = T(0);
             H[j] = T(0);
         }
-        StorePut<T, NV> put(fout + (size_t)y * a.nx + x, ps, active);
+        StorePut<T, NV, false> put(fout + (size_t)y * a.nx + x, ps, active);  // global loads
         for (int r = 1; r <= NV; ++r) {
             const GlobalRow<T, NV> cur(fin, r - 1, x, y, a.nx, a.ny);
             const GlobalRow<T, NV> nxt(fin, r < NV ? r : r - 1, x, y, a.nx, a.ny);
@@ -1018,12 +1018,12 @@ LearnArgs learn_args(const Ctx2D* c, const void* f0, const void* f1, const DevSt
 }
 
 // One learned step from the buffers of a (parity from a.st): flow, density, network, step.
-int enqueue_learned(Ctx2D* c, const Step2DArgs& a, int grid, int k, cudaStream_t s) {
+int enqueue_learned(Ctx2D* c, const Step2DArgs& a, int k, cudaStream_t s) {
     const LearnArgs la = learn_args(c, a.f[0], a.f[1], a.st);
     CK2(launch_rho_star(c->nv, la, k, s));
     if (c->learn == 2) CK2(launch_mlp_tc(c->nv, la, c->d_wtc, c->sm_count, k, s));
     else CK2(launch_mlp_f32(c->nv, la, k, s));
-    CK2(launch_step2d_corr(c->nv, grid, a, c->d_G, k, s));
+    CK2(launch_step2d_corr(c->nv, c->sm_count, a, c->d_G, k, s));
     return LAT_OK;
 }
 
@@ -1037,7 +1037,7 @@ int enqueue2d(Ctx2D* c, void* const f[2], int n, cudaStream_t s, int dry) {
             if (rc != LAT_OK) return rc;
         }
         if (c->learn) {
-            const int rc = enqueue_learned(c, a, grid, k, s);
+            const int rc = enqueue_learned(c, a, k, s);
             if (rc != LAT_OK) return rc;
         } else if (c->scheme == LAT_SCHEME_KOREN) {
             CK2(launch_step2d_limited(c->dtype, a, c->nv, c->mu, c->d_lim, k, c->sm_count, s));
@@ -1543,7 +1543,6 @@ int ctx2d_learn_grad(Ctx2D* c, void* const f[2], int cur, int n, const float* ta
         // forward rollout on explicit buffers F[k] -> F[k+1] (zero step counter: parity 0)
         Step2DArgs a = step_args(c, f);
         a.st = c->d_st0;
-        const int grid = grid_of(c, a.ntiles);
         for (int k = 0; k < n && rc == LAT_OK; ++k) {
             if (modes && launch_flow(c, k, 0, s) != LAT_OK) fail(LAT_ECUDA);
             const float* u = c->flow_kind == LAT_FLOW_FIELD ? static_cast<const float*>(c->field)
@@ -1558,7 +1557,7 @@ int ctx2d_learn_grad(Ctx2D* c, void* const f[2], int cur, int n, const float* ta
             a.u = la.u;
             if (launch_rho_star(c->nv, la, 0, s) != cudaSuccess ||
                 launch_mlp_f32(c->nv, la, 0, s) != cudaSuccess ||
-                launch_step2d_corr(c->nv, grid, a, c->d_G, 0, s) != cudaSuccess)
+                launch_step2d_corr(c->nv, c->sm_count, a, c->d_G, 0, s) != cudaSuccess)
                 fail(LAT_ECUDA);
         }
         if (rc != LAT_OK) break;

@@ -194,9 +194,10 @@ __device__ __forceinline__ void final_row(T (&A)[NV], HArr& H, T rr, Put& put) {
     }
 }
 
-// Steps an output pointer by one velocity plane.  The sum is opaque to the compiler, which
-// otherwise keeps all N_v per-plane store addresses live across the row loop (two registers
-// each) and spills the flux rows instead.
+// Steps an output pointer by one velocity plane through a volatile asm statement.  In the
+// shared-memory sweeps this keeps the compiler from moving the row's loads ahead of earlier
+// stores, which would hold many loaded values live across the row and spill the flux rows.
+// Kernels that read f* from global memory need those loads in flight early: they step plainly.
 template <typename T>
 __device__ __forceinline__ T* next_plane(T* p, size_t pstride) {
     unsigned long long q = reinterpret_cast<unsigned long long>(p + pstride);
@@ -204,8 +205,9 @@ __device__ __forceinline__ T* next_plane(T* p, size_t pstride) {
     return reinterpret_cast<T*>(q);
 }
 
-// Plain store of every output value: out points at cell (x, y) of plane (0, 0).
-template <typename T, int NV>
+// Plain store of every output value: out points at cell (x, y) of plane (0, 0).  OPAQUE: step
+// the pointer with next_plane (shared-memory sweeps) instead of a plain addition.
+template <typename T, int NV, bool OPAQUE = true>
 struct StorePut {
     T* out;
     size_t pstride;
@@ -216,7 +218,8 @@ struct StorePut {
     __device__ __forceinline__ void begin(int row) { p = out + (size_t)row * NV * pstride; }
     __device__ __forceinline__ void operator()(T o) {
         if (active) *p = o;
-        p = next_plane(p, pstride);
+        if constexpr (OPAQUE) p = next_plane(p, pstride);
+        else p += pstride;
     }
 };
 

@@ -185,7 +185,7 @@ struct HalfPutG {
         float back;
         const S h = enc(o, pow2_inv(*sp), &back);
         if (active) *p = h;
-        p = next_plane(p, pstride);
+        p += pstride;  // global loads: plain steps
         const unsigned m = warp_max_abs(back, active);
         if ((threadIdx.x & 31) == 0 && m) atomicMax(mp, m);
         ++sp;
