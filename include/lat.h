@@ -154,8 +154,9 @@ int lat_prepare(lat_ctx* c, int n);
 int lat_moments(lat_ctx* c, double* rho, double* mean_v, double* mean_v2, double* globals);
 
 /* lat_step(c, n) followed by lat_moments(c, ...), with the moments of the final state computed
- * inside the last step (no second pass over f) when the 1D producer/consumer kernel is in use;
- * otherwise exactly the two calls.  Same arguments, outputs, synchronisation and status as
+ * inside the last step (no second pass over f) when the 1D producer/consumer kernel is in use,
+ * or, in 2D, FP32 storage with the upwind drag on launch kernel 4 or 5; otherwise exactly the
+ * two calls.  Same arguments, outputs, synchronisation and status as
  * lat_moments.  The per-cell outputs equal lat_moments' bit for bit; the globals agree to the
  * rounding order of the compensated sums. */
 int lat_step_moments(lat_ctx* c, int n, double* rho, double* mean_v, double* mean_v2,

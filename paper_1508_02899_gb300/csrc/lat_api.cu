@@ -549,6 +549,17 @@ int lat_moments(lat_ctx* c, double* rho, double* mean_v, double* mean_v2, double
 int lat_step_moments(lat_ctx* c, int n, double* rho, double* mean_v, double* mean_v2,
                      double* globals) {
     if (!c || n < 1) return LAT_EINVAL;
+    if (c->d == 2 && ctx2d_moments_fusable(c->c2)) {
+        if (n > 1) {
+            int rc = lat_step(c, n - 1);
+            if (rc != LAT_OK) return rc;
+        }
+        int rc = ctx2d_step_moments(c->c2, c->f, rho, mean_v, mean_v2, globals, c->stream);
+        if (rc != LAT_OK) return rc;
+        c->h_step += 1;
+        c->cur = (int)(c->h_step & 1);
+        return lat_status(c);  // synchronises
+    }
     const bool fused = c->d == 1 && c->variant == STEP1D_PC && c->mode != 1 &&
                        step1d_moments_supported(c->dtype, c->nv);
     if (!fused) {

@@ -23,6 +23,7 @@
 #include <vector>
 
 #include <algorithm>
+#include <type_traits>
 #include <map>
 
 #include "lat2d.h"
@@ -36,6 +37,7 @@ namespace lat {
 namespace {
 
 using namespace k2d;
+using namespace cs;
 
 constexpr int WIN = TW + 4;   // floats copied per plane row (x window rounded to 16 bytes)
 #ifndef LAT_RING2D_SLOTS
@@ -379,6 +381,55 @@ __device__ __forceinline__ void produce_rows(const Step2DArgs& a, const float* f
         mbar_wait_bounded(&full[d % NS], (unsigned)((d / NS) & 1));
 }
 
+// Moment outputs of a step that also reduces the moments of the state it writes (the FP32
+// producer/consumer kernel with MOM): per-cell arrays as lat_moments (any may be null) and one
+// compensated partial [4][2] per consumer warp.
+struct Mom2DOut {
+    double* rho = nullptr;
+    double* mv = nullptr;
+    double* mv2 = nullptr;
+    double* partials = nullptr;
+    double dv = 0.0;
+};
+
+// Output writer that also sums the written values of one cell in the order and precision of
+// k_moments2d<float> (velocity rows in order, TwoSum row masses, FMA-weighted sums), so that
+// the per-cell moments come out with the same bits.
+template <int NV>
+struct MomPut {
+    static constexpr int J = (NV - 1) / 2;
+    StorePut<float, NV> st;
+    FComp s0, ey;
+    float s1 = 0.f, s2 = 0.f, s3 = 0.f, ex = 0.f, fy = 0.f, fy2 = 0.f;
+    int row = -1, jx = 0;
+    __device__ __forceinline__ MomPut(float* out, size_t ps, bool act) : st(out, ps, act) {}
+    __device__ __forceinline__ void close() {
+        s0.merge(ey);
+        s1 = __fadd_rn(s1, ex);
+        s2 = __fmaf_rn(fy, __fsub_rn(ey.s, ey.c), s2);
+    }
+    __device__ __forceinline__ void begin(int r) {
+        if (r != row) {  // sweep_row opens row 0 once without values, then again with them
+            if (row >= 0) close();
+            row = r;
+            fy = (float)(r - J);
+            fy2 = fy * fy;
+            ey = FComp{};
+            ex = 0.f;
+        }
+        jx = 0;
+        st.begin(r);
+    }
+    __device__ __forceinline__ void operator()(float o) {  // jx = 0 .. NV - 1 in order
+        st(o);
+        const float fx = (float)(jx - J);
+        ey.add_exact(o);
+        ex = __fmaf_rn(fx, o, ex);
+        s3 = __fmaf_rn(__fmaf_rn(fx, fx, fy2), o, s3);
+        ++jx;
+    }
+};
+
 template <int NV, int NS, bool GSM, bool HSM = false>
 struct PCShape {
     static constexpr int consumers = TW / 32;
@@ -393,10 +444,11 @@ size_t pc_smem() {
 }
 
 // HSM: the vy-diffusion flux row H in shared memory too (fewer registers, no spills).
-template <int NV, int NS, bool GSM, bool HSM>
+// MOM: the consumers also reduce the moments of the cells they write (Mom2DOut).
+template <int NV, int NS, bool GSM, bool HSM, bool MOM>
 __global__ void __launch_bounds__(PCShape<NV, NS, GSM, HSM>::threads,
                                   PCShape<NV, NS, GSM, HSM>::min_blocks)
-    k_step2d_pc(const Step2DArgs a, int kstep) {
+    k_step2d_pc(const Step2DArgs a, int kstep, const Mom2DOut m) {
     constexpr int NC = PCShape<NV, NS, GSM, HSM>::consumers;
     extern __shared__ __align__(128) unsigned char smem[];
     float* ring = reinterpret_cast<float*>(smem);
@@ -427,7 +479,8 @@ __global__ void __launch_bounds__(PCShape<NV, NS, GSM, HSM>::threads,
         return;
     }
     const int cell = threadIdx.x;
-    bool failed = false;
+    bool failed = false, bad = false;
+    FComp t[4];  // MOM: this thread's cells
     for (int lt = 0; lt < ntl && !failed; ++lt) {
         const int tile = tile_of((long long)lt * NV);
         const int y = tile / a.ntx;
@@ -447,7 +500,8 @@ __global__ void __launch_bounds__(PCShape<NV, NS, GSM, HSM>::threads,
             if (GSM) Gs[j] = 0.f;
             else Greg[j] = 0.f;
         }
-        StorePut<float, NV> put(fout + (size_t)y * a.nx + x, ps, active);
+        std::conditional_t<MOM, MomPut<NV>, StorePut<float, NV>> put(
+            fout + (size_t)y * a.nx + x, ps, active);
         const long long s0 = (long long)lt * NV;
         for (int r = 0; r <= NV; ++r) {
             const long long s = s0 + r;
@@ -468,9 +522,43 @@ __global__ void __launch_bounds__(PCShape<NV, NS, GSM, HSM>::threads,
         if (!failed) {
             if constexpr (HSM) final_row<float, NV>(A, Hs, rr, put);
             else final_row<float, NV>(A, Hreg, rr, put);
+            if constexpr (MOM) {
+                if (active) {
+                    put.close();
+                    bad |= !isfinite(put.s0.s) || !isfinite(put.s3);
+                    const long long c = (long long)y * a.nx + x, ncell = (long long)a.nx * a.ny;
+                    if (m.rho || m.mv || m.mv2) {  // FP64 per cell only when asked for
+                        const double dv2 = __dmul_rn(m.dv, m.dv);
+                        const double m0 = nval(put.s0.to_comp(1.0));
+                        if (m.rho) m.rho[c] = m0 * dv2;
+                        if (m.mv) {
+                            m.mv[c] = m0 != 0.0 ? __dmul_rn((double)put.s1, m.dv) / m0 : 0.0;
+                            m.mv[ncell + c] = m0 != 0.0 ? __dmul_rn((double)put.s2, m.dv) / m0 : 0.0;
+                        }
+                        if (m.mv2) m.mv2[c] = m0 != 0.0 ? __dmul_rn((double)put.s3, dv2) / m0 : 0.0;
+                    }
+                    t[0].merge(put.s0);
+                    t[1].merge(FComp{put.s1, 0.f});
+                    t[2].merge(FComp{put.s2, 0.f});
+                    t[3].merge(FComp{put.s3, 0.f});
+                }
+            }
         }
     }
     if (failed && lane == 0) atomicOr(&a.st->status, ST_TIMEOUT);
+    if constexpr (MOM) {  // one partial per consumer warp, lanes folded in butterfly order
+        if (bad) atomicOr(&a.st->status, ST_NUMERIC);
+        for (int q = 0; q < 4; ++q) warp_reduce(t[q]);
+        if (lane == 0) {
+            const double sc[4] = {1.0, m.dv, m.dv, __dmul_rn(m.dv, m.dv)};
+            double* p = m.partials + ((size_t)blockIdx.x * NC + warp) * 8;
+            for (int q = 0; q < 4; ++q) {
+                const Comp cq = t[q].to_comp(sc[q]);
+                p[2 * q] = cq.s;
+                p[2 * q + 1] = cq.c;
+            }
+        }
+    }
 }
 
 // ---- flow: u = (d_y psi, -d_x psi) of psi = sum a_m cos(theta_m) --------------------------------
@@ -764,30 +852,51 @@ int occupancy_ring_c(int chunks) {
 // 5 = G in shared memory, 3 slots; 6 = G and H in shared memory, 3 slots; 7 = the same, 2 slots.
 #define LAT2D_PC(n) ((n) >= 9)
 
-template <int NV, int NS, bool GSM, bool HSM = false>
-cudaError_t launch_pc(int grid, const Step2DArgs& a, int k, cudaStream_t s) {
+template <int NV, int NS, bool GSM, bool HSM = false, bool MOM = false>
+cudaError_t launch_pc(int grid, const Step2DArgs& a, int k, cudaStream_t s,
+                      const Mom2DOut& m = Mom2DOut()) {
     static bool attr = false;
     const size_t bytes = pc_smem<NV, NS, GSM, HSM>();
     if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute(k_step2d_pc<NV, NS, GSM, HSM>,
+        cudaError_t e = cudaFuncSetAttribute(k_step2d_pc<NV, NS, GSM, HSM, MOM>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)bytes);
         if (e != cudaSuccess) return e;
         attr = true;
     }
-    k_step2d_pc<NV, NS, GSM, HSM><<<grid, PCShape<NV, NS, GSM, HSM>::threads, bytes, s>>>(a, k);
+    k_step2d_pc<NV, NS, GSM, HSM, MOM>
+        <<<grid, PCShape<NV, NS, GSM, HSM>::threads, bytes, s>>>(a, k, m);
     return cudaGetLastError();
 }
 
-template <int NV, int NS, bool GSM, bool HSM = false>
+template <int NV, int NS, bool GSM, bool HSM = false, bool MOM = false>
 int occupancy_pc_t() {
     int nb = 0;
     const size_t bytes = pc_smem<NV, NS, GSM, HSM>();
-    cudaFuncSetAttribute(k_step2d_pc<NV, NS, GSM, HSM>,
+    cudaFuncSetAttribute(k_step2d_pc<NV, NS, GSM, HSM, MOM>,
                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_step2d_pc<NV, NS, GSM, HSM>,
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_step2d_pc<NV, NS, GSM, HSM, MOM>,
                                                   PCShape<NV, NS, GSM, HSM>::threads, bytes);
     return nb;
+}
+
+// Variants 4 and 5 with the moment epilogue: the grid of its own resident blocks (at most bps
+// per SM when bps > 0), so that no block waits for a free slot.
+template <int NV>
+cudaError_t launch_pc_mom(int v, int bps, int sm_count, const Step2DArgs& a, int k,
+                          const Mom2DOut& m, int* grid_out, cudaStream_t s) {
+    if constexpr (LAT2D_PC(NV)) {
+        if (v == 4 || v == 5) {
+            int occ = v == 4 ? occupancy_pc_t<NV, 4, true, false, true>()
+                             : occupancy_pc_t<NV, 3, true, false, true>();
+            occ = std::max(1, bps > 0 ? std::min(bps, occ) : occ);
+            const int grid = std::max(1, std::min(a.ntiles, occ * sm_count));
+            *grid_out = grid;
+            return v == 4 ? launch_pc<NV, 4, true, false, true>(grid, a, k, s, m)
+                          : launch_pc<NV, 3, true, false, true>(grid, a, k, s, m);
+        }
+    }
+    return cudaErrorInvalidValue;
 }
 
 template <int NV>
@@ -833,6 +942,17 @@ cudaError_t launch_step2d(int dtype, int nv, bool ring, int chunks, int pcv, int
         if (ring && pcv) return launch_pc_v<n>(pcv, grid, a, k, s);            \
         if (ring) return launch_ring_c<n>(chunks, grid, a, k, s);              \
         return launch_plain<float, n>(grid, a, k, s);
+        LAT2D_NV_LIST(X)
+#undef X
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t launch_step2d_mom(int nv, int pcv, int bps, int sm_count, const Step2DArgs& a, int k,
+                              const Mom2DOut& m, int* grid_out, cudaStream_t s) {
+    switch (nv) {
+#define X(n) \
+    case n: return launch_pc_mom<n>(pcv, bps, sm_count, a, k, m, grid_out, s);
         LAT2D_NV_LIST(X)
 #undef X
         default: return cudaErrorInvalidValue;
@@ -1114,7 +1234,9 @@ int ctx2d_create(Ctx2D** out, const lat_grid* g, DevState* st, int sm_count, cud
     if (half && !c->pcv) c->ring = false;
     const long long ncell = (long long)c->nx * c->ny;
     c->mom_blocks = (int)std::min<long long>((ncell + 255) / 256, 8LL * sm_count);
-    if (cudaMalloc(&c->d_partials, sizeof(double) * 8 * c->mom_blocks) != cudaSuccess ||
+    // room for the moment kernel's block partials or the fused step's warp partials
+    const size_t npart = std::max<size_t>(c->mom_blocks, (size_t)8 * sm_count * (TW / 32));
+    if (cudaMalloc(&c->d_partials, sizeof(double) * 8 * npart) != cudaSuccess ||
         cudaMalloc(&c->d_glob, sizeof(double) * 4) != cudaSuccess ||
         cudaMallocHost(&c->h_glob, sizeof(double) * 4) != cudaSuccess) {
         ctx2d_destroy(c);
@@ -1307,6 +1429,40 @@ int ctx2d_moments(Ctx2D* c, const void* f, int cur, double* rho, double* mean_v,
                                                         rho, mean_v, mean_v2, c->d_partials, c->st);
     CK2(cudaGetLastError());
     k_finalize2d<<<1, kFin2DThreads, 0, s>>>(c->d_partials, c->mom_blocks,
+                                             c->dx * c->dx * c->dv * c->dv, c->d_glob);
+    CK2(cudaGetLastError());
+    if (globals) {
+        CK2(cudaMemcpyAsync(c->h_glob, c->d_glob, sizeof(double) * 4, cudaMemcpyDeviceToHost, s));
+        CK2(cudaStreamSynchronize(s));
+        memcpy(globals, c->h_glob, sizeof(double) * 4);
+    }
+    return LAT_OK;
+}
+
+bool ctx2d_moments_fusable(const Ctx2D* c) {
+    return c->dtype == LAT_F32 && !c->half && !c->learn && c->scheme == LAT_SCHEME_UPWIND &&
+           c->ring && (c->pcv == 4 || c->pcv == 5) && pc_supported(c->nv);
+}
+
+int ctx2d_step_moments(Ctx2D* c, void* const f[2], double* rho, double* mean_v,
+                       double* mean_v2, double* globals, cudaStream_t s) {
+    if (!ctx2d_moments_fusable(c)) return LAT_EINVAL;
+    const Step2DArgs a = step_args(c, f);
+    if (c->flow_kind == LAT_FLOW_MODES) {
+        const int rc = launch_flow(c, 0, 0, s);
+        if (rc != LAT_OK) return rc;
+    }
+    Mom2DOut m;
+    m.rho = rho;
+    m.mv = mean_v;
+    m.mv2 = mean_v2;
+    m.partials = c->d_partials;
+    m.dv = c->dv;
+    int grid = 0;
+    CK2(launch_step2d_mom(c->nv, c->pcv, c->bps, c->sm_count, a, 0, m, &grid, s));
+    k_advance2d<<<1, 1, 0, s>>>(c->st, 1);
+    CK2(cudaGetLastError());
+    k_finalize2d<<<1, kFin2DThreads, 0, s>>>(c->d_partials, grid * (TW / 32),
                                              c->dx * c->dx * c->dv * c->dv, c->d_glob);
     CK2(cudaGetLastError());
     if (globals) {

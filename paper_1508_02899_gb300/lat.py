@@ -305,6 +305,20 @@ class Lattice(_Ctx):
         code = _lib.lat_moments(self._h, _ptr(rho), _ptr(mv), _ptr(mv2), _dptr(glob))
         return code, rho, mv, mv2, glob
 
+    def step_moments(self, n: int = 1, per_cell: bool = True,
+                     globals_out: np.ndarray | None = None):
+        """n steps, then the moments of the new state (fused into the last step where the
+        launch allows it); the outputs of moments()."""
+        ncell = self.nx * self.ny
+        dev = self.f[0].device
+        rho = torch.empty(ncell, dtype=torch.float64, device=dev) if per_cell else None
+        mv = torch.empty(self.d * ncell, dtype=torch.float64, device=dev) if per_cell else None
+        mv2 = torch.empty(ncell, dtype=torch.float64, device=dev) if per_cell else None
+        glob = globals_out if globals_out is not None else np.zeros(self.d + 2)
+        code = _lib.lat_step_moments(self._h, int(n), _ptr(rho), _ptr(mv), _ptr(mv2),
+                                     _dptr(glob))
+        return code, rho, mv, mv2, glob
+
 
 class Ensemble(_Ctx):
     """Independent 1D lattices advanced together (one persistent launch per step)."""

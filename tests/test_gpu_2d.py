@@ -258,3 +258,38 @@ def test_full_size_512_sampled(lat, flow):
     assert abs(s.double().sum().item() / m0 - 1) < 1e-6
     assert s.min().item() >= -1e-6 * s.max().item()
     lt.close()
+
+
+@pytest.mark.parametrize("kernel,nv", [(1, 9), (4, 9), (5, 9), (4, 17), (5, 33)])
+def test_step_moments_equal_step_then_moments(lat, kernel, nv):
+    """lat_step_moments against lat_step + lat_moments from the same start: the state and the
+    per-cell moments bit for bit, the globals to the rounding order of the compensated sums.
+    Kernels 4 and 5 reduce the moments inside the last step; kernel 1 takes the two calls.
+    136 x 23: a ragged last tile (136 = 128 + 8) and several tiles per block."""
+    c = make2d(136, 23, nv, 1.0, 1e-3, 5, 40 + nv)
+    outs = []
+    for fused in (False, True):
+        t = torch.tensor(c["f0"], dtype=torch.float32, device="cuda")
+        lt = lat.Lattice(t, d=2, nx=136, ny=23, nv=nv, L=L, tau_p=c["tau_p"], kappa=c["kappa"],
+                         dt=c["dt"])
+        lt.set_launch(kernel=kernel, blocks_per_sm=1)
+        fl = c["fl"]
+        lt.set_flow_modes_2d(fl.kvec, fl.a, fl.phi0, fl.tau_f)
+        lt.set_noise(fl.noise)
+        lt.step(1)
+        if fused:
+            code, rho, mv, mv2, glob = lt.step_moments(4)
+        else:
+            lt.step(4)
+            code, rho, mv, mv2, glob = lt.moments()
+        assert code == 0 and lt.status() == 0 and lt.steps_done == 5
+        outs.append((lt.state.cpu().numpy().copy(), rho.cpu().numpy(), mv.cpu().numpy(),
+                     mv2.cpu().numpy(), glob.copy()))
+        lt.close()
+    (s0, r0, v0, w0, g0), (s1, r1, v1, w1, g1) = outs
+    assert np.array_equal(s0, s1)
+    assert np.array_equal(r0, r1) and np.array_equal(v0, v1) and np.array_equal(w0, w1)
+    # mass and energy (positive sums) to 1e-12; momentum, a sum of both signs, to 1e-12 of
+    # sqrt(M E), which bounds the sum of |v| f by Cauchy-Schwarz
+    np.testing.assert_allclose(g1[[0, 3]], g0[[0, 3]], rtol=1e-12)
+    np.testing.assert_allclose(g1[1:3], g0[1:3], rtol=0, atol=1e-12 * math.sqrt(g0[0] * g0[3]))
