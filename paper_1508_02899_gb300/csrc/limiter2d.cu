@@ -82,10 +82,11 @@ __device__ __forceinline__ int wrap1(int v, int n) {
 // vx split fluxes and faces slide along the row (each face once), the vy faces jy -+ 1/2 come from
 // the column values jy - 2 .. jy + 2 at each jx.  grid.x = jy, grid.y over the spatial cells
 // (consecutive blocks take the same cells in every row, so the other rows are still in L2).
-template <typename T, int STAGE>
+// NVT > 0: N_v known at compile time (the velocity loop unrolled); 0: any N_v.
+template <typename T, int STAGE, int NVT = 0>
 __global__ void __launch_bounds__(kLimThreads) k_lim2d_stage(const Lim2DArgs a, int kstep) {
     using O = Ops<T>;
-    const int nx = a.nx, ny = a.ny, nv = a.nv, J = (nv - 1) / 2;
+    const int nx = a.nx, ny = a.ny, nv = NVT > 0 ? NVT : a.nv, J = (nv - 1) / 2;
     const unsigned ncell = (unsigned)nx * (unsigned)ny;
     const T g = T(a.g), mu = T(a.mu);
     const int par = (int)((a.st->step + kstep) & 1);
@@ -139,6 +140,7 @@ __global__ void __launch_bounds__(kLimThreads) k_lim2d_stage(const Lim2DArgs a, 
             Mw[k] = O::mul(fmin(ca, T(0)), Vw[k]);
         }
         T Fxl = T(0);  // face jx - 1/2 (the wall face for jx = 0)
+#pragma unroll(NVT > 0 ? NVT : 1)
         for (int jx = 0; jx < nv; ++jx) {
             // face jx + 1/2 from cells jx - 1 .. jx + 2
             T Fxr = T(0);
@@ -204,17 +206,30 @@ __global__ void __launch_bounds__(kLimThreads) k_lim2d_diffuse(const Lim2DArgs a
     }
 }
 
+template <typename T, int NVT>
+void launch_stages(const Lim2DArgs& a, int k, dim3 grow, cudaStream_t s) {
+    k_lim2d_stage<T, 1, NVT><<<grow, kLimThreads, 0, s>>>(a, k);
+    k_lim2d_stage<T, 2, NVT><<<grow, kLimThreads, 0, s>>>(a, k);
+}
+
 template <typename T>
 cudaError_t launch_lim2d_t(const Lim2DArgs& a, int k, int sm_count, cudaStream_t s) {
     const long long ncell = (long long)a.nx * a.ny;
     (void)sm_count;
     const unsigned chunks = (unsigned)std::min((ncell + kLimThreads - 1) / kLimThreads, 65535ll);
     const dim3 grow((unsigned)a.nv, chunks), gcell((unsigned)(a.nv * a.nv), chunks);
-    k_lim2d_stage<T, 1><<<grow, kLimThreads, 0, s>>>(a, k);
+    // FP32 lattices of the common sizes take the unrolled stages
+    bool done = false;
+    if constexpr (sizeof(T) == 4) {
+        done = true;
+        if (a.nv == 9) launch_stages<T, 9>(a, k, grow, s);
+        else if (a.nv == 17) launch_stages<T, 17>(a, k, grow, s);
+        else if (a.nv == 19) launch_stages<T, 19>(a, k, grow, s);
+        else if (a.nv == 33) launch_stages<T, 33>(a, k, grow, s);
+        else done = false;
+    }
+    if (!done) launch_stages<T, 0>(a, k, grow, s);
     cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
-    k_lim2d_stage<T, 2><<<grow, kLimThreads, 0, s>>>(a, k);
-    e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     k_lim2d_diffuse<T><<<gcell, kLimThreads, 0, s>>>(a, k);
     return cudaGetLastError();
