@@ -8,9 +8,10 @@
 //   2. h = (q + y1 - dFx(y1) - dFy(y1)) / 2                                          -> scratch
 //   3. out = h + (Dx_{+} - Dx_{-}) + (Dy_{+} - Dy_{-}),  D = r (h_next - h)           -> output buffer
 // Each flux through face i + 1/2 needs the cells i - 1 .. i + 2 of its axis (cells beyond the
-// walls count as empty; the wall fluxes are zero).  The stages sweep velocity rows, so a cell
-// reads 5 values per stage.  The passes trade the fused kernels' single read and write for
-// simplicity: about three reads and three writes of the state per step.
+// walls count as empty; the wall fluxes are zero).  The stages sweep pairs of velocity rows, so
+// a pair of cells reads 6 values of its column per stage.  The passes trade the fused kernels'
+// single read and write for simplicity: about three reads and three writes of the state per
+// step.
 #include "lat_internal.h"
 #include "step2d_dev.h"
 
@@ -42,24 +43,6 @@ __device__ __forceinline__ T face_flux(const T (&P)[4], const T (&M)[4], T mu) {
     return O::add(pos, neg);
 }
 
-// Limited flux difference F_{j+1/2} - F_{j-1/2} along one axis at index j, given the values of
-// cells j - 2 .. j + 2 (v[k] for cell j - 2 + k, zero beyond the walls) and c a at those cells.
-template <typename T>
-__device__ __forceinline__ T flux_diff(const T (&v)[5], const T (&ca)[5], int j, int nv, T mu) {
-    using O = Ops<T>;
-    T P[5], M[5];
-#pragma unroll
-    for (int k = 0; k < 5; ++k) {
-        P[k] = O::mul(fmax(ca[k], T(0)), v[k]);
-        M[k] = O::mul(fmin(ca[k], T(0)), v[k]);
-    }
-    const T Pl[4] = {P[0], P[1], P[2], P[3]}, Ml[4] = {M[0], M[1], M[2], M[3]};
-    const T Pr[4] = {P[1], P[2], P[3], P[4]}, Mr[4] = {M[1], M[2], M[3], M[4]};
-    const T Fl = j > 0 ? face_flux<T>(Pl, Ml, mu) : T(0);        // face j - 1/2
-    const T Fr = j < nv - 1 ? face_flux<T>(Pr, Mr, mu) : T(0);   // face j + 1/2
-    return O::sub(Fr, Fl);
-}
-
 struct Lim2DArgs {
     void* f[2];        // state buffers: step s reads f[s & 1] (f before streaming) and writes
                        // f[(s + 1) & 1] (stage 1's result first, then the step's result)
@@ -78,10 +61,13 @@ __device__ __forceinline__ int wrap1(int v, int n) {
 
 // Stage 1 (STAGE = 1): y1 = q - dFx - dFy with q = f* -> f[par ^ 1].  Stage 2: h = (q + y1 -
 // dFx(y1) - dFy(y1)) / 2 with y1 from f[par ^ 1] -> scratch.
-// A thread takes one spatial cell and one velocity row jy and sweeps jx = 0 .. N_v - 1: the
-// vx split fluxes and faces slide along the row (each face once), the vy faces jy -+ 1/2 come from
-// the column values jy - 2 .. jy + 2 at each jx.  grid.x = jy, grid.y over the spatial cells
-// (consecutive blocks take the same cells in every row, so the other rows are still in L2).
+// A thread takes one spatial cell and the velocity rows jy0 = 2 blockIdx.x and jy0 + 1 and
+// sweeps jx = 0 .. N_v - 1: the vx split fluxes and faces of each row slide along it (each face
+// once), and the three vy faces jy0 - 1/2, jy0 + 1/2, jy0 + 3/2 of the column come from the
+// values of rows jy0 - 2 .. jy0 + 3 (the middle face serves both rows).  grid.x = row pairs,
+// grid.y over the spatial cells (consecutive blocks take the same cells in every row pair, so
+// the other rows are still in L2).  Every face is formed by the same operations as in a sweep
+// of one row, so the result does not depend on the pairing.
 // NVT > 0: N_v known at compile time (the velocity loop unrolled); 0: any N_v.
 template <typename T, int STAGE, int NVT = 0>
 __global__ void __launch_bounds__(kLimThreads) k_lim2d_stage(const Lim2DArgs a, int kstep) {
@@ -96,7 +82,8 @@ __global__ void __launch_bounds__(kLimThreads) k_lim2d_stage(const Lim2DArgs a, 
     const T* src = STAGE == 1 ? fin : y1;  // the values the fluxes act on
     const T cflf = O::mul(g, O::add(T(1), mu));
     const T* ux = static_cast<const T*>(a.u);
-    const int jy = blockIdx.x;
+    const int jy0 = 2 * (int)blockIdx.x, jy1 = jy0 + 1;
+    const bool two = jy1 < nv;  // the last pair of an odd N_v holds one row
     bool cfl = false;
     for (unsigned cc = blockIdx.y * blockDim.x + threadIdx.x; cc < ncell;
          cc += gridDim.y * blockDim.x) {
@@ -106,14 +93,14 @@ __global__ void __launch_bounds__(kLimThreads) k_lim2d_stage(const Lim2DArgs a, 
             wx = O::mul(ux[cc], T(a.inv_dv));
             wy = O::mul(ux[ncell + cc], T(a.inv_dv));
         }
-        if (STAGE == 1 && jy == 0 && cflf * (T(2 * J) + fabs(wx) + fabs(wy)) > T(1)) cfl = true;
-        // rows jy - 2 .. jy + 2: plane-row offsets (0 flags a row outside the box) and c a_y
-        unsigned rowoff[5];
-        bool rowin[5];
-        T cay[5];
+        if (STAGE == 1 && jy0 == 0 && cflf * (T(2 * J) + fabs(wx) + fabs(wy)) > T(1)) cfl = true;
+        // rows jy0 - 2 .. jy0 + 3: plane-row offsets (rowin false outside the box) and c a_y
+        unsigned rowoff[6];
+        bool rowin[6];
+        T cay[6];
 #pragma unroll
-        for (int k = 0; k < 5; ++k) {
-            const int jr = jy - 2 + k;
+        for (int k = 0; k < 6; ++k) {
+            const int jr = jy0 - 2 + k;
             rowin[k] = jr >= 0 && jr < nv;
             const int yr = STAGE == 1 ? wrap1(y - (jr - J), ny) : y;
             rowoff[k] = rowin[k] ? (unsigned)(jr * nv) * ncell + (unsigned)yr * nx : 0u;
@@ -127,54 +114,90 @@ __global__ void __launch_bounds__(kLimThreads) k_lim2d_stage(const Lim2DArgs a, 
         };
         auto cax = [&](int jxp) { return O::mul(g, O::sub(wx, T(jxp - J))); };
         // stage 2 averages with f* of the cell, read streamed from the input buffer
-        const unsigned rowq =
-            (unsigned)(jy * nv) * ncell + (unsigned)wrap1(y - (jy - J), ny) * (unsigned)nx;
-        // x window: values and split fluxes of cells jx - 1 .. jx + 2 of row jy (index 0 .. 3)
-        T Vw[4], Pw[4], Mw[4];
-        Vw[0] = Pw[0] = Mw[0] = T(0);  // cell -1, beyond the wall
+        const unsigned rowq0 =
+            (unsigned)(jy0 * nv) * ncell + (unsigned)wrap1(y - (jy0 - J), ny) * (unsigned)nx;
+        const unsigned rowq1 =
+            (unsigned)(jy1 * nv) * ncell + (unsigned)wrap1(y - (jy1 - J), ny) * (unsigned)nx;
+        // x windows of rows jy0 (A, stencil row 2) and jy1 (B, row 3): values and split fluxes
+        // of cells jx - 1 .. jx + 2 (index 0 .. 3)
+        T VA[4], PA[4], MA[4], VB[4], PB[4], MB[4];
+        VA[0] = PA[0] = MA[0] = VB[0] = PB[0] = MB[0] = T(0);  // cell -1, beyond the wall
 #pragma unroll
         for (int k = 1; k < 4; ++k) {
-            Vw[k] = val(k - 1, 2);
             const T ca = cax(k - 1);
-            Pw[k] = O::mul(fmax(ca, T(0)), Vw[k]);
-            Mw[k] = O::mul(fmin(ca, T(0)), Vw[k]);
+            VA[k] = val(k - 1, 2);
+            PA[k] = O::mul(fmax(ca, T(0)), VA[k]);
+            MA[k] = O::mul(fmin(ca, T(0)), VA[k]);
+            VB[k] = val(k - 1, 3);
+            PB[k] = O::mul(fmax(ca, T(0)), VB[k]);
+            MB[k] = O::mul(fmin(ca, T(0)), VB[k]);
         }
-        T Fxl = T(0);  // face jx - 1/2 (the wall face for jx = 0)
+        T FxlA = T(0), FxlB = T(0);  // faces jx - 1/2 (the wall face for jx = 0)
 #pragma unroll(NVT > 0 ? NVT : 1)
         for (int jx = 0; jx < nv; ++jx) {
-            // face jx + 1/2 from cells jx - 1 .. jx + 2
-            T Fxr = T(0);
+            // faces jx + 1/2 from cells jx - 1 .. jx + 2
+            T FxrA = T(0), FxrB = T(0);
             if (jx < nv - 1) {
-                const T P4[4] = {Pw[0], Pw[1], Pw[2], Pw[3]};
-                const T M4[4] = {Mw[0], Mw[1], Mw[2], Mw[3]};
-                Fxr = face_flux<T>(P4, M4, mu);
+                const T P4[4] = {PA[0], PA[1], PA[2], PA[3]}, M4[4] = {MA[0], MA[1], MA[2], MA[3]};
+                FxrA = face_flux<T>(P4, M4, mu);
+                if (two) {
+                    const T Q4[4] = {PB[0], PB[1], PB[2], PB[3]};
+                    const T N4[4] = {MB[0], MB[1], MB[2], MB[3]};
+                    FxrB = face_flux<T>(Q4, N4, mu);
+                }
             }
-            // the column jx: rows jy - 2 .. jy + 2
-            const T cval = Vw[1];
-            T vy[5];
+            // the column jx: rows jy0 - 2 .. jy0 + 3 and their split fluxes
+            T P[6], M[6];
 #pragma unroll
-            for (int k = 0; k < 5; ++k) vy[k] = k == 2 ? cval : val(jx, k);
-            const T dfy = flux_diff<T>(vy, cay, jy, nv, mu);
-            const T stage = O::sub(O::sub(cval, O::sub(Fxr, Fxl)), dfy);
-            const unsigned o = (unsigned)(jy * nv + jx) * ncell + cc;
-            if (STAGE == 1) {
-                dst[o] = stage;
-            } else {
-                const T q0 = fin[rowq + (unsigned)jx * ncell + (unsigned)wrap1(x - (jx - J), nx)];
-                dst[o] = O::mul(T(0.5), O::add(q0, stage));
+            for (int k = 0; k < 6; ++k) {
+                const T v = k == 2 ? VA[1] : (k == 3 ? VB[1] : val(jx, k));
+                P[k] = O::mul(fmax(cay[k], T(0)), v);
+                M[k] = O::mul(fmin(cay[k], T(0)), v);
             }
-            // slide the window to cells jx .. jx + 3
-            Fxl = Fxr;
+            const T Pm[4] = {P[0], P[1], P[2], P[3]}, Mm[4] = {M[0], M[1], M[2], M[3]};
+            const T Pc[4] = {P[1], P[2], P[3], P[4]}, Mc[4] = {M[1], M[2], M[3], M[4]};
+            const T Fm = jy0 > 0 ? face_flux<T>(Pm, Mm, mu) : T(0);       // face jy0 - 1/2
+            const T F0 = jy0 < nv - 1 ? face_flux<T>(Pc, Mc, mu) : T(0);  // face jy0 + 1/2
+            const T stageA = O::sub(O::sub(VA[1], O::sub(FxrA, FxlA)), O::sub(F0, Fm));
+            const unsigned oA = (unsigned)(jy0 * nv + jx) * ncell + cc;
+            if (STAGE == 1) {
+                dst[oA] = stageA;
+            } else {
+                const T q0 = fin[rowq0 + (unsigned)jx * ncell + (unsigned)wrap1(x - (jx - J), nx)];
+                dst[oA] = O::mul(T(0.5), O::add(q0, stageA));
+            }
+            if (two) {
+                const T Pp[4] = {P[2], P[3], P[4], P[5]}, Mp[4] = {M[2], M[3], M[4], M[5]};
+                const T Fp = jy1 < nv - 1 ? face_flux<T>(Pp, Mp, mu) : T(0);  // face jy1 + 1/2
+                const T stageB = O::sub(O::sub(VB[1], O::sub(FxrB, FxlB)), O::sub(Fp, F0));
+                const unsigned oB = oA + (unsigned)nv * ncell;
+                if (STAGE == 1) {
+                    dst[oB] = stageB;
+                } else {
+                    const T q1 =
+                        fin[rowq1 + (unsigned)jx * ncell + (unsigned)wrap1(x - (jx - J), nx)];
+                    dst[oB] = O::mul(T(0.5), O::add(q1, stageB));
+                }
+            }
+            // slide the windows to cells jx .. jx + 3
+            FxlA = FxrA;
+            FxlB = FxrB;
 #pragma unroll
             for (int k = 0; k < 3; ++k) {
-                Vw[k] = Vw[k + 1];
-                Pw[k] = Pw[k + 1];
-                Mw[k] = Mw[k + 1];
+                VA[k] = VA[k + 1];
+                PA[k] = PA[k + 1];
+                MA[k] = MA[k + 1];
+                VB[k] = VB[k + 1];
+                PB[k] = PB[k + 1];
+                MB[k] = MB[k + 1];
             }
-            Vw[3] = val(jx + 3, 2);
             const T ca = cax(jx + 3);
-            Pw[3] = O::mul(fmax(ca, T(0)), Vw[3]);
-            Mw[3] = O::mul(fmin(ca, T(0)), Vw[3]);
+            VA[3] = val(jx + 3, 2);
+            PA[3] = O::mul(fmax(ca, T(0)), VA[3]);
+            MA[3] = O::mul(fmin(ca, T(0)), VA[3]);
+            VB[3] = val(jx + 3, 3);
+            PB[3] = O::mul(fmax(ca, T(0)), VB[3]);
+            MB[3] = O::mul(fmin(ca, T(0)), VB[3]);
         }
     }
     if (cfl) atomicOr(&a.st->status, ST_CFL);
@@ -217,7 +240,7 @@ cudaError_t launch_lim2d_t(const Lim2DArgs& a, int k, int sm_count, cudaStream_t
     const long long ncell = (long long)a.nx * a.ny;
     (void)sm_count;
     const unsigned chunks = (unsigned)std::min((ncell + kLimThreads - 1) / kLimThreads, 65535ll);
-    const dim3 grow((unsigned)a.nv, chunks), gcell((unsigned)(a.nv * a.nv), chunks);
+    const dim3 grow((unsigned)(a.nv + 1) / 2, chunks), gcell((unsigned)(a.nv * a.nv), chunks);
     // FP32 lattices of the common sizes take the unrolled stages
     bool done = false;
     if constexpr (sizeof(T) == 4) {
