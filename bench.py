@@ -635,7 +635,7 @@ def main():
         g2 = c2 * 20 / (ms2 / 1e3) / 1e9
         forms["2d_cellular_koren_fp32_1024x1024_19x19"] = {
             "gcups": g2, "ms_per_step": ms2 / 20, "hbm_frac_of_8B": g2 * 8 / peak,
-            "kernel": "k_lim2d_stage<float,1>, k_lim2d_stage<float,2>, k_lim2d_diffuse<float>",
+            "kernel": "k_lim2d_stage<float,1,19>, k_lim2d_stage<float,2,19>, k_lim2d_diffuse<float>",
             "steps": 20, "status": st2,
             "flow": "tilted cellular flow, flux-limited drag (Koren, mu = 2/3), Heun's method"}
         lt.close()
