@@ -203,29 +203,54 @@ __global__ void __launch_bounds__(kLimThreads) k_lim2d_stage(const Lim2DArgs a, 
     if (cfl) atomicOr(&a.st->status, ST_CFL);
 }
 
-// out = h + (Dx_{+} - Dx_{-}) + (Dy_{+} - Dy_{-}), D = r (h_next - h), zero at the walls
-template <typename T>
+// out = h + (Dx_{+} - Dx_{-}) + (Dy_{+} - Dy_{-}), D = r (h_next - h), zero at the walls.
+// A thread takes one spatial cell and the velocity rows jy0 = 2 blockIdx.x and jy0 + 1 and sweeps
+// jx: the row values slide along jx (one new load per row and step), the rows jy0 - 1 and
+// jy0 + 2 give the vy neighbours, so a pair of cells loads four values.  grid as the stages.
+template <typename T, int NVT = 0>
 __global__ void __launch_bounds__(kLimThreads) k_lim2d_diffuse(const Lim2DArgs a, int kstep) {
     using O = Ops<T>;
-    const int nx = a.nx, ny = a.ny, nv = a.nv;
-    const long long ncell = (long long)nx * ny;
-    const long long n = ncell * nv * nv;
+    const int nv = NVT > 0 ? NVT : a.nv;
+    const unsigned ncell = (unsigned)a.nx * (unsigned)a.ny;
     const T r = T(a.r);
     const int par = (int)((a.st->step + kstep) & 1);
     const T* h = static_cast<const T*>(a.scr);
     T* out = static_cast<T*>(a.f[par ^ 1]);
-    (void)n;
-    const int p = blockIdx.x;
-    const int jy = p / nv, jx = p - jy * nv;
-    for (unsigned cc = blockIdx.y * blockDim.x + threadIdx.x; cc < (unsigned)ncell;
+    const int jy0 = 2 * (int)blockIdx.x, jy1 = jy0 + 1;
+    const bool two = jy1 < nv;
+    for (unsigned cc = blockIdx.y * blockDim.x + threadIdx.x; cc < ncell;
          cc += gridDim.y * blockDim.x) {
-        const unsigned i = (unsigned)p * (unsigned)ncell + cc;
-        const T hc = h[i];
-        const T Dxr = jx < nv - 1 ? O::mul(r, O::sub(h[i + ncell], hc)) : T(0);
-        const T Dxl = jx > 0 ? O::mul(r, O::sub(hc, h[i - ncell])) : T(0);
-        const T Dyr = jy < nv - 1 ? O::mul(r, O::sub(h[i + ncell * nv], hc)) : T(0);
-        const T Dyl = jy > 0 ? O::mul(r, O::sub(hc, h[i - ncell * nv])) : T(0);
-        out[i] = O::add(O::add(hc, O::sub(Dxr, Dxl)), O::sub(Dyr, Dyl));
+        const T* r0 = h + (unsigned)(jy0 * nv) * ncell + cc;  // row jy0, column 0
+        const T* r1 = r0 + (unsigned)nv * ncell;              // row jy1
+        const unsigned ps = ncell;
+        // row values at jx - 1, jx, jx + 1 (index 0 .. 2)
+        T a0 = T(0), a1 = r0[0], b0 = T(0), b1 = two ? r1[0] : T(0);
+#pragma unroll(NVT > 0 ? NVT : 1)
+        for (int jx = 0; jx < nv; ++jx) {
+            const T a2 = jx < nv - 1 ? r0[(unsigned)(jx + 1) * ps] : T(0);
+            const T b2 = (two && jx < nv - 1) ? r1[(unsigned)(jx + 1) * ps] : T(0);
+            const T dn = jy0 > 0 ? *(r0 + (unsigned)jx * ps - (unsigned)nv * ps) : T(0);
+            const T hc = a1;
+            const T Dxr = jx < nv - 1 ? O::mul(r, O::sub(a2, hc)) : T(0);
+            const T Dxl = jx > 0 ? O::mul(r, O::sub(hc, a0)) : T(0);
+            const T Dyr = jy0 < nv - 1 ? O::mul(r, O::sub(b1, hc)) : T(0);
+            const T Dyl = jy0 > 0 ? O::mul(r, O::sub(hc, dn)) : T(0);
+            out[(unsigned)(jy0 * nv + jx) * ps + cc] = O::add(O::add(hc, O::sub(Dxr, Dxl)), O::sub(Dyr, Dyl));
+            if (two) {
+                const T up = jy1 < nv - 1 ? r1[(unsigned)jx * ps + (unsigned)nv * ps] : T(0);
+                const T hd = b1;
+                const T Exr = jx < nv - 1 ? O::mul(r, O::sub(b2, hd)) : T(0);
+                const T Exl = jx > 0 ? O::mul(r, O::sub(hd, b0)) : T(0);
+                const T Eyr = jy1 < nv - 1 ? O::mul(r, O::sub(up, hd)) : T(0);
+                const T Eyl = O::mul(r, O::sub(hd, hc));
+                out[(unsigned)(jy1 * nv + jx) * ps + cc] =
+                    O::add(O::add(hd, O::sub(Exr, Exl)), O::sub(Eyr, Eyl));
+            }
+            a0 = a1;
+            a1 = a2;
+            b0 = b1;
+            b1 = b2;
+        }
     }
 }
 
@@ -233,6 +258,7 @@ template <typename T, int NVT>
 void launch_stages(const Lim2DArgs& a, int k, dim3 grow, cudaStream_t s) {
     k_lim2d_stage<T, 1, NVT><<<grow, kLimThreads, 0, s>>>(a, k);
     k_lim2d_stage<T, 2, NVT><<<grow, kLimThreads, 0, s>>>(a, k);
+    k_lim2d_diffuse<T, NVT><<<grow, kLimThreads, 0, s>>>(a, k);
 }
 
 template <typename T>
@@ -240,7 +266,7 @@ cudaError_t launch_lim2d_t(const Lim2DArgs& a, int k, int sm_count, cudaStream_t
     const long long ncell = (long long)a.nx * a.ny;
     (void)sm_count;
     const unsigned chunks = (unsigned)std::min((ncell + kLimThreads - 1) / kLimThreads, 65535ll);
-    const dim3 grow((unsigned)(a.nv + 1) / 2, chunks), gcell((unsigned)(a.nv * a.nv), chunks);
+    const dim3 grow((unsigned)(a.nv + 1) / 2, chunks);
     // FP32 lattices of the common sizes take the unrolled stages
     bool done = false;
     if constexpr (sizeof(T) == 4) {
@@ -252,9 +278,6 @@ cudaError_t launch_lim2d_t(const Lim2DArgs& a, int k, int sm_count, cudaStream_t
         else done = false;
     }
     if (!done) launch_stages<T, 0>(a, k, grow, s);
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
-    k_lim2d_diffuse<T><<<gcell, kLimThreads, 0, s>>>(a, k);
     return cudaGetLastError();
 }
 
