@@ -106,6 +106,19 @@ def parse_profile(txt: str) -> dict:
     return vals
 
 
+# The ncu summary each timed workload takes its DRAM traffic from, and the source files its
+# dominant kernel is compiled from (the summary's hash covers them, in this order).
+_CSRC = "paper_1508_02899_gb300/csrc/"
+KERNEL_PROFILES = {
+    "ensemble": ("step1d_ensemble_fp32_nv65.md", (_CSRC + "step1d.cu",)),
+    "ensemble_koren": ("step1d_ensemble_koren_fp32_nv65.md", (_CSRC + "step1d.cu",)),
+    "2d": ("step2d_512_fp32_nv33.md", (_CSRC + "step2d.cu", _CSRC + "step2d_dev.h")),
+    "2d_f16": ("step2d_1024_f16_nv33.md", (_CSRC + "step2d_h.cu", _CSRC + "step2d_dev.h")),
+    "2d_bf16": ("step2d_1024_bf16_nv33.md", (_CSRC + "step2d_h.cu", _CSRC + "step2d_dev.h")),
+    "2d_learned": ("learn_tc_2048_nv9.md", (_CSRC + "learn_tc.cu",)),
+}
+
+
 def source_hash(src) -> str:
     """First 16 hex digits of the SHA-256 of the kernel's source files, concatenated in order."""
     import hashlib
@@ -488,29 +501,28 @@ def main():
     if args.workload == "2d_learned":
         ctx, cells, noise_row, glob, desc = build_learned(args, I, lat, torch, dev, rank, nsteps,
                                                           n=args.size or 2048)
-        nv, prof, src = 9, "learn_tc_2048_nv9.md", "paper_1508_02899_gb300/csrc/learn_tc.cu"
+        nv = 9
+        prof, src = KERNEL_PROFILES["2d_learned"]
         launches_per_step = 4  # flow, streamed density, network, corrected step
     elif args.workload == "2d":
         ctx, cells, noise_row, glob, desc = build_2d(args, I, lat, torch, dev, rank, nsteps,
                                                      n=args.size or 512)
-        nv, prof = 33, "step2d_512_fp32_nv33.md"
-        src = ("paper_1508_02899_gb300/csrc/step2d.cu", "paper_1508_02899_gb300/csrc/step2d_dev.h")
+        nv = 33
+        prof, src = KERNEL_PROFILES["2d"]
         launches_per_step = 2  # flow evaluation + fused step
     elif args.workload in ("2d_f16", "2d_bf16"):
         store = args.workload[3:]
         ctx, cells, noise_row, glob, desc = build_2d(args, I, lat, torch, dev, rank, nsteps,
                                                      n=args.size or 1024, store=store)
         nv = 33
-        prof = f"step2d_1024_{store}_nv33.md"
-        src = ("paper_1508_02899_gb300/csrc/step2d_h.cu", "paper_1508_02899_gb300/csrc/step2d_dev.h")
+        prof, src = KERNEL_PROFILES[args.workload]
         launches_per_step = 3  # flow evaluation + output scales + fused step
         bytes_per_cell, lines = 4, nv * nv * (args.size or 1024)
     else:
         ctx, cells, noise_row, glob, desc = build_ensemble(args, I, lat, torch, dev, rank, nsteps,
                                                            scheme=args.scheme)
-        nv, src = NV, "paper_1508_02899_gb300/csrc/step1d.cu"
-        prof = ("step1d_ensemble_fp32_nv65.md" if args.scheme == "upwind"
-                else "step1d_ensemble_koren_fp32_nv65.md")
+        nv = NV
+        prof, src = KERNEL_PROFILES["ensemble" if args.scheme == "upwind" else "ensemble_koren"]
         launches_per_step = 1
     best = None
     if args.launch:
