@@ -73,11 +73,11 @@ def test_committed_profiles_carry_their_roofline_inputs():
 
 
 def test_timed_workloads_have_current_traffic_figures():
-    """The ncu summary of the dominant kernel of the default workload and of the 2D FP32, FP16
-    and learned workloads was taken on the current sources, so that bench.py reports its DRAM
+    """The ncu summary of the dominant kernel of every timed workload was taken on the current
+    sources, so that bench.py reports its DRAM
     traffic (a summary left behind by a kernel change reads as a null traffic figure)."""
     import bench
-    for workload in ("ensemble", "ensemble_koren", "2d", "2d_f16", "2d_learned"):
+    for workload in ("ensemble", "ensemble_koren", "2d", "2d_f16", "2d_bf16", "2d_learned"):
         prof, src = bench.KERNEL_PROFILES[workload]
         assert bench.profile_traffic(prof, src) is not None, (workload, bench.source_hash(src))
 
