@@ -19,7 +19,7 @@ heavy particle suspensions", arXiv:1508.02899):
   CFL number of Eq. (cfl) is below one; the diffusion step is the finite-difference interface
   flux kappa (f_{j+1} - f_j)/dv, stable when kappa dt / dv^2 < 1/2 (Eq. stabLapl).
 
-Readings taken where the paper is silent or ambiguous (each one is listed in the design doc):
+Readings R1-R6, taken where the paper is silent or ambiguous:
 
 * R1  dv = 2 V_max / (N_v - 1): cell centres j*dv, j = -J..J, J = (N_v-1)/2 (Section 2 and the
       caption of Fig. 14 disagree; this is the reading that reproduces the time step of Sec. 3.2).

@@ -8,7 +8,7 @@ Section 2 of the paper offers, besides the first-order upwind drag step, a flux-
 after Hundsdorfer et al. (1995): a higher-order interface flux where f is smooth, lowered towards
 upwind near strong gradients by a nonlinear function of the ratio of consecutive differences,
 total-variation diminishing (TVD) so that it stays stable; the limiter is Koren's (1993) "with
-parameter 2/3".  Readings taken here (each one is listed in the design doc):
+parameter 2/3".  Readings K1-K3, taken here:
 
 * K1  Koren's limiter in Hundsdorfer et al.'s form.  The value carried through interface
       j+1/2 from its upwind side is q_j + psi(theta_j) (q_{j+1} - q_j), with

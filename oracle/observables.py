@@ -12,7 +12,7 @@ module: only ``tests/``, ``__graft_entry__.smoke()`` and the ``cpu_baseline`` /
       S1(r) = < int dv int dv' f(x, v) f(x + r, v') |v - v'| > / < int dv int dv' f(x, v) f(x + r, v') >,
   the averages taken over positions x.
 
-Lattice readings (listed in the design doc):
+Lattice readings O1-O2:
 
 * O1  r = w dx for a whole number w of cells; the window of cell i covers cells i .. i + w - 1
       (periodic).  The average over every cell of the domain does not depend on where the

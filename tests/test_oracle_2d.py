@@ -148,6 +148,82 @@ def test_relaxation_toward_constant_flow():
     assert abs((v[:, None] * c).sum() / c.sum() + 0.3) < 1e-6
 
 
+def check_moments_2d_known(mod=O):
+    """Per-cell and global 2D moments of hand-built velocity distributions (Sec. 3.2: the mass
+    of a cell is f dx^2 dv^2; Sec. 4.2: rho is the sum over both velocity components).
+
+    Cell (y, x) = (0, 0): all mass 2 in velocity cell (jx, jy) = (+3, -1): rho = 2 dv^2, the
+    mean velocity is that cell's velocity, <|v|^2> its squared norm.  (0, 1): two points
+    (+2, -1) and (-2, +1) of mass 1: mean 0, <|v|^2> = 5 dv^2.  (1, 0): empty: zeros.  (1, 1):
+    mass 1 at (+3, 0) and 3 at (0, -1): <v> = (3/4, -3/4) dv, <|v|^2> = (9 + 3)/4 dv^2, which
+    tells v_x from v_y and catches a dropped component of |v|^2.  dx and dv are powers of two,
+    so every expected value is exact in binary."""
+    nv, dx, dv = 9, 0.5, 0.25
+    J = (nv - 1) // 2
+    f = np.zeros((nv, nv, 2, 2))
+
+    def put(y, x, jx, jy, m):
+        f[jy + J, jx + J, y, x] += m
+
+    put(0, 0, 3, -1, 2.0)
+    put(0, 1, 2, -1, 1.0)
+    put(0, 1, -2, 1, 1.0)
+    put(1, 1, 3, 0, 1.0)
+    put(1, 1, 0, -1, 3.0)
+    rho, mvx, mvy, mv2, glob = mod.moments_2d(f, dx, dv)
+    assert rho.shape == (2, 2)
+    assert rho[0, 0] == 2.0 * dv * dv and rho[0, 1] == 2.0 * dv * dv
+    assert rho[1, 0] == 0.0 and rho[1, 1] == 4.0 * dv * dv
+    assert mvx[0, 0] == 3 * dv and mvy[0, 0] == -1 * dv and mv2[0, 0] == 10 * dv * dv
+    assert mvx[0, 1] == 0.0 and mvy[0, 1] == 0.0 and mv2[0, 1] == 5 * dv * dv
+    assert mvx[1, 0] == 0.0 and mvy[1, 0] == 0.0 and mv2[1, 0] == 0.0
+    assert mvx[1, 1] == 0.75 * dv and mvy[1, 1] == -0.75 * dv and mv2[1, 1] == 3 * dv * dv
+    w = dx * dx * dv * dv
+    # M = 2 + 2 + 4; P_x = 2(3) + (2 - 2) + 1(3) = 9 dv; P_y = 2(-1) + (-1 + 1) + 3(-1) = -5 dv;
+    # E = 2(10) + 5 + 5 + (9 + 3) = 42 dv^2
+    assert glob[0] == 8.0 * w
+    assert glob[1] == 9.0 * dv * w
+    assert glob[2] == -5.0 * dv * w
+    assert glob[3] == 42.0 * dv * dv * w
+
+
+def test_moments_2d_known():
+    check_moments_2d_known()
+
+
+def check_moments_2d_reduce_to_1d(mod=O):
+    """A 2D state supported on the row jy = 0 (v_y = 0) has the 1D moments of that row for
+    rho / dv, <v_x> and <|v|^2>, zero <v_y>; the same state transposed in (jx, jy) swaps
+    <v_x> and <v_y> (x <-> y symmetry of the velocity lattice).  The 1D moments are pinned by
+    test_oracle_1d.test_moments_of_known_distributions."""
+    rng = np.random.default_rng(11)
+    nv, ny, nx, dx, dv = 7, 3, 4, 0.3, 0.7
+    J = (nv - 1) // 2
+    row = rng.random((nv, ny * nx))
+    row[:, 5] = 0.0  # one empty cell
+    f = np.zeros((nv, nv, ny, nx))
+    f[J] = row.reshape(nv, ny, nx)
+    rho, mvx, mvy, mv2, glob = mod.moments_2d(f, dx, dv)
+    r1, m1, m21, g1 = mod.moments_1d(row, dx, dv)
+    np.testing.assert_allclose(rho.ravel(), r1 * dv, rtol=1e-15, atol=0)
+    np.testing.assert_allclose(mvx.ravel(), m1, rtol=1e-14, atol=1e-300)
+    np.testing.assert_allclose(mv2.ravel(), m21, rtol=1e-14, atol=1e-300)
+    assert np.all(mvy == 0.0)
+    np.testing.assert_allclose(glob[[0, 1, 3]], np.asarray(g1) * dx * dv, rtol=1e-14)
+    assert glob[2] == 0.0
+    ft = np.ascontiguousarray(np.swapaxes(f, 0, 1))
+    rt, mxt, myt, m2t, gt = mod.moments_2d(ft, dx, dv)
+    np.testing.assert_array_equal(rt, rho)
+    np.testing.assert_allclose(myt, mvx, rtol=1e-15, atol=0)
+    np.testing.assert_allclose(mxt, mvy, rtol=1e-15, atol=0)
+    np.testing.assert_allclose(m2t, mv2, rtol=1e-15, atol=0)
+    np.testing.assert_allclose(gt[[0, 2, 1, 3]], glob, rtol=1e-15)
+
+
+def test_moments_2d_reduce_to_1d():
+    check_moments_2d_reduce_to_1d()
+
+
 def check_flow2d_is_perp_gradient(mod=O):
     """u = (d_y psi, -d_x psi) and div u = 0, checked with spectral derivatives of psi."""
     nx = ny = 64

@@ -55,6 +55,17 @@ MUTATIONS = [
     ("2D diffusion drops the vy direction",
      "return f + c * (Dx[:, 1:] - Dx[:, :-1]) + c * (Dy[1:] - Dy[:-1])",
      "return f + c * (Dx[:, 1:] - Dx[:, :-1])", [P2.check_golden_2d]),
+    ("2D energy drops v_y^2", "s2 = ((vx * vx + vy * vy) * f).sum(axis=(0, 1))",
+     "s2 = ((vx * vx) * f).sum(axis=(0, 1))",
+     [P2.check_moments_2d_known, P2.check_moments_2d_reduce_to_1d]),
+    ("2D density missing one dv", "rho = s0 * dv * dv", "rho = s0 * dv",
+     [P2.check_moments_2d_known, P2.check_moments_2d_reduce_to_1d]),
+    ("2D moment velocity axes transposed",
+     "vx = np.broadcast_to(v[None, :, None, None], f.shape)",
+     "vx = np.broadcast_to(v[:, None, None, None], f.shape)",
+     [P2.check_moments_2d_known, P2.check_moments_2d_reduce_to_1d]),
+    ("2D global energy drops v_y^2", "math.fsum(((vx * vx + vy * vy) * f).ravel()) * w",
+     "math.fsum(((vx * vx) * f).ravel()) * w", [P2.check_moments_2d_known]),
 ]
 
 
