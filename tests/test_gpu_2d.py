@@ -100,6 +100,34 @@ def test_gaussian_start_with_flow_1000_steps(lat):
         lt.close()
 
 
+def test_128x128_33x33_100_steps(lat):
+    """The 2D size at which the 16-bit forms are validated: 128^2 x 33^2, St = 1, random-phase
+    flow, 100 steps, FP64 (1e-12) and FP32 (1e-5) storage in the default launch shape."""
+    c = make2d(128, 128, 33, 1.0, 1e-3, 100, 13)
+    want = oracle2d(c)
+    for dtype in (torch.float64, torch.float32):
+        got, lt = gpu2d(lat, c, dtype)
+        err = rel_l1(got, want)
+        print(f"\n[{dtype}] relative L1 {err:.3e}", end="")
+        assert err <= TOL[dtype], (dtype, err)
+        lt.close()
+
+
+@pytest.mark.parametrize("st", [0.1, 10.0])
+@pytest.mark.parametrize("kernel", [1, 5])
+def test_stokes_numbers_match_oracle(lat, st, kernel):
+    """St = 0.1 (smallest tau_p: largest V_max and drag Courant number under Eq. cfl) and
+    St = 10 on 136 x 24 x 17^2 (two tiles with a ragged second one), 150 steps, plain loads and
+    the producer/consumer ring, FP64 (plain loads only) and FP32."""
+    c = make2d(136, 24, 17, st, 1e-3, 150, 31 + int(10 * st))
+    want = oracle2d(c)
+    for dtype in ((torch.float64, torch.float32) if kernel == 1 else (torch.float32,)):
+        got, lt = gpu2d(lat, c, dtype, kernel=kernel)
+        assert rel_l1(got, want) <= TOL[dtype], (st, dtype, rel_l1(got, want))
+        assert got.min() >= -1e-6 * got.max()
+        lt.close()
+
+
 @pytest.mark.parametrize("kernel", [1, 2, 3, 4, 5, 6, 7])
 def test_free_streaming_is_exact(lat, kernel):
     nx, ny, nv = 136, 12, 9

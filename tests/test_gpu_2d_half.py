@@ -216,6 +216,13 @@ def test_long_run_against_fp64(lat, fmt):
     code, rho, _, _, g16 = lt.moments()
     code64, rho64, _, _, g64 = l64.moments()
     assert code == 0 and code64 == 0
+    # the FP64 run that judges the 16-bit one is itself the oracle's, at 1e-12
+    want, _ = O.run_2d(x0.astype(np.float64), 100, tau_p=c["tau_p"], kappa=c["kappa"],
+                       dt=c["dt"], dv=c["dv"], dx=c["dx"], kvec=fl.kvec, a=fl.a, phi0=fl.phi0,
+                       tau_f=fl.tau_f, noise=fl.noise)
+    got64 = l64.state.cpu().numpy()
+    err64 = np.abs(got64 - want).sum() / np.abs(want).sum()
+    assert err64 <= 1e-12, err64
     # mass: the carried residuals keep it at the FP32 arithmetic level (the FP64 run: 1e-15)
     e16, e64 = g16[3] / g16[0], g64[3] / g64[0]
     print(f"\n[{fmt}] mass drift {abs(g16[0] - m0[0]) / m0[0]:.3e}  <|v|^2> rel diff "
