@@ -33,7 +33,7 @@ struct DevState {
     long long noise_base;  // step at which noise row 0 applies
     long long noise_rows;  // rows in the noise table
     unsigned status;
-    unsigned pad;
+    unsigned stall;        // != 0: the bulk-copy producers issue nothing (lat_debug_stall)
 };
 
 // One 1D lattice instance as the kernels see it.
@@ -127,6 +127,14 @@ cudaError_t launch_coarse2d(const double* rho, int nx, int ny, double dx, const 
 cudaError_t launch_s1_1d(int dtype, const void* f, const Inst1D* inst, int n_inst, int nv,
                          const double* rho, const int* seps, int ns, double* num, double* den,
                          int sm_count, cudaStream_t s);
+
+// State I/O (state_io.cu): element conversions between FP64 and FP32 arrays of n values, and
+// the device step counter, noise window and status of a restored checkpoint.
+cudaError_t launch_f64_to_f32(const double* src, float* dst, long long n, cudaStream_t s);
+cudaError_t launch_f32_to_f64(const float* src, double* dst, long long n, cudaStream_t s);
+cudaError_t launch_set_devstate(DevState* st, long long step, long long noise_base,
+                                long long noise_rows, cudaStream_t s);
+cudaError_t launch_set_stall(DevState* st, unsigned on, cudaStream_t s);
 
 cudaError_t launch_finalize1d(const double* partials, const int* inst_item_begin,
                               const Inst1D* inst, int n_inst, double* glob, int per_item,

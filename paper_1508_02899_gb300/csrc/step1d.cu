@@ -532,8 +532,10 @@ __global__ void __launch_bounds__(PC1_THREADS) k_step1d_pc(const Step1DArgs a, c
     }
     __syncthreads();
     if (warp == PC1_CONSUMERS) {
+        // a stalled context issues no copies: every consumer's bounded wait runs out
+        const int nfill = a.st->stall ? 0 : nloc;
         int k = 0;
-        for (; k < nloc; ++k) {
+        for (; k < nfill; ++k) {
             const int q = k % NS;
             if (k >= NS && !mbar_wait_bounded(&empty[q], (unsigned)(((k / NS) + 1) & 1))) {
                 if (lane == 0) atomicOr(&a.st->status, ST_TIMEOUT);

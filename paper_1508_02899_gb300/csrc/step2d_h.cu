@@ -366,7 +366,8 @@ __device__ __forceinline__ void produce_rows_h(const Step2DArgs& a, const S* fin
                                                const TileOf& tile_of) {
     constexpr int NLP = NV * nv_padded(NV);
     const int lane = threadIdx.x & 31;
-    const long long total = (long long)ntl * NV;
+    // a stalled context issues no copies: every consumer's bounded wait runs out
+    const long long total = a.st->stall ? 0 : (long long)ntl * NV;
     auto flush = [&](int t) {  // tile t's maxima to global memory; clear the buffer
         const int yt = tile_of((long long)t * NV) / a.ntx;
         unsigned* m = mxs + (t & 1) * NLP;
