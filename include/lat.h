@@ -306,6 +306,63 @@ int lat_s1(lat_ctx* c, int ns, const int* seps, double* num, double* den);
  * (host, may be NULL) receives {kernel, block, blocks_per_sm, microseconds per step}. */
 int lat_autotune(lat_ctx* c, int reps, double* best);
 
+/* ---- host density I/O and checkpoints ------------------------------------------------------ */
+
+/* Copy the current state to HOST memory as FP64 values, in the layout of f (N_v^d values per
+ * spatial cell, instances concatenated; see the conventions above).  f_host: caller-owned host
+ * array of N_v^d * (sum of the instances' N_x, or N_x N_y) doubles.  FP32 and 16-bit states
+ * are widened exactly (16-bit values are decoded as h * S with their line scales).  Uses a
+ * temporary device buffer (at most 512 MiB for FP32 states; 12 bytes per value for 16-bit
+ * states).  Synchronises; returns the pending device status. */
+int lat_get_density(lat_ctx* c, double* f_host);
+
+/* Replace the current state by the FP64 HOST array f_host (layout as lat_get_density).  FP32
+ * storage rounds each value to nearest; 16-bit storage encodes the FP32-rounded values with
+ * fresh line scales, as lat_encode does.  The step count, the flow and the noise table are not
+ * touched.  Synchronises; returns the pending device status (LAT_EOVERFLOW if a value does not
+ * fit the 16-bit format). */
+int lat_set_density(lat_ctx* c, const double* f_host);
+
+/*
+ * Checkpoints.  The image holds everything of a context that evolves with the steps, so that a
+ * run resumed from it continues bit for bit (Section 2's scheme is a deterministic map of this
+ * state and the noise draws):
+ *   - the current density buffer in its storage type, and for 16-bit storage its line scales
+ *     and line maxima;
+ *   - the step count;
+ *   - the flow state at that step: the Ornstein-Uhlenbeck amplitudes of a 1D modal flow (FP64
+ *     and the FP32 copy the FP32 kernels read) or the phases of a 2D modal flow;
+ *   - the noise rows the context holds for this and later steps, with where they start.
+ * It does not hold what the caller sets once: the geometry, the flow's kind, wave vectors and
+ * constants, a FIELD flow's array, the drag scheme, the launch shape and the learned closure's
+ * parameters.  To resume, create a context with the same lat_grid (or instances), call
+ * lat_set_flow with the same flow (and lat_learn / lat_set_scheme as before), then
+ * lat_set_state.  The image is a flat byte array in host byte order, starting with a header
+ * that identifies the context's geometry and flow; it is not meant to move between hosts of
+ * different byte order.
+ */
+/* Size in bytes of the image of the context's present state (HOST long long).  Synchronises. */
+int lat_state_bytes(lat_ctx* c, long long* bytes);
+/* Write the image into the HOST buffer `image` of `bytes` bytes (at least lat_state_bytes).
+ * Synchronises; LAT_EINVAL if the buffer is too small.  The context is not changed. */
+int lat_get_state(lat_ctx* c, void* image, long long bytes);
+/* Restore the state from an image made by lat_get_state of a context with the same geometry,
+ * instances, dtype and flow kind / mode count (LAT_EINVAL otherwise, the context unchanged).
+ * Writes the density into the buffer that the image's step count selects (lat_current), the
+ * scales, the flow state into both parities and the noise rows into the noise table (grown if
+ * needed); clears the pending status.  Synchronises. */
+int lat_set_state(lat_ctx* c, const void* image, long long bytes);
+
+/* Test hook of the timeout path (the paper has no counterpart; the waits are this library's
+ * bulk-copy pipelines).  While on != 0, the producer warp of every producer/consumer step
+ * kernel (1D launch kernels 5..7, 2D kernels 3..7, 16-bit kernels 4..7: the defaults where the
+ * sizes allow them) issues no copies, so each consumer warp's bounded wait on its first row
+ * gives up after about one second; the step then writes no output and the next synchronising
+ * call returns LAT_ETIMEOUT.  No copy is in flight when a wait gives up, and the context stays
+ * usable: turn the hook off and step again.  Kernels without a pipeline ignore it.
+ * Asynchronous (ordered on the context's stream). */
+int lat_debug_stall(lat_ctx* c, int on);
+
 /* Human-readable text of a status code. */
 const char* lat_strerror(int status);
 

@@ -38,4 +38,22 @@ int ctx2d_set_launch(Ctx2D* c, int kernel, int block, int bps, int mode);
 int ctx2d_autotune(Ctx2D* c, void* const f[2], int reps, double* best, cudaStream_t s);
 void ctx2d_destroy(Ctx2D* c);
 
+// Parts of a 2D context that a checkpoint saves and restores (pointers into its scratch).
+struct Ctx2DDyn {
+    long long nlines = 0;        // 16-bit line scales (and maxima) per parity; 0 otherwise
+    float* sc = nullptr;         // [2][nlines]
+    unsigned* mx = nullptr;      // [2][nlines]
+    int flow_kind = 0, nmodes = 0;
+    double* phase = nullptr;     // [2][nmodes], MODES flows
+    double* noise = nullptr;     // noise table, [rows][nmodes]
+    long long noise_cap = 0;     // doubles
+    double g = 0, r = 0;         // dt / tau_p, kappa dt / dv^2
+    bool frozen = true;          // the flow does not evolve (no noise consumed)
+};
+void ctx2d_dyn(const Ctx2D* c, Ctx2DDyn* out);
+// Grow the noise table to at least `doubles` values (contents not kept).
+int ctx2d_noise_reserve(Ctx2D* c, long long doubles, cudaStream_t s);
+// Drop the cached step graphs (a restored state may have moved the noise table).
+void ctx2d_drop_graphs(Ctx2D* c);
+
 }  // namespace lat

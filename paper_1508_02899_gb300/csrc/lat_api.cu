@@ -842,6 +842,340 @@ int lat_autotune(lat_ctx* c, int reps, double* best) {
     return rc;
 }
 
+}  // extern "C"
+
+// ---- host density I/O and checkpoints ----------------------------------------------------------
+namespace {
+
+constexpr long long kConvChunk = 1ll << 26;  // values per FP32 <-> FP64 conversion pass
+
+size_t elem_bytes(int dtype) {
+    return dtype == LAT_F64 ? 8 : (dtype == LAT_F32 ? 4 : 2);
+}
+
+// Values of one density buffer (all instances).
+long long state_values(const lat_ctx* c) {
+    if (c->d == 2) {
+        int nx, ny, nv;
+        double dx, dv;
+        ctx2d_geometry(c->c2, &nx, &ny, &nv, &dx, &dv);
+        return (long long)nv * nv * nx * ny;
+    }
+    return (long long)c->nv * c->total_x;
+}
+
+// RAII device scratch of the I/O calls.
+struct DevBuf {
+    void* p = nullptr;
+    ~DevBuf() {
+        if (p) cudaFree(p);
+    }
+    bool alloc(size_t bytes) { return cudaMalloc(&p, bytes) == cudaSuccess; }
+};
+
+// FNV-1a over the bytes of the values that fix a context's lattice, so that an image is only
+// restored into a context of the same geometry and parameters.
+struct Fnv {
+    unsigned long long h = 1469598103934665603ull;
+    template <class T>
+    void add(const T& v) {
+        const unsigned char* b = reinterpret_cast<const unsigned char*>(&v);
+        for (size_t i = 0; i < sizeof(T); ++i) {
+            h ^= b[i];
+            h *= 1099511628211ull;
+        }
+    }
+};
+
+struct ImgHeader {
+    char magic[8];
+    int version, d, dtype, nv, nx, ny, n_inst, flow_kind, nmodes, reserved;
+    long long values;        // density values (all instances)
+    long long step;
+    long long noise_start;   // the first stored noise row applies at step + noise_start
+    long long noise_rows;
+    long long noise_row_len; // doubles per row
+    long long f_bytes, sc_bytes, flow_bytes, noise_bytes;
+    unsigned long long lattice_hash;
+};
+const char kImgMagic[8] = {'L', 'A', 'T', 'S', 'T', 'A', 'T', 'E'};
+constexpr int kImgVersion = 1;
+
+// What a context's image holds, from its host fields and its device state word (synchronises).
+int image_layout(lat_ctx* c, ImgHeader* h, DevState* ds) {
+    memset(h, 0, sizeof(*h));
+    memcpy(h->magic, kImgMagic, 8);
+    h->version = kImgVersion;
+    h->d = c->d;
+    h->dtype = c->dtype;
+    h->nv = c->nv;
+    h->n_inst = c->n_inst;
+    h->values = state_values(c);
+    Fnv fh;
+    long long row_len = 0;
+    bool moving = false;  // a modal flow that consumes noise rows
+    if (c->d == 2) {
+        int nx, ny, nv;
+        double dx, dv;
+        ctx2d_geometry(c->c2, &nx, &ny, &nv, &dx, &dv);
+        Ctx2DDyn dy;
+        ctx2d_dyn(c->c2, &dy);
+        h->nx = nx;
+        h->ny = ny;
+        h->flow_kind = dy.flow_kind;
+        h->nmodes = dy.nmodes;
+        fh.add(nx), fh.add(ny), fh.add(nv), fh.add(dx), fh.add(dv), fh.add(dy.g), fh.add(dy.r);
+        h->sc_bytes = (long long)dy.nlines * (sizeof(float) + sizeof(unsigned));
+        h->flow_bytes = dy.flow_kind == LAT_FLOW_MODES ? (long long)sizeof(double) * dy.nmodes : 0;
+        row_len = dy.nmodes;
+        moving = dy.flow_kind == LAT_FLOW_MODES && !dy.frozen;
+    } else {
+        h->nx = (int)std::min<long long>(c->total_x, 0x7fffffff);
+        h->ny = 1;
+        h->flow_kind = c->flow_kind;
+        h->nmodes = c->flow_kind == LAT_FLOW_MODES ? c->nmodes : 0;
+        for (const Inst1D& q : c->h_inst) {
+            fh.add(q.nx), fh.add(q.dx), fh.add(q.dv), fh.add(q.g), fh.add(q.r);
+            fh.add(q.ou_e), fh.add(q.ou_s);
+        }
+        h->flow_bytes = c->flow_kind == LAT_FLOW_MODES
+                            ? (long long)(sizeof(double) + sizeof(float)) * c->amp_stride
+                            : 0;
+        row_len = c->flow_kind == LAT_FLOW_MODES ? c->noise_row_len : 0;
+        moving = c->flow_kind == LAT_FLOW_MODES && !c->frozen;
+    }
+    h->lattice_hash = fh.h;
+    h->f_bytes = h->values * (long long)elem_bytes(c->dtype);
+    CK(cudaMemcpyAsync(ds, c->d_state, sizeof(DevState), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    h->step = ds->step;
+    h->noise_row_len = row_len;
+    if (row_len > 0 && moving && ds->noise_rows > 0) {
+        const long long skip = std::max(0ll, ds->step - ds->noise_base);
+        h->noise_rows = std::max(0ll, ds->noise_rows - skip);
+        h->noise_start = std::max(0ll, ds->noise_base - ds->step);
+    }
+    h->noise_bytes = (long long)sizeof(double) * h->noise_rows * row_len;
+    return LAT_OK;
+}
+
+long long image_bytes(const ImgHeader& h) {
+    return (long long)sizeof(ImgHeader) + h.f_bytes + h.sc_bytes + h.flow_bytes + h.noise_bytes;
+}
+
+}  // namespace
+
+extern "C" {
+
+int lat_get_density(lat_ctx* c, double* f_host) {
+    if (!c || !f_host) return LAT_EINVAL;
+    const long long n = state_values(c);
+    void* cur = c->f[c->cur];
+    if (c->dtype == LAT_F64) {
+        CK(cudaMemcpyAsync(f_host, cur, sizeof(double) * n, cudaMemcpyDeviceToHost, c->stream));
+    } else if (c->dtype == LAT_F32) {
+        const long long chunk = std::min(n, kConvChunk);
+        DevBuf t;
+        if (!t.alloc(sizeof(double) * chunk)) return LAT_ENOMEM;
+        for (long long i = 0; i < n; i += chunk) {
+            const long long m = std::min(chunk, n - i);
+            CK(launch_f32_to_f64(static_cast<const float*>(cur) + i, (double*)t.p, m, c->stream));
+            CK(cudaMemcpyAsync(f_host + i, t.p, sizeof(double) * m, cudaMemcpyDeviceToHost,
+                               c->stream));
+            CK(cudaStreamSynchronize(c->stream));  // t is reused by the next pass
+        }
+    } else {
+        DevBuf t32, t64;
+        if (!t32.alloc(sizeof(float) * n) || !t64.alloc(sizeof(double) * n)) return LAT_ENOMEM;
+        int rc = ctx2d_decode(c->c2, c->f, c->cur, (float*)t32.p, nullptr, c->stream);
+        if (rc != LAT_OK) return rc;
+        CK(launch_f32_to_f64((const float*)t32.p, (double*)t64.p, n, c->stream));
+        CK(cudaMemcpyAsync(f_host, t64.p, sizeof(double) * n, cudaMemcpyDeviceToHost,
+                           c->stream));
+        CK(cudaStreamSynchronize(c->stream));
+    }
+    return lat_status(c);  // synchronises
+}
+
+int lat_set_density(lat_ctx* c, const double* f_host) {
+    if (!c || !f_host) return LAT_EINVAL;
+    const long long n = state_values(c);
+    void* cur = c->f[c->cur];
+    if (c->dtype == LAT_F64) {
+        CK(cudaMemcpyAsync(cur, f_host, sizeof(double) * n, cudaMemcpyHostToDevice, c->stream));
+    } else if (c->dtype == LAT_F32) {
+        const long long chunk = std::min(n, kConvChunk);
+        DevBuf t;
+        if (!t.alloc(sizeof(double) * chunk)) return LAT_ENOMEM;
+        for (long long i = 0; i < n; i += chunk) {
+            const long long m = std::min(chunk, n - i);
+            CK(cudaMemcpyAsync(t.p, f_host + i, sizeof(double) * m, cudaMemcpyHostToDevice,
+                               c->stream));
+            CK(launch_f64_to_f32((const double*)t.p, static_cast<float*>(cur) + i, m, c->stream));
+            CK(cudaStreamSynchronize(c->stream));
+        }
+    } else {
+        DevBuf t32, t64;
+        if (!t32.alloc(sizeof(float) * n) || !t64.alloc(sizeof(double) * n)) return LAT_ENOMEM;
+        CK(cudaMemcpyAsync(t64.p, f_host, sizeof(double) * n, cudaMemcpyHostToDevice,
+                           c->stream));
+        CK(launch_f64_to_f32((const double*)t64.p, (float*)t32.p, n, c->stream));
+        int rc = ctx2d_encode(c->c2, (const float*)t32.p, c->f, c->cur, c->stream);
+        if (rc != LAT_OK) return rc;
+        CK(cudaStreamSynchronize(c->stream));
+    }
+    return lat_status(c);
+}
+
+int lat_state_bytes(lat_ctx* c, long long* bytes) {
+    if (!c || !bytes) return LAT_EINVAL;
+    ImgHeader h;
+    int rc = image_layout(c, &h, c->h_state);
+    if (rc != LAT_OK) return rc;
+    *bytes = image_bytes(h);
+    return LAT_OK;
+}
+
+int lat_get_state(lat_ctx* c, void* image, long long bytes) {
+    if (!c || !image) return LAT_EINVAL;
+    ImgHeader h;
+    DevState ds;
+    int rc = image_layout(c, &h, c->h_state);
+    if (rc != LAT_OK) return rc;
+    ds = *c->h_state;
+    if (bytes < image_bytes(h)) return LAT_EINVAL;
+    const int par = (int)(h.step & 1);
+    unsigned char* p = static_cast<unsigned char*>(image);
+    memcpy(p, &h, sizeof(h));
+    p += sizeof(h);
+    CK(cudaMemcpyAsync(p, c->f[par], h.f_bytes, cudaMemcpyDeviceToHost, c->stream));
+    p += h.f_bytes;
+    if (h.sc_bytes) {
+        Ctx2DDyn dy;
+        ctx2d_dyn(c->c2, &dy);
+        CK(cudaMemcpyAsync(p, dy.sc + (size_t)par * dy.nlines, sizeof(float) * dy.nlines,
+                           cudaMemcpyDeviceToHost, c->stream));
+        p += sizeof(float) * dy.nlines;
+        CK(cudaMemcpyAsync(p, dy.mx + (size_t)par * dy.nlines, sizeof(unsigned) * dy.nlines,
+                           cudaMemcpyDeviceToHost, c->stream));
+        p += sizeof(unsigned) * dy.nlines;
+    }
+    if (h.flow_bytes) {
+        if (c->d == 2) {
+            Ctx2DDyn dy;
+            ctx2d_dyn(c->c2, &dy);
+            CK(cudaMemcpyAsync(p, dy.phase + (size_t)par * dy.nmodes, h.flow_bytes,
+                               cudaMemcpyDeviceToHost, c->stream));
+        } else {
+            const size_t na = (size_t)c->amp_stride;
+            CK(cudaMemcpyAsync(p, c->d_amp + (size_t)par * na, sizeof(double) * na,
+                               cudaMemcpyDeviceToHost, c->stream));
+            CK(cudaMemcpyAsync(p + sizeof(double) * na, c->d_ampf + (size_t)par * na,
+                               sizeof(float) * na, cudaMemcpyDeviceToHost, c->stream));
+        }
+        p += h.flow_bytes;
+    }
+    if (h.noise_bytes) {
+        const double* table = c->d == 2 ? [&] {
+            Ctx2DDyn dy;
+            ctx2d_dyn(c->c2, &dy);
+            return (const double*)dy.noise;
+        }() : c->d_noise;
+        const long long skip = std::max(0ll, ds.step - ds.noise_base);
+        CK(cudaMemcpyAsync(p, table + skip * h.noise_row_len, h.noise_bytes,
+                           cudaMemcpyDeviceToHost, c->stream));
+    }
+    CK(cudaStreamSynchronize(c->stream));
+    return LAT_OK;
+}
+
+int lat_set_state(lat_ctx* c, const void* image, long long bytes) {
+    if (!c || !image || bytes < (long long)sizeof(ImgHeader)) return LAT_EINVAL;
+    ImgHeader img;
+    memcpy(&img, image, sizeof(img));
+    ImgHeader mine;
+    int rc = image_layout(c, &mine, c->h_state);
+    if (rc != LAT_OK) return rc;
+    if (memcmp(img.magic, kImgMagic, 8) != 0 || img.version != kImgVersion) return LAT_EINVAL;
+    if (img.d != mine.d || img.dtype != mine.dtype || img.nv != mine.nv || img.nx != mine.nx ||
+        img.ny != mine.ny || img.n_inst != mine.n_inst || img.values != mine.values ||
+        img.flow_kind != mine.flow_kind || img.nmodes != mine.nmodes ||
+        img.lattice_hash != mine.lattice_hash || img.f_bytes != mine.f_bytes ||
+        img.sc_bytes != mine.sc_bytes || img.flow_bytes != mine.flow_bytes ||
+        img.noise_row_len != mine.noise_row_len || img.step < 0 || img.noise_rows < 0 ||
+        img.noise_start < 0 || img.noise_bytes != (long long)sizeof(double) * img.noise_rows *
+                                                      img.noise_row_len)
+        return LAT_EINVAL;
+    if (bytes < image_bytes(img)) return LAT_EINVAL;
+    const long long need = img.noise_rows * img.noise_row_len;
+    double* table = nullptr;
+    if (c->d == 2) {
+        rc = ctx2d_noise_reserve(c->c2, need, c->stream);
+        if (rc != LAT_OK) return rc;
+        Ctx2DDyn dy;
+        ctx2d_dyn(c->c2, &dy);
+        table = dy.noise;
+    } else if (need > c->noise_cap) {
+        CK(cudaStreamSynchronize(c->stream));
+        double* q = nullptr;
+        if (cudaMalloc(&q, sizeof(double) * need) != cudaSuccess) return LAT_ENOMEM;
+        if (c->d_noise) cudaFree(c->d_noise);
+        c->d_noise = q;
+        c->noise_cap = need;
+        table = q;
+    } else {
+        table = c->d_noise;
+    }
+    const int par = (int)(img.step & 1);
+    const unsigned char* p = static_cast<const unsigned char*>(image) + sizeof(ImgHeader);
+    CK(cudaMemcpyAsync(c->f[par], p, img.f_bytes, cudaMemcpyHostToDevice, c->stream));
+    p += img.f_bytes;
+    if (img.sc_bytes) {
+        Ctx2DDyn dy;
+        ctx2d_dyn(c->c2, &dy);
+        CK(cudaMemcpyAsync(dy.sc + (size_t)par * dy.nlines, p, sizeof(float) * dy.nlines,
+                           cudaMemcpyHostToDevice, c->stream));
+        p += sizeof(float) * dy.nlines;
+        CK(cudaMemcpyAsync(dy.mx + (size_t)par * dy.nlines, p, sizeof(unsigned) * dy.nlines,
+                           cudaMemcpyHostToDevice, c->stream));
+        p += sizeof(unsigned) * dy.nlines;
+    }
+    if (img.flow_bytes) {
+        // both parities: a frozen flow reads either, a moving one overwrites the other
+        for (int q = 0; q < 2; ++q) {
+            if (c->d == 2) {
+                Ctx2DDyn dy;
+                ctx2d_dyn(c->c2, &dy);
+                CK(cudaMemcpyAsync(dy.phase + (size_t)q * dy.nmodes, p, img.flow_bytes,
+                                   cudaMemcpyHostToDevice, c->stream));
+            } else {
+                const size_t na = (size_t)c->amp_stride;
+                CK(cudaMemcpyAsync(c->d_amp + (size_t)q * na, p, sizeof(double) * na,
+                                   cudaMemcpyHostToDevice, c->stream));
+                CK(cudaMemcpyAsync(c->d_ampf + (size_t)q * na, p + sizeof(double) * na,
+                                   sizeof(float) * na, cudaMemcpyHostToDevice, c->stream));
+            }
+        }
+        p += img.flow_bytes;
+    }
+    if (img.noise_bytes)
+        CK(cudaMemcpyAsync(table, p, img.noise_bytes, cudaMemcpyHostToDevice, c->stream));
+    CK(launch_set_devstate(c->d_state, img.step, img.step + img.noise_start, img.noise_rows,
+                           c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    c->h_step = img.step;
+    c->cur = par;
+    drop_graphs(c);
+    if (c->d == 2) ctx2d_drop_graphs(c->c2);
+    return LAT_OK;
+}
+
+int lat_debug_stall(lat_ctx* c, int on) {
+    if (!c) return LAT_EINVAL;
+    CK(launch_set_stall(c->d_state, on ? 1u : 0u, c->stream));
+    return LAT_OK;
+}
+
 void lat_free(lat_ctx* c) {
     if (!c) return;
     if (c->stream) cudaStreamSynchronize(c->stream);

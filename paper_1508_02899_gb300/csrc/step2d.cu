@@ -367,8 +367,10 @@ __device__ __forceinline__ void produce_rows(const Step2DArgs& a, const float* f
                                              uint64_t* full, uint64_t* empty, long long total,
                                              const TileOf& tile_of) {
     const int lane = threadIdx.x & 31;
+    // a stalled context issues no copies: every consumer's bounded wait runs out
+    const long long nfill = a.st->stall ? 0 : total;
     long long f = 0;
-    for (; f < total; ++f) {
+    for (; f < nfill; ++f) {
         const int q = (int)(f % NS);
         if (f >= NS && !mbar_wait_bounded(&empty[q], (unsigned)(((f / NS) + 1) & 1))) {
             if (lane == 0) atomicOr(&a.st->status, ST_TIMEOUT);
@@ -1573,6 +1575,34 @@ int ctx2d_init_state(Ctx2D* c, void* const f[2], int cur, cudaStream_t s) {
                          c->d_mx + (size_t)cur * c->nlines, c->nv, c->nx, c->ny, s));
     return LAT_OK;
 }
+
+void ctx2d_dyn(const Ctx2D* c, Ctx2DDyn* o) {
+    o->nlines = c->half ? c->nlines : 0;
+    o->sc = c->d_sc;
+    o->mx = c->d_mx;
+    o->flow_kind = c->flow_kind;
+    o->nmodes = c->flow_kind == LAT_FLOW_MODES ? c->nmodes : 0;
+    o->phase = c->d_phase;
+    o->noise = c->d_noise;
+    o->noise_cap = c->noise_cap;
+    o->g = c->g;
+    o->r = c->r;
+    o->frozen = c->frozen;
+}
+
+int ctx2d_noise_reserve(Ctx2D* c, long long need, cudaStream_t s) {
+    if (need <= c->noise_cap) return LAT_OK;
+    CK2(cudaStreamSynchronize(s));
+    double* p = nullptr;
+    if (cudaMalloc(&p, sizeof(double) * need) != cudaSuccess) return LAT_ENOMEM;
+    cudaFree(c->d_noise);
+    c->d_noise = p;
+    c->noise_cap = need;
+    drop(c);
+    return LAT_OK;
+}
+
+void ctx2d_drop_graphs(Ctx2D* c) { drop(c); }
 
 int ctx2d_encode(Ctx2D* c, const float* src, void* const f[2], int cur, cudaStream_t s) {
     if (!c->half || !src) return LAT_EINVAL;

@@ -76,6 +76,12 @@ def _load():
         "lat_learn_grad": (c_int, [P, c_int, P, c_double, POINTER(c_double),
                                    POINTER(ctypes.c_float)]),
         "lat_decode": (c_int, [P, P, P]),
+        "lat_get_density": (c_int, [P, POINTER(c_double)]),
+        "lat_set_density": (c_int, [P, POINTER(c_double)]),
+        "lat_state_bytes": (c_int, [P, POINTER(c_longlong)]),
+        "lat_get_state": (c_int, [P, P, c_longlong]),
+        "lat_set_state": (c_int, [P, P, c_longlong]),
+        "lat_debug_stall": (c_int, [P, c_int]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -210,6 +216,39 @@ class _Ctx:
         _check(_lib.lat_autotune(self._h, reps, _dptr(best)), "lat_autotune")
         return {"kernel": int(best[0]), "block": int(best[1]), "blocks_per_sm": int(best[2]),
                 "us_per_step": float(best[3])}
+
+    def _values(self) -> int:
+        return self.f[0].numel()
+
+    def get_density(self) -> np.ndarray:
+        """The current state as FP64 host values, flat in the layout of f."""
+        out = np.empty(self._values(), dtype=np.float64)
+        _check(_lib.lat_get_density(self._h, _dptr(out)), "lat_get_density")
+        return out
+
+    def set_density(self, f: np.ndarray):
+        """Replace the current state by the FP64 host values f (layout of f)."""
+        f = np.ascontiguousarray(np.asarray(f, dtype=np.float64).reshape(-1))
+        if f.size != self._values():
+            raise ValueError(f"expected {self._values()} values")
+        _check(_lib.lat_set_density(self._h, _dptr(f)), "lat_set_density")
+
+    def get_state(self) -> np.ndarray:
+        """Checkpoint image of the context (host bytes)."""
+        n = c_longlong()
+        _check(_lib.lat_state_bytes(self._h, byref(n)), "lat_state_bytes")
+        img = np.empty(n.value, dtype=np.uint8)
+        _check(_lib.lat_get_state(self._h, c_void_p(img.ctypes.data), n.value), "lat_get_state")
+        return img
+
+    def set_state(self, img: np.ndarray):
+        """Restore a checkpoint image made by get_state."""
+        img = np.ascontiguousarray(img, dtype=np.uint8)
+        _check(_lib.lat_set_state(self._h, c_void_p(img.ctypes.data), img.size), "lat_set_state")
+
+    def debug_stall(self, on: bool):
+        """Timeout-path test hook: the pipeline kernels' producers issue no copies while on."""
+        _check(_lib.lat_debug_stall(self._h, int(bool(on))), "lat_debug_stall")
 
     def close(self):
         if self._h:
