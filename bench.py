@@ -467,7 +467,8 @@ def kernel_label(workload, best, nv):
         if k >= 3:
             return {3: f"k_step2d_pc<{nv},4,false,false>", 4: f"k_step2d_pc<{nv},4,true,false>",
                     5: f"k_step2d_pc<{nv},3,true,false>", 6: f"k_step2d_pc<{nv},3,true,true>",
-                    7: f"k_step2d_pc<{nv},2,true,true>"}[k]
+                    7: f"k_step2d_pc<{nv},2,true,true>", 8: f"k_step2d_pc2<{nv},3,false>",
+                    9: f"k_step2d_pc2<{nv},3,true>", 10: f"k_step2d_pc2<{nv},2,true>"}[k]
         return f"k_step2d_{'ring' if k == 2 else 'plain'}<{nv}>"
     if k >= 5:
         return f"k_step1d_pc<{nv},{k - 3}>"

@@ -28,6 +28,7 @@
 
 #include "lat2d.h"
 #include "step2d_dev.h"
+#include "step2d_x2.h"
 #include "step2d_h.h"
 #include "learn.h"
 #include "lat_reduce.h"
@@ -51,7 +52,8 @@ struct Flow2DArgs {
     const double* cx;         // [M] coefficient of sin(theta) in u_x
     const double* cy;         // [M] coefficient of sin(theta) in u_y
     double* phase;            // [2][M] parity-indexed phases
-    const double* noise;      // [rows][M]
+    const double* noise;      // [rows][M] in the caller's mode order
+    const int* perm;          // [M] caller's index of mode m (modes are kept sorted by kx)
     double walk;              // sqrt(2 dt / tau_f)
     const void* xtab;         // [2 kmax+1][nx][2] of T
     const void* ytab;         // [2 kmax+1][ny][2] of T
@@ -565,54 +567,180 @@ __global__ void __launch_bounds__(PCShape<NV, NS, GSM, HSM>::threads,
 
 // ---- flow: u = (d_y psi, -d_x psi) of psi = sum a_m cos(theta_m) --------------------------------
 
+// Per-mode terms of the flow at step `step` into shared memory, sh = [M] cos phi, [M] sin phi
+// (phases in FP64, terms stored as T), by threads t = t0, t0 + nt, ...; the writer also stores
+// the next step's phases (unless the flow is frozen or the run is dry) and flags a missing
+// noise row.  The caller synchronises the threads that read sh afterwards.
 template <typename T>
-__global__ void __launch_bounds__(256) k_flow2d(const Flow2DArgs a, int kstep) {
-    extern __shared__ double sh_raw[];
-    T* sh = reinterpret_cast<T*>(sh_raw);  // [M] cos phi, [M] sin phi, [M] c_x, [M] c_y
+__device__ __forceinline__ void flow_modes_prepare(const Flow2DArgs& a, long long step, T* sh,
+                                                   int t, int nt, bool writer) {
     const int M = a.nmodes;
-    const long long step = a.st->step + kstep;
     const int par = (int)(step & 1);
     const double* ph = a.phase + (size_t)par * M;
-    for (int m = threadIdx.x; m < M; m += blockDim.x) {
+    for (int m = t; m < M; m += nt) {
         double s, c;
         sincos(ph[m], &s, &c);
         sh[m] = T(c);
         sh[M + m] = T(s);
-        sh[2 * M + m] = T(a.cx[m]);
-        sh[3 * M + m] = T(a.cy[m]);
     }
-    __syncthreads();
-    if (blockIdx.x == 0 && !a.frozen && !a.dry) {
+    if (writer && !a.frozen && !a.dry) {
         const long long row = step - a.st->noise_base;
         const bool have = row >= 0 && row < a.st->noise_rows;
-        for (int m = threadIdx.x; m < a.nmodes; m += blockDim.x) {
-            const double xi = have ? a.noise[row * a.nmodes + m] : 0.0;
-            a.phase[(size_t)(par ^ 1) * a.nmodes + m] = __dadd_rn(ph[m], __dmul_rn(a.walk, xi));
+        for (int m = t; m < M; m += nt) {
+            const double xi = have ? a.noise[row * M + a.perm[m]] : 0.0;
+            a.phase[(size_t)(par ^ 1) * M + m] = __dadd_rn(ph[m], __dmul_rn(a.walk, xi));
         }
-        if (!have && threadIdx.x == 0) atomicOr(&a.st->status, ST_NOISE);
+        if (!have && t == 0) atomicOr(&a.st->status, ST_NOISE);
     }
+}
+
+// u = (d_y psi, -d_x psi) = sum over the modes of (c_x, c_y) sin(theta_m), theta_m =
+// 2 pi (kx x / nx + ky y / ny) + phi_m.  With e^{i theta} = X_kx(x) Y_ky(y) e^{i phi} from the
+// separable tables, sin(theta) = Im(X w), w = Y e^{i phi}: one block per row y forms
+// W_m = (c_x w, c_y w) for every mode in shared memory, then each thread sums over the modes for
+// its cells with four FMAs per mode.  Modes are sorted by kx, so a thread loads X_kx(x) once per
+// distinct kx.  Explicit rounding throughout.
+template <typename T>
+__global__ void __launch_bounds__(256) k_flow2d(const Flow2DArgs a, int kstep) {
+    using O = Ops<T>;
+    extern __shared__ double sh_raw[];
+    const int M = a.nmodes;
+    T* sh = reinterpret_cast<T*>(sh_raw);   // [M] cos phi, [M] sin phi
+    T* W = sh + 2 * M;                      // [M][4]: c_x w_re, c_x w_im, c_y w_re, c_y w_im
+    const long long step = a.st->step + kstep;
+    flow_modes_prepare<T>(a, step, sh, threadIdx.x, blockDim.x, blockIdx.x == 0);
+    __syncthreads();
     const long long ncell = (long long)a.nx * a.ny;
     const T* xt = static_cast<const T*>(a.xtab);  // [kx + kmax][x][cos, sin] of 2 pi kx x / nx
     const T* yt = static_cast<const T*>(a.ytab);  // [ky + kmax][y][cos, sin] of 2 pi ky y / ny
-    for (long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x; c < ncell;
-         c += (long long)gridDim.x * blockDim.x) {
-        const int x = (int)(c % a.nx), y = (int)(c / a.nx);
-        T ux = T(0), uy = T(0);
-        for (int m = 0; m < M; ++m) {
+    T* u = static_cast<T*>(a.u);
+    for (int y = blockIdx.x; y < a.ny; y += gridDim.x) {
+        for (int m = threadIdx.x; m < M; m += blockDim.x) {
             const int2 k = a.k[m];
-            const T* X = xt + 2 * ((size_t)(k.x + a.kmax) * a.nx + x);
             const T* Y = yt + 2 * ((size_t)(k.y + a.kmax) * a.ny + y);
-            // e^{i theta_int} = e^{i 2 pi kx x / nx} e^{i 2 pi ky y / ny}
-            const T zr = X[0] * Y[0] - X[1] * Y[1];
-            const T zi = X[0] * Y[1] + X[1] * Y[0];
-            const T s = zi * sh[m] + zr * sh[M + m];  // sin(theta_int + phi)
-            ux += sh[2 * M + m] * s;
-            uy += sh[3 * M + m] * s;
+            const T c = sh[m], s = sh[M + m];
+            const T w0 = O::fma(Y[0], c, -O::mul(Y[1], s));
+            const T w1 = O::fma(Y[0], s, O::mul(Y[1], c));
+            const T cx = T(a.cx[m]), cy = T(a.cy[m]);
+            W[4 * m] = O::mul(cx, w0);
+            W[4 * m + 1] = O::mul(cx, w1);
+            W[4 * m + 2] = O::mul(cy, w0);
+            W[4 * m + 3] = O::mul(cy, w1);
         }
-        T* u = static_cast<T*>(a.u);
-        u[c] = ux;
-        u[ncell + c] = uy;
+        __syncthreads();
+        for (int x = threadIdx.x; x < a.nx; x += blockDim.x) {
+            T ux = T(0), uy = T(0), X0 = T(0), X1 = T(0);
+            int kxc = 0x7fffffff;
+            for (int m = 0; m < M; ++m) {
+                const int kx = a.k[m].x;
+                if (kx != kxc) {
+                    kxc = kx;
+                    const T* X = xt + 2 * ((size_t)(kx + a.kmax) * a.nx + x);
+                    X0 = X[0];
+                    X1 = X[1];
+                }
+                // Im(X w) (c_x, c_y) = X_re (c w_im) + X_im (c w_re)
+                ux = O::fma(X0, W[4 * m + 1], O::fma(X1, W[4 * m], ux));
+                uy = O::fma(X0, W[4 * m + 3], O::fma(X1, W[4 * m + 2], uy));
+            }
+            u[(size_t)y * a.nx + x] = ux;
+            u[ncell + (size_t)y * a.nx + x] = uy;
+        }
+        __syncthreads();
     }
+}
+
+// ---- packed producer/consumer kernel -----------------------------------------------------------
+// The producer/consumer design with the packed two-lane sweep (step2d_x2.h): one producer warp
+// fills the ring, four consumer warps sweep one cell each, holding a velocity row as two
+// half-rows in f32x2 register pairs.  Same bits as every other FP32 launch variant.  GSM: the
+// vy-drag flux pairs in shared memory instead of registers.
+template <int NV, int NS, bool GSM>
+struct PC2Shape {
+    static constexpr int consumers = TW / 32;
+    static constexpr int threads = 32 * (consumers + 1);
+    static constexpr int min_blocks = GSM ? 3 : 2;
+};
+
+template <int NV, int NS, bool GSM>
+size_t pc2_smem() {
+    return (size_t)NS * NV * WIN * sizeof(float) +
+           (GSM ? (size_t)Pairs<NV>::n * TW * sizeof(f2) : 0) + 2 * NS * sizeof(uint64_t);
+}
+
+template <int NV, int NS, bool GSM>
+__global__ void __launch_bounds__(PC2Shape<NV, NS, GSM>::threads,
+                                  PC2Shape<NV, NS, GSM>::min_blocks)
+    k_step2d_pc2(const Step2DArgs a, int kstep) {
+    constexpr int NC = PC2Shape<NV, NS, GSM>::consumers;
+    constexpr int NP = Pairs<NV>::n;
+    extern __shared__ __align__(128) unsigned char smem[];
+    float* ring = reinterpret_cast<float*>(smem);
+    f2* gsm = reinterpret_cast<f2*>(ring + (size_t)NS * NV * WIN);
+    uint64_t* full = reinterpret_cast<uint64_t*>(gsm + (GSM ? NP * TW : 0));
+    uint64_t* empty = full + NS;
+    const long long step = a.st->step + kstep;
+    const int par = (int)(step & 1);
+    const float g = float(a.g), rr = float(a.r);
+    const float* fin = static_cast<const float*>(a.f[par]);
+    float* fout = static_cast<float*>(a.f[par ^ 1]);
+    const size_t ps = (size_t)a.nx * a.ny;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int ntl = a.ntiles > (int)blockIdx.x ? (a.ntiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
+    const long long total = (long long)ntl * NV;
+    auto tile_of = [&](long long s) { return (int)(blockIdx.x + (s / NV) * gridDim.x); };
+    if (threadIdx.x == 0) {
+        for (int q = 0; q < NS; ++q) {
+            mbar_init(&full[q], 1);
+            mbar_init(&empty[q], NC);
+        }
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    if (warp == NC) {
+        produce_rows<NV, NS>(a, fin, ring, full, empty, total, tile_of);
+        return;
+    }
+    const int cell = threadIdx.x;
+    bool failed = false;
+    for (int lt = 0; lt < ntl && !failed; ++lt) {
+        const int tile = tile_of((long long)lt * NV);
+        const int y = tile / a.ntx;
+        const int xr = (tile % a.ntx) * TW + cell;
+        const bool active = xr < a.nx;
+        const int x = active ? xr : 0;
+        float wx, wy;
+        load_w<float>(a, x, y, wx, wy);
+        cfl_check<float, NV>(a, g, wx, wy, active);
+        f2 A[NP], Hd[NP], Greg[NP];
+        SmemCol2 Gs{gsm + cell};
+#pragma unroll
+        for (int p = 0; p < NP; ++p) {
+            A[p] = 0ull;
+            Hd[p] = 0ull;
+            if (GSM) Gs[p] = 0ull;
+            else Greg[p] = 0ull;
+        }
+        StorePut2<NV> put(fout + (size_t)y * a.nx + x, ps, active);
+        const long long s0 = (long long)lt * NV;
+        for (int r = 0; r <= NV; ++r) {
+            const long long s = s0 + r;
+            if (r < NV && !mbar_wait_bounded(&full[s % NS], (unsigned)((s / NS) & 1))) {
+                failed = true;
+                break;
+            }
+            if (r >= 1) {
+                const RingRow<NV> cur{ring + (size_t)((s - 1) % NS) * NV * WIN + cell};
+                const RingRow<NV> nxt{ring + (size_t)(s % NS) * NV * WIN + cell};
+                if constexpr (GSM) sweep_row2<NV>(A, Gs, Hd, r, cur, nxt, g, wx, wy, rr, put);
+                else sweep_row2<NV>(A, Greg, Hd, r, cur, nxt, g, wx, wy, rr, put);
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&empty[(s - 1) % NS]);  // row s - 1 is done
+            }
+        }
+        if (!failed) final_row2<NV>(A, Hd, rr, put);
+    }
+    if (failed && lane == 0) atomicOr(&a.st->status, ST_TIMEOUT);
 }
 
 // ---- moments ----------------------------------------------------------------------------------
@@ -901,9 +1029,38 @@ cudaError_t launch_pc_mom(int v, int bps, int sm_count, const Step2DArgs& a, int
     return cudaErrorInvalidValue;
 }
 
+template <int NV, int NS, bool GSM>
+cudaError_t launch_pc2(int grid, const Step2DArgs& a, int k, cudaStream_t s) {
+    static bool attr = false;
+    const size_t bytes = pc2_smem<NV, NS, GSM>();
+    if (!attr) {
+        cudaError_t e = cudaFuncSetAttribute(k_step2d_pc2<NV, NS, GSM>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)bytes);
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    k_step2d_pc2<NV, NS, GSM><<<grid, PC2Shape<NV, NS, GSM>::threads, bytes, s>>>(a, k);
+    return cudaGetLastError();
+}
+
+template <int NV, int NS, bool GSM>
+int occupancy_pc2_t() {
+    int nb = 0;
+    const size_t bytes = pc2_smem<NV, NS, GSM>();
+    cudaFuncSetAttribute(k_step2d_pc2<NV, NS, GSM>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)bytes);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_step2d_pc2<NV, NS, GSM>,
+                                                  PC2Shape<NV, NS, GSM>::threads, bytes);
+    return nb;
+}
+
 template <int NV>
 cudaError_t launch_pc_v(int v, int grid, const Step2DArgs& a, int k, cudaStream_t s) {
     if constexpr (LAT2D_PC(NV)) {
+        if (v == 8) return launch_pc2<NV, 3, false>(grid, a, k, s);
+        if (v == 9) return launch_pc2<NV, 3, true>(grid, a, k, s);
+        if (v == 10) return launch_pc2<NV, 2, true>(grid, a, k, s);
         if (v == 3) return launch_pc<NV, 4, false>(grid, a, k, s);
         if (v == 4) return launch_pc<NV, 4, true>(grid, a, k, s);
         if (v == 5) return launch_pc<NV, 3, true>(grid, a, k, s);
@@ -916,6 +1073,9 @@ cudaError_t launch_pc_v(int v, int grid, const Step2DArgs& a, int k, cudaStream_
 template <int NV>
 int occupancy_pc_v(int v) {
     if constexpr (LAT2D_PC(NV)) {
+        if (v == 8) return occupancy_pc2_t<NV, 3, false>();
+        if (v == 9) return occupancy_pc2_t<NV, 3, true>();
+        if (v == 10) return occupancy_pc2_t<NV, 2, true>();
         if (v == 3) return occupancy_pc_t<NV, 4, false>();
         if (v == 4) return occupancy_pc_t<NV, 4, true>();
         if (v == 5) return occupancy_pc_t<NV, 3, true>();
@@ -983,7 +1143,8 @@ struct Ctx2D {
     int flow_kind = LAT_FLOW_NONE;
     const void* field = nullptr;
     int nmodes = 0;
-    int2* d_k = nullptr;
+    int2* d_k = nullptr;      // modes sorted by kx (see k_flow2d)
+    int* d_perm = nullptr;    // caller's index of each mode (noise columns)
     double* d_cx = nullptr;
     double* d_cy = nullptr;
     double* d_phase = nullptr;
@@ -1093,9 +1254,10 @@ int grid_of(const Ctx2D* c, int ntiles) {
 // current buffer and writes the other one, so the state and the flow are left as they were.
 // Flow of step st->step + k into d_u (modal flow only); the phases of the following step are
 // written unless dry.
-int launch_flow(Ctx2D* c, int k, int dry, cudaStream_t s) {
+Flow2DArgs flow_args(const Ctx2D* c, int dry) {
     Flow2DArgs fa;
-            fa.k = c->d_k;
+    fa.k = c->d_k;
+    fa.perm = c->d_perm;
     fa.cx = c->d_cx;
     fa.cy = c->d_cy;
     fa.phase = c->d_phase;
@@ -1111,9 +1273,13 @@ int launch_flow(Ctx2D* c, int k, int dry, cudaStream_t s) {
     fa.st = c->st;
     fa.frozen = c->frozen ? 1 : 0;
     fa.dry = dry;
-    const long long ncell = (long long)c->nx * c->ny;
-    const int fg = (int)std::min<long long>((ncell + 255) / 256, 8LL * c->sm_count);
-    const size_t sh = 4 * sizeof(double) * c->nmodes;
+    return fa;
+}
+
+int launch_flow(Ctx2D* c, int k, int dry, cudaStream_t s) {
+    const Flow2DArgs fa = flow_args(c, dry);
+    const int fg = std::max(1, std::min(c->ny, 4 * c->sm_count));  // rows per block: grid stride
+    const size_t sh = 6 * sizeof(double) * c->nmodes;
     if (c->dtype == LAT_F64) k_flow2d<double><<<fg, 256, sh, s>>>(fa, k);
     else k_flow2d<float><<<fg, 256, sh, s>>>(fa, k);
     CK2(cudaGetLastError());
@@ -1232,7 +1398,7 @@ int ctx2d_create(Ctx2D** out, const lat_grid* g, DevState* st, int sm_count, cud
     c->sm_count = sm_count;
     c->ring = ring_ok(c);
     c->chunks = chunks_supported(c->nv, 3) ? 3 : 1;
-    c->pcv = c->ring && pc_ok(c) ? (half ? 6 : 4) : 0;
+    c->pcv = c->ring && pc_ok(c) ? (half ? 6 : 9) : 0;
     if (half && !c->pcv) c->ring = false;
     const long long ncell = (long long)c->nx * c->ny;
     c->mom_blocks = (int)std::min<long long>((ncell + 255) / 256, 8LL * sm_count);
@@ -1273,15 +1439,21 @@ int ctx2d_set_flow(Ctx2D* c, const lat_flow* fl, bool frozen, cudaStream_t s) {
     } else if (fl->kind == LAT_FLOW_MODES) {
         const int M = fl->nmodes;
         if (M < 1 || M > kMaxModes2D || !fl->k || !fl->amp0 || !fl->phase0) return LAT_EINVAL;
+        // modes in ascending kx (stable), so that the flow kernel loads each x table row once
+        std::vector<int> perm(M);
+        for (int m = 0; m < M; ++m) perm[m] = m;
+        std::stable_sort(perm.begin(), perm.end(),
+                         [&](int i, int j) { return fl->k[2 * i] < fl->k[2 * j]; });
         std::vector<int2> k(M);
         std::vector<double> cx(M), cy(M), ph(2 * M);
         const double Lx = c->nx * c->dx, Ly = c->ny * c->dx;
         for (int m = 0; m < M; ++m) {
-            k[m] = make_int2(fl->k[2 * m], fl->k[2 * m + 1]);
-            cx[m] = -fl->amp0[m] * (2.0 * M_PI * k[m].y / Ly);
-            cy[m] = fl->amp0[m] * (2.0 * M_PI * k[m].x / Lx);
-            ph[m] = fl->phase0[m];
-            ph[M + m] = fl->phase0[m];
+            const int q = perm[m];
+            k[m] = make_int2(fl->k[2 * q], fl->k[2 * q + 1]);
+            cx[m] = -fl->amp0[q] * (2.0 * M_PI * k[m].y / Ly);
+            cy[m] = fl->amp0[q] * (2.0 * M_PI * k[m].x / Lx);
+            ph[m] = fl->phase0[q];
+            ph[M + m] = fl->phase0[q];
         }
         cudaFree(c->d_k);
         cudaFree(c->d_cx);
@@ -1289,6 +1461,10 @@ int ctx2d_set_flow(Ctx2D* c, const lat_flow* fl, bool frozen, cudaStream_t s) {
         cudaFree(c->d_phase);
         c->d_k = nullptr;
         c->d_cx = c->d_cy = c->d_phase = nullptr;
+        cudaFree(c->d_perm);
+        c->d_perm = nullptr;
+        if (cudaMalloc(&c->d_perm, sizeof(int) * M) != cudaSuccess) return LAT_ENOMEM;
+        CK2(cudaMemcpy(c->d_perm, perm.data(), sizeof(int) * M, cudaMemcpyHostToDevice));
         if (cudaMalloc(&c->d_k, sizeof(int2) * M) != cudaSuccess ||
             cudaMalloc(&c->d_cx, sizeof(double) * M) != cudaSuccess ||
             cudaMalloc(&c->d_cy, sizeof(double) * M) != cudaSuccess ||
@@ -1443,7 +1619,7 @@ int ctx2d_moments(Ctx2D* c, const void* f, int cur, double* rho, double* mean_v,
 
 bool ctx2d_moments_fusable(const Ctx2D* c) {
     return c->dtype == LAT_F32 && !c->half && !c->learn && c->scheme == LAT_SCHEME_UPWIND &&
-           c->ring && (c->pcv == 4 || c->pcv == 5) && pc_supported(c->nv);
+           c->ring && (c->pcv == 4 || c->pcv == 5 || c->pcv >= 8) && pc_supported(c->nv);
 }
 
 int ctx2d_step_moments(Ctx2D* c, void* const f[2], double* rho, double* mean_v,
@@ -1461,7 +1637,9 @@ int ctx2d_step_moments(Ctx2D* c, void* const f[2], double* rho, double* mean_v,
     m.partials = c->d_partials;
     m.dv = c->dv;
     int grid = 0;
-    CK2(launch_step2d_mom(c->nv, c->pcv, c->bps, c->sm_count, a, 0, m, &grid, s));
+    // the packed kernels write the same bits as kernel 5, which also reduces the moments
+    const int v = c->pcv >= 8 ? 5 : c->pcv;
+    CK2(launch_step2d_mom(c->nv, v, c->pcv >= 8 ? 0 : c->bps, c->sm_count, a, 0, m, &grid, s));
     k_advance2d<<<1, 1, 0, s>>>(c->st, 1);
     CK2(cudaGetLastError());
     k_finalize2d<<<1, kFin2DThreads, 0, s>>>(c->d_partials, grid * (TW / 32),
@@ -1478,9 +1656,9 @@ int ctx2d_step_moments(Ctx2D* c, void* const f[2], double* rho, double* mean_v,
 int ctx2d_set_launch(Ctx2D* c, int kernel, int block, int bps, int mode) {
     // kernel: 0 keep, 1 plain loads (128 threads), >= 2 bulk-copy ring; for the ring, block =
     // 128 C threads splits every cell's jx range over C warp groups (C = 1..4)
-    // kernel 3..7: producer/consumer variants (block fixed at 160 threads)
-    if (kernel < 0 || kernel > 7) return LAT_EINVAL;
-    if (c->half && (kernel == 2 || kernel == 3)) return LAT_EINVAL;
+    // kernel 3..7: producer/consumer variants, 8..10 the packed two-lane sweep (160 threads)
+    if (kernel < 0 || kernel > 10) return LAT_EINVAL;
+    if (c->half && (kernel == 2 || kernel == 3 || kernel >= 8)) return LAT_EINVAL;
     if (kernel >= 2 && !ring_ok(c)) return LAT_EINVAL;
     if (c->half && kernel >= 4 && !pc_ok(c)) return LAT_EINVAL;
     if (kernel >= 3 && !pc_supported(c->nv)) return LAT_EINVAL;
@@ -1519,12 +1697,12 @@ int ctx2d_autotune(Ctx2D* c, void* const f[2], int reps, double* best, cudaStrea
     double best_us = 1e300;
     bool best_ring = c->ring;
     int best_bps = c->bps, best_chunks = c->chunks, best_pcv = c->pcv;
-    // variant 0: plain loads; 1..4: ring with that many chunks; 5..9: producer/consumer 3..7
-    for (int variant = 0; variant <= 9; ++variant) {
+    // variant 0: plain loads; 1..4: ring with that many chunks; 5..12: producer/consumer 3..10
+    for (int variant = 0; variant <= 12; ++variant) {
         if (variant > 0 && !ring_ok(c)) continue;
         if (variant >= 1 && variant <= 4 && !chunks_supported(c->nv, variant)) continue;
         if (variant >= 5 && !pc_ok(c)) continue;
-        if (c->half && (variant >= 1 && variant <= 5)) continue;  // 16-bit: plain, pc 4..7
+        if (c->half && ((variant >= 1 && variant <= 5) || variant >= 10)) continue;  // 16-bit: plain, pc 4..7
         for (int bps : {1, 2, 3, 4, 6, 8}) {
             c->ring = variant > 0;
             c->chunks = (variant >= 1 && variant <= 4) ? variant : 1;
@@ -1797,6 +1975,7 @@ void ctx2d_destroy(Ctx2D* c) {
     if (!c) return;
     drop(c);
     cudaFree(c->d_k);
+    cudaFree(c->d_perm);
     cudaFree(c->d_cx);
     cudaFree(c->d_cy);
     cudaFree(c->d_phase);

@@ -128,7 +128,7 @@ def test_stokes_numbers_match_oracle(lat, st, kernel):
         lt.close()
 
 
-@pytest.mark.parametrize("kernel", [1, 2, 3, 4, 5, 6, 7])
+@pytest.mark.parametrize("kernel", [1, 2, 3, 4, 5, 6, 7, 8, 9, 10])
 def test_free_streaming_is_exact(lat, kernel):
     nx, ny, nv = 136, 12, 9
     rng = np.random.default_rng(3)
@@ -321,3 +321,19 @@ def test_step_moments_equal_step_then_moments(lat, kernel, nv):
     # sqrt(M E), which bounds the sum of |v| f by Cauchy-Schwarz
     np.testing.assert_allclose(g1[[0, 3]], g0[[0, 3]], rtol=1e-12)
     np.testing.assert_allclose(g1[1:3], g0[1:3], rtol=0, atol=1e-12 * math.sqrt(g0[0] * g0[3]))
+
+
+@pytest.mark.parametrize("nv", [9, 13, 17, 19, 21, 33])
+def test_packed_sweep_gives_the_scalar_bits(lat, nv):
+    """Launch kernels 8..10 (a velocity row as two half-rows in f32x2 register pairs) write the
+    bits of the scalar sweep (plain loads, kernel 1; producer/consumer, kernel 5), on a flowing
+    random state with ragged tiles, and stay within the FP32 tolerance of the oracle."""
+    c = make2d(136, 20, nv, 1.0, 2e-3, 12, 40 + nv)
+    plain, lt1 = gpu2d(lat, c, torch.float32, kernel=1)
+    lt1.close()
+    for k in (5, 8, 9, 10):
+        got, lt = gpu2d(lat, c, torch.float32, kernel=k)
+        assert np.array_equal(got, plain), (k, np.abs(got - plain).max())
+        lt.close()
+    want = oracle2d(c)
+    assert rel_l1(plain, want) <= 1e-5
