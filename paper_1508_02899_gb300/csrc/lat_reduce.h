@@ -3,6 +3,8 @@
 
 #include <cuda_runtime.h>
 
+#include "f32x2.h"
+
 namespace lat {
 namespace cs {
 
@@ -101,6 +103,51 @@ struct ColumnSums {
         s0 = Comp{(double)a0.s, -(double)a0.c};
         s1 = Comp{__dmul_rn((double)b1, dv), 0.0};
         s2 = Comp{__dmul_rn((double)b2, dv2), 0.0};
+    }
+};
+
+// The column sums of ColumnSums over two half-columns at once, one per f32x2 lane (the packed
+// 1D sweep's lanes): lane 0 takes the column's values 0 .. h - 1 and lane 1 the values h .. 2h,
+// each in ascending order; collapse() merges lane 1 into lane 0 (FComp merge for the mass, one
+// addition for each weighted sum).  Every FP32 column reduction of the library that must give
+// the bits of another uses this order.
+struct ColumnSums2 {
+    f2 s = 0ull, c = 0ull, b1 = 0ull, b2 = 0ull;
+    // v: the two lanes' values; j, jsq: their velocity indices and squares (exact)
+    __device__ __forceinline__ void add(f2 j, f2 jsq, f2 v) {
+        const f2 t = add2(s, v);
+        const f2 bb = sub2(t, s);
+        const f2 e = add2(sub2(s, sub2(t, bb)), sub2(v, bb));
+        s = t;
+        c = sub2(c, e);
+        b1 = fma2(j, v, b1);
+        b2 = fma2(jsq, v, b2);
+    }
+    // lane 0 alone
+    __device__ __forceinline__ void add_lo(float j, float v) {
+        FComp a{lo(s), lo(c)};
+        a.add_exact(v);
+        s = pk(a.s, hi(s));
+        c = pk(a.c, hi(c));
+        b1 = pk(__fmaf_rn(j, v, lo(b1)), hi(b1));
+        b2 = pk(__fmaf_rn(__fmul_rn(j, j), v, lo(b2)), hi(b2));
+    }
+    // lane 1 alone
+    __device__ __forceinline__ void add_hi(float j, float v) {
+        FComp a{hi(s), hi(c)};
+        a.add_exact(v);
+        s = pk(lo(s), a.s);
+        c = pk(lo(c), a.c);
+        b1 = pk(lo(b1), __fmaf_rn(j, v, hi(b1)));
+        b2 = pk(lo(b2), __fmaf_rn(__fmul_rn(j, j), v, hi(b2)));
+    }
+    __device__ __forceinline__ ColumnSums collapse() const {
+        ColumnSums r;
+        r.a0 = FComp{lo(s), lo(c)};
+        r.a0.merge(FComp{hi(s), hi(c)});
+        r.b1 = __fadd_rn(lo(b1), hi(b1));
+        r.b2 = __fadd_rn(lo(b2), hi(b2));
+        return r;
     }
 };
 

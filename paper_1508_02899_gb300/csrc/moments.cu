@@ -64,12 +64,28 @@ __global__ void __launch_bounds__(1024) k_moments1d(const Mom1DArgs a, const int
             }
         } else {
             ColumnSums sums;
-            if (on) {
+            if (on && nv >= 5) {
+                // two half-columns, as the fused step epilogue sums them (ColumnSums2)
+                ColumnSums2 s2;
+                for (int p = 1; p <= J; ++p) {
+                    const float f0 = (float)f[(size_t)(p - 1) * in.nx + x];
+                    const float f1 = (float)f[(size_t)(p - 1 + J) * in.nx + x];
+                    bad |= !isfinite(f0) || !isfinite(f1);
+                    const f2 jv = pk((float)(p - 1 - J), (float)(p - 1));
+                    s2.add(jv, mul2(jv, jv), pk(f0, f1));
+                }
+                const float fl = (float)f[(size_t)(nv - 1) * in.nx + x];
+                bad |= !isfinite(fl);
+                s2.add_hi((float)J, fl);
+                sums = s2.collapse();
+            } else if (on) {
                 for (int jj = 0; jj < nv; ++jj) {
                     const float fv = (float)f[(size_t)jj * in.nx + x];
                     bad |= !isfinite(fv);
                     sums.add((float)(jj - J), fv);
                 }
+            }
+            if (on) {
                 if (a.rho || a.mean_v || a.mean_v2) {  // FP64 per cell only when asked for
                     Comp s0, s1, s2;
                     sums.result(in.dv, s0, s1, s2);
@@ -126,7 +142,18 @@ __global__ void __launch_bounds__(kNoAllocTile)
     Comp t0{0, 0}, t1{0, 0}, t2{0, 0};
     if (x < nx) {
         ColumnSums sums;
-        for (int jj = 0; jj < nv; ++jj) sums.add((float)(jj - J), f[(size_t)jj * nx + x]);
+        if (nv >= 5) {  // the two half-columns of lat_moments (ColumnSums2 order)
+            ColumnSums2 s2;
+            for (int p = 1; p <= J; ++p) {
+                const f2 jv = pk((float)(p - 1 - J), (float)(p - 1));
+                s2.add(jv, mul2(jv, jv),
+                       pk(f[(size_t)(p - 1) * nx + x], f[(size_t)(p - 1 + J) * nx + x]));
+            }
+            s2.add_hi((float)J, f[(size_t)(nv - 1) * nx + x]);
+            sums = s2.collapse();
+        } else {
+            for (int jj = 0; jj < nv; ++jj) sums.add((float)(jj - J), f[(size_t)jj * nx + x]);
+        }
         sums.result(dv, t0, t1, t2);
     }
     for (int off = 16; off > 0; off >>= 1) {

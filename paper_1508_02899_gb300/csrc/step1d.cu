@@ -22,6 +22,7 @@
 
 #include <algorithm>
 
+#include "f32x2.h"
 #include "lat_internal.h"
 #include "lat_reduce.h"
 
@@ -86,6 +87,54 @@ __device__ __forceinline__ void sweep_column(T w, T g, T r, const Get& get, cons
         s = sn;
     }
     put(NV - 1, Ops<T>::add(dprev, Ops<T>::sub(T(0), Dprev)));
+}
+
+// Packed two-lane form of sweep_column (FP32, N_v = 2h + 1 >= 5): lane 0 of an f32x2 pair
+// sweeps cells 0 .. h, lane 1 cells h .. 2h, with exactly the operations of sweep_column in the
+// same order, so the outputs have the same bits.  Lane 1 starts from the drag fluxes of faces
+// h - 3/2 and h - 1/2 and the drag output of cell h - 1, which it computes from f*_{h-2..h}
+// first.  put2(p, o) for p = 1..h stores lane 0's o at cell p - 1 and lane 1's at p - 1 + h;
+// put_last(v) stores cell 2h.
+template <int NV, class Get, class Put2, class PutLast>
+__device__ __forceinline__ void sweep_column2(float w, float g, float r, const Get& get,
+                                              const Put2& put2, const PutLast& put_last) {
+    constexpr int J = (NV - 1) / 2, h = J;
+    static_assert(NV >= 5, "packed sweep needs N_v >= 5");
+    const f2 g2 = pk(g, g), w2 = pk(w, w), r2 = pk(r, r);
+    const f2 one2 = opaque2(pk(1.f, 1.f));
+    f2 kk = opaque2(pk(float(-J), 0.f));  // velocity indices of step p: (p - J, p)
+    f2 cac = mul2(g2, sub2(w2, kk));
+    // lane 1's entry state at cell h
+    const float fm2 = get(h - 2), fm1 = get(h - 1), f0 = get(h);
+    const float Fa = dflux<float>(cacc<float>(g, w, -2), cacc<float>(g, w, -1), fm2, fm1);
+    const float Fb = dflux<float>(cacc<float>(g, w, -1), cacc<float>(g, w, 0), fm1, f0);
+    const float dm1 = Ops<float>::sub(fm1, Ops<float>::sub(Fb, Fa));
+    f2 s2 = pk(get(0), f0);
+    f2 Fp = pk(0.f, Fb);
+    f2 dp = pk(0.f, dm1);
+    f2 Dp = 0ull;
+#pragma unroll
+    for (int p = 0; p <= h; ++p) {
+        const f2 kn = add2(kk, one2);
+        const f2 can = mul2(g2, sub2(w2, kn));
+        const f2 sn = p < h ? pk(get(p + 1), get(p + 1 + h)) : pk(get(h + 1), 0.f);
+        f2 Fn = fma2(max0(cac), s2, mul2(min0(can), sn));
+        if (p == h) Fn = pk(lo(Fn), 0.f);  // lane 1 reached the wall
+        const f2 d = sub2(s2, sub2(Fn, Fp));
+        Fp = Fn;
+        const f2 D = mul2(r2, sub2(d, dp));
+        if (p == 0) {
+            Dp = pk(0.f, hi(D));  // lane 0 has no face below cell 0; lane 1: face h - 1/2
+        } else {
+            put2(p, add2(dp, sub2s(D, Dp)));
+            Dp = D;
+        }
+        dp = d;
+        s2 = sn;
+        cac = can;
+        kk = kn;
+    }
+    put_last(Ops<float>::add(hi(dp), Ops<float>::sub(0.f, hi(Dp))));
 }
 
 // ---- flux-limited drag (scheme KOREN) -----------------------------------------------------------
@@ -214,10 +263,13 @@ __device__ __forceinline__ const double* amp_ptr<double>(const Step1DArgs& a, in
 
 // u(x_i, t_n) = sum_m A_m cos(2 pi k_m i / N_x) + B_m sin(2 pi k_m i / N_x); the phase is
 // reduced in integers (k_m i mod N_x) and evaluated as sin/cos of pi * (2 (k_m i mod N_x)/N_x).
+// Explicit rounding, so that every kernel variant gets the same bits whatever the compiler
+// contracts around it.
 template <typename T>
 __device__ __forceinline__ T flow_at(const Step1DArgs& a, const Inst1D& in, const T* amp, int x) {
     if (a.flow_kind == LAT_FLOW_FIELD) return static_cast<const T*>(a.field)[in.xoff + x];
     if (a.flow_kind != LAT_FLOW_MODES) return T(0);
+    using O = Ops<T>;
     const int M = a.nmodes;
     const T two_over_nx = T(in.two_over_nx);
     T u = T(0);
@@ -226,8 +278,8 @@ __device__ __forceinline__ T flow_at(const Step1DArgs& a, const Inst1D& in, cons
         kx = in.pow2 ? (kx & (in.nx - 1)) : (kx % in.nx);
         if (kx < 0) kx += in.nx;
         T s, c;
-        sincospi_t(T(kx) * two_over_nx, &s, &c);
-        u += __ldg(amp + m) * c + __ldg(amp + M + m) * s;
+        sincospi_t(O::mul(T(kx), two_over_nx), &s, &c);
+        u = O::add(u, O::fma(__ldg(amp + m), c, O::mul(__ldg(amp + M + m), s)));
     }
     return u;
 }
@@ -566,13 +618,39 @@ __global__ void __launch_bounds__(PC1_THREADS) k_step1d_pc(const Step1DArgs a, c
             const float* col = ring + (size_t)(k % NS) * NV * WIN1 + tid;
             float* dst = fout + in.off + x;
             const int nx = in.nx;
-            sweep_scheme<float, NV, LIM>(
-                a, w, g, r,
-                [&](int jj) { return col[jj * WIN1 + ((J - jj) % 4 + 4) % 4]; },
-                [&](int jj, float v) {
+            auto get = [&](int jj) { return col[jj * WIN1 + ((J - jj) % 4 + 4) % 4]; };
+            if constexpr (!LIM && NV >= 5) {
+                // packed two-lane sweep; the moments in ColumnSums2 order (lane 0: cells
+                // 0 .. J - 1, lane 1: J .. 2J), the order of the moment kernel
+                cs::ColumnSums2 s2;
+                const f2 one2 = pk(1.f, 1.f);
+                f2 jv = pk(float(-J), 0.f);
+                sweep_column2<NV>(
+                    w, g, r, get,
+                    [&](int p, f2 o) {
+                        dst[(size_t)(p - 1) * nx] = lo(o);
+                        dst[(size_t)(p - 1 + J) * nx] = hi(o);
+                        if constexpr (MOM) {
+                            s2.add(jv, mul2(jv, jv), o);
+                            jv = add2(jv, one2);
+                        }
+                    },
+                    [&](float v) {
+                        dst[(size_t)(NV - 1) * nx] = v;
+                        if constexpr (MOM) s2.add_hi(float(J), v);
+                    });
+                if constexpr (MOM) sums = s2.collapse();
+            } else {
+                cs::ColumnSums2 s2;
+                sweep_scheme<float, NV, LIM>(a, w, g, r, get, [&](int jj, float v) {
                     dst[(size_t)jj * nx] = v;
-                    if constexpr (MOM) sums.add((float)(jj - J), v);
+                    if constexpr (MOM) {
+                        if (jj < J) s2.add_lo((float)(jj - J), v);
+                        else s2.add_hi((float)(jj - J), v);
+                    }
                 });
+                if constexpr (MOM) sums = s2.collapse();
+            }
             cfl_flag<float, J, LIM>(a, g, w);
         }
         __syncwarp();
@@ -750,7 +828,10 @@ int step1d_ring_occupancy(int nv, int slots, int variant) {
     }
 }
 
-bool step1d_moments_supported(int dtype, int nv) { return step1d_ring_supported(dtype, nv); }
+// the fused epilogue reduces in the two-lane order of ColumnSums2 (N_v >= 5)
+bool step1d_moments_supported(int dtype, int nv) {
+    return nv >= 5 && step1d_ring_supported(dtype, nv);
+}
 
 cudaError_t launch_step1d_moments(int nv, int grid, const Step1DArgs& a, cudaStream_t s) {
     if (grid <= 0) return cudaSuccess;

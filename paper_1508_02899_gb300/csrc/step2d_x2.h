@@ -12,54 +12,11 @@
 // are formed from the other lane's values read at the start of the row.
 #pragma once
 
+#include "f32x2.h"
 #include "step2d_dev.h"
 
 namespace lat {
 namespace k2d {
-
-typedef unsigned long long f2;  // lane 0 in the low word
-
-__device__ __forceinline__ f2 pk(float a, float b) {
-    f2 r;
-    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
-    return r;
-}
-__device__ __forceinline__ float lo(f2 v) {
-    float a, b;
-    asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(v));
-    return a;
-}
-__device__ __forceinline__ float hi(f2 v) {
-    float a, b;
-    asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(v));
-    return b;
-}
-__device__ __forceinline__ f2 add2(f2 a, f2 b) {
-    f2 r;
-    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
-    return r;
-}
-__device__ __forceinline__ f2 sub2(f2 a, f2 b) {
-    f2 r;
-    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
-    return r;
-}
-__device__ __forceinline__ f2 mul2(f2 a, f2 b) {
-    f2 r;
-    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
-    return r;
-}
-__device__ __forceinline__ f2 fma2(f2 a, f2 b, f2 c) {
-    f2 r;
-    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(a), "l"(b), "l"(c));
-    return r;
-}
-__device__ __forceinline__ f2 max0(f2 v) { return pk(fmaxf(lo(v), 0.f), fmaxf(hi(v), 0.f)); }
-__device__ __forceinline__ f2 min0(f2 v) { return pk(fminf(lo(v), 0.f), fminf(hi(v), 0.f)); }
-__device__ __forceinline__ f2 opaque2(f2 v) {
-    asm volatile("mov.b64 %0, %0;" : "+l"(v));
-    return v;
-}
 
 template <int NV>
 struct Pairs {
