@@ -109,6 +109,10 @@ def parse_profile(txt: str) -> dict:
 # The ncu summary each timed workload takes its DRAM traffic from, and the source files its
 # dominant kernel is compiled from (the summary's hash covers them, in this order).
 _CSRC = "paper_1508_02899_gb300/csrc/"
+# the learned closure's trained parameters (python -m paper_1508_02899_gb300.train, recipe inside)
+CLOSURE_PARAMS = os.path.join(ROOT, "paper_1508_02899_gb300", "closure_params.npz")
+EVAL_FINE_STEPS = (100, 400)
+
 KERNEL_PROFILES = {
     "ensemble": ("step1d_ensemble_fp32_nv65.md", (_CSRC + "step1d.cu",)),
     "ensemble_koren": ("step1d_ensemble_koren_fp32_nv65.md", (_CSRC + "step1d.cu",)),
@@ -399,7 +403,7 @@ def build_learned(args, I, lat, torch, dev, rank, nsteps, n=2048):
     lt = lat.Lattice(f0, d=2, nx=n, ny=n, nv=nv, L=L, tau_p=tau_p, kappa=kappa, dt=dt)
     lt.set_flow_modes_2d(fl.kvec, fl.a, fl.phi0, fl.tau_f)
     lt.set_noise(fl.noise)
-    lt.learn(T.init_params(SEED + 17, scale=0.5), 2)
+    lt.learn(T.load_params(CLOSURE_PARAMS), 2)  # trained by train.py (recipe in the file)
     return lt, n * n * nv * nv, fl.noise[:1], np.zeros(4), WORKLOAD_LEARNED.format(n=n)
 
 
@@ -702,6 +706,18 @@ def main():
         forms["2d_learned_2048x2048_9x9"]["coarse_steps_per_fine_step"] = T.COARSE_PER_FINE
         lt.close()
         del lt
+        torch.cuda.empty_cache()
+        # the stated error: <|v|^2> and <rho_r^2> (r = 16 cells) of the plain 9^2 lattice and of
+        # the closure against the plain 33^2 lattice, frozen random-phase flow, same start
+        ev = T.evaluate(T.load_params(CLOSURE_PARAMS), 2048, 33, 1.0, 1e-3, flow_seed=505,
+                        init_seed=506, times=EVAL_FINE_STEPS, r=16, kmax=8, mode=2)
+        forms["2d_learned_2048x2048_9x9"]["error_vs_fine_33x33"] = {
+            "fine_steps": list(EVAL_FINE_STEPS), "r_cells": 16,
+            "flow": "frozen random-phase flow |k| <= 8 (seed 505), St = 1, kappa = 1e-3",
+            "plain_9x9": {"v2_rel": [e[0] for e in ev["plain"]],
+                          "rho_r2_rel": [e[1] for e in ev["plain"]]},
+            "learned_9x9": {"v2_rel": [e[0] for e in ev["learned"]],
+                            "rho_r2_rel": [e[1] for e in ev["learned"]]}}
         torch.cuda.empty_cache()
 
     cpu = None

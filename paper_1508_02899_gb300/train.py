@@ -70,11 +70,17 @@ def make_pair(nx: int, ny: int, nv_fine: int, st: float, kappa: float, flow_seed
     dx = L / nx
     dv_f = dx / dt_f
     J = (nv_fine - 1) // 2
-    f0 = I.gaussian_initial_2d(nx, ny, nv_fine, dx, dv_f, 0.3 * J * dv_f)
-    rng = np.random.default_rng(init_seed)
-    f0 = f0 * (1 + 0.5 * rng.random((1, 1, ny, nx)))
-    f0 = f0 / (f0.sum() * dx * dx * dv_f * dv_f)
-    ff = torch.tensor(f0, dtype=torch.float32, device=device)
+    # f0 = G(vx) G(vy) m(x, y) with unit mass, built on the device one velocity row at a time
+    v = np.arange(-J, J + 1, dtype=np.float64) * dv_f
+    g = np.exp(-0.5 * (v / (0.3 * J * dv_f)) ** 2)
+    col = np.outer(g, g)
+    m = 1 + 0.5 * np.random.default_rng(init_seed).random((ny, nx))
+    colt = torch.tensor(col / col.sum(), dtype=torch.float64, device=device)
+    mt = torch.tensor(m / (m.sum() * dx * dx * dv_f * dv_f), dtype=torch.float64, device=device)
+    ff = torch.empty((nv_fine, nv_fine, ny, nx), dtype=torch.float32, device=device)
+    for jy in range(nv_fine):
+        ff[jy] = (colt[jy][:, None, None] * mt[None]).float()
+    del mt
     fine = lat.Lattice(ff, d=2, nx=nx, ny=ny, nv=nv_fine, L=L, tau_p=tau_p, kappa=kappa, dt=dt_f)
     fc = lat.restrict(ff, nx, ny)
     nv_c = (nv_fine - 1) // 4 + 1
@@ -124,8 +130,111 @@ def train(pairs, trajectories, iters: int, lr: float = 1e-3, seed: int = 0, scal
 
 
 def observables(lt: lat.Lattice, dx: float, r: int):
-    """<|v|^2> = E / M and <rho_r^2> (mass in r x r boxes, mean square) of a lattice."""
-    code, rho, _, _, g = lt.moments()
-    rho = rho.cpu().numpy().reshape(lt.ny, lt.nx)
-    boxes = rho.reshape(lt.ny // r, r, lt.nx // r, r).sum(axis=(1, 3)) * dx * dx
-    return g[3] / g[0], float(np.mean(boxes * boxes)), code
+    """<|v|^2> = E / M (lat_moments) and <rho_r^2> of Eq. (def_coarse) for windows of r x r cells,
+    averaged over every position (lat_coarse_moment); dx is unused (kept for callers)."""
+    code, _, _, _, g = lt.moments(per_cell=False)
+    rho2 = float(lt.coarse_moment([r])[0, 0])
+    return g[3] / g[0], rho2, code
+
+
+def evaluate(params, n: int, nv_fine: int, st: float, kappa: float, flow_seed: int,
+             init_seed: int, times, r: int, kmax: int = 4, mode: int = 2):
+    """Relative errors of <|v|^2> and <rho_r^2> of the plain coarse lattice and of the coarse
+    lattice with the closure (network mode `mode`) against the fine lattice, in one frozen flow,
+    at the fine steps `times`.  Returns {"plain": [(ev, er), ...], "learned": [...]}."""
+    base = make_pair(n, n, nv_fine, st, kappa, flow_seed=flow_seed, init_seed=init_seed,
+                     kmax=kmax)
+    learned = make_pair(n, n, nv_fine, st, kappa, flow_seed=flow_seed, init_seed=init_seed,
+                        kmax=kmax)
+    learned.fine.close()
+    learned.coarse.learn(params, mode)
+    base.fine.set_launch(kernel=0)
+    base.fine.autotune(reps=2)
+    out = {"plain": [], "learned": []}
+    done = 0
+    for k in sorted(times):
+        base.fine.step(k - done)
+        base.coarse.step(COARSE_PER_FINE * (k - done))
+        learned.coarse.step(COARSE_PER_FINE * (k - done))
+        done = k
+        vf, rf, cf = observables(base.fine, base.dx, r)
+        if cf != 0:
+            raise lat.LatError(cf, "fine lattice")
+        for name, lt in (("plain", base.coarse), ("learned", learned.coarse)):
+            v, rr, code = observables(lt, base.dx, r)
+            if code != 0:
+                raise lat.LatError(code, name)
+            out[name].append((abs(v - vf) / vf, abs(rr - rf) / rf))
+    for lt in (base.fine, base.coarse, learned.coarse):
+        lt.close()
+    return out
+
+
+def save_params(path: str, params: np.ndarray, **recipe):
+    np.savez(path, params=np.asarray(params, dtype=np.float32),
+             recipe=np.array(repr(sorted(recipe.items()))))
+
+
+def load_params(path: str) -> np.ndarray:
+    with np.load(path) as z:
+        p = np.asarray(z["params"], dtype=np.float32)
+    if p.size != lat.LEARN_NPARAM:
+        raise ValueError(f"{path}: {p.size} parameters, expected {lat.LEARN_NPARAM}")
+    return p
+
+
+def main(argv=None):
+    """Train the closure on GPU fine runs and write its parameters (np.savez); optionally
+    evaluate them.  Pairs of every listed grid size and flow seed (frozen random-phase flows,
+    N_v 33 -> 9, St = 1, kappa = 1e-3) supply restricted fine trajectories; each Adam iteration
+    takes one pair and one start at random."""
+    import argparse
+    import json
+    import time
+    ap = argparse.ArgumentParser(description=main.__doc__)
+    ap.add_argument("--sizes", default="128,256")
+    ap.add_argument("--seeds", default="101,102")
+    ap.add_argument("--iters", type=int, default=400)
+    ap.add_argument("--kmax", type=int, default=8)
+    ap.add_argument("--fine-steps", type=int, default=4)
+    ap.add_argument("--traj", type=int, default=40)
+    ap.add_argument("--lr", type=float, default=1e-3)
+    ap.add_argument("--rho-weight", type=float, default=0.3)
+    ap.add_argument("--out", required=True)
+    ap.add_argument("--eval", default="",
+                    help="evaluations n:times:r[;...] after training, e.g. 2048:100,400:16")
+    a = ap.parse_args(argv)
+    sizes = [int(v) for v in a.sizes.split(",")]
+    seeds = [int(v) for v in a.seeds.split(",")]
+    t0 = time.time()
+    pairs = [make_pair(n, n, 33, 1.0, 1e-3, flow_seed=s + n, init_seed=s + n + 7, kmax=a.kmax)
+             for n in sizes for s in seeds]
+    trajs = [restricted_trajectory(p, a.traj) for p in pairs]
+    for p in pairs:
+        p.fine.close()
+
+    def log(it, loss):
+        if it % 50 == 0:
+            print(f"iter {it} loss {loss:.4e} ({time.time() - t0:.0f} s)", flush=True)
+
+    params = train(pairs, trajs, a.iters, lr=a.lr, seed=1, fine_steps=a.fine_steps,
+                   rho_weight=a.rho_weight, log=log)
+    save_params(a.out, params, sizes=sizes, seeds=seeds, iters=a.iters, kmax=a.kmax,
+                fine_steps=a.fine_steps, traj=a.traj, lr=a.lr, rho_weight=a.rho_weight)
+    print(f"wrote {a.out} after {time.time() - t0:.0f} s", flush=True)
+    for p in pairs:
+        p.coarse.close()
+    del pairs, trajs
+    torch.cuda.empty_cache()
+    for spec in filter(None, a.eval.split(";")):
+        n, times, r = spec.split(":")
+        times = [int(v) for v in times.split(",")]
+        e = evaluate(params, int(n), 33, 1.0, 1e-3, flow_seed=505, init_seed=506, times=times,
+                     r=int(r), kmax=a.kmax, mode=2)
+        print(json.dumps({"n": int(n), "r_cells": int(r), "fine_steps": times,
+                          "plain": e["plain"], "learned": e["learned"]}), flush=True)
+        torch.cuda.empty_cache()
+
+
+if __name__ == "__main__":
+    main()

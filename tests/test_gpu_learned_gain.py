@@ -6,9 +6,9 @@ Set-up (reading R-L1..R-L5 of the closure): 32 x 32 grid, St = 1, kappa = 1e-3, 
 flows, Gaussian velocity start (sigma = 0.3 V_max) with a seeded spatial modulation.  Training data:
 three flows (seeds 101..103), 60 fine steps each, restricted to the coarse lattice; Adam on the
 loss of 32 coarse steps (8 fine steps) with a density term (rho_weight 0.3).  Held out: flows 202
-and 303.  Errors: relative errors of <|v|^2> and <rho_r^2> (r = 4 cells) against the fine run,
-averaged over fine steps 30, 60, 90 and 120; both must fall below those of the plain coarse
-lattice, for the FP32 network and for the BF16 tensor-core network.
+and 303.  Errors: relative errors of <|v|^2> and <rho_r^2> (r = 4 cells, lat_coarse_moment) against the
+fine run, averaged over fine steps 30, 60, 90 and 120; both must fall below 0.85 times those of
+the plain coarse lattice, for the FP32 network and for the BF16 tensor-core network.
 """
 import numpy as np
 import pytest
@@ -58,5 +58,7 @@ def test_learned_closure_beats_the_plain_coarse_lattice(lat, trained, seed, mode
     print(f"\n[seed {seed} mode {mode}] <|v|^2> err plain {e['plain'][0]:.3e} learned "
           f"{e['learned'][0]:.3e}; <rho_r^2> err plain {e['plain'][1]:.3e} learned "
           f"{e['learned'][1]:.3e}", end="")
-    assert e["learned"][0] < e["plain"][0]
-    assert e["learned"][1] < e["plain"][1]
+    # measured: the closure cuts the <|v|^2> error by about a third and the <rho_r^2> error
+    # by about half on both held-out flows; asserted with a margin
+    assert e["learned"][0] < 0.85 * e["plain"][0]
+    assert e["learned"][1] < 0.85 * e["plain"][1]
