@@ -114,9 +114,11 @@ CLOSURE_PARAMS = os.path.join(ROOT, "paper_1508_02899_gb300", "closure_params.np
 EVAL_FINE_STEPS = (100, 400)
 
 KERNEL_PROFILES = {
-    "ensemble": ("step1d_ensemble_fp32_nv65.md", (_CSRC + "step1d.cu",)),
-    "ensemble_koren": ("step1d_ensemble_koren_fp32_nv65.md", (_CSRC + "step1d.cu",)),
-    "2d": ("step2d_512_fp32_nv33.md", (_CSRC + "step2d.cu", _CSRC + "step2d_dev.h")),
+    "ensemble": ("step1d_ensemble_fp32_nv65.md", (_CSRC + "step1d.cu", _CSRC + "f32x2.h")),
+    "ensemble_koren": ("step1d_ensemble_koren_fp32_nv65.md",
+                       (_CSRC + "step1d.cu", _CSRC + "f32x2.h")),
+    "2d": ("step2d_512_fp32_nv33.md", (_CSRC + "step2d.cu", _CSRC + "step2d_dev.h",
+                                       _CSRC + "step2d_x2.h", _CSRC + "f32x2.h")),
     "2d_f16": ("step2d_1024_f16_nv33.md", (_CSRC + "step2d_h.cu", _CSRC + "step2d_dev.h")),
     "2d_bf16": ("step2d_1024_bf16_nv33.md", (_CSRC + "step2d_h.cu", _CSRC + "step2d_dev.h")),
     "2d_learned": ("learn_tc_2048_nv9.md", (_CSRC + "learn_tc.cu",)),
