@@ -216,7 +216,9 @@ int lat_learn(lat_ctx* c, const float* params, int mode);
  * streamed density of the previous call and runs the network alone (same state and step).
  * Asynchronous; LAT_EINVAL without lat_learn. */
 int lat_learn_corrections(lat_ctx* c, float* G, int reuse_inputs);
-/* Training loss after nsteps learned steps (FP32 network) from the current state against the
+/* Training loss after nsteps learned steps (the network of the lat_learn mode: FP32 on CUDA cores,
+ * or BF16 on the tensor cores, whose backward and weight-gradient sums then run as tcgen05 MMAs
+ * as well) from the current state against the
  * DEVICE array target (layout of f):
  *     loss = mean over all values of (f - target)^2 + rho_weight * mean over the spatial cells
  *            of (sum_j (f - target))^2,

@@ -95,6 +95,10 @@ struct LearnBwdArgs {
 cudaError_t launch_diffuse_adjoint(int nv, const float* lam, float* out, float r, int nx, int ny,
                                    cudaStream_t s);
 cudaError_t launch_mlp_bwd(int nv, const LearnBwdArgs& a, int sm_count, cudaStream_t s);
+// The same outputs for the BF16 network on the tensor cores (forward again, network backward and
+// the weight-gradient sums as tcgen05 MMAs), from the image launch_learn_tc_pack builds.
+cudaError_t launch_mlp_bwd_tc(int nv, const LearnBwdArgs& a, const void* wtc, int sm_count,
+                              cudaStream_t s);
 cudaError_t launch_gather_adjoint(int nv, const LearnBwdArgs& a, cudaStream_t s);
 // Fine 2D state (N_v = nvf, 4 k + 1) -> coarse state (N_v = (nvf - 1)/4 + 1), per velocity axis.
 cudaError_t launch_restrict(const float* fine, int nvf, int nx, int ny, float* coarse,

@@ -455,6 +455,394 @@ __global__ void k_pack(const float* P, unsigned char* img) {
     }
 }
 
+// ---- backward pass on the tensor cores ------------------------------------------------------
+// The gradient of a learned step with respect to the network's parameters, for the BF16
+// network: per tile of 128 phase cells the forward again (layers 1-3 as in k_mlp_tc, the ReLU
+// masks and activations kept), the adjoint of the corrected drag fluxes (CUDA cores, as in
+// learn.cu's k_mlp_bwd), then three more MMAs for the network's backward, each with M = 128
+// cells:
+//   dz2 = (dz3 W3^T) [h2 > 0]  (K = 16, N = 64),   dz1 = (dz2 W2^T) [h1 > 0]  (K = 64, N = 64),
+//   dX = dz1 W1^T  (K = 64, N = 16),
+// and three for the weight gradients, which sum over the tile's cells (K = 128 cells) into
+// accumulators that stay in tensor memory across all of a CTA's tiles:
+//   [dz2 | dz1]^T [h1 1 0]  -> rows 0..63: dW2^T with db2 in column 64   (M = 128, N = 80),
+//   [dz2 | dz1]^T X         -> rows 64..127: dW1^T, db1 = column 15      (M = 128, N = 16),
+//   [h2 1 0]^T dz3          -> rows 0..63: dW3, row 64: db3               (M = 128, N = 16).
+// The weight-gradient operands are the tile's values transposed (rows = features, K = cells):
+// every thread scatters its cell's BF16 values into column `cell` of those K-major tiles.
+// Backward B operands, packed from the FP32 parameters after the forward image:
+//   B4 [n = i][k = o] = W3[i][o] (o < 2),  B5 [n = i][k = j] = W2[i][j],  B6 [n = q][k = i] = W1[q][i].
+constexpr int kB4 = kImage;                   // N 64 x K 16 (2 KB)
+constexpr int kB5 = kB4 + 64 * 16 * 2;        // N 64 x K 64 (8 KB)
+constexpr int kB6 = kB5 + 64 * 64 * 2;        // N 16 x K 64 (2 KB)
+constexpr int kImageAll = kB6 + 16 * 64 * 2;
+static_assert(kImageAll % 16 == 0, "image copied in 16-byte pieces");
+
+__global__ void k_pack_bwd(const float* P, unsigned char* img) {
+    const int n4 = 64 * 16, n5 = 64 * 64, n6 = 16 * 64;
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n4 + n5 + n6;
+         e += gridDim.x * blockDim.x) {
+        if (e < n4) {
+            const int i = e / 16, o = e % 16;
+            const float w = o < kLNO ? P[kOffW3 + i * kLNO + o] : 0.f;
+            *reinterpret_cast<__nv_bfloat16*>(img + kB4 + tile_off(i, o, 64)) = __float2bfloat16_rn(w);
+        } else if (e < n4 + n5) {
+            const int q = e - n4, i = q / 64, j = q % 64;
+            *reinterpret_cast<__nv_bfloat16*>(img + kB5 + tile_off(i, j, 64)) =
+                __float2bfloat16_rn(P[kOffW2 + i * kLNH + j]);
+        } else {
+            const int q = e - n4 - n5, qq = q / 64, i = q % 64;
+            *reinterpret_cast<__nv_bfloat16*>(img + kB6 + tile_off(qq, i, 16)) =
+                __float2bfloat16_rn(P[kOffW1 + qq * kLNH + i]);
+        }
+    }
+}
+
+// Shared memory of the backward kernel (byte offsets; every tile 1024-byte aligned).
+constexpr int kBW = 0;                                  // forward + backward images
+constexpr int kBA1 = (kImageAll + 1023) / 1024 * 1024;  // X        [128][16]
+constexpr int kBA2 = kBA1 + 128 * 16 * 2;               // [h1 1 0] [128][80]
+constexpr int kBA3 = kBA2 + 128 * kK2 * 2;              // [h2 1 0] [128][80]
+constexpr int kBZ3 = kBA3 + 128 * kK2 * 2;              // dz3      [128][16]
+constexpr int kBZ2 = kBZ3 + 128 * 16 * 2;               // dz2      [128][64]
+constexpr int kBZ1 = kBZ2 + 128 * 64 * 2;               // dz1      [128][64]
+constexpr int kTDZ = kBZ1 + 128 * 64 * 2;               // [dz2 | dz1]^T [128][128 cells]
+constexpr int kTH1 = kTDZ + 128 * 128 * 2;              // [h1 1 0]^T    [80][128]
+constexpr int kTX = kTH1 + 80 * 128 * 2;                // X^T           [16][128]
+constexpr int kTH2 = kTX + 16 * 128 * 2;                // [h2 1 0]^T    [128][128]
+constexpr int kTZ3 = kTH2 + 128 * 128 * 2;              // dz3^T         [16][128]
+constexpr int kBBar = kTZ3 + 16 * 128 * 2;
+constexpr int kBSmem = kBBar + 16;
+static_assert(kBSmem <= 227 * 1024, "backward kernel's shared memory");
+// tensor memory: per-tile accumulator, then the three weight-gradient accumulators
+constexpr int kBTmemCols = 256;
+constexpr int kTD = 0, kTW2 = 64, kTW1 = 144, kTW3 = 160;
+
+__device__ __forceinline__ void put_bf16(unsigned char* tile, unsigned off, float v) {
+    *reinterpret_cast<__nv_bfloat16*>(tile + off) = __float2bfloat16_rn(v);
+}
+__device__ __forceinline__ void put_bits(unsigned char* tile, unsigned off, unsigned short b) {
+    *reinterpret_cast<unsigned short*>(tile + off) = b;
+}
+
+// ReLU of 64 accumulator columns of this thread's row (cell r) into row r of A (as epilogue64)
+// and into column r of the transposed tile T (rows = features, `trows` rows); bit k of mask is
+// set where column k was positive.
+__device__ __forceinline__ void epilogue64_t(unsigned taddr, unsigned char* A, unsigned char* T,
+                                             int trows, int r, unsigned (&mask)[2]) {
+    mask[0] = mask[1] = 0u;
+#pragma unroll
+    for (int c0 = 0; c0 < 64; c0 += 32) {
+        unsigned v[2][16];
+        tmem_ld16(taddr + c0, v[0]);
+        tmem_ld16(taddr + c0 + 16, v[1]);
+        tmem_wait();
+#pragma unroll
+        for (int g = 0; g < 4; ++g) {
+            const unsigned* u = v[g >> 1] + 8 * (g & 1);
+            unsigned w[4];
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                const float a = __uint_as_float(u[2 * e]), b = __uint_as_float(u[2 * e + 1]);
+                w[e] = pack_relu_bf16(a, b);
+                const int col = c0 + 8 * g + 2 * e;
+                mask[col >> 5] |= (a > 0.f ? 1u : 0u) << (col & 31);
+                mask[col >> 5] |= (b > 0.f ? 1u : 0u) << ((col + 1) & 31);
+                put_bits(T, tile_off(col, r, trows), (unsigned short)(w[e] & 0xffffu));
+                put_bits(T, tile_off(col + 1, r, trows), (unsigned short)(w[e] >> 16));
+            }
+            *reinterpret_cast<uint4*>(A + tile_off(r, c0 + 8 * g, 128)) =
+                make_uint4(w[0], w[1], w[2], w[3]);
+        }
+    }
+}
+
+// The masked product of a backward MMA (64 accumulator columns of cell r) as BF16 into row r
+// of D and into rows row0 .. row0 + 63 of column r of the transposed tile T (128 rows).
+__device__ __forceinline__ void epilogue64_mask(unsigned taddr, const unsigned (&mask)[2],
+                                                bool on, unsigned char* D, unsigned char* T,
+                                                int row0, int r) {
+#pragma unroll
+    for (int c0 = 0; c0 < 64; c0 += 32) {
+        unsigned v[2][16];
+        tmem_ld16(taddr + c0, v[0]);
+        tmem_ld16(taddr + c0 + 16, v[1]);
+        tmem_wait();
+#pragma unroll
+        for (int g = 0; g < 4; ++g) {
+            const unsigned* u = v[g >> 1] + 8 * (g & 1);
+            unsigned w[4];
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                const int col = c0 + 8 * g + 2 * e;
+                const bool ma = on && ((mask[col >> 5] >> (col & 31)) & 1u);
+                const bool mb = on && ((mask[(col + 1) >> 5] >> ((col + 1) & 31)) & 1u);
+                w[e] = pack_bf16(ma ? __uint_as_float(u[2 * e]) : 0.f,
+                                 mb ? __uint_as_float(u[2 * e + 1]) : 0.f);
+                put_bits(T, tile_off(row0 + col, r, 128), (unsigned short)(w[e] & 0xffffu));
+                put_bits(T, tile_off(row0 + col + 1, r, 128), (unsigned short)(w[e] >> 16));
+            }
+            *reinterpret_cast<uint4*>(D + tile_off(r, c0 + 8 * g, 128)) =
+                make_uint4(w[0], w[1], w[2], w[3]);
+        }
+    }
+}
+
+// n MMAs over K = 16 n: D (+)= A B^T, A [128][16 n] and B [N][16 n] K-major tiles.
+__device__ __forceinline__ void mma_k(unsigned dt, unsigned a, unsigned a_lbo, unsigned b,
+                                      unsigned b_lbo, unsigned n_out, int nk, bool acc) {
+    for (int kk = 0; kk < nk; ++kk)
+        mma(dt, sdesc(a + kk * 2 * a_lbo, a_lbo, 128), sdesc(b + kk * 2 * b_lbo, b_lbo, 128),
+            idesc_n(n_out), (acc || kk > 0) ? 1 : 0);
+}
+
+// One CTA of 128 threads per SM (about 199 KB of shared memory) walks tiles of 128 phase cells
+// in storage order; thread t owns cell t of the tile.  Outputs as learn.cu's k_mlp_bwd: cxy,
+// lfs, dX9 per cell, lrho (atomic per spatial cell) and the parameter gradient (atomic, once per
+// CTA at the end).
+template <int NV>
+__global__ void __launch_bounds__(128, 1) k_mlp_bwd_tc(const LearnBwdArgs b,
+                                                      const unsigned char* image) {
+    extern __shared__ __align__(1024) unsigned char sm[];
+    const LearnArgs& a = b.fw;
+    unsigned char* W = sm + kBW;
+    unsigned char* A1 = sm + kBA1;
+    unsigned char* A2 = sm + kBA2;
+    unsigned char* A3 = sm + kBA3;
+    unsigned char* Z3 = sm + kBZ3;
+    unsigned char* Z2 = sm + kBZ2;
+    unsigned char* Z1 = sm + kBZ1;
+    unsigned char* TDZ = sm + kTDZ;
+    unsigned char* TH1 = sm + kTH1;
+    unsigned char* TX = sm + kTX;
+    unsigned char* TH2 = sm + kTH2;
+    unsigned char* TZ3 = sm + kTZ3;
+    uint64_t* bar = reinterpret_cast<uint64_t*>(sm + kBBar);
+    unsigned* tslot = reinterpret_cast<unsigned*>(sm + kBBar + 8);
+    const int t = threadIdx.x, warp = t >> 5;
+    for (int i = t; i < kImageAll / 16; i += blockDim.x)
+        reinterpret_cast<uint4*>(W)[i] = reinterpret_cast<const uint4*>(image)[i];
+    {   // constant parts of the operand tiles (never overwritten)
+        const uint4 one = make_uint4(pack_bf16(1.f, 0.f), 0u, 0u, 0u);
+        const uint4 zero = make_uint4(0u, 0u, 0u, 0u);
+        *reinterpret_cast<uint4*>(A2 + tile_off(t, 64, 128)) = one;
+        *reinterpret_cast<uint4*>(A2 + tile_off(t, 72, 128)) = zero;
+        *reinterpret_cast<uint4*>(A3 + tile_off(t, 64, 128)) = one;
+        *reinterpret_cast<uint4*>(A3 + tile_off(t, 72, 128)) = zero;
+        *reinterpret_cast<uint4*>(Z3 + tile_off(t, 8, 128)) = zero;
+        for (int rr = 64; rr < 80; ++rr) put_bf16(TH1, tile_off(rr, t, 80), rr == 64 ? 1.f : 0.f);
+        for (int rr = 64; rr < 128; ++rr) put_bf16(TH2, tile_off(rr, t, 128), rr == 64 ? 1.f : 0.f);
+        for (int rr = 2; rr < 16; ++rr) put_bf16(TZ3, tile_off(rr, t, 16), 0.f);
+    }
+    if (t == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(su32(bar)) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         su32(tslot)),
+                     "r"(kBTmemCols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const unsigned tmem = *tslot;
+    const unsigned trow = tmem + ((unsigned)(warp * 32) << 16);
+    const unsigned w = su32(W);
+    const float* f = a.f[0];
+    const long long ncell = (long long)a.nx * a.ny;
+    const long long n = ncell * NV * NV;
+    const long long ntiles = (n + 127) / 128;
+    unsigned phase = 0;
+    bool failed = false, first = true;
+    auto wait_mma = [&]() -> bool {
+        bool ok = true;
+        if (warp == 0) ok = wait_parity(bar, phase);
+        phase ^= 1;
+        const bool bad = __syncthreads_or(!ok);
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        return !bad;
+    };
+    auto sync_for_mma = [&]() {
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        __syncthreads();
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    };
+    for (long long tile = blockIdx.x; tile < ntiles && !failed; tile += gridDim.x) {
+        const long long i = tile * 128 + t;
+        const bool on = i < n;
+        int p = 0, x = 0, y = 0, jx = 0, jy = 0;
+        Raw r;
+        float X[kLNF];
+        if (on) {
+            split_index((unsigned)i, (unsigned)ncell, (unsigned)a.nx, p, x, y);
+            jy = p / NV;
+            jx = p % NV;
+            load_raw<NV>(a, f, jx, jy, x, y, r);
+            features_of<NV>(a, r, jx, jy, X);
+        } else {
+#pragma unroll
+            for (int q = 0; q < kLNF; ++q) X[q] = 0.f;
+        }
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            uint4 v;
+            v.x = pack_bf16(X[8 * h + 0], X[8 * h + 1]);
+            v.y = pack_bf16(X[8 * h + 2], X[8 * h + 3]);
+            v.z = pack_bf16(X[8 * h + 4], X[8 * h + 5]);
+            v.w = pack_bf16(X[8 * h + 6], X[8 * h + 7]);
+            *reinterpret_cast<uint4*>(A1 + tile_off(t, 8 * h, 128)) = v;
+        }
+#pragma unroll
+        for (int q = 0; q < kLNF; ++q) put_bf16(TX, tile_off(q, t, 16), X[q]);
+        // forward: layers 1-3, keeping the activations (rows and transposed) and ReLU masks
+        unsigned m1[2], m2[2];
+        sync_for_mma();
+        if (t == 0) {
+            mma_k(tmem + kTD, su32(A1), 2048, w + kW1T, 1024, 64, 1, false);
+            commit(bar);
+        }
+        if (!wait_mma()) { failed = true; break; }
+        epilogue64_t(trow + kTD, A2, TH1, 80, t, m1);
+        sync_for_mma();
+        if (t == 0) {
+            mma_k(tmem + kTD, su32(A2), 2048, w + kW2T, 1024, 64, kK2 / 16, false);
+            commit(bar);
+        }
+        if (!wait_mma()) { failed = true; break; }
+        epilogue64_t(trow + kTD, A3, TH2, 128, t, m2);
+        sync_for_mma();
+        if (t == 0) {
+            mma_k(tmem + kTD, su32(A3), 2048, w + kW3T, 256, 16, kK2 / 16, false);
+            commit(bar);
+        }
+        if (!wait_mma()) { failed = true; break; }
+        float z0, z1;
+        tmem_ld2(trow + kTD, z0, z1);
+        // adjoint of the corrected drag fluxes (learn.cu's k_mlp_bwd, same operations)
+        float dz30 = 0.f, dz31 = 0.f, lf = 0.f, inv = 0.f;
+        if (on) {
+            const float t0 = tanh_fast(z0), t1 = tanh_fast(z1);
+            const float b0 = z0 > 0.f ? anti_bound(X[13], a.g) : kYMax;
+            const float b1 = z1 > 0.f ? anti_bound(X[14], a.g) : kYMax;
+            const float y0 = __fmul_rn(b0, t0), y1 = __fmul_rn(b1, t1);
+            const float* L = b.lss;
+            const float l0 = L[i];
+            const float lxp = jx < NV - 1 ? __fsub_rn(L[i + ncell], l0) : 0.f;
+            const float lxm = jx > 0 ? __fsub_rn(l0, L[i - ncell]) : 0.f;
+            const float lyp = jy < NV - 1 ? __fsub_rn(L[i + NV * ncell], l0) : 0.f;
+            const float lym = jy > 0 ? __fsub_rn(l0, L[i - NV * ncell]) : 0.f;
+            const float cax = X[13], cay = X[14];
+            lf = l0;
+            lf = __fmaf_rn(fmaxf(cax, 0.f), lxp, lf);
+            lf = __fmaf_rn(fminf(cax, 0.f), lxm, lf);
+            lf = __fmaf_rn(fmaxf(cay, 0.f), lyp, lf);
+            lf = __fmaf_rn(fminf(cay, 0.f), lym, lf);
+            const float cx = __fmul_rn(y0, lxp), cy = __fmul_rn(y1, lyp);
+            lf = __fsub_rn(__fsub_rn(lf, cx), cy);
+            b.cxy[i] = cx;
+            b.cxy[n + i] = cy;
+            const float dy0 = __fmul_rn(lxp, __fsub_rn(r.fs[5], r.fs[4]));
+            const float dy1 = __fmul_rn(lyp, __fsub_rn(r.fs[7], r.fs[4]));
+            dz30 = __fmul_rn(dy0, __fmul_rn(b0, __fsub_rn(1.f, __fmul_rn(t0, t0))));
+            dz31 = __fmul_rn(dy1, __fmul_rn(b1, __fsub_rn(1.f, __fmul_rn(t1, t1))));
+            inv = r.fa.x;
+        }
+        *reinterpret_cast<uint4*>(Z3 + tile_off(t, 0, 128)) =
+            make_uint4(pack_bf16(dz30, dz31), 0u, 0u, 0u);
+        put_bf16(TZ3, tile_off(0, t, 16), dz30);
+        put_bf16(TZ3, tile_off(1, t, 16), dz31);
+        // network backward: dz2 = (dz3 W3^T)[h2 > 0], dz1 = (dz2 W2^T)[h1 > 0], dX = dz1 W1^T
+        sync_for_mma();
+        if (t == 0) {
+            mma_k(tmem + kTD, su32(Z3), 2048, w + kB4, 1024, 64, 1, false);
+            commit(bar);
+        }
+        if (!wait_mma()) { failed = true; break; }
+        epilogue64_mask(trow + kTD, m2, on, Z2, TDZ, 0, t);
+        sync_for_mma();
+        if (t == 0) {
+            mma_k(tmem + kTD, su32(Z2), 2048, w + kB5, 1024, 64, 4, false);
+            commit(bar);
+        }
+        if (!wait_mma()) { failed = true; break; }
+        epilogue64_mask(trow + kTD, m1, on, Z1, TDZ, 64, t);
+        sync_for_mma();
+        if (t == 0) {
+            mma_k(tmem + kTD, su32(Z1), 2048, w + kB6, 256, 16, 4, false);
+            // weight gradients, summed over the tile's cells into the CTA's accumulators
+            mma_k(tmem + kTW2, su32(TDZ), 2048, su32(TH1), 1280, 80, 8, !first);
+            mma_k(tmem + kTW1, su32(TDZ), 2048, su32(TX), 256, 16, 8, !first);
+            mma_k(tmem + kTW3, su32(TH2), 2048, su32(TZ3), 256, 16, 8, !first);
+            commit(bar);
+        }
+        if (!wait_mma()) { failed = true; break; }
+        first = false;
+        unsigned dx[16];
+        tmem_ld16(trow + kTD, dx);
+        tmem_wait();
+        if (on) {
+            float lr = 0.f;
+#pragma unroll
+            for (int q = 0; q < 9; ++q) {
+                const float d = __uint_as_float(dx[q]);
+                b.dX9[(size_t)q * n + i] = __fmul_rn(d, inv);
+                lr = __fsub_rn(lr, __fmul_rn(__fmul_rn(d, X[q]), inv));
+            }
+            b.lfs[i] = lf;
+            atomicAdd(&b.lrho[(long long)y * a.nx + x], lr);
+        }
+    }
+    if (!failed && !first) {
+        // rows 0..63 of the W2 accumulator: dW2^T[j][i] (i < 64) and db2[j] (i = 64)
+        if (t < 64) {
+#pragma unroll 1
+            for (int c0 = 0; c0 < 80; c0 += 16) {
+                unsigned v[16];
+                tmem_ld16(trow + kTW2 + c0, v);
+                tmem_wait();
+                for (int e = 0; e < 16; ++e) {
+                    const int col = c0 + e;
+                    const float g = __uint_as_float(v[e]);
+                    if (col < 64) atomicAdd(&b.grad[kOffW2 + col * kLNH + t], g);
+                    else if (col == 64) atomicAdd(&b.grad[kOffB2 + t], g);
+                }
+            }
+        } else {  // rows 64..127 of the W1 accumulator: dW1^T[i][q]; q = 15 meets the constant 1
+            unsigned v[16];
+            tmem_ld16(trow + kTW1, v);
+            tmem_wait();
+            const int ii = t - 64;
+            for (int q = 0; q < kLNF; ++q) {
+                const float g = __uint_as_float(v[q]);
+                atomicAdd(&b.grad[kOffW1 + q * kLNH + ii], g);
+                if (q == kLNF - 1) atomicAdd(&b.grad[kOffB1 + ii], g);
+            }
+        }
+        // rows 0..64 of the W3 accumulator: dW3[i][o], row 64 (the constant) db3[o]
+        float g0, g1;
+        tmem_ld2(trow + kTW3, g0, g1);
+        if (t < 64) {
+            atomicAdd(&b.grad[kOffW3 + t * kLNO], g0);
+            atomicAdd(&b.grad[kOffW3 + t * kLNO + 1], g1);
+        } else if (t == 64) {
+            atomicAdd(&b.grad[kOffB3], g0);
+            atomicAdd(&b.grad[kOffB3 + 1], g1);
+        }
+    }
+    if (failed && t == 0) atomicOr(const_cast<unsigned*>(&a.st->status), ST_TIMEOUT);
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                     "r"(kBTmemCols)
+                     : "memory");
+}
+
 }  // namespace
 
 #define LEARN_TC_NV_LIST(X) X(3) X(5) X(9) X(13) X(17)
@@ -469,11 +857,37 @@ bool learn_tc_supported(int nv) {
     }
 }
 
-size_t learn_tc_bytes() { return (size_t)kImage; }
+size_t learn_tc_bytes() { return (size_t)kImageAll; }
 
 cudaError_t launch_learn_tc_pack(const float* params, void* wtc, cudaStream_t s) {
     k_pack<<<24, 256, 0, s>>>(params, static_cast<unsigned char*>(wtc));
+    k_pack_bwd<<<24, 256, 0, s>>>(params, static_cast<unsigned char*>(wtc));
     return cudaGetLastError();
+}
+
+cudaError_t launch_mlp_bwd_tc(int nv, const LearnBwdArgs& b, const void* wtc, int sm_count,
+                              cudaStream_t s) {
+    const long long n = (long long)b.fw.nx * b.fw.ny * nv * nv;
+    const int grid = (int)std::max<long long>(1, std::min<long long>((n + 127) / 128, sm_count));
+    const unsigned char* img = static_cast<const unsigned char*>(wtc);
+    switch (nv) {
+#define X(nn)                                                                                   \
+    case nn: {                                                                                  \
+        static bool attr = false;                                                               \
+        if (!attr) {                                                                            \
+            cudaError_t e = cudaFuncSetAttribute(k_mlp_bwd_tc<nn>,                              \
+                                                 cudaFuncAttributeMaxDynamicSharedMemorySize,   \
+                                                 kBSmem);                                       \
+            if (e != cudaSuccess) return e;                                                     \
+            attr = true;                                                                        \
+        }                                                                                       \
+        k_mlp_bwd_tc<nn><<<grid, 128, kBSmem, s>>>(b, img);                                     \
+        return cudaGetLastError();                                                              \
+    }
+        LEARN_TC_NV_LIST(X)
+#undef X
+        default: return cudaErrorInvalidValue;
+    }
 }
 
 cudaError_t launch_mlp_tc(int nv, const LearnArgs& a, const void* wtc, int sm_count, int k,

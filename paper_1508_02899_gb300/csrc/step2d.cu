@@ -1919,8 +1919,10 @@ int ctx2d_learn_grad(Ctx2D* c, void* const f[2], int cur, int n, const float* ta
             LearnArgs la = learn_args(c, a.f[0], a.f[1], c->d_st0);
             la.u = U + (size_t)k * 2 * ncell;
             a.u = la.u;
+            // the network of the context's mode: FP32 on CUDA cores, or BF16 on tensor cores
             if (launch_rho_star(c->nv, la, 0, s) != cudaSuccess ||
-                launch_mlp_f32(c->nv, la, 0, s) != cudaSuccess ||
+                (c->learn == 2 ? launch_mlp_tc(c->nv, la, c->d_wtc, c->sm_count, 0, s)
+                               : launch_mlp_f32(c->nv, la, 0, s)) != cudaSuccess ||
                 launch_step2d_corr(c->nv, c->sm_count, a, c->d_G, 0, s) != cudaSuccess)
                 fail(LAT_ECUDA);
         }
@@ -1948,7 +1950,8 @@ int ctx2d_learn_grad(Ctx2D* c, void* const f[2], int cur, int n, const float* ta
             if (launch_diffuse_adjoint(c->nv, lamA, lss, (float)c->r, c->nx, c->ny, s) != cudaSuccess ||
                 cudaMemsetAsync(lrho, 0, sizeof(float) * ncell, s) != cudaSuccess ||
                 launch_rho_star(c->nv, b.fw, 0, s) != cudaSuccess ||
-                launch_mlp_bwd(c->nv, b, c->sm_count, s) != cudaSuccess ||
+                (c->learn == 2 ? launch_mlp_bwd_tc(c->nv, b, c->d_wtc, c->sm_count, s)
+                               : launch_mlp_bwd(c->nv, b, c->sm_count, s)) != cudaSuccess ||
                 launch_gather_adjoint(c->nv, b, s) != cudaSuccess)
                 fail(LAT_ECUDA);
             std::swap(lamA, lamB);

@@ -103,15 +103,17 @@ def restricted_trajectory(p: Pair, nsteps: int):
 
 
 def train(pairs, trajectories, iters: int, lr: float = 1e-3, seed: int = 0, scale: float = 0.1,
-          fine_steps: int = 1, rho_weight: float = 0.0, log=None) -> np.ndarray:
+          fine_steps: int = 1, rho_weight: float = 0.0, log=None, mode: int = 1) -> np.ndarray:
     """Adam on the loss of 4 * fine_steps coarse steps from a restricted state at a random fine
     step k of a random trajectory against the restricted state at k + fine_steps, normalised by
-    the target's mean square so that every sample weighs alike."""
+    the target's mean square so that every sample weighs alike.  mode: the network whose
+    gradient lat_learn_grad takes (1: FP32 on CUDA cores; 2: BF16 on the tensor cores, forward
+    and backward)."""
     params = init_params(seed, scale)
     opt = Adam(params.size, lr)
     rng = np.random.default_rng(seed)
     for p in pairs:
-        p.coarse.learn(params, 1)
+        p.coarse.learn(params, mode)
     for it in range(iters):
         q = int(rng.integers(0, len(pairs)))
         p, states = pairs[q], trajectories[q]
@@ -123,7 +125,7 @@ def train(pairs, trajectories, iters: int, lr: float = 1e-3, seed: int = 0, scal
         w = 1.0 / float((target.double() ** 2).mean())
         params = opt.step(params, g.astype(np.float64) * w)
         for pp in pairs:
-            pp.coarse.learn(params, 1)
+            pp.coarse.learn(params, mode)
         if log is not None:
             log(it, loss * w)
     return params
@@ -200,6 +202,7 @@ def main(argv=None):
     ap.add_argument("--traj", type=int, default=40)
     ap.add_argument("--lr", type=float, default=1e-3)
     ap.add_argument("--rho-weight", type=float, default=0.3)
+    ap.add_argument("--mode", type=int, default=1, help="1: FP32 network, 2: tensor cores")
     ap.add_argument("--out", required=True)
     ap.add_argument("--eval", default="",
                     help="evaluations n:times:r[;...] after training, e.g. 2048:100,400:16")
@@ -218,7 +221,7 @@ def main(argv=None):
             print(f"iter {it} loss {loss:.4e} ({time.time() - t0:.0f} s)", flush=True)
 
     params = train(pairs, trajs, a.iters, lr=a.lr, seed=1, fine_steps=a.fine_steps,
-                   rho_weight=a.rho_weight, log=log)
+                   rho_weight=a.rho_weight, log=log, mode=a.mode)
     save_params(a.out, params, sizes=sizes, seeds=seeds, iters=a.iters, kmax=a.kmax,
                 fine_steps=a.fine_steps, traj=a.traj, lr=a.lr, rho_weight=a.rho_weight)
     print(f"wrote {a.out} after {time.time() - t0:.0f} s", flush=True)
