@@ -235,6 +235,14 @@ int lat_learn_grad(lat_ctx* c, int nsteps, const float* target, double rho_weigh
  * DEVICE array of (m + 1)^2 ny nx floats.  Asynchronous on `stream`. */
 int lat_restrict(const float* fine, int nv_fine, int nx, int ny, float* coarse, void* stream);
 
+/* One Adam step (Kingma and Ba) of the learned closure's training, on DEVICE arrays of n floats
+ * (caller-owned): g = grad_scale * grad; m <- beta1 m + (1 - beta1) g; v <- beta2 v +
+ * (1 - beta2) g^2; params <- params - lr (m / (1 - beta1^t)) / (sqrt(v / (1 - beta2^t)) + eps),
+ * t >= 1 the step number.  FP32 arithmetic.  The paper has no counterpart (it trains nothing);
+ * the closure's training is this library's.  Asynchronous on `stream`. */
+int lat_adam(float* params, float* m, float* v, const float* grad, int n, int t, double lr,
+             double beta1, double beta2, double eps, double grad_scale, void* stream);
+
 /* Steps taken since init. */
 long long lat_steps_done(const lat_ctx* c);
 

@@ -82,6 +82,8 @@ def _load():
         "lat_get_state": (c_int, [P, P, c_longlong]),
         "lat_set_state": (c_int, [P, P, c_longlong]),
         "lat_debug_stall": (c_int, [P, c_int]),
+        "lat_adam": (c_int, [P, P, P, P, c_int, c_int, c_double, c_double, c_double, c_double,
+                             c_double, P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -422,6 +424,17 @@ class Ensemble(_Ctx):
 
 def exported_symbols():
     return [n for n in dir(_lib) if n.startswith("lat_")]
+
+
+def adam(params: torch.Tensor, m: torch.Tensor, v: torch.Tensor, grad: torch.Tensor, t: int,
+         lr: float, beta1: float = 0.9, beta2: float = 0.999, eps: float = 1e-8,
+         grad_scale: float = 1.0, stream=None):
+    """One Adam step on device float32 tensors of the same size (in place: params, m, v)."""
+    for x in (params, m, v, grad):
+        if x.dtype != torch.float32 or not x.is_cuda or not x.is_contiguous():
+            raise ValueError("adam takes contiguous CUDA float32 tensors")
+    _check(_lib.lat_adam(_ptr(params), _ptr(m), _ptr(v), _ptr(grad), params.numel(), int(t),
+                         lr, beta1, beta2, eps, grad_scale, _stream(stream)), "lat_adam")
 
 
 def restrict(fine: torch.Tensor, nx: int, ny: int, stream=None) -> torch.Tensor:

@@ -35,19 +35,25 @@ def init_params(seed: int, scale: float = 0.1) -> np.ndarray:
 
 
 class Adam:
-    def __init__(self, n: int, lr: float, b1: float = 0.9, b2: float = 0.999, eps: float = 1e-8):
-        self.m = np.zeros(n)
-        self.v = np.zeros(n)
+    """Adam with its moments and the parameters on the device; each step is lat_adam (the
+    gradient comes back from lat_learn_grad as host floats and goes up once)."""
+
+    def __init__(self, params: np.ndarray, lr: float, b1: float = 0.9, b2: float = 0.999,
+                 eps: float = 1e-8, device="cuda"):
+        self.p = torch.tensor(np.asarray(params, dtype=np.float32), device=device)
+        self.m = torch.zeros_like(self.p)
+        self.v = torch.zeros_like(self.p)
+        self.g = torch.zeros_like(self.p)
         self.t = 0
         self.lr, self.b1, self.b2, self.eps = lr, b1, b2, eps
 
-    def step(self, p: np.ndarray, g: np.ndarray) -> np.ndarray:
+    def step(self, g: np.ndarray, scale: float = 1.0) -> np.ndarray:
+        """Apply the gradient g (times scale); returns the new parameters (host float32)."""
         self.t += 1
-        self.m = self.b1 * self.m + (1 - self.b1) * g
-        self.v = self.b2 * self.v + (1 - self.b2) * g * g
-        mh = self.m / (1 - self.b1 ** self.t)
-        vh = self.v / (1 - self.b2 ** self.t)
-        return (p - self.lr * mh / (np.sqrt(vh) + self.eps)).astype(np.float32)
+        self.g.copy_(torch.from_numpy(np.asarray(g, dtype=np.float32)))
+        lat.adam(self.p, self.m, self.v, self.g, self.t, self.lr, self.b1, self.b2, self.eps,
+                 scale)
+        return self.p.cpu().numpy()
 
 
 @dataclass
@@ -110,7 +116,7 @@ def train(pairs, trajectories, iters: int, lr: float = 1e-3, seed: int = 0, scal
     gradient lat_learn_grad takes (1: FP32 on CUDA cores; 2: BF16 on the tensor cores, forward
     and backward)."""
     params = init_params(seed, scale)
-    opt = Adam(params.size, lr)
+    opt = Adam(params, lr)
     rng = np.random.default_rng(seed)
     for p in pairs:
         p.coarse.learn(params, mode)
@@ -123,7 +129,7 @@ def train(pairs, trajectories, iters: int, lr: float = 1e-3, seed: int = 0, scal
         target = states[k + fine_steps]
         loss, g = c.learn_grad(COARSE_PER_FINE * fine_steps, target, rho_weight)
         w = 1.0 / float((target.double() ** 2).mean())
-        params = opt.step(params, g.astype(np.float64) * w)
+        params = opt.step(g, w)
         for pp in pairs:
             pp.coarse.learn(params, mode)
         if log is not None:

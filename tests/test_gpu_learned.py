@@ -239,3 +239,28 @@ def test_corrections_match_oracle(lat, mode, tol, nx):
     assert np.linalg.norm(got - want) <= tol * np.linalg.norm(want), (
         np.linalg.norm(got - want) / np.linalg.norm(want))
     lt.close()
+
+
+def test_adam_kernel_matches_the_update_rule(lat):
+    """lat_adam against the Adam update written out in FP64 (Kingma and Ba), three steps."""
+    rng = np.random.default_rng(9)
+    n = 5378
+    p = rng.standard_normal(n).astype(np.float32)
+    pd = torch.tensor(p, device="cuda")
+    m = torch.zeros_like(pd)
+    v = torch.zeros_like(pd)
+    gd = torch.zeros_like(pd)
+    pr, mr, vr = p.astype(np.float64), np.zeros(n), np.zeros(n)
+    lr, b1, b2, eps, sc = 1e-3, 0.9, 0.999, 1e-8, 3.0
+    for t in (1, 2, 3):
+        g = (rng.standard_normal(n) * 1e-3).astype(np.float32)
+        gd.copy_(torch.tensor(g))
+        lat.adam(pd, m, v, gd, t, lr, b1, b2, eps, sc)
+        gg = g.astype(np.float64) * sc
+        mr = b1 * mr + (1 - b1) * gg
+        vr = b2 * vr + (1 - b2) * gg * gg
+        pr = pr - lr * (mr / (1 - b1 ** t)) / (np.sqrt(vr / (1 - b2 ** t)) + eps)
+    got = pd.cpu().numpy().astype(np.float64)
+    assert np.max(np.abs(got - pr)) <= 1e-6 * (np.abs(pr).max() + 1), np.max(np.abs(got - pr))
+    with pytest.raises(lat.LatError):
+        lat.adam(pd, m, v, gd, 0, lr)
