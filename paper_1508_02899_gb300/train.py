@@ -228,7 +228,7 @@ def main(argv=None):
 
     params = train(pairs, trajs, a.iters, lr=a.lr, seed=1, fine_steps=a.fine_steps,
                    rho_weight=a.rho_weight, log=log, mode=a.mode)
-    save_params(a.out, params, sizes=sizes, seeds=seeds, iters=a.iters, kmax=a.kmax,
+    save_params(a.out, params, sizes=sizes, seeds=seeds, iters=a.iters, kmax=a.kmax, mode=a.mode,
                 fine_steps=a.fine_steps, traj=a.traj, lr=a.lr, rho_weight=a.rho_weight)
     print(f"wrote {a.out} after {time.time() - t0:.0f} s", flush=True)
     for p in pairs:

@@ -58,7 +58,7 @@ def test_learned_closure_beats_the_plain_coarse_lattice(lat, trained, seed, mode
     print(f"\n[seed {seed} mode {mode}] <|v|^2> err plain {e['plain'][0]:.3e} learned "
           f"{e['learned'][0]:.3e}; <rho_r^2> err plain {e['plain'][1]:.3e} learned "
           f"{e['learned'][1]:.3e}", end="")
-    # measured: the closure cuts the <|v|^2> error by about a third and the <rho_r^2> error
-    # by about half on both held-out flows; asserted with a margin
+    # measured: the closure cuts the <|v|^2> error by about 45 % and the <rho_r^2> error by
+    # about two thirds on both held-out flows; asserted with a margin
     assert e["learned"][0] < 0.85 * e["plain"][0]
     assert e["learned"][1] < 0.85 * e["plain"][1]
