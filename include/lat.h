@@ -256,12 +256,20 @@ long long lat_steps_done(const lat_ctx* c);
  *                 cell's jx range over C = 1..4 warp groups);
  *                 3..7 producer warp + consumer warps (3: vy-drag flux row in registers,
  *                 4 slots; 4: in shared memory, 4 slots; 5: in shared memory, 3 slots; 6: the
- *                 vy-diffusion flux row in shared memory too, 3 slots; 7: as 6, 2 slots).
+ *                 vy-diffusion flux row in shared memory too, 3 slots; 7: as 6, 2 slots;
+ *                 8..10 the sweep of two half-rows per thread in FP32 register pairs, the
+ *                 vy-drag flux row in registers with 3 slots (8), in shared memory with 3 (9)
+ *                 or 2 slots (10)).
  *          d = 2 with 16-bit storage: 1 plain loads (any size); 4..7 as above (N_x a
  *                 multiple of 8 and >= 136, N_v >= 9).
+ *          d = 2 with the flux-limited scheme (lat_set_scheme): 1 three passes over the state
+ *                 (any N_v); 2 one fused kernel per step (N_v >= 5; the default where it
+ *                 exists).  Same bits up to the sign of zero values.
  *  block:  threads per block (= x cells per tile) for kernel 1; the copy pipelines fix a 128-cell
  *          tile (2D kernel 2: 128 C threads); 0 keeps.
- *  blocks_per_sm: resident blocks per SM of the persistent grid; 0 keeps.
+ *  blocks_per_sm: resident blocks per SM of the persistent grid; 0 keeps.  The fused
+ *          flux-limited kernel takes 1 or 2 (FP32, N_v = 17 and 19: the register budget it is
+ *          compiled for; 2 by default) and ignores it otherwise.
  *  mode:   -1 keep; 0 one persistent launch per step, n steps captured in one CUDA graph;
  *          1 one launch per instance per step (the unbatched baseline, 1D); 2 persistent
  *          launches issued directly (no graph).

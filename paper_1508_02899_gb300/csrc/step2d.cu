@@ -1173,9 +1173,12 @@ struct Ctx2D {
     void* d_wtc = nullptr;       // tensor-core weight tiles (BF16) and biases
     float* d_rho = nullptr;      // [ny][nx]
     float4* d_feat = nullptr;    // [ny][nx][2]: spatial parts of the features (BF16 network)
-    // drag scheme: upwind (the fused kernels) or flux-limited (limiter2d.cu, scratch d_lim)
+    // drag scheme: upwind (the fused kernels) or flux-limited (limiter2d.cu: one fused kernel,
+    // or three passes with the scratch state d_lim)
     int scheme = LAT_SCHEME_UPWIND;
     double mu = 2.0 / 3.0;
+    int lim_kernel = 0;  // limited step: 0 the fastest form, 1 three passes, 2 fused, 3 packed
+    int lim_bps = 2;     // blocks per SM of the fused limited kernel, where two shapes exist
     void* d_lim = nullptr;
     float* d_G = nullptr;        // [2][N_v^2][ny][nx]
     DevState* d_st0 = nullptr;   // step 0, no flags: explicit-buffer rollouts
@@ -1210,6 +1213,27 @@ bool ring_ok(const Ctx2D* c) {
 }
 
 bool pc_ok(const Ctx2D* c) { return c->half ? c->nv >= 9 : pc_supported(c->nv); }
+
+// Launch form of the flux-limited step (1 three passes, 2 fused, 3 fused on FP32 register
+// pairs): the caller's choice, else the packed form for FP32 and the fused one for FP64 where
+// the kernels are built for N_v, else the three passes.
+int lim_form(const Ctx2D* c) {
+    if (!limiter2d_fused_supported(c->nv)) return 1;
+    if (c->lim_kernel) return c->lim_kernel;
+    return c->dtype == LAT_F32 ? 3 : 2;
+}
+
+// The three passes' scratch state, allocated while they are the limited scheme's launch form.
+int lim_scratch(Ctx2D* c) {
+    if (c->scheme != LAT_SCHEME_KOREN || lim_form(c) != 1 || c->d_lim) return LAT_OK;
+    const size_t bytes =
+        (size_t)c->nx * c->ny * c->nv * c->nv * (c->dtype == LAT_F64 ? 8 : 4);
+    if (cudaMalloc(&c->d_lim, bytes) != cudaSuccess) {
+        c->d_lim = nullptr;
+        return LAT_ENOMEM;
+    }
+    return LAT_OK;
+}
 
 Step2DHArgs half_args(const Ctx2D* c, const Step2DArgs& a) {
     Step2DHArgs h;
@@ -1328,7 +1352,8 @@ int enqueue2d(Ctx2D* c, void* const f[2], int n, cudaStream_t s, int dry) {
             const int rc = enqueue_learned(c, a, k, s);
             if (rc != LAT_OK) return rc;
         } else if (c->scheme == LAT_SCHEME_KOREN) {
-            CK2(launch_step2d_limited(c->dtype, a, c->nv, c->mu, c->d_lim, k, c->sm_count, s));
+            CK2(launch_step2d_limited(c->dtype, a, c->nv, c->mu, c->d_lim, lim_form(c),
+                                      c->lim_bps, k, c->sm_count, s));
         } else if (c->half) {
             const Step2DHArgs ha = half_args(c, a);
             CK2(launch_scale2d(c->nv, c->ny, ha, k, s));
@@ -1568,11 +1593,13 @@ int ctx2d_set_scheme(Ctx2D* c, int scheme, double mu) {
         // that is 2 g J (1 + mu)
         const int J = (c->nv - 1) / 2;
         if (2.0 * c->g * J * (1.0 + mu) > 1.0) return LAT_ECFL;
-        if (!c->d_lim) {
-            const size_t bytes = (size_t)n * (c->dtype == LAT_F64 ? 8 : 4);
-            if (cudaMalloc(&c->d_lim, bytes) != cudaSuccess) return LAT_ENOMEM;
-        }
         c->mu = mu;
+        c->scheme = scheme;
+        const int rc = lim_scratch(c);
+        if (rc != LAT_OK) {
+            c->scheme = LAT_SCHEME_UPWIND;
+            return rc;
+        }
     } else {
         cudaFree(c->d_lim);
         c->d_lim = nullptr;
@@ -1657,6 +1684,24 @@ int ctx2d_set_launch(Ctx2D* c, int kernel, int block, int bps, int mode) {
     // kernel: 0 keep, 1 plain loads (128 threads), >= 2 bulk-copy ring; for the ring, block =
     // 128 C threads splits every cell's jx range over C warp groups (C = 1..4)
     // kernel 3..7: producer/consumer variants, 8..10 the packed two-lane sweep (160 threads)
+    if (c->scheme == LAT_SCHEME_KOREN) {  // 1 three passes, 2 fused, 3 fused on FP32 pairs
+        if (kernel < 0 || kernel > 3) return LAT_EINVAL;
+        if (kernel >= 2 && !limiter2d_fused_supported(c->nv)) return LAT_EINVAL;
+        if (kernel == 3 && c->dtype != LAT_F32) return LAT_EINVAL;
+        if (mode == 1 || mode > 2) return LAT_EINVAL;
+        if (bps < 0 || bps > 2) return LAT_EINVAL;
+        const int was = c->lim_kernel;
+        if (kernel) c->lim_kernel = kernel;
+        if (bps) c->lim_bps = bps;
+        const int rc = lim_scratch(c);
+        if (rc != LAT_OK) {
+            c->lim_kernel = was;
+            return rc;
+        }
+        if (mode == 0 || mode == 2) c->mode = mode;
+        drop(c);
+        return LAT_OK;
+    }
     if (kernel < 0 || kernel > 10) return LAT_EINVAL;
     if (c->half && (kernel == 2 || kernel == 3 || kernel >= 8)) return LAT_EINVAL;
     if (kernel >= 2 && !ring_ok(c)) return LAT_EINVAL;

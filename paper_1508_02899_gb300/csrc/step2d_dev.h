@@ -268,9 +268,13 @@ struct SmemCol {  // one thread's column in a [NV][TW] shared array
 
 }  // namespace k2d
 
-// Flux-limited 2D step (limiter2d.cu): stage 1, stage 2 and the diffusion of step k of a batch;
-// scratch holds one state.
+// Flux-limited 2D step (limiter2d.cu): stage 1, stage 2 and the diffusion of step k of a batch.
+// form 1: three passes, with `scratch` holding one state; 2: one fused kernel for the whole
+// step (N_v with limiter2d_fused_supported; bps 1 or 2 the resident blocks per SM where both
+// are built); 3: the fused kernel on cell pairs in FP32 register pairs (FP32 storage).
 cudaError_t launch_step2d_limited(int dtype, const k2d::Step2DArgs& s2, int nv, double mu,
-                                  void* scratch, int k, int sm_count, cudaStream_t s);
+                                  void* scratch, int form, int bps, int k, int sm_count,
+                                  cudaStream_t s);
+bool limiter2d_fused_supported(int nv);
 
 }  // namespace lat

@@ -2,7 +2,8 @@
 oracle/limiter.py.  1D: single lattices after 1000 steps (1e-12 FP64, 1e-5 FP32), every launch
 variant bit for bit, an ensemble with ragged sizes, the benchmark ensemble at full size on sampled
 instances, mass and positivity, and the host-side checks.  2D (the scheme of the paper's 2D runs):
-random-phase flows on three shapes, the tilted cellular flow, mass and positivity."""
+random-phase flows on four shapes (the fused kernel, the default), the fused kernel against the
+three passes bit for bit, the tilted cellular flow, mass and positivity."""
 import math
 
 import numpy as np
@@ -216,11 +217,13 @@ def oracle2d(c):
     return f
 
 
-def gpu2d(lat, c, dtype):
+def gpu2d(lat, c, dtype, launch=None):
     t = torch.tensor(c["f0"], dtype=dtype, device="cuda")
     lt = lat.Lattice(t, d=2, nx=c["nx"], ny=c["ny"], nv=c["nv"], L=L, tau_p=c["tau_p"],
                      kappa=c["kappa"], dt=c["dt"])
     lt.set_scheme(lat.SCHEME_KOREN, c["mu"])
+    if launch:
+        lt.set_launch(**launch)
     fl = c["fl"]
     lt.set_flow_modes_2d(fl.kvec, fl.a, fl.phi0, fl.tau_f)
     lt.set_noise(fl.noise)
@@ -236,6 +239,58 @@ def test_2d_matches_oracle(lat, dtype, nx, ny, nv, mu):
     want = oracle2d(c)
     got, lt = gpu2d(lat, c, dtype)
     assert rel_l1(got, want) <= TOL[dtype], rel_l1(got, want)
+    lt.close()
+
+
+def test_2d_33x33_matches_oracle(lat):
+    """The velocity lattice of the 2D configurations (33^2), on a ragged 40 x 36 grid."""
+    for dtype in (torch.float64, torch.float32):
+        c = case2d(40, 36, 33, 1.0, 2e-3, 8, 91)
+        want = oracle2d(c)
+        got, lt = gpu2d(lat, c, dtype)
+        assert rel_l1(got, want) <= TOL[dtype], (dtype, rel_l1(got, want))
+        lt.close()
+
+
+@pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
+@pytest.mark.parametrize("nx,ny,nv,st", [(70, 24, 5, 1.0), (100, 31, 9, 0.1), (40, 20, 13, 1.0),
+                                         (64, 20, 17, 1.0), (97, 40, 19, 10.0),
+                                         (50, 26, 21, 1.0), (45, 34, 33, 0.5)])
+def test_2d_fused_gives_the_three_pass_bits(lat, dtype, nx, ny, nv, st):
+    """One kernel per step (tiles of 32, or of 16 and 8 cells for the larger FP64 and N_v = 33
+    planes; ragged and odd N_x), scalar and on FP32 register pairs, against the three passes:
+    the same faces with the same operations, so equal values (a skipped zero part can change
+    only the sign of a zero)."""
+    c = case2d(nx, ny, nv, st, 2e-3, 12, nx + 7 * nv)
+    ref, lt = gpu2d(lat, c, dtype, launch=dict(kernel=1))
+    lt.close()
+    shapes = [dict(kernel=2, blocks_per_sm=1), dict(kernel=2, blocks_per_sm=2)]
+    if dtype == torch.float32:
+        shapes.append(dict(kernel=3))  # cell pairs in FP32 register pairs
+    for launch in shapes:
+        got, lt = gpu2d(lat, c, dtype, launch=launch)
+        lt.close()
+        assert np.array_equal(got, ref), (launch, np.abs(got - ref).max())
+
+
+def test_2d_launch_forms(lat):
+    c = case2d(48, 40, 3, 1.0, 2e-3, 2, 5)  # N_v = 3: three passes only
+    t = torch.tensor(c["f0"], dtype=torch.float32, device="cuda")
+    lt = lat.Lattice(t, d=2, nx=48, ny=40, nv=3, L=L, tau_p=c["tau_p"], kappa=c["kappa"],
+                     dt=c["dt"])
+    lt.set_scheme(lat.SCHEME_KOREN, MU)
+    with pytest.raises(lat.LatError) as e:
+        lt.set_launch(kernel=2)
+    assert e.value.code == lat.LAT_EINVAL
+    with pytest.raises(lat.LatError) as e:
+        lt.set_launch(kernel=5)
+    assert e.value.code == lat.LAT_EINVAL
+    with pytest.raises(lat.LatError) as e:
+        lt.set_launch(kernel=3)
+    assert e.value.code == lat.LAT_EINVAL
+    lt.set_launch(kernel=1)
+    lt.step(2)
+    assert lt.status() == 0
     lt.close()
 
 
