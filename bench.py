@@ -335,7 +335,7 @@ def build_ensemble(args, I, lat, torch, dev, rank, nsteps, scheme="upwind"):
     desc = WORKLOAD if n_inst == N_INST else f"{WORKLOAD} (profiling case: {n_inst} instances)"
     if koren:
         desc += "; flux-limited drag (Koren limiter, mu = 2/3, Heun's method)"
-    return ens, cells, fl.noise[:1], np.zeros((n_inst, 3)), desc
+    return ens, cells, fl.noise, np.zeros((n_inst, 3)), desc
 
 
 def build_2d(args, I, lat, torch, dev, rank, nsteps, n=512, nv=33, store="f32"):
@@ -362,7 +362,7 @@ def build_2d(args, I, lat, torch, dev, rank, nsteps, n=512, nv=33, store="f32"):
     del f0
     lt.set_flow_modes_2d(fl.kvec, fl.a, fl.phi0, fl.tau_f)
     lt.set_noise(fl.noise)
-    return lt, n * n * nv * nv, fl.noise[:1], np.zeros(4), desc
+    return lt, n * n * nv * nv, fl.noise, np.zeros(4), desc
 
 
 def build_cellular(args, I, lat, torch, dev, rank, n=1024, nv=19, koren=False):
@@ -406,7 +406,7 @@ def build_learned(args, I, lat, torch, dev, rank, nsteps, n=2048):
     lt.set_flow_modes_2d(fl.kvec, fl.a, fl.phi0, fl.tau_f)
     lt.set_noise(fl.noise)
     lt.learn(T.load_params(CLOSURE_PARAMS), 2)  # trained by train.py (recipe in the file)
-    return lt, n * n * nv * nv, fl.noise[:1], np.zeros(4), WORKLOAD_LEARNED.format(n=n)
+    return lt, n * n * nv * nv, fl.noise, np.zeros(4), WORKLOAD_LEARNED.format(n=n)
 
 
 def time_network(lt, reps, torch):
@@ -446,19 +446,41 @@ def timed(ctx, K, W, torch, dist, world, local, dev):
     return max_over_ranks(ev0.elapsed_time(ev1), world, dist, torch, dev), ck
 
 
-def end_to_end(ctx, noise_row, glob, steps, torch):
-    """Per step, through the C ABI with host buffers: the step's noise row from pinned host
-    memory, one step, and the moments (globals) back to host memory."""
-    pinned = torch.from_numpy(np.ascontiguousarray(noise_row)).pin_memory()
+def end_to_end(ctx, noise, first, glob, steps, torch, pipelined=True):
+    """Per step, through the C ABI with host buffers: the step's noise row (rows first, first + 1,
+    ... of the flow's noise table) from pinned host memory, one step, and the moments (globals)
+    back to host memory, where the host reads them (the total mass).  Pipelined: lat_step_moments_async puts each step's globals in one of two
+    pinned buffers, and the host reads step k - 1's once step k is enqueued (its event passed);
+    otherwise lat_step_moments, which synchronises every step.  Returns the time, the bytes
+    copied per step each way and the masses read."""
+    rows = torch.from_numpy(np.ascontiguousarray(noise[first:first + steps])).pin_memory()
+    assert rows.shape[0] == steps, "noise table too short"
+    outs = [torch.zeros(glob.shape, dtype=torch.float64).pin_memory() for _ in range(2)]
+    masses = []
     ctx.prepare(1)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    for _ in range(steps):
-        ctx.set_noise_pinned(pinned)
-        # the moments fused into the step where the launch allows it, else a second pass
-        ctx.step_moments(1, per_cell=False, globals_out=glob)
+    if pipelined:
+        evs = []
+        for k in range(steps):
+            ctx.set_noise_pinned(rows[k:k + 1])
+            # the moments fused into the step where the launch allows it, else a second pass
+            ctx.step_moments_async(1, outs[k % 2])
+            evs.append(torch.cuda.Event())
+            evs[-1].record()
+            if k >= 1:
+                evs[k - 1].synchronize()
+                masses.append(float(outs[(k - 1) % 2].numpy()[..., 0].sum()))
+        evs[-1].synchronize()
+        masses.append(float(outs[(steps - 1) % 2].numpy()[..., 0].sum()))
+        glob[...] = outs[(steps - 1) % 2].numpy()
+    else:
+        for k in range(steps):
+            ctx.set_noise_pinned(rows[k:k + 1])
+            ctx.step_moments(1, per_cell=False, globals_out=glob)
+            masses.append(float(glob[..., 0].sum()))
     torch.cuda.synchronize()
-    return time.perf_counter() - t0, int(pinned.numel() * 8), int(glob.size * 8)
+    return time.perf_counter() - t0, int(rows[0].numel() * 8), int(glob.size * 8), masses
 
 
 def kernel_label(workload, best, nv):
@@ -503,30 +525,30 @@ def main():
 
     K, W = args.steps, args.warmup
     K_e2e = max(3, min(K, 50))
-    nsteps = W + K + K_e2e + 2
+    nsteps = W + K + 2 * K_e2e + 2  # warm-up, timed, pipelined and synchronous end to end
     bytes_per_cell, lines = 8, 0
     if args.workload == "2d_learned":
-        ctx, cells, noise_row, glob, desc = build_learned(args, I, lat, torch, dev, rank, nsteps,
+        ctx, cells, noise, glob, desc = build_learned(args, I, lat, torch, dev, rank, nsteps,
                                                           n=args.size or 2048)
         nv = 9
         prof, src = KERNEL_PROFILES["2d_learned"]
         launches_per_step = 4  # flow, streamed density, network, corrected step
     elif args.workload == "2d":
-        ctx, cells, noise_row, glob, desc = build_2d(args, I, lat, torch, dev, rank, nsteps,
+        ctx, cells, noise, glob, desc = build_2d(args, I, lat, torch, dev, rank, nsteps,
                                                      n=args.size or 512)
         nv = 33
         prof, src = KERNEL_PROFILES["2d"]
         launches_per_step = 2  # flow evaluation + fused step
     elif args.workload in ("2d_f16", "2d_bf16"):
         store = args.workload[3:]
-        ctx, cells, noise_row, glob, desc = build_2d(args, I, lat, torch, dev, rank, nsteps,
+        ctx, cells, noise, glob, desc = build_2d(args, I, lat, torch, dev, rank, nsteps,
                                                      n=args.size or 1024, store=store)
         nv = 33
         prof, src = KERNEL_PROFILES[args.workload]
         launches_per_step = 3  # flow evaluation + output scales + fused step
         bytes_per_cell, lines = 4, nv * nv * (args.size or 1024)
     else:
-        ctx, cells, noise_row, glob, desc = build_ensemble(args, I, lat, torch, dev, rank, nsteps,
+        ctx, cells, noise, glob, desc = build_ensemble(args, I, lat, torch, dev, rank, nsteps,
                                                            scheme=args.scheme)
         nv = NV
         prof, src = KERNEL_PROFILES["ensemble" if args.scheme == "upwind" else "ensemble_koren"]
@@ -555,8 +577,14 @@ def main():
     ms_max, ck = timed(ctx, K, W, torch, dist, world, local, dev)
     status = ctx.status()
     value = job_throughput(cells, K, world, ms_max)
-    e2e_s, h2d, d2h = end_to_end(ctx, noise_row, glob, K_e2e, torch)
+    first = ctx.steps_done  # the noise rows after those of the steps taken so far
+    e2e_s, h2d, d2h, masses = end_to_end(ctx, noise, first, glob, K_e2e, torch)
     e2e_value = world * cells * K_e2e / e2e_s / 1e9
+    e2e_status = ctx.status()
+    sync_s, _, _, _ = end_to_end(ctx, noise, first + K_e2e, glob, K_e2e, torch,
+                                 pipelined=False)
+    e2e_sync = world * cells * K_e2e / sync_s / 1e9
+    mass_drift = (max(masses) - min(masses)) / abs(masses[0]) if masses and masses[0] else None
 
     peak, peak_src = measured_peaks()
     # one read and one write of every cell; 16-bit storage adds per line its input scale, its
@@ -758,7 +786,10 @@ def main():
                                  "bytes_per_launch": bytes_per_launch},
             "cpu_baseline": cpu,
             "e2e": {"value": e2e_value, "unit": UNIT, "steps": K_e2e,
-                    "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+                    "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                    "api": "lat_step_moments_async, globals read one step behind",
+                    "sync_value": e2e_sync, "sync_api": "lat_step_moments (synchronises)",
+                    "status": e2e_status, "mass_rel_spread": mass_drift},
             "gpu_launches": launches_per_step * K + 1,
             "clocks": ck,
         }

@@ -155,12 +155,22 @@ int lat_moments(lat_ctx* c, double* rho, double* mean_v, double* mean_v2, double
 
 /* lat_step(c, n) followed by lat_moments(c, ...), with the moments of the final state computed
  * inside the last step (no second pass over f) when the 1D producer/consumer kernel is in use,
- * or, in 2D, FP32 storage with the upwind drag on launch kernel 4 or 5; otherwise exactly the
- * two calls.  Same arguments, outputs, synchronisation and status as
+ * or, in 2D, FP32 storage with the upwind drag on launch kernel 4, 5 or 8-10; otherwise exactly
+ * the two calls.  Same arguments, outputs, synchronisation and status as
  * lat_moments.  The per-cell outputs equal lat_moments' bit for bit; the globals agree to the
  * rounding order of the compensated sums. */
 int lat_step_moments(lat_ctx* c, int n, double* rho, double* mean_v, double* mean_v2,
                      double* globals);
+
+/* lat_step_moments without the synchronisation, for a caller that reads each step's globals while
+ * later steps run: enqueues the n steps, the reduction of the final state's global moments and
+ * their copy into `globals` (HOST memory, pinned or registered, per instance [M, P_1..P_d, E] as
+ * for lat_moments; not NULL) on the context's stream, and returns.  The values are in `globals`
+ * once the stream has passed that point (the caller's cudaStreamSynchronize or event, or the
+ * next synchronising call); `globals` must stay valid until then.  The device status of these
+ * steps is reported by the next lat_status (or any synchronising call).  LAT_EINVAL for a NULL
+ * `globals` or n < 1. */
+int lat_step_moments_async(lat_ctx* c, int n, double* globals);
 
 /* Synchronise, return and clear the pending device status. */
 int lat_status(lat_ctx* c);

@@ -15,13 +15,16 @@ int ctx2d_step(Ctx2D* c, void* const f[2], int n, cudaStream_t s);
 int ctx2d_prepare(Ctx2D* c, void* const f[2], int n);
 void ctx2d_geometry(const Ctx2D* c, int* nx, int* ny, int* nv, double* dx, double* dv);
 int ctx2d_set_scheme(Ctx2D* c, int scheme, double mu);
+// The moments of buffer f; the globals go to host memory, through a stream synchronisation
+// (wait) or by an asynchronous copy into the caller's pinned buffer.
 int ctx2d_moments(Ctx2D* c, const void* f, int cur, double* rho, double* mean_v,
-                  double* mean_v2, double* globals, cudaStream_t s);
+                  double* mean_v2, double* globals, bool wait, cudaStream_t s);
 // One step whose kernel also reduces the moments of the state it writes (FP32 storage, upwind,
-// producer/consumer launch variant 4 or 5); LAT_EINVAL otherwise (ctx2d_moments_fusable).
+// producer/consumer launch variants 4, 5 and 8-10); LAT_EINVAL otherwise
+// (ctx2d_moments_fusable).  globals and wait as for ctx2d_moments.
 bool ctx2d_moments_fusable(const Ctx2D* c);
 int ctx2d_step_moments(Ctx2D* c, void* const f[2], double* rho, double* mean_v,
-                       double* mean_v2, double* globals, cudaStream_t s);
+                       double* mean_v2, double* globals, bool wait, cudaStream_t s);
 // 16-bit storage: line maxima of the caller's initial state (scales 1), encoding of an FP32
 // state into the current buffer, decoding of the current buffer (dst and/or its line scales).
 int ctx2d_init_state(Ctx2D* c, void* const f[2], int cur, cudaStream_t s);

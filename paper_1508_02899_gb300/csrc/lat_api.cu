@@ -144,6 +144,16 @@ int build_items(lat_ctx* c) {
     return LAT_OK;
 }
 
+// The 1D globals [instances][M, P, E] of the last reduction to host memory: into the pinned
+// context buffer (wait: the caller synchronises and copies them on), or straight into the
+// caller's pinned buffer.
+int copy_globals_1d(lat_ctx* c, double* gdst, bool wait) {
+    if (!gdst) return LAT_OK;
+    CK(cudaMemcpyAsync(wait ? c->h_glob : gdst, c->d_glob, sizeof(double) * 3 * c->n_inst,
+                       cudaMemcpyDeviceToHost, c->stream));
+    return LAT_OK;
+}
+
 int persistent_grid(const lat_ctx* c) {
     return std::max(1, std::min(c->nitems, c->bps * c->sm_count));
 }
@@ -514,14 +524,18 @@ int lat_status(lat_ctx* c) {
     return status_code(c->h_state->status);
 }
 
-int lat_moments(lat_ctx* c, double* rho, double* mean_v, double* mean_v2, double* globals) {
-    if (!c) return LAT_EINVAL;
-    if (c->d == 2) {
-        int rc = ctx2d_moments(c->c2, c->f[c->cur], c->cur, rho, mean_v, mean_v2, globals,
-                               c->stream);
-        if (rc != LAT_OK) return rc;
-        return lat_status(c);
-    }
+}  // extern "C"
+
+namespace {
+
+// The moments of the current state, enqueued: per-cell arrays on the device, the globals to host
+// memory (gdst, or none): through the pinned context buffer and a synchronisation (wait), or by
+// an asynchronous copy into the caller's pinned buffer.
+int enqueue_moments(lat_ctx* c, double* rho, double* mean_v, double* mean_v2, double* gdst,
+                    bool wait) {
+    if (c->d == 2)
+        return ctx2d_moments(c->c2, c->f[c->cur], c->cur, rho, mean_v, mean_v2, gdst, wait,
+                             c->stream);
     Mom1DArgs a;
     a.f = c->f[c->cur];
     a.inst = c->d_inst;
@@ -536,36 +550,31 @@ int lat_moments(lat_ctx* c, double* rho, double* mean_v, double* mean_v2, double
     const int grid = std::max(1, std::min(c->nitems, 8 * c->sm_count));
     CK(launch_moments1d(c->dtype, tile_of(c), 1, grid, a, c->stream));
     CK(launch_finalize1d(c->d_partials, c->d_inst_begin, c->d_inst, c->n_inst, c->d_glob,
-                         tile_of(c) / 32,
-                         c->stream));
-    if (globals)
-        CK(cudaMemcpyAsync(c->h_glob, c->d_glob, sizeof(double) * 3 * c->n_inst,
-                           cudaMemcpyDeviceToHost, c->stream));
-    int rc = lat_status(c);  // synchronises
-    if (globals) memcpy(globals, c->h_glob, sizeof(double) * 3 * c->n_inst);
-    return rc;
+                         tile_of(c) / 32, c->stream));
+    return copy_globals_1d(c, gdst, wait);
 }
 
-int lat_step_moments(lat_ctx* c, int n, double* rho, double* mean_v, double* mean_v2,
-                     double* globals) {
-    if (!c || n < 1) return LAT_EINVAL;
+// n steps and the moments of the state the last one writes (fused into it where the launch
+// allows it), enqueued; gdst and wait as for enqueue_moments.
+int enqueue_step_moments(lat_ctx* c, int n, double* rho, double* mean_v, double* mean_v2,
+                         double* gdst, bool wait) {
     if (c->d == 2 && ctx2d_moments_fusable(c->c2)) {
         if (n > 1) {
             int rc = lat_step(c, n - 1);
             if (rc != LAT_OK) return rc;
         }
-        int rc = ctx2d_step_moments(c->c2, c->f, rho, mean_v, mean_v2, globals, c->stream);
+        int rc = ctx2d_step_moments(c->c2, c->f, rho, mean_v, mean_v2, gdst, wait, c->stream);
         if (rc != LAT_OK) return rc;
         c->h_step += 1;
         c->cur = (int)(c->h_step & 1);
-        return lat_status(c);  // synchronises
+        return LAT_OK;
     }
     const bool fused = c->d == 1 && c->variant == STEP1D_PC && c->mode != 1 &&
                        step1d_moments_supported(c->dtype, c->nv);
     if (!fused) {
         int rc = lat_step(c, n);
         if (rc != LAT_OK) return rc;
-        return lat_moments(c, rho, mean_v, mean_v2, globals);
+        return enqueue_moments(c, rho, mean_v, mean_v2, gdst, wait);
     }
     if (n > 1) {
         int rc = lat_step(c, n - 1);
@@ -582,12 +591,35 @@ int lat_step_moments(lat_ctx* c, int n, double* rho, double* mean_v, double* mea
                          kPcConsumerWarps, c->stream));
     c->h_step += 1;
     c->cur = (int)(c->h_step & 1);
-    if (globals)
-        CK(cudaMemcpyAsync(c->h_glob, c->d_glob, sizeof(double) * 3 * c->n_inst,
-                           cudaMemcpyDeviceToHost, c->stream));
-    int rc = lat_status(c);  // synchronises
-    if (globals) memcpy(globals, c->h_glob, sizeof(double) * 3 * c->n_inst);
+    return copy_globals_1d(c, gdst, wait);
+}
+
+}  // namespace
+
+extern "C" {
+
+int lat_moments(lat_ctx* c, double* rho, double* mean_v, double* mean_v2, double* globals) {
+    if (!c) return LAT_EINVAL;
+    int rc = enqueue_moments(c, rho, mean_v, mean_v2, globals, true);
+    if (rc != LAT_OK) return rc;
+    rc = lat_status(c);  // synchronises
+    if (globals && c->d == 1) memcpy(globals, c->h_glob, sizeof(double) * 3 * c->n_inst);
     return rc;
+}
+
+int lat_step_moments(lat_ctx* c, int n, double* rho, double* mean_v, double* mean_v2,
+                     double* globals) {
+    if (!c || n < 1) return LAT_EINVAL;
+    int rc = enqueue_step_moments(c, n, rho, mean_v, mean_v2, globals, true);
+    if (rc != LAT_OK) return rc;
+    rc = lat_status(c);  // synchronises
+    if (globals && c->d == 1) memcpy(globals, c->h_glob, sizeof(double) * 3 * c->n_inst);
+    return rc;
+}
+
+int lat_step_moments_async(lat_ctx* c, int n, double* globals) {
+    if (!c || n < 1 || !globals) return LAT_EINVAL;
+    return enqueue_step_moments(c, n, nullptr, nullptr, nullptr, globals, false);
 }
 
 int lat_current(const lat_ctx* c) { return c ? c->cur : -1; }

@@ -102,23 +102,34 @@ __global__ void __launch_bounds__(1024) k_moments1d(const Mom1DArgs a, const int
     }
 }
 
-// One warp per instance folds that instance's partials (per_item partials per work item):
-// lane l takes partials l, l + 32, ... in order, then a fixed butterfly; glob[i] = [M, P, E].
+// Eight lanes per instance (four instances per warp) fold that instance's partials (per_item
+// partials per work item): lane l of the group takes partials l, l + 8, ... in order, then a
+// fixed three-level butterfly; glob[i] = [M, P, E].  (FP64 is slow on this part: eight lanes
+// keep the butterfly's share of the merges small, and the order stays fixed.)
+constexpr int kFinLanes = 8;
+
 __global__ void k_finalize1d(const double* partials, const int* begin, const Inst1D* inst,
                              int n_inst, double* glob, int per_item) {
-    const int i = blockIdx.x;
-    if (i >= n_inst) return;
     const int lane = threadIdx.x & 31;
-    if (threadIdx.x >= 32) return;
+    const int i = blockIdx.x * (32 / kFinLanes) + lane / kFinLanes;
+    const int l = lane % kFinLanes;
+    const bool on = i < n_inst;
     Comp t0{0, 0}, t1{0, 0}, t2{0, 0};
-    for (long long it = (long long)begin[i] * per_item + lane;
-         it < (long long)begin[i + 1] * per_item; it += 32) {
-        nmerge(t0, Comp{partials[it * 6 + 0], partials[it * 6 + 1]});
-        nmerge(t1, Comp{partials[it * 6 + 2], partials[it * 6 + 3]});
-        nmerge(t2, Comp{partials[it * 6 + 4], partials[it * 6 + 5]});
+    if (on) {
+        for (long long it = (long long)begin[i] * per_item + l;
+             it < (long long)begin[i + 1] * per_item; it += kFinLanes) {
+            nmerge(t0, Comp{partials[it * 6 + 0], partials[it * 6 + 1]});
+            nmerge(t1, Comp{partials[it * 6 + 2], partials[it * 6 + 3]});
+            nmerge(t2, Comp{partials[it * 6 + 4], partials[it * 6 + 5]});
+        }
     }
-    warp_reduce3(t0, t1, t2);
-    if (lane == 0) {
+    for (int off = kFinLanes / 2; off > 0; off >>= 1) {  // within the group of eight lanes
+        const Comp o0 = shfl_down(t0, off), o1 = shfl_down(t1, off), o2 = shfl_down(t2, off);
+        nmerge(t0, o0);
+        nmerge(t1, o1);
+        nmerge(t2, o2);
+    }
+    if (on && l == 0) {
         const double w = inst[i].dx * inst[i].dv;
         glob[i * 3 + 0] = nval(t0) * w;
         glob[i * 3 + 1] = nval(t1) * w;
@@ -227,7 +238,9 @@ cudaError_t launch_finalize1d(const double* partials, const int* inst_item_begin
                               const Inst1D* inst, int n_inst, double* glob, int per_item,
                               cudaStream_t s) {
     if (n_inst <= 0) return cudaSuccess;
-    k_finalize1d<<<n_inst, 32, 0, s>>>(partials, inst_item_begin, inst, n_inst, glob, per_item);
+    const int groups = 32 / kFinLanes;
+    k_finalize1d<<<(n_inst + groups - 1) / groups, 32, 0, s>>>(partials, inst_item_begin, inst,
+                                                               n_inst, glob, per_item);
     return cudaGetLastError();
 }
 

@@ -1617,8 +1617,23 @@ void ctx2d_geometry(const Ctx2D* c, int* nx, int* ny, int* nv, double* dx, doubl
     *dv = c->dv;
 }
 
+// The four globals of the last reduction to host memory: through the context's pinned buffer
+// and a stream synchronisation (wait), or copied straight into the caller's (pinned) buffer
+// without waiting.
+int copy_globals(Ctx2D* c, double* globals, bool wait, cudaStream_t s) {
+    if (!globals) return LAT_OK;
+    if (!wait) {
+        CK2(cudaMemcpyAsync(globals, c->d_glob, sizeof(double) * 4, cudaMemcpyDeviceToHost, s));
+        return LAT_OK;
+    }
+    CK2(cudaMemcpyAsync(c->h_glob, c->d_glob, sizeof(double) * 4, cudaMemcpyDeviceToHost, s));
+    CK2(cudaStreamSynchronize(s));
+    memcpy(globals, c->h_glob, sizeof(double) * 4);
+    return LAT_OK;
+}
+
 int ctx2d_moments(Ctx2D* c, const void* f, int cur, double* rho, double* mean_v,
-                  double* mean_v2, double* globals, cudaStream_t s) {
+                  double* mean_v2, double* globals, bool wait, cudaStream_t s) {
     const float* sc = c->half ? c->d_sc + (size_t)cur * c->nlines : nullptr;
     if (c->dtype == LAT_F16)
         k_moments2d<__half><<<c->mom_blocks, 32 * kMom2DWarps, 0, s>>>(f, sc, c->nv, c->nx, c->ny, c->dv,
@@ -1636,12 +1651,7 @@ int ctx2d_moments(Ctx2D* c, const void* f, int cur, double* rho, double* mean_v,
     k_finalize2d<<<1, kFin2DThreads, 0, s>>>(c->d_partials, c->mom_blocks,
                                              c->dx * c->dx * c->dv * c->dv, c->d_glob);
     CK2(cudaGetLastError());
-    if (globals) {
-        CK2(cudaMemcpyAsync(c->h_glob, c->d_glob, sizeof(double) * 4, cudaMemcpyDeviceToHost, s));
-        CK2(cudaStreamSynchronize(s));
-        memcpy(globals, c->h_glob, sizeof(double) * 4);
-    }
-    return LAT_OK;
+    return copy_globals(c, globals, wait, s);
 }
 
 bool ctx2d_moments_fusable(const Ctx2D* c) {
@@ -1650,7 +1660,7 @@ bool ctx2d_moments_fusable(const Ctx2D* c) {
 }
 
 int ctx2d_step_moments(Ctx2D* c, void* const f[2], double* rho, double* mean_v,
-                       double* mean_v2, double* globals, cudaStream_t s) {
+                       double* mean_v2, double* globals, bool wait, cudaStream_t s) {
     if (!ctx2d_moments_fusable(c)) return LAT_EINVAL;
     const Step2DArgs a = step_args(c, f);
     if (c->flow_kind == LAT_FLOW_MODES) {
@@ -1672,12 +1682,7 @@ int ctx2d_step_moments(Ctx2D* c, void* const f[2], double* rho, double* mean_v,
     k_finalize2d<<<1, kFin2DThreads, 0, s>>>(c->d_partials, grid * (TW / 32),
                                              c->dx * c->dx * c->dv * c->dv, c->d_glob);
     CK2(cudaGetLastError());
-    if (globals) {
-        CK2(cudaMemcpyAsync(c->h_glob, c->d_glob, sizeof(double) * 4, cudaMemcpyDeviceToHost, s));
-        CK2(cudaStreamSynchronize(s));
-        memcpy(globals, c->h_glob, sizeof(double) * 4);
-    }
-    return LAT_OK;
+    return copy_globals(c, globals, wait, s);
 }
 
 int ctx2d_set_launch(Ctx2D* c, int kernel, int block, int bps, int mode) {

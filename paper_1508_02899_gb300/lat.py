@@ -58,6 +58,7 @@ def _load():
         "lat_prepare": (c_int, [P, c_int]),
         "lat_moments": (c_int, [P, P, P, P, POINTER(c_double)]),
         "lat_step_moments": (c_int, [P, c_int, P, P, P, POINTER(c_double)]),
+        "lat_step_moments_async": (c_int, [P, c_int, P]),
         "lat_status": (c_int, [P]),
         "lat_current": (c_int, [P]),
         "lat_steps_done": (c_longlong, [P]),
@@ -183,6 +184,16 @@ class _Ctx:
     @property
     def steps_done(self) -> int:
         return _lib.lat_steps_done(self._h)
+
+    def step_moments_async(self, n: int, globals_out: torch.Tensor):
+        """n steps and the globals of the final state into globals_out (a pinned host float64
+        tensor, per instance [M, P_1..P_d, E]) without synchronising: the values are there once
+        the stream has passed this point.  The tensor is kept referenced until then."""
+        if globals_out.is_cuda or globals_out.dtype != torch.float64 or not globals_out.is_pinned():
+            raise ValueError("globals_out must be a pinned host float64 tensor")
+        self._keep_async = getattr(self, "_keep_async", [])[-63:] + [globals_out]
+        _check(_lib.lat_step_moments_async(self._h, int(n), c_void_p(globals_out.data_ptr())),
+               "lat_step_moments_async")
 
     def set_launch(self, kernel=0, block=0, blocks_per_sm=0, mode=-1):
         _check(_lib.lat_set_launch(self._h, kernel, block, blocks_per_sm, mode), "lat_set_launch")
