@@ -3,7 +3,8 @@ oracle/limiter.py.  1D: single lattices after 1000 steps (1e-12 FP64, 1e-5 FP32)
 variant bit for bit, an ensemble with ragged sizes, the benchmark ensemble at full size on sampled
 instances, mass and positivity, and the host-side checks.  2D (the scheme of the paper's 2D runs):
 random-phase flows on four shapes (the fused kernel, the default), the fused kernel against the
-three passes bit for bit, the tilted cellular flow, mass and positivity."""
+three passes bit for bit, the tilted cellular flow, mass and positivity, and the bench's
+1024^2 x 19^2 form at full size on sampled cells."""
 import math
 
 import numpy as np
@@ -326,3 +327,47 @@ def test_2d_cellular_flow_limited_matches_oracle(lat):
     assert lt.status() == 0
     assert rel_l1(lt.state.cpu().numpy(), want) <= 1e-12
     lt.close()
+
+
+def test_2d_full_size_cellular_sampled(lat):
+    """The bench's flux-limited form at full size: 1024^2 x 19^2 FP32 (3.8e8 phase cells), the
+    tilted cellular flow, the default launch (the fused kernel on FP32 pairs).  One step from a
+    seeded random state; 32 sampled cells recomputed by the oracle one by one from their
+    gathered f* (the limited step acts on each cell's velocity plane), with the FP32 flow values
+    the kernel reads."""
+    n, nv = 1024, 19
+    tau_p, kappa = 1.0, 8 * math.pi * 1e-3
+    dt = I.choose_dt(2, n, L, nv, tau_p, kappa, u_rms=0.1, cfl_factor=1 + MU)
+    dx = L / n
+    dv = dx / dt
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(17)
+    f0 = torch.rand((nv, nv, n, n), generator=gen, device="cuda") + 0.1
+    lt = lat.Lattice(f0.clone(), d=2, nx=n, ny=n, nv=nv, L=L, tau_p=tau_p, kappa=kappa, dt=dt)
+    lt.set_scheme(lat.SCHEME_KOREN, MU)
+    ux, uy = I.cellular_flow(n, n, L, 1.0)
+    u = torch.tensor(np.stack([ux, uy]), dtype=torch.float32, device="cuda")
+    lt.set_flow_field(u)
+    u64 = u.double().cpu().numpy()
+    lt.step(1)
+    assert lt.status() == 0
+    out = lt.state
+    rng = np.random.default_rng(23)
+    J = (nv - 1) // 2
+    jj = np.arange(nv)
+    xs0 = list(rng.integers(n, size=28)) + [0, n - 1, 5, n - 3]  # and cells near the wraps
+    ys0 = list(rng.integers(n, size=28)) + [n - 1, 0, n - 2, 3]
+    for x, y in zip(xs0, ys0):
+        x, y = int(x), int(y)
+        ys = [(y - (jy - J)) % n for jy in range(nv)]
+        xs = [(x - (jx - J)) % n for jx in range(nv)]
+        block = f0[:, :, ys][:, :, :, xs].double().cpu().numpy()
+        col = block[jj[:, None], jj[None, :], jj[:, None], jj[None, :]]  # f*(x, y; jx, jy)
+        uxc = np.array([[u64[0, y, x]]])
+        uyc = np.array([[u64[1, y, x]]])
+        want = O.diffuse_2d(K.drag_2d(col[:, :, None, None], uxc, uyc, tau_p, dt, dv, MU),
+                            kappa, dt, dv)[:, :, 0, 0]
+        got = out[:, :, y, x].double().cpu().numpy()
+        assert rel_l1(got, want) <= 1e-6, (x, y, rel_l1(got, want))
+    lt.close()
+
