@@ -183,26 +183,14 @@ __global__ void __launch_bounds__(128) k_mlp_f32(const LearnArgs a, int kstep) {
     }
 }
 
-// Corrections of one cell: G[0] and G[1] at (plane, cell).
-struct GlobCorr {
-    static constexpr bool active = true;
-    const float* cx;  // G + cell
-    const float* cy;  // G + N_v^2 ncell + cell
-    size_t ps;
-    int nv;
-    template <typename T>
-    __device__ __forceinline__ T gx(int rb, int jx) const { return cx[(size_t)(rb * nv + jx) * ps]; }
-    template <typename T>
-    __device__ __forceinline__ T gy(int rb, int jx) const { return cy[(size_t)(rb * nv + jx) * ps]; }
-};
 
 template <int NV>
 __global__ void __launch_bounds__(TW) k_step2d_corr(const Step2DArgs a, const float* G, int kstep) {
     const long long step = a.st->step + kstep;
     const int par = (int)(step & 1);
     const float g = float(a.g), rr = float(a.r);
-    const float* fin = static_cast<const float*>(a.f[par]);
-    float* fout = static_cast<float*>(a.f[par ^ 1]);
+    const float* fin = static_cast<const float*>(par ? a.f[1] : a.f[0]);
+    float* fout = static_cast<float*>(par ? a.f[0] : a.f[1]);
     const size_t ps = (size_t)a.nx * a.ny;
     for (int tile = blockIdx.x; tile < a.ntiles; tile += gridDim.x) {
         const int y = tile / a.ntx;

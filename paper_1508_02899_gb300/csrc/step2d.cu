@@ -70,8 +70,8 @@ __global__ void __launch_bounds__(TW) k_step2d_plain(const Step2DArgs a, int kst
     const long long step = a.st->step + kstep;
     const int par = (int)(step & 1);
     const T g = T(a.g), rr = T(a.r);
-    const T* fin = static_cast<const T*>(a.f[par]);
-    T* fout = static_cast<T*>(a.f[par ^ 1]);
+    const T* fin = static_cast<const T*>(par ? a.f[1] : a.f[0]);
+    T* fout = static_cast<T*>(par ? a.f[0] : a.f[1]);
     const size_t ps = (size_t)a.nx * a.ny;
     for (int tile = blockIdx.x; tile < a.ntiles; tile += gridDim.x) {
         const int y = tile / a.ntx;
@@ -111,21 +111,40 @@ struct RingRow {
 };
 
 // Issue the bulk copies of f* row `row` of tile `tile` into ring slot `slot` (warp 0 only).
-template <int NV>
+// A slot holds NV windows of WIN floats, then GX floats more.  With corrections (gcorr, GX =
+// 2 NV TW): the row's learned-closure corrections G[c][row][jx] at the tile's cells, unshifted,
+// as rows of TW floats ([c][jx][cell]); the tile's cells only (N_x a multiple of 4 keeps every
+// piece a multiple of 16 bytes).
+template <int NV, int GX = 0>
 __device__ __forceinline__ void issue_row(const Step2DArgs& a, const float* fin, float* ring,
-                                          uint64_t* bar, int slot, int tile, int row) {
+                                          uint64_t* bar, int slot, int tile, int row,
+                                          const float* gcorr = nullptr) {
     constexpr int J = (NV - 1) / 2;
+    constexpr size_t SL = (size_t)NV * WIN + GX;  // floats per slot
     const int lane = threadIdx.x & 31;
-    if (lane == 0) mbar_expect_tx(&bar[slot], (unsigned)(NV * WIN * sizeof(float)));
-    __syncwarp();
     const int y = tile / a.ntx;
     const int x0 = (tile % a.ntx) * TW;
+    const int ncx = min(TW, a.nx - x0);  // cells of the tile
+    unsigned bytes = (unsigned)(NV * WIN * sizeof(float));
+    if constexpr (GX > 0) bytes += (unsigned)(2 * NV * ncx * sizeof(float));
+    if (lane == 0) mbar_expect_tx(&bar[slot], bytes);
+    __syncwarp();
     const int ys = wrap(y - (row - J), a.ny);
+    if constexpr (GX > 0) {
+        const size_t ps = (size_t)a.nx * a.ny;
+        float* gdst = ring + (size_t)slot * SL + (size_t)NV * WIN;
+        for (int i = lane; i < 2 * NV; i += 32) {  // i = c NV + jx
+            const int cmp = i / NV, jx = i - cmp * NV;
+            const float* src =
+                gcorr + (size_t)cmp * NV * NV * ps + ((size_t)row * NV + jx) * ps + (size_t)y * a.nx + x0;
+            bulk_g2s(gdst + (size_t)i * TW, src, (unsigned)(ncx * sizeof(float)), &bar[slot]);
+        }
+    }
     for (int jx = lane; jx < NV; jx += 32) {
         const float* prow = fin + (((size_t)row * NV + jx) * a.ny + ys) * a.nx;
         const int s = x0 - (jx - J);
         const int base = wrap(s - ((s % 4) + 4) % 4, a.nx);
-        float* dst = ring + ((size_t)slot * NV + jx) * WIN;
+        float* dst = ring + (size_t)slot * SL + (size_t)jx * WIN;
         if (base + WIN <= a.nx) {
             bulk_g2s(dst, prow + base, WIN * sizeof(float), &bar[slot]);
         } else {
@@ -258,8 +277,8 @@ __global__ void __launch_bounds__(RingShape<NV, C>::threads, RingShape<NV, C>::m
     const long long step = a.st->step + kstep;
     const int par = (int)(step & 1);
     const float g = float(a.g), rr = float(a.r);
-    const float* fin = static_cast<const float*>(a.f[par]);
-    float* fout = static_cast<float*>(a.f[par ^ 1]);
+    const float* fin = static_cast<const float*>(par ? a.f[1] : a.f[0]);
+    float* fout = static_cast<float*>(par ? a.f[0] : a.f[1]);
     const size_t ps = (size_t)a.nx * a.ny;
     const int tid = threadIdx.x;
     const int cell = tid % TW;
@@ -364,10 +383,11 @@ __global__ void __launch_bounds__(RingShape<NV, C>::threads, RingShape<NV, C>::m
 // registers, which lowers register pressure and raises occupancy.
 // Producer warp of the producer/consumer kernels: fill f (row f % NV of the block's tile f / NV)
 // goes to slot f % NS once the consumers released that slot's previous content (fill f - NS).
-template <int NV, int NS, class TileOf>
+template <int NV, int NS, class TileOf, int GX = 0>
 __device__ __forceinline__ void produce_rows(const Step2DArgs& a, const float* fin, float* ring,
                                              uint64_t* full, uint64_t* empty, long long total,
-                                             const TileOf& tile_of) {
+                                             const TileOf& tile_of,
+                                             const float* gcorr = nullptr) {
     const int lane = threadIdx.x & 31;
     // a stalled context issues no copies: every consumer's bounded wait runs out
     const long long nfill = a.st->stall ? 0 : total;
@@ -378,7 +398,7 @@ __device__ __forceinline__ void produce_rows(const Step2DArgs& a, const float* f
             if (lane == 0) atomicOr(&a.st->status, ST_TIMEOUT);
             break;
         }
-        issue_row<NV>(a, fin, ring, full, q, tile_of(f), (int)(f % NV));
+        issue_row<NV, GX>(a, fin, ring, full, q, tile_of(f), (int)(f % NV), gcorr);
     }
     // the copies issued last must land before this warp leaves (the block may finish early)
     for (long long d = std::max(0ll, f - NS); d < f; ++d)
@@ -441,30 +461,48 @@ struct PCShape {
     static constexpr int min_blocks = HSM ? (NS == 2 ? 3 : 2) : ((GSM && NS == 3) ? 3 : 2);
 };
 
-template <int NV, int NS, bool GSM, bool HSM = false>
+template <int NV, int NS, bool GSM, bool HSM = false, int GX = 0>
 size_t pc_smem() {
-    return (size_t)NS * NV * WIN * sizeof(float) + (GSM ? (size_t)NV * TW * sizeof(float) : 0) +
+    return (size_t)NS * ((size_t)NV * WIN + GX) * sizeof(float) +
+           (GSM ? (size_t)NV * TW * sizeof(float) : 0) +
            (HSM ? (size_t)NV * TW * sizeof(float) : 0) + 2 * NS * sizeof(uint64_t);
 }
 
+// The corrections of one cell's row rb in the ring slot of f* row rb ([c][jx][cell] rows of TW,
+// see issue_row): gx(rb, jx) through face jx + 1/2, gy(rb, jx) through face rb + 1/2.
+template <int NV>
+struct RingCorr {
+    static constexpr bool active = true;
+    const float* p;  // slot's corrections + cell
+    template <typename T>
+    __device__ __forceinline__ T gx(int, int jx) const { return p[jx * TW]; }
+    template <typename T>
+    __device__ __forceinline__ T gy(int, int jx) const { return p[(NV + jx) * TW]; }
+};
+
 // HSM: the vy-diffusion flux row H in shared memory too (fewer registers, no spills).
 // MOM: the consumers also reduce the moments of the cells they write (Mom2DOut).
-template <int NV, int NS, bool GSM, bool HSM, bool MOM>
+// CORR: the learned closure's corrected step, the corrections G [2][N_v^2][N_y][N_x] added to
+// the interior drag fluxes (register rows only).
+template <int NV, int NS, bool GSM, bool HSM, bool MOM, bool CORR = false>
 __global__ void __launch_bounds__(PCShape<NV, NS, GSM, HSM>::threads,
                                   PCShape<NV, NS, GSM, HSM>::min_blocks)
-    k_step2d_pc(const Step2DArgs a, int kstep, const Mom2DOut m) {
+    k_step2d_pc(const Step2DArgs a, int kstep, const Mom2DOut m, const float* gcorr) {
+    static_assert(!CORR || (!GSM && !HSM && !MOM), "corrections with register rows only");
     constexpr int NC = PCShape<NV, NS, GSM, HSM>::consumers;
+    constexpr int GX = CORR ? 2 * NV * TW : 0;       // correction rows per ring slot
+    constexpr size_t SL = (size_t)NV * WIN + GX;  // floats per slot
     extern __shared__ __align__(128) unsigned char smem[];
     float* ring = reinterpret_cast<float*>(smem);
-    float* gsm = ring + (size_t)NS * NV * WIN;
+    float* gsm = ring + (size_t)NS * SL;
     float* hsm = gsm + (GSM ? NV * TW : 0);
     uint64_t* full = reinterpret_cast<uint64_t*>(hsm + (HSM ? NV * TW : 0));
     uint64_t* empty = full + NS;
     const long long step = a.st->step + kstep;
     const int par = (int)(step & 1);
     const float g = float(a.g), rr = float(a.r);
-    const float* fin = static_cast<const float*>(a.f[par]);
-    float* fout = static_cast<float*>(a.f[par ^ 1]);
+    const float* fin = static_cast<const float*>(par ? a.f[1] : a.f[0]);
+    float* fout = static_cast<float*>(par ? a.f[0] : a.f[1]);
     const size_t ps = (size_t)a.nx * a.ny;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int ntl = a.ntiles > (int)blockIdx.x ? (a.ntiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
@@ -479,7 +517,8 @@ __global__ void __launch_bounds__(PCShape<NV, NS, GSM, HSM>::threads,
     }
     __syncthreads();
     if (warp == NC) {
-        produce_rows<NV, NS>(a, fin, ring, full, empty, total, tile_of);
+        produce_rows<NV, NS, decltype(tile_of), GX>(a, fin, ring, full, empty, total, tile_of,
+                                                    gcorr);
         return;
     }
     const int cell = threadIdx.x;
@@ -514,11 +553,19 @@ __global__ void __launch_bounds__(PCShape<NV, NS, GSM, HSM>::threads,
                 break;
             }
             if (r >= 1) {
-                const RingRow<NV> cur{ring + (size_t)((s - 1) % NS) * NV * WIN + cell};
-                const RingRow<NV> nxt{ring + (size_t)(s % NS) * NV * WIN + cell};
-                if constexpr (HSM) sweep_row<float, NV>(A, Gs, Hs, r, cur, nxt, g, wx, wy, rr, put);
-                else if constexpr (GSM) sweep_row<float, NV>(A, Gs, Hreg, r, cur, nxt, g, wx, wy, rr, put);
-                else sweep_row<float, NV>(A, Greg, Hreg, r, cur, nxt, g, wx, wy, rr, put);
+                const RingRow<NV> cur{ring + (size_t)((s - 1) % NS) * SL + cell};
+                const RingRow<NV> nxt{ring + (size_t)(s % NS) * SL + cell};
+                if constexpr (CORR) {  // the corrections of row r - 1 came with its f* row
+                    const RingCorr<NV> rc{ring + (size_t)((s - 1) % NS) * SL +
+                                          (size_t)NV * WIN + cell};
+                    sweep_row<float, NV>(A, Greg, Hreg, r, cur, nxt, g, wx, wy, rr, put, rc);
+                } else if constexpr (HSM) {
+                    sweep_row<float, NV>(A, Gs, Hs, r, cur, nxt, g, wx, wy, rr, put);
+                } else if constexpr (GSM) {
+                    sweep_row<float, NV>(A, Gs, Hreg, r, cur, nxt, g, wx, wy, rr, put);
+                } else {
+                    sweep_row<float, NV>(A, Greg, Hreg, r, cur, nxt, g, wx, wy, rr, put);
+                }
                 __syncwarp();
                 if (lane == 0) mbar_arrive(&empty[(s - 1) % NS]);  // row s - 1 is done
             }
@@ -682,8 +729,8 @@ __global__ void __launch_bounds__(PC2Shape<NV, NS, GSM>::threads,
     const long long step = a.st->step + kstep;
     const int par = (int)(step & 1);
     const float g = float(a.g), rr = float(a.r);
-    const float* fin = static_cast<const float*>(a.f[par]);
-    float* fout = static_cast<float*>(a.f[par ^ 1]);
+    const float* fin = static_cast<const float*>(par ? a.f[1] : a.f[0]);
+    float* fout = static_cast<float*>(par ? a.f[0] : a.f[1]);
     const size_t ps = (size_t)a.nx * a.ny;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int ntl = a.ntiles > (int)blockIdx.x ? (a.ntiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
@@ -995,8 +1042,45 @@ cudaError_t launch_pc(int grid, const Step2DArgs& a, int k, cudaStream_t s,
         attr = true;
     }
     k_step2d_pc<NV, NS, GSM, HSM, MOM>
-        <<<grid, PCShape<NV, NS, GSM, HSM>::threads, bytes, s>>>(a, k, m);
+        <<<grid, PCShape<NV, NS, GSM, HSM>::threads, bytes, s>>>(a, k, m, nullptr);
     return cudaGetLastError();
+}
+
+// The learned closure's corrected step on the bulk-copy ring (kernel 3's shape: four slots,
+// register rows), as many resident blocks as fit.
+template <int NV>
+cudaError_t launch_pc_corr_t(int sm_count, const Step2DArgs& a, const float* G, int k,
+                             cudaStream_t s) {
+    static int occ = 0;
+    const size_t bytes = pc_smem<NV, 4, false, false, 2 * NV * TW>();
+    if (occ == 0) {
+        cudaError_t e = cudaFuncSetAttribute(k_step2d_pc<NV, 4, false, false, false, true>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)bytes);
+        if (e != cudaSuccess) return e;
+        int nb = 0;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+            &nb, k_step2d_pc<NV, 4, false, false, false, true>, PCShape<NV, 4, false, false>::threads,
+            bytes);
+        if (e != cudaSuccess) return e;
+        occ = nb > 0 ? nb : 1;
+    }
+    const int grid = std::max(1, std::min(a.ntiles, occ * sm_count));
+    k_step2d_pc<NV, 4, false, false, false, true>
+        <<<grid, PCShape<NV, 4, false, false>::threads, bytes, s>>>(a, k, Mom2DOut(), G);
+    return cudaGetLastError();
+}
+
+// The corrected step on the ring for the learned lattices it is built for (N_v = 9, 13, 17);
+// cudaErrorNotSupported otherwise.
+cudaError_t launch_corr_ring(int nv, int sm_count, const Step2DArgs& a, const float* G, int k,
+                             cudaStream_t s) {
+    switch (nv) {
+        case 9: return launch_pc_corr_t<9>(sm_count, a, G, k, s);
+        case 13: return launch_pc_corr_t<13>(sm_count, a, G, k, s);
+        case 17: return launch_pc_corr_t<17>(sm_count, a, G, k, s);
+        default: return cudaErrorNotSupported;
+    }
 }
 
 template <int NV, int NS, bool GSM, bool HSM = false, bool MOM = false>
@@ -1329,13 +1413,21 @@ LearnArgs learn_args(const Ctx2D* c, const void* f0, const void* f1, const DevSt
     return la;
 }
 
+// The corrected step of the learned closure: on the bulk-copy ring when the context's launch
+// uses the ring and the kernel is built for N_v, else with plain loads (the same bits).
+cudaError_t launch_corrected(const Ctx2D* c, const Step2DArgs& a, int k, cudaStream_t s) {
+    if (c->ring && ring_ok(c) && (c->nv == 9 || c->nv == 13 || c->nv == 17))
+        return launch_corr_ring(c->nv, c->sm_count, a, c->d_G, k, s);
+    return launch_step2d_corr(c->nv, c->sm_count, a, c->d_G, k, s);
+}
+
 // One learned step from the buffers of a (parity from a.st): flow, density, network, step.
 int enqueue_learned(Ctx2D* c, const Step2DArgs& a, int k, cudaStream_t s) {
     const LearnArgs la = learn_args(c, a.f[0], a.f[1], a.st);
     CK2(launch_rho_star(c->nv, la, k, s));
     if (c->learn == 2) CK2(launch_mlp_tc(c->nv, la, c->d_wtc, c->sm_count, k, s));
     else CK2(launch_mlp_f32(c->nv, la, k, s));
-    CK2(launch_step2d_corr(c->nv, c->sm_count, a, c->d_G, k, s));
+    CK2(launch_corrected(c, a, k, s));
     return LAT_OK;
 }
 
@@ -1973,7 +2065,7 @@ int ctx2d_learn_grad(Ctx2D* c, void* const f[2], int cur, int n, const float* ta
             if (launch_rho_star(c->nv, la, 0, s) != cudaSuccess ||
                 (c->learn == 2 ? launch_mlp_tc(c->nv, la, c->d_wtc, c->sm_count, 0, s)
                                : launch_mlp_f32(c->nv, la, 0, s)) != cudaSuccess ||
-                launch_step2d_corr(c->nv, c->sm_count, a, c->d_G, 0, s) != cudaSuccess)
+                launch_corrected(c, a, 0, s) != cudaSuccess)
                 fail(LAT_ECUDA);
         }
         if (rc != LAT_OK) break;

@@ -132,6 +132,20 @@ struct NoCorr {
     __device__ __forceinline__ T gy(int, int) const { return T(0); }
 };
 
+// The learned closure's corrections of one cell, G [2][N_v^2][N_y][N_x] FP32: the vx faces at
+// (plane, cell) from cx = G + cell, the vy faces from cy = G + N_v^2 N_x N_y + cell.
+struct GlobCorr {
+    static constexpr bool active = true;
+    const float* cx;
+    const float* cy;
+    size_t ps;
+    int nv;
+    template <typename T>
+    __device__ __forceinline__ T gx(int rb, int jx) const { return cx[(size_t)(rb * nv + jx) * ps]; }
+    template <typename T>
+    __device__ __forceinline__ T gy(int rb, int jx) const { return cy[(size_t)(rb * nv + jx) * ps]; }
+};
+
 // The output goes through `put`: put.begin(row) before output row `row`, then put(o) for
 // jx = 0..NV-1 in order (StorePut for FP32/FP64 storage).  G (vy-drag flux row) and H
 // (vy-diffusion flux row) are register arrays or per-thread shared-memory columns (SmemCol).

@@ -199,8 +199,8 @@ __global__ void __launch_bounds__(TW) k_step2d_plain_h(const Step2DHArgs ha, int
     const long long step = a.st->step + kstep;
     const int par = (int)(step & 1);
     const float g = float(a.g), rr = float(a.r);
-    const S* fin = static_cast<const S*>(a.f[par]);
-    S* fout = static_cast<S*>(a.f[par ^ 1]);
+    const S* fin = static_cast<const S*>(par ? a.f[1] : a.f[0]);
+    S* fout = static_cast<S*>(par ? a.f[0] : a.f[1]);
     const float* s_in = ha.sc[par];
     const float* s_out = ha.sc[par ^ 1];
     unsigned* m_out = ha.mx[par ^ 1];
@@ -426,8 +426,8 @@ __global__ void __launch_bounds__(PCHShape<NV, NS>::threads, PCHShape<NV, NS>::m
     const long long step = a.st->step + kstep;
     const int par = (int)(step & 1);
     const float g = float(a.g), rr = float(a.r);
-    const S* fin = static_cast<const S*>(a.f[par]);
-    S* fout = static_cast<S*>(a.f[par ^ 1]);
+    const S* fin = static_cast<const S*>(par ? a.f[1] : a.f[0]);
+    S* fout = static_cast<S*>(par ? a.f[0] : a.f[1]);
     const float* s_in = ha.sc[par];
     const float* s_out = ha.sc[par ^ 1];
     unsigned* m_out = ha.mx[par ^ 1];

@@ -127,6 +127,27 @@ def test_tensor_core_network_matches_oracle(lat, nx, ny, nv):
 
 
 @pytest.mark.parametrize("mode", [1, 2])
+@pytest.mark.parametrize("nx,ny,nv", [(256, 10, 9), (136, 6, 9), (264, 12, 17)])
+def test_corrected_step_on_the_ring_gives_the_plain_bits(lat, mode, nx, ny, nv):
+    """The corrected step on the bulk-copy ring (the default where N_x allows it) against the
+    plain-load corrected step (launch kernel 1): the same sweep with the same corrections,
+    including a ragged last tile."""
+    c = case(nx, ny, nv, 3, 31 + nv)
+    W = quantised_weights(9, 0.4)
+    out = []
+    for plain in (True, False):
+        lt = lattice(lat, c)
+        if plain:
+            lt.set_launch(kernel=1)
+        lt.learn(pack(W), mode)
+        lt.step(3)
+        assert lt.status() == 0
+        out.append(lt.state.cpu().numpy())
+        lt.close()
+    assert np.array_equal(out[0], out[1])
+
+
+@pytest.mark.parametrize("mode", [1, 2])
 def test_learned_step_keeps_mass(lat, mode):
     c = case(64, 32, 9, 20, 5)
     lt = lattice(lat, c)
