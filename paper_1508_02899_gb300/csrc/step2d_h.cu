@@ -22,10 +22,11 @@
 // velocity cell, so the reduced-precision store does not drift the mass: the mass drift stays
 // at the level of the FP32 arithmetic.
 //
-// Line maxima.  The step records max |stored value| per output line: a warp maximum (redux) per
-// value, then the block's maximum per line in shared memory (producer/consumer kernel) or a
-// global atomicMax per warp (plain kernel).  The producer/consumer kernel flushes a tile's
-// maxima to global memory with one atomicMax per line once all consumer warps are past it.
+// Line maxima.  Every step records max |stored value| per output line.  The plain kernel takes a
+// warp maximum (redux) per value and a global atomicMax per warp.  After the producer/consumer
+// kernel, k_linemax_step reads the stored output once more (2 bytes per cell) and reduces each
+// line; with |h S| = |h| S exactly for a power-of-two S, both give the same bits, and the
+// separate pass costs a fraction of the in-sweep reduction.
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 #include <math.h>
@@ -78,9 +79,9 @@ __global__ void __launch_bounds__(256) k_scale2d(const Step2DHArgs a, int kstep)
     constexpr int J = (NV - 1) / 2;
     const long long step = a.b.st->step + kstep;
     const int par = (int)(step & 1);
-    const unsigned* mxi = a.mx[par];
-    float* so = a.sc[par ^ 1];
-    unsigned* mxo = a.mx[par ^ 1];
+    const unsigned* mxi = (par ? a.mx[1] : a.mx[0]);
+    float* so = (par ? a.sc[0] : a.sc[1]);
+    unsigned* mxo = (par ? a.mx[0] : a.mx[1]);
     constexpr int NVP = nv_padded(NV);
     const int ny = a.b.ny;
     const long long nl = (long long)ny * NV * NVP;
@@ -201,9 +202,9 @@ __global__ void __launch_bounds__(TW) k_step2d_plain_h(const Step2DHArgs ha, int
     const float g = float(a.g), rr = float(a.r);
     const S* fin = static_cast<const S*>(par ? a.f[1] : a.f[0]);
     S* fout = static_cast<S*>(par ? a.f[0] : a.f[1]);
-    const float* s_in = ha.sc[par];
-    const float* s_out = ha.sc[par ^ 1];
-    unsigned* m_out = ha.mx[par ^ 1];
+    const float* s_in = (par ? ha.sc[1] : ha.sc[0]);
+    const float* s_out = (par ? ha.sc[0] : ha.sc[1]);
+    unsigned* m_out = (par ? ha.mx[0] : ha.mx[1]);
     const size_t ps = (size_t)a.nx * a.ny;
     bool bad = false;
     for (int tile = blockIdx.x; tile < a.ntiles; tile += gridDim.x) {
@@ -238,7 +239,7 @@ __global__ void __launch_bounds__(TW) k_step2d_plain_h(const Step2DHArgs ha, int
 // The FP32 producer/consumer design with 16-bit rows in the ring.  One producer warp bulk-copies,
 // per f* row, the shifted plane windows (16-byte aligned, split at the periodic wrap) and the
 // row's N_v decode scales (one aligned run); with the first row of a tile it also copies the
-// scales of the tile's N_v^2 output lines, and it flushes the line maxima of the tile two back.
+// scales of the tile's N_v^2 output lines.
 // Every copy of a row completes on that row's "full" mbarrier.  Four consumer warps sweep the
 // columns, the vy-drag flux row G in shared memory.
 template <int NV, int NS>
@@ -257,7 +258,7 @@ struct PCHLayout {
     static constexpr size_t gsm = (size_t)(HSM ? 2 : 1) * NV * TW * sizeof(float);
     static constexpr size_t dsc = (size_t)NS * NVP * sizeof(float);
     static constexpr size_t enc = ((size_t)2 * NLP + 15) / 16 * 16;  // exponent bytes
-    static constexpr size_t mxs = (size_t)2 * NLP * sizeof(unsigned);
+    static constexpr size_t mxs = 0;  // the line maxima come from k_linemax_step
     static constexpr size_t bars = (size_t)2 * NS * sizeof(uint64_t);
     static constexpr size_t o_gsm = ring;
     static constexpr size_t o_dsc = o_gsm + gsm;
@@ -279,6 +280,9 @@ struct RingRowH {
     }
 };
 
+// Output writer of the producer/consumer kernel.  The line maxima of what it writes are not
+// reduced here (a warp maximum and a shared atomic per value cost a quarter of the step): the
+// next launch, k_linemax_step, takes them from the stored output, the same values exactly.
 template <typename S, int NV>
 struct HalfPutS {
     S* out;
@@ -286,18 +290,14 @@ struct HalfPutS {
     bool active;
     const unsigned char* sc_tab;  // biased exponents of the tile's output scales [NV][NVP]
                                   // (shared memory; the scales are powers of two)
-    unsigned* mxs;                // the tile's line maxima [NV][NVP] (shared memory)
     Encoder<S> enc;
     S* p;
     const unsigned char* sp;
-    unsigned* mp;
-    __device__ __forceinline__ HalfPutS(S* out_, size_t ps, bool act, const unsigned char* e,
-                                        unsigned* m)
-        : out(out_), pstride(ps), active(act), sc_tab(e), mxs(m), p(out_), sp(e), mp(m) {}
+    __device__ __forceinline__ HalfPutS(S* out_, size_t ps, bool act, const unsigned char* e)
+        : out(out_), pstride(ps), active(act), sc_tab(e), p(out_), sp(e) {}
     __device__ __forceinline__ void begin(int row) {
         p = out + (size_t)row * NV * pstride;
         sp = sc_tab + row * nv_padded(NV);
-        mp = mxs + row * nv_padded(NV);
     }
     __device__ __forceinline__ void operator()(float o) {
         float back;
@@ -305,9 +305,6 @@ struct HalfPutS {
         ++sp;
         if (active) *p = h;
         p = next_plane(p, pstride);
-        const unsigned m = warp_max_abs(back, active);
-        if ((threadIdx.x & 31) == 0 && m) atomicMax(mp, m);
-        ++mp;
     }
 };
 
@@ -354,32 +351,17 @@ __device__ __forceinline__ void issue_row_h(const Step2DArgs& a, const S* fin, S
     }
 }
 
-// Producer warp of the 16-bit producer/consumer kernels (NT threads per block): fills the ring,
-// copies the scales, and flushes the tiles' line maxima (tile t - 2 when tile t starts, the last
-// two after every consumer is done).
-template <typename S, int NV, int NS, int NT, class TileOf>
+// Producer warp of the 16-bit producer/consumer kernels: fills the ring and copies the scales.
+template <typename S, int NV, int NS, class TileOf>
 __device__ __forceinline__ void produce_rows_h(const Step2DArgs& a, const S* fin, S* ring,
                                                uint64_t* full, uint64_t* empty, float* dsc,
                                                const float* s_in, const float* s_out,
-                                               unsigned char* enc,
-                                               unsigned* mxs, unsigned* m_out, int ntl,
+                                               unsigned char* enc, int ntl,
                                                const TileOf& tile_of) {
     constexpr int NLP = NV * nv_padded(NV);
     const int lane = threadIdx.x & 31;
     // a stalled context issues no copies: every consumer's bounded wait runs out
     const long long total = a.st->stall ? 0 : (long long)ntl * NV;
-    auto flush = [&](int t) {  // tile t's maxima to global memory; clear the buffer
-        const int yt = tile_of((long long)t * NV) / a.ntx;
-        unsigned* m = mxs + (t & 1) * NLP;
-        unsigned* g_row = m_out + (size_t)yt * NLP;
-        for (int i = lane; i < NLP; i += 32) {
-            const unsigned v = m[i];
-            if (v) atomicMax(&g_row[i], v);
-            m[i] = 0u;
-        }
-        __syncwarp();
-    };
-    int flushed = 0;  // tiles below this one are flushed
     long long f = 0;
     for (; f < total; ++f) {
         const int q = (int)(f % NS);
@@ -387,24 +369,15 @@ __device__ __forceinline__ void produce_rows_h(const Step2DArgs& a, const S* fin
             if (lane == 0) atomicOr(&a.st->status, ST_TIMEOUT);
             break;
         }
+        // the exponent table of tile t (written with its row 0) alternates between two
+        // buffers: every consumer released fill f - NS, a row of tile t - 1, so all of them are
+        // past tile t - 2, its previous user
         const int t = (int)(f / NV);
-        if (f % NV == 0 && t >= 2) {
-            // every consumer warp has released fill f - NS (a row of tile t - 1, NS <= NV), so
-            // all of them are past tile t - 2, the previous user of these buffers; the
-            // generic-proxy writes of the flush and the async copies below touch disjoint
-            // buffers (maxima vs scales)
-            flush(t - 2);
-            flushed = t - 1;
-        }
         issue_row_h<S, NV>(a, fin, ring, full, dsc, s_in, s_out, enc + (t & 1) * NLP, q,
                            tile_of(f), (int)(f % NV));
     }
     for (long long d = std::max(0ll, f - NS); d < f; ++d)
         mbar_wait_bounded(&full[d % NS], (unsigned)((d / NS) & 1));
-    // wait for the consumers, then flush the tiles not flushed yet
-    asm volatile("bar.sync 1, %0;" ::"r"(NT) : "memory");
-    for (int t = flushed; t < ntl; ++t)
-        if (t >= ntl - 2) flush(t);
 }
 
 template <typename S, int NV, int NS, bool HSM>
@@ -420,7 +393,6 @@ __global__ void __launch_bounds__(PCHShape<NV, NS>::threads, PCHShape<NV, NS>::m
     float* gsm = reinterpret_cast<float*>(smem + Lay::o_gsm);
     float* dsc = reinterpret_cast<float*>(smem + Lay::o_dsc);
     unsigned char* enc = smem + Lay::o_enc;
-    unsigned* mxs = reinterpret_cast<unsigned*>(smem + Lay::o_mxs);
     uint64_t* full = reinterpret_cast<uint64_t*>(smem + Lay::o_bar);
     uint64_t* empty = full + NS;
     const long long step = a.st->step + kstep;
@@ -428,14 +400,12 @@ __global__ void __launch_bounds__(PCHShape<NV, NS>::threads, PCHShape<NV, NS>::m
     const float g = float(a.g), rr = float(a.r);
     const S* fin = static_cast<const S*>(par ? a.f[1] : a.f[0]);
     S* fout = static_cast<S*>(par ? a.f[0] : a.f[1]);
-    const float* s_in = ha.sc[par];
-    const float* s_out = ha.sc[par ^ 1];
-    unsigned* m_out = ha.mx[par ^ 1];
+    const float* s_in = (par ? ha.sc[1] : ha.sc[0]);
+    const float* s_out = (par ? ha.sc[0] : ha.sc[1]);
     const size_t ps = (size_t)a.nx * a.ny;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int ntl = a.ntiles > (int)blockIdx.x ? (a.ntiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
     auto tile_of = [&](long long s) { return (int)(blockIdx.x + (s / NV) * gridDim.x); };
-    for (int i = threadIdx.x; i < 2 * NLP; i += blockDim.x) mxs[i] = 0u;
     if (threadIdx.x == 0) {
         for (int q = 0; q < NS; ++q) {
             mbar_init(&full[q], 1);
@@ -445,9 +415,8 @@ __global__ void __launch_bounds__(PCHShape<NV, NS>::threads, PCHShape<NV, NS>::m
     }
     __syncthreads();
     if (warp == NC) {
-        produce_rows_h<S, NV, NS, PCHShape<NV, NS>::threads>(a, fin, ring, full, empty, dsc, s_in,
-                                                              s_out, enc, mxs, m_out, ntl,
-                                                              tile_of);
+        produce_rows_h<S, NV, NS>(a, fin, ring, full, empty, dsc, s_in, s_out, enc, ntl,
+                                  tile_of);
         return;
     }
     const int cell = threadIdx.x;
@@ -470,8 +439,7 @@ __global__ void __launch_bounds__(PCHShape<NV, NS>::threads, PCHShape<NV, NS>::m
             else Hreg[j] = 0.f;
             Gs[j] = 0.f;
         }
-        HalfPutS<S, NV> put(fout + (size_t)y * a.nx + x, ps, active, enc + (lt & 1) * NLP,
-                            mxs + (lt & 1) * NLP);
+        HalfPutS<S, NV> put(fout + (size_t)y * a.nx + x, ps, active, enc + (lt & 1) * NLP);
         const long long s0 = (long long)lt * NV;
         for (int r = 0; r <= NV; ++r) {
             const long long s = s0 + r;
@@ -497,7 +465,6 @@ __global__ void __launch_bounds__(PCHShape<NV, NS>::threads, PCHShape<NV, NS>::m
     }
     if (failed && lane == 0) atomicOr(&a.st->status, ST_TIMEOUT);
     if (bad) atomicOr(&a.st->status, ST_OVERFLOW);
-    asm volatile("bar.sync 1, %0;" ::"r"(PCHShape<NV, NS>::threads) : "memory");
 }
 
 // ---- state conversion -------------------------------------------------------------------------
@@ -528,6 +495,39 @@ __global__ void __launch_bounds__(256) k_linemax(const T* f, const float* sc, un
             if (mx) mx[si] = m;
             if (scale_out) scale_out[si] = scale_for(m);
         }
+    }
+}
+
+// The line maxima of the output of step kstep of a batch (buffer, scales and maxima of parity
+// (step + kstep + 1) & 1), one warp per line, 16-byte loads (N_x a multiple of 8): the values
+// and bits of k_linemax.
+template <typename S>
+__global__ void __launch_bounds__(256) k_linemax_step(const Step2DHArgs ha, int kstep, int nv) {
+    const Step2DArgs& a = ha.b;
+    const bool par = ((a.st->step + kstep) & 1) != 0;
+    const S* f = static_cast<const S*>(par ? a.f[0] : a.f[1]);
+    const float* sc = par ? ha.sc[0] : ha.sc[1];
+    unsigned* mx = par ? ha.mx[0] : ha.mx[1];
+    const int nx = a.nx, ny = a.ny;
+    const long long nlines = (long long)nv * nv * ny;
+    constexpr int EL = 16 / (int)sizeof(S);
+    const int lane = threadIdx.x & 31;
+    const long long w0 = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
+    for (long long l = w0; l < nlines; l += nw) {
+        const uint4* row = reinterpret_cast<const uint4*>(f + (size_t)l * nx);
+        const size_t si = scale_index((int)(l / ny), (int)(l % ny), nv);
+        const float s = sc[si];
+        unsigned m = 0;
+        for (int c = lane; c < nx / EL; c += 32) {
+            const uint4 v = row[c];
+            const S* h = reinterpret_cast<const S*>(&v);
+#pragma unroll
+            for (int e = 0; e < EL; ++e)
+                m = max(m, __float_as_uint(fabsf(__fmul_rn(HTraits<S>::dec(h[e]), s))));
+        }
+        m = __reduce_max_sync(0xffffffffu, m);
+        if (lane == 0) mx[si] = m;
     }
 }
 
@@ -611,13 +611,26 @@ int occupancy_pch() {
     return nb;
 }
 
+template <typename S>
+cudaError_t launch_linemax_step(const Step2DHArgs& a, int k, int nv, cudaStream_t s) {
+    const long long nl = (long long)nv * nv * a.b.ny;
+    k_linemax_step<S><<<grid_for(nl * 32, 256), 256, 0, s>>>(a, k, nv);
+    return cudaGetLastError();
+}
+
+// The producer/consumer kernels, each followed by the line maxima of what it wrote.
 template <typename S, int NV>
 cudaError_t launch_h_t(int pcv, int grid, const Step2DHArgs& a, int k, cudaStream_t s) {
     if constexpr (LATH_PC(NV)) {
-        if (pcv == 4) return launch_pch<S, NV, 4>(grid, a, k, s);
-        if (pcv == 5) return launch_pch<S, NV, 3>(grid, a, k, s);
-        if (pcv == 6) return launch_pch<S, NV, 3, true>(grid, a, k, s);
-        if (pcv == 7) return launch_pch<S, NV, 2, true>(grid, a, k, s);
+        cudaError_t e = cudaErrorInvalidValue;
+        if (pcv == 4) e = launch_pch<S, NV, 4>(grid, a, k, s);
+        else if (pcv == 5) e = launch_pch<S, NV, 3>(grid, a, k, s);
+        else if (pcv == 6) e = launch_pch<S, NV, 3, true>(grid, a, k, s);
+        else if (pcv == 7) e = launch_pch<S, NV, 2, true>(grid, a, k, s);
+        if (pcv >= 4 && pcv <= 7) {
+            if (e != cudaSuccess) return e;
+            return launch_linemax_step<S>(a, k, NV, s);
+        }
     }
     if (pcv == 0) {
         k_step2d_plain_h<S, NV><<<grid, TW, 0, s>>>(a, k);
