@@ -124,7 +124,16 @@ struct Encoder {
     bool bad = false;
     // returns the stored value; *back = its decoded value
     __device__ __forceinline__ S operator()(float o, float inv, float* back) {
-        const float sc = pow2_inv(inv);
+        return code(o, inv, pow2_inv(inv), back, true);
+    }
+    // the same from the scale's biased exponent e (S = 2^(e - 127)), without the overflow test:
+    // a value out of the format is an infinite code, which the line maxima of the stored
+    // output show (k_linemax_step)
+    __device__ __forceinline__ S from_exponent(float o, unsigned e, float* back) {
+        const unsigned sb = e << 23;
+        return code(o, __uint_as_float((254u << 23) - sb), __uint_as_float(sb), back, false);
+    }
+    __device__ __forceinline__ S code(float o, float inv, float sc, float* back, bool test) {
         const float lim = __fmul_rn(HTraits<S>::kCarryLim, sc);
         const float used = fminf(fmaxf(carry, -lim), lim);
         const float t = __fadd_rn(o, used);
@@ -132,7 +141,7 @@ struct Encoder {
         const float hd = HTraits<S>::dec(h);
         *back = __fmul_rn(hd, sc);
         carry = __fadd_rn(__fsub_rn(t, *back), __fsub_rn(carry, used));
-        bad |= !(fabsf(hd) <= HTraits<S>::kMax);
+        if (test) bad |= !(fabsf(hd) <= HTraits<S>::kMax);
         return h;
     }
 };
@@ -301,7 +310,7 @@ struct HalfPutS {
     }
     __device__ __forceinline__ void operator()(float o) {
         float back;
-        const S h = enc(o, pow2_inv(__int_as_float((int)((unsigned)*sp << 23))), &back);
+        const S h = enc.from_exponent(o, *sp, &back);
         ++sp;
         if (active) *p = h;
         p = next_plane(p, pstride);
@@ -420,7 +429,7 @@ __global__ void __launch_bounds__(PCHShape<NV, NS>::threads, PCHShape<NV, NS>::m
         return;
     }
     const int cell = threadIdx.x;
-    bool failed = false, bad = false;
+    bool failed = false;
     for (int lt = 0; lt < ntl && !failed; ++lt) {
         const int tile = tile_of((long long)lt * NV);
         const int y = tile / a.ntx;
@@ -461,10 +470,9 @@ __global__ void __launch_bounds__(PCHShape<NV, NS>::threads, PCHShape<NV, NS>::m
             if constexpr (HSM) final_row<float, NV>(A, Hs, rr, put);
             else final_row<float, NV>(A, Hreg, rr, put);
         }
-        bad |= put.enc.bad && active;
     }
     if (failed && lane == 0) atomicOr(&a.st->status, ST_TIMEOUT);
-    if (bad) atomicOr(&a.st->status, ST_OVERFLOW);
+    // encoder overflows show as infinite line maxima: k_linemax_step reports them
 }
 
 // ---- state conversion -------------------------------------------------------------------------
@@ -527,7 +535,12 @@ __global__ void __launch_bounds__(256) k_linemax_step(const Step2DHArgs ha, int 
                 m = max(m, __float_as_uint(fabsf(__fmul_rn(HTraits<S>::dec(h[e]), s))));
         }
         m = __reduce_max_sync(0xffffffffu, m);
-        if (lane == 0) mx[si] = m;
+        if (lane == 0) {
+            mx[si] = m;
+            // an infinite or NaN stored value on this line: the encoder's overflow (the test
+            // the plain kernel's encoder makes per value)
+            if (m >= 0x7f800000u) atomicOr(&a.st->status, ST_OVERFLOW);
+        }
     }
 }
 
