@@ -216,7 +216,7 @@ def test_long_run_against_fp64(lat, fmt):
     code, rho, _, _, g16 = lt.moments()
     code64, rho64, _, _, g64 = l64.moments()
     assert code == 0 and code64 == 0
-    # the FP64 run that judges the 16-bit one is itself the oracle's, at 1e-12
+    # the FP64 run the 16-bit one is measured against matches the oracle at 1e-12
     want, _ = O.run_2d(x0.astype(np.float64), 100, tau_p=c["tau_p"], kappa=c["kappa"],
                        dt=c["dt"], dv=c["dv"], dx=c["dx"], kvec=fl.kvec, a=fl.a, phi0=fl.phi0,
                        tau_f=fl.tau_f, noise=fl.noise)
