@@ -54,11 +54,12 @@ struct Flow2DArgs {
     double* phase;            // [2][M] parity-indexed phases
     const double* noise;      // [rows][M] in the caller's mode order
     const int* perm;          // [M] caller's index of mode m (modes are kept sorted by kx)
+    const int* runs;          // [nruns + 1][2]: first mode and kx of each run of equal kx
     double walk;              // sqrt(2 dt / tau_f)
     const void* xtab;         // [2 kmax+1][nx][2] of T
     const void* ytab;         // [2 kmax+1][ny][2] of T
     int kmax;
-    int nmodes, nx, ny;
+    int nmodes, nx, ny, nruns;
     void* u;                  // [2][ny][nx] of T
     DevState* st;
     int frozen, dry;
@@ -625,10 +626,21 @@ __device__ __forceinline__ void flow_modes_prepare(const Flow2DArgs& a, long lon
     const int par = (int)(step & 1);
     const double* ph = a.phase + (size_t)par * M;
     for (int m = t; m < M; m += nt) {
-        double s, c;
-        sincos(ph[m], &s, &c);
-        sh[m] = T(c);
-        sh[M + m] = T(s);
+        if constexpr (sizeof(T) == 4) {
+            // FP32 terms: the FP64 phase reduced to [-pi, pi] in FP64, then sincosf (FP64
+            // arithmetic runs at a small fraction of FP32's here)
+            constexpr double kTwoPi = 6.283185307179586;
+            const double q = rint(__dmul_rn(ph[m], 1.0 / kTwoPi));
+            float sf, cf;
+            sincosf((float)__fma_rn(-q, kTwoPi, ph[m]), &sf, &cf);
+            sh[m] = T(cf);
+            sh[M + m] = T(sf);
+        } else {
+            double sd, cd;
+            sincos(ph[m], &sd, &cd);
+            sh[m] = T(cd);
+            sh[M + m] = T(sd);
+        }
     }
     if (writer && !a.frozen && !a.dry) {
         const long long row = step - a.st->noise_base;
@@ -645,8 +657,8 @@ __device__ __forceinline__ void flow_modes_prepare(const Flow2DArgs& a, long lon
 // 2 pi (kx x / nx + ky y / ny) + phi_m.  With e^{i theta} = X_kx(x) Y_ky(y) e^{i phi} from the
 // separable tables, sin(theta) = Im(X w), w = Y e^{i phi}: one block per row y forms
 // W_m = (c_x w, c_y w) for every mode in shared memory, then each thread sums over the modes for
-// its cells with four FMAs per mode.  Modes are sorted by kx, so a thread loads X_kx(x) once per
-// distinct kx.  Explicit rounding throughout.
+// its cells with four FMAs per mode.  Modes are sorted by kx and taken run by run (runs of equal
+// kx), so a thread loads X_kx(x) once per run.  Explicit rounding throughout.
 template <typename T>
 __global__ void __launch_bounds__(256) k_flow2d(const Flow2DArgs a, int kstep) {
     using O = Ops<T>;
@@ -676,19 +688,17 @@ __global__ void __launch_bounds__(256) k_flow2d(const Flow2DArgs a, int kstep) {
         }
         __syncthreads();
         for (int x = threadIdx.x; x < a.nx; x += blockDim.x) {
-            T ux = T(0), uy = T(0), X0 = T(0), X1 = T(0);
-            int kxc = 0x7fffffff;
-            for (int m = 0; m < M; ++m) {
-                const int kx = a.k[m].x;
-                if (kx != kxc) {
-                    kxc = kx;
-                    const T* X = xt + 2 * ((size_t)(kx + a.kmax) * a.nx + x);
-                    X0 = X[0];
-                    X1 = X[1];
+            T ux = T(0), uy = T(0);
+            for (int q = 0; q < a.nruns; ++q) {
+                const int m0 = a.runs[2 * q], m1 = a.runs[2 * q + 2], kx = a.runs[2 * q + 1];
+                const T* X = xt + 2 * ((size_t)(kx + a.kmax) * a.nx + x);
+                const T X0 = X[0], X1 = X[1];
+#pragma unroll 4
+                for (int m = m0; m < m1; ++m) {
+                    // Im(X w) (c_x, c_y) = X_re (c w_im) + X_im (c w_re)
+                    ux = O::fma(X0, W[4 * m + 1], O::fma(X1, W[4 * m], ux));
+                    uy = O::fma(X0, W[4 * m + 3], O::fma(X1, W[4 * m + 2], uy));
                 }
-                // Im(X w) (c_x, c_y) = X_re (c w_im) + X_im (c w_re)
-                ux = O::fma(X0, W[4 * m + 1], O::fma(X1, W[4 * m], ux));
-                uy = O::fma(X0, W[4 * m + 3], O::fma(X1, W[4 * m + 2], uy));
             }
             u[(size_t)y * a.nx + x] = ux;
             u[ncell + (size_t)y * a.nx + x] = uy;
@@ -1229,6 +1239,8 @@ struct Ctx2D {
     int nmodes = 0;
     int2* d_k = nullptr;      // modes sorted by kx (see k_flow2d)
     int* d_perm = nullptr;    // caller's index of each mode (noise columns)
+    int* d_runs = nullptr;    // runs of equal kx among the sorted modes ([nruns + 1][2])
+    int nruns = 0;
     double* d_cx = nullptr;
     double* d_cy = nullptr;
     double* d_phase = nullptr;
@@ -1366,6 +1378,8 @@ Flow2DArgs flow_args(const Ctx2D* c, int dry) {
     Flow2DArgs fa;
     fa.k = c->d_k;
     fa.perm = c->d_perm;
+    fa.runs = c->d_runs;
+    fa.nruns = c->nruns;
     fa.cx = c->d_cx;
     fa.cy = c->d_cy;
     fa.phase = c->d_phase;
@@ -1582,6 +1596,20 @@ int ctx2d_set_flow(Ctx2D* c, const lat_flow* fl, bool frozen, cudaStream_t s) {
         c->d_perm = nullptr;
         if (cudaMalloc(&c->d_perm, sizeof(int) * M) != cudaSuccess) return LAT_ENOMEM;
         CK2(cudaMemcpy(c->d_perm, perm.data(), sizeof(int) * M, cudaMemcpyHostToDevice));
+        // runs of equal kx: [first mode, kx] per run, then [M, 0]
+        std::vector<int> runs;
+        for (int m = 0; m < M; ++m)
+            if (m == 0 || k[m].x != k[m - 1].x) {
+                runs.push_back(m);
+                runs.push_back(k[m].x);
+            }
+        c->nruns = (int)runs.size() / 2;
+        runs.push_back(M);
+        runs.push_back(0);
+        cudaFree(c->d_runs);
+        c->d_runs = nullptr;
+        if (cudaMalloc(&c->d_runs, sizeof(int) * runs.size()) != cudaSuccess) return LAT_ENOMEM;
+        CK2(cudaMemcpy(c->d_runs, runs.data(), sizeof(int) * runs.size(), cudaMemcpyHostToDevice));
         if (cudaMalloc(&c->d_k, sizeof(int2) * M) != cudaSuccess ||
             cudaMalloc(&c->d_cx, sizeof(double) * M) != cudaSuccess ||
             cudaMalloc(&c->d_cy, sizeof(double) * M) != cudaSuccess ||
@@ -2121,6 +2149,7 @@ void ctx2d_destroy(Ctx2D* c) {
     drop(c);
     cudaFree(c->d_k);
     cudaFree(c->d_perm);
+    cudaFree(c->d_runs);
     cudaFree(c->d_cx);
     cudaFree(c->d_cy);
     cudaFree(c->d_phase);
