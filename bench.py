@@ -722,7 +722,7 @@ def main():
         forms["2d_learned_2048x2048_9x9"] = {
             "gcups": c2 * 20 / (ms2 / 1e3) / 1e9, "ms_per_step": ms2 / 20,
             "network_ms": net_ms, "network_tflops": tf, "network_frac_bf16": tf / tpeak,
-            "kernel": "k_mlp_tc<9> + k_step2d_corr<9>", "steps": 20, "status": st2}
+            "kernel": "k_mlp_tc<9> + k_step2d_pc<9,4,0,0,0,1>", "steps": 20, "status": st2}
         lt.close()
         del lt
         torch.cuda.empty_cache()
