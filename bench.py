@@ -600,7 +600,7 @@ def main():
         tf = flops / (net_ms / 1e3) / 1e12
         roof = {"bound": "tensor", "achieved": tf, "peak": tpeak, "unit": "TFLOP/s",
                 "frac": tf / tpeak, "traffic": None, "peak_source": tsrc,
-                "kernel": "k_mlp_tc<9>", "flop_per_launch": flops, "ms_per_launch": net_ms}
+                "kernel": "k_mlp_tc_units<9>", "flop_per_launch": flops, "ms_per_launch": net_ms}
     tr = profile_traffic(prof, src)
     traffic = None
     if tr is not None:
@@ -722,7 +722,7 @@ def main():
         forms["2d_learned_2048x2048_9x9"] = {
             "gcups": c2 * 20 / (ms2 / 1e3) / 1e9, "ms_per_step": ms2 / 20,
             "network_ms": net_ms, "network_tflops": tf, "network_frac_bf16": tf / tpeak,
-            "kernel": "k_mlp_tc<9> + k_step2d_pc<9,4,0,0,0,1>", "steps": 20, "status": st2}
+            "kernel": "k_mlp_tc_units<9> + k_step2d_pc<9,4,0,0,0,1>", "steps": 20, "status": st2}
         lt.close()
         del lt
         torch.cuda.empty_cache()

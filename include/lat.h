@@ -275,6 +275,10 @@ long long lat_steps_done(const lat_ctx* c);
  *          d = 2 with the flux-limited scheme (lat_set_scheme): 1 three passes over the state
  *                 (any N_v); 2 one fused kernel per step (N_v >= 5; the default where it
  *                 exists).  Same bits up to the sign of zero values.
+ *          d = 2 with the learned closure on the tensor cores (lat_learn mode 2): with a copy
+ *                 pipeline and N_x a multiple of 128 the network takes all velocity planes of
+ *                 128 x of one grid row in turn; with kernel 1 it takes tiles of 128 phase cells
+ *                 in storage order.  Same bits.
  *  block:  threads per block (= x cells per tile) for kernel 1; the copy pipelines fix a 128-cell
  *          tile (2D kernel 2: 128 C threads); 0 keeps.
  *  blocks_per_sm: resident blocks per SM of the persistent grid; 0 keeps.  The fused

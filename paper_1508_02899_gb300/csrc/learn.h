@@ -66,12 +66,15 @@ bool learn_nv_supported(int nv);
 cudaError_t launch_rho_star(int nv, const LearnArgs& a, int k, cudaStream_t s);
 cudaError_t launch_mlp_f32(int nv, const LearnArgs& a, int k, cudaStream_t s);
 // The same network in BF16 on the tensor cores (tcgen05, FP32 accumulation in TMEM), from the
-// parameter tiles that launch_learn_tc_pack builds from the FP32 parameters.
+// parameter tiles that launch_learn_tc_pack builds from the FP32 parameters.  With `units` and
+// N_x a multiple of 128 a CTA takes all planes of 128 x of one grid row in turn, sliding the
+// velocity neighbourhood of f* from plane to plane; otherwise tiles of 128 phase cells in
+// storage order.  Both give the same bits.
 bool learn_tc_supported(int nv);
 size_t learn_tc_bytes();
 cudaError_t launch_learn_tc_pack(const float* params, void* wtc, cudaStream_t s);
-cudaError_t launch_mlp_tc(int nv, const LearnArgs& a, const void* wtc, int sm_count, int k,
-                          cudaStream_t s);
+cudaError_t launch_mlp_tc(int nv, const LearnArgs& a, const void* wtc, int sm_count, bool units,
+                          int k, cudaStream_t s);
 // The plain 2D FP32 step (Step2DArgs) with the corrections G added to the drag fluxes, on a
 // persistent grid of as many blocks as are resident on sm_count SMs.
 cudaError_t launch_step2d_corr(int nv, int sm_count, const k2d::Step2DArgs& a, const float* G,

@@ -9,6 +9,11 @@
 // (K = 80, N = 16 with two live outputs) the same way; the bounded outputs y = b tanh(z) times
 // the density differences across the +jx and +jy faces are the corrections.
 //
+// Tile order: with N_x a multiple of 128 a CTA takes units of 128 x of one grid row, all N_v^2
+// planes of a unit in turn, and keeps the 3 x 3 velocity neighbourhood of f* in registers as it
+// slides from plane to plane (UnitFeed); otherwise tiles of 128 phase cells in storage order,
+// each gathering its nine neighbours (StorageFeed).
+//
 // Biases ride in the products: feature 15 is the constant 1, so b1 joins row 15 of W1; the
 // activation tiles carry a constant 1 in column 64 (columns 65..79 zero, K padded to a multiple
 // of 16), so b2 and b3 join row 64 of W2 and W3.  The three layers share one 64-column TMEM
@@ -225,32 +230,203 @@ __device__ __forceinline__ void features_of(const LearnArgs& a, const Raw& r, in
     X[15] = 1.f;
 }
 
-// Division of 32-bit unsigned n by a divisor d fixed at launch, by one high multiply (Granlund and
-// Montgomery's round-up method): with l = ceil(log2 d) and m = floor(2^32 (2^l - d) / d) + 1,
-// n / d = (mulhi(m, n) + n) >> l, the sum formed in 64 bits.
-struct FastDiv {
-    unsigned m;
-    int l;
-    unsigned d;
-};
-FastDiv fast_div(unsigned d) {
-    int l = 0;
-    while ((1ull << l) < d) ++l;
-    const unsigned long long m = ((1ull << 32) * ((1ull << l) - d)) / d + 1;
-    return FastDiv{(unsigned)m, l, d};
-}
-__device__ __forceinline__ unsigned fdiv(unsigned n, const FastDiv& f) {
-    return (unsigned)(((unsigned long long)__umulhi(f.m, n) + n) >> f.l);
+// The corrections of one phase cell: the outputs y = b tanh(z), with b the bound for z's sign,
+// times the differences of f* across the cell's +jx and +jy faces (zero at the upper walls).
+template <int NV>
+__device__ __forceinline__ void write_corrections(const LearnArgs& a, unsigned n, unsigned i,
+                                                  int jx, int jy, float c13, float c14, float f0,
+                                                  float fx, float fy, float z0, float z1) {
+    const float y0 = __fmul_rn(z0 > 0.f ? anti_bound(c13, a.g) : kYMax, tanh_fast(z0));
+    const float y1 = __fmul_rn(z1 > 0.f ? anti_bound(c14, a.g) : kYMax, tanh_fast(z1));
+    a.G[i] = jx < NV - 1 ? __fmul_rn(y0, __fsub_rn(fx, f0)) : 0.f;
+    a.G[(size_t)n + i] = jy < NV - 1 ? __fmul_rn(y1, __fsub_rn(fy, f0)) : 0.f;
 }
 
-// Tiles: with N_x a multiple of 128, tile t covers 128 consecutive x of one spatial row in plane
-// t mod N_v^2 (planes fastest), so that the velocity neighbours a tile gathers were just loaded
-// by the tiles of the neighbouring planes; nbx = N_x / 128.  Otherwise tiles run through the
-// phase cells in their storage order.
+// ---- tile sources -----------------------------------------------------------------------------
+// A feed hands a CTA its tiles in order.  load() issues the global loads of the next tile (while
+// the tensor cores work on the current one); features() forms that tile's 16 features, which
+// run_network stores into A1; out() writes the corrections of a finished tile.  A Slot carries
+// one tile from load() to out(); `valid` (the tile exists) is the same for every thread of the
+// CTA.
+
+// Tiles of 128 phase cells in storage order: tile b, b + G, b + 2G, ... for CTA b of G.  Any N_x;
+// the last tile may be ragged.
 template <int NV>
-__global__ void __launch_bounds__(128) k_mlp_tc(const LearnArgs a, const unsigned char* image,
-                                                int kstep, const FastDiv nbx) {
-    extern __shared__ __align__(1024) unsigned char sm[];
+struct StorageFeed {
+    struct Slot {
+        Raw r;
+        unsigned i;
+        int jx, jy;
+        bool valid, on;
+        float c13, c14;  // features 13 and 14, which bound the outputs
+    };
+    const LearnArgs& a;
+    const float* f;
+    unsigned n, ncell;
+    long long tile, ntiles;  // the next tile to load
+    int t;
+
+    __device__ StorageFeed(const LearnArgs& a_, const float* f_, int t_)
+        : a(a_), f(f_), t(t_) {
+        ncell = (unsigned)a.nx * (unsigned)a.ny;
+        n = ncell * (unsigned)(NV * NV);
+        ntiles = ((long long)n + 127) / 128;
+        tile = blockIdx.x;
+    }
+    __device__ __forceinline__ void load(Slot& q) {
+        const long long i = tile * 128 + t;
+        q.valid = tile < ntiles;
+        q.on = q.valid && i < (long long)n;
+        q.jx = q.jy = 0;
+        q.i = (unsigned)i;
+        if (q.on) {
+            int p, x, y;
+            split_index((unsigned)i, ncell, (unsigned)a.nx, p, x, y);
+            q.jy = p / NV;
+            q.jx = p % NV;
+            load_raw<NV>(a, f, q.jx, q.jy, x, y, q.r);
+        }
+        tile += gridDim.x;
+    }
+    __device__ __forceinline__ void features(Slot& q, float (&X)[kLNF]) {
+        if (q.on) {
+            features_of<NV>(a, q.r, q.jx, q.jy, X);
+        } else {
+#pragma unroll
+            for (int k = 0; k < kLNF; ++k) X[k] = 0.f;
+        }
+        q.c13 = X[13];
+        q.c14 = X[14];
+    }
+    __device__ __forceinline__ void out(const Slot& q, float z0, float z1) {
+        // f* of the cell and of its +jx, +jy neighbours: entries 4, 5 and 7 of the 3 x 3 block
+        if (q.on) write_corrections<NV>(a, n, q.i, q.jx, q.jy, q.c13, q.c14, q.r.fs[4],
+                                        q.r.fs[5], q.r.fs[7], z0, z1);
+    }
+};
+
+// With N_x a multiple of 128: units of 128 consecutive x of one grid row, unit b, b + G, ... for
+// CTA b of G, each taken as its N_v^2 planes in storage order (jx fastest), one tile per plane.
+// Along a plane row the 3 x 3 velocity neighbourhood of f* slides by one column per tile, so a
+// tile loads one new column (three values; two columns at the start of a row) where a tile in
+// storage order gathers all nine, and the spatial part of the features is loaded once per unit.
+// The features, and so every correction, have the same bits as in storage order.
+template <int NV>
+struct UnitFeed {
+    static constexpr int J = (NV - 1) / 2;
+    static constexpr int NN = NV * NV;
+    struct Slot {
+        unsigned i;
+        int jx, jy;
+        bool valid;
+        float c13, c14;    // features 13 and 14, which bound the outputs
+        float f0, fx, fy;  // f* of the cell and of its +jx and +jy neighbours
+    };
+    const LearnArgs& a;
+    const float* f;
+    unsigned nx, ny, ncell, n, nbx, nunits;
+    unsigned unit;     // unit of the next tile to load
+    int p;             // its plane
+    unsigned x, y;     // this thread's spatial cell in that unit
+    unsigned roff[3];  // source rows y - (jy2 - J), wrapped, times N_x, for jy2 = jy - 1 .. jy + 1
+    float w[3][3];     // f* at (jy - 1 .. jy + 1, jx - 1 .. jx + 1) of the tile staged last
+    float in[2][3];    // columns loaded for the next tile: jx and jx + 1 at a row start, else jx + 1
+    float4 fa, fb;     // spatial features of this thread's cell in the unit loaded last
+    int t;
+
+    __device__ UnitFeed(const LearnArgs& a_, const float* f_, int t_) : a(a_), f(f_), t(t_) {
+        nx = (unsigned)a.nx;
+        ny = (unsigned)a.ny;
+        ncell = nx * ny;
+        n = ncell * (unsigned)NN;
+        nbx = nx / 128;
+        nunits = ny * nbx;
+        unit = blockIdx.x;
+        p = 0;
+        x = y = 0;
+    }
+    // column jx2 of the 3 x 3 block of plane row jy (zero outside the velocity box)
+    __device__ __forceinline__ void column(int jy, int jx2, float (&v)[3]) const {
+        const unsigned xs = (unsigned)wrap_near((int)x - (jx2 - J), (int)nx);
+#pragma unroll
+        for (int r = 0; r < 3; ++r) {
+            const int jy2 = jy - 1 + r;
+            v[r] = (jx2 < NV && jy2 >= 0 && jy2 < NV)
+                       ? f[(unsigned)(jy2 * NV + jx2) * ncell + roff[r] + xs]
+                       : 0.f;
+        }
+    }
+    __device__ __forceinline__ void load(Slot& q) {
+        q.valid = unit < nunits;
+        if (!q.valid) return;
+        const int jy = p / NV, jx = p - jy * NV;
+        q.jx = jx;
+        q.jy = jy;
+        if (p == 0) {  // a new unit: its spatial cell and features
+            y = unit / nbx;
+            x = (unit - y * nbx) * 128u + (unsigned)t;
+            const unsigned c = y * nx + x;
+            fa = a.feat[2 * c];
+            fb = a.feat[2 * c + 1];
+        }
+        if (jx == 0) {  // a new plane row: its source rows and the first two columns
+#pragma unroll
+            for (int r = 0; r < 3; ++r)
+                roff[r] = (unsigned)wrap_near((int)y - (jy - 1 + r - J), (int)ny) * nx;
+            column(jy, 0, in[0]);
+            column(jy, 1, in[1]);
+        } else {
+            column(jy, jx + 1, in[1]);
+        }
+        q.i = (unsigned)p * ncell + y * nx + x;
+        if (++p == NN) {
+            p = 0;
+            unit += gridDim.x;
+        }
+    }
+    __device__ __forceinline__ void features(Slot& q, float (&X)[kLNF]) {
+        if (!q.valid) {
+#pragma unroll
+            for (int k = 0; k < kLNF; ++k) X[k] = 0.f;
+            return;
+        }
+#pragma unroll
+        for (int r = 0; r < 3; ++r) {
+            if (q.jx == 0) {
+                w[r][0] = 0.f;
+                w[r][1] = in[0][r];
+            } else {
+                w[r][0] = w[r][1];
+                w[r][1] = w[r][2];
+            }
+            w[r][2] = in[1][r];
+        }
+        Raw raw;
+#pragma unroll
+        for (int r = 0; r < 3; ++r)
+#pragma unroll
+            for (int c = 0; c < 3; ++c) raw.fs[3 * r + c] = w[r][c];
+        raw.fa = fa;
+        raw.fb = fb;
+        features_of<NV>(a, raw, q.jx, q.jy, X);
+        q.c13 = X[13];
+        q.c14 = X[14];
+        q.f0 = w[1][1];
+        q.fx = w[1][2];
+        q.fy = w[2][1];
+    }
+    __device__ __forceinline__ void out(const Slot& q, float z0, float z1) {
+        if (q.valid)
+            write_corrections<NV>(a, n, q.i, q.jx, q.jy, q.c13, q.c14, q.f0, q.fx, q.fy, z0, z1);
+    }
+};
+
+// The network over a CTA's tiles from a feed.  Per tile, the MMAs of the current tile (features
+// already in A1) run while the feed loads and stages the next; two slots alternate, so nothing
+// is copied between tiles.
+template <class Feed>
+__device__ __forceinline__ void run_network(Feed& feed, unsigned char* sm,
+                                            const unsigned char* image, const LearnArgs& a) {
     unsigned char* W = sm;
     unsigned char* A1 = sm + kSA1;
     unsigned char* A2 = sm + kSA2;
@@ -284,58 +460,19 @@ __global__ void __launch_bounds__(128) k_mlp_tc(const LearnArgs a, const unsigne
     const unsigned tmem = *tslot;
     const unsigned trow = tmem + ((unsigned)(warp * 32) << 16);  // this warp's lanes
     const unsigned wbase = su32(W), a1 = su32(A1), a2 = su32(A2);
-    const float* f = a.f[(int)((a.st->step + kstep) & 1)];
-    const long long ncell = (long long)a.nx * a.ny;
-    const long long n = ncell * NV * NV;
-    const long long ntiles = (n + 127) / 128;
     unsigned phase = 0;
-    bool failed = false;
-    const bool row_tiles = a.nx % 128 == 0;
-    // One tile's cell for this thread: raw inputs loaded early, features formed late.
-    struct Cell {
-        Raw r;
-        int jx, jy;
-        long long i;
-        bool on;
-    };
-    auto load = [&](long long tile, Cell& q) {
-        q.i = tile * 128 + t;
-        q.on = tile < ntiles && q.i < n;
-        q.jx = q.jy = 0;
-        if (q.on) {
-            int p, x, y;
-            if (row_tiles) {  // the tile is 128 consecutive x of one row of one plane
-                constexpr unsigned NN = NV * NV;
-                p = (int)((unsigned)tile % NN);
-                const unsigned rb = (unsigned)tile / NN;
-                const unsigned yy = fdiv(rb, nbx);
-                y = (int)yy;
-                x = (int)((rb - yy * nbx.d) * 128u) + t;
-                q.i = (long long)p * ncell + (long long)y * a.nx + x;
-            } else {
-                split_index((unsigned)q.i, (unsigned)ncell, (unsigned)a.nx, p, x, y);
-            }
-            q.jy = p / NV;
-            q.jx = p % NV;
-            load_raw<NV>(a, f, q.jx, q.jy, x, y, q.r);
-        }
-    };
-    // features of q into A1 (zeros past the end); X kept for the output bounds
-    auto store_a1 = [&](const Cell& q, float (&X)[kLNF]) {
-        if (q.on) {
-            features_of<NV>(a, q.r, q.jx, q.jy, X);
-        } else {
-#pragma unroll
-            for (int k = 0; k < kLNF; ++k) X[k] = 0.f;
-        }
+    // features of q into row t of A1 (zeros past the end)
+    auto stage = [&](typename Feed::Slot& q) {
+        float X[kLNF];
+        feed.features(q, X);
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
-            uint4 w;
-            w.x = pack_bf16(X[8 * h + 0], X[8 * h + 1]);
-            w.y = pack_bf16(X[8 * h + 2], X[8 * h + 3]);
-            w.z = pack_bf16(X[8 * h + 4], X[8 * h + 5]);
-            w.w = pack_bf16(X[8 * h + 6], X[8 * h + 7]);
-            *reinterpret_cast<uint4*>(A1 + tile_off(t, 8 * h, 128)) = w;
+            uint4 v;
+            v.x = pack_bf16(X[8 * h + 0], X[8 * h + 1]);
+            v.y = pack_bf16(X[8 * h + 2], X[8 * h + 3]);
+            v.z = pack_bf16(X[8 * h + 4], X[8 * h + 5]);
+            v.w = pack_bf16(X[8 * h + 6], X[8 * h + 7]);
+            *reinterpret_cast<uint4*>(A1 + tile_off(t, 8 * h, 128)) = v;
         }
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     };
@@ -354,17 +491,14 @@ __global__ void __launch_bounds__(128) k_mlp_tc(const LearnArgs a, const unsigne
         __syncthreads();
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     };
-    // One tile: the MMAs of `cur` (features already in A1) while `nxt`, the block's next tile,
-    // is loaded and staged.  Two Cell/feature sets alternate, so nothing is copied per tile.
-    auto one_tile = [&](long long tile, const Cell& cur, const float (&Xc)[kLNF], Cell& nxt,
-                        float (&Xn)[kLNF]) -> bool {
-        // layer 1: D = A1 (128 x 16) W1^T, while the next tile's features load
+    auto one_tile = [&](const typename Feed::Slot& cur, typename Feed::Slot& nxt) -> bool {
+        // layer 1: D = A1 (128 x 16) W1^T, while the next tile's inputs load
         sync_for_mma();
         if (t == 0) {
             mma(tmem, sdesc(a1, 2048, 128), sdesc(wbase + kW1T, 1024, 128), idesc_n(64), 0);
             commit(bar);
         }
-        load(tile + gridDim.x, nxt);
+        feed.load(nxt);
         if (!wait_mma()) return false;
         epilogue64(trow, A2, t);
         // layer 2: D = [H1 1 0] (128 x 80) W2^T; A1 is free again: stage the next features
@@ -376,7 +510,7 @@ __global__ void __launch_bounds__(128) k_mlp_tc(const LearnArgs a, const unsigne
                     sdesc(wbase + kW2T + kk * 2 * 1024, 1024, 128), idesc_n(64), kk);
             commit(bar);
         }
-        store_a1(nxt, Xn);
+        stage(nxt);
         if (!wait_mma()) return false;
         epilogue64(trow, A2, t);  // MMA 2 is done with A2: overwrite with H2
         // layer 3: D[0..15] = [H2 1 0] (128 x 80) W3^T
@@ -391,35 +525,24 @@ __global__ void __launch_bounds__(128) k_mlp_tc(const LearnArgs a, const unsigne
         if (!wait_mma()) return false;
         float z0, z1;
         tmem_ld2(trow, z0, z1);
-        if (cur.on) {
-            const float y0 = __fmul_rn(z0 > 0.f ? anti_bound(Xc[13], a.g) : kYMax, tanh_fast(z0));
-            const float y1 = __fmul_rn(z1 > 0.f ? anti_bound(Xc[14], a.g) : kYMax, tanh_fast(z1));
-            const unsigned gi = (unsigned)cur.i;
-            // f* of the cell and of its +jx, +jy neighbours: entries 4, 5 and 7 of the 3 x 3 block
-            a.G[gi] = cur.jx < NV - 1 ? __fmul_rn(y0, __fsub_rn(cur.r.fs[5], cur.r.fs[4])) : 0.f;
-            a.G[(size_t)n + gi] =
-                cur.jy < NV - 1 ? __fmul_rn(y1, __fsub_rn(cur.r.fs[7], cur.r.fs[4])) : 0.f;
-        }
+        feed.out(cur, z0, z1);
         // the next layer-1 MMA (after sync_for_mma) overwrites D only once every thread has read it
         return true;
     };
-    Cell c0, c1;
-    float X0[kLNF], X1[kLNF];
-    long long tile = blockIdx.x;
-    load(tile, c0);
-    store_a1(c0, X0);
-    while (tile < ntiles) {
-        if (!one_tile(tile, c0, X0, c1, X1)) {
+    typename Feed::Slot s0, s1;
+    bool failed = false;
+    feed.load(s0);
+    stage(s0);
+    while (s0.valid) {
+        if (!one_tile(s0, s1)) {
             failed = true;
             break;
         }
-        tile += gridDim.x;
-        if (tile >= ntiles) break;
-        if (!one_tile(tile, c1, X1, c0, X0)) {
+        if (!s1.valid) break;
+        if (!one_tile(s1, s0)) {
             failed = true;
             break;
         }
-        tile += gridDim.x;
     }
     if (failed && t == 0) atomicOr(const_cast<unsigned*>(&a.st->status), ST_TIMEOUT);
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -428,6 +551,28 @@ __global__ void __launch_bounds__(128) k_mlp_tc(const LearnArgs a, const unsigne
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
                      "r"(kTmemCols)
                      : "memory");
+}
+
+// the state buffer a step reads: parity (st->step + kstep) & 1, chosen without indexing the
+// kernel's parameters
+__device__ __forceinline__ const float* state_in(const LearnArgs& a, int kstep) {
+    return ((a.st->step + kstep) & 1) ? a.f[1] : a.f[0];
+}
+
+template <int NV>
+__global__ void __launch_bounds__(128) k_mlp_tc(const LearnArgs a, const unsigned char* image,
+                                                int kstep) {
+    extern __shared__ __align__(1024) unsigned char sm[];
+    StorageFeed<NV> feed(a, state_in(a, kstep), threadIdx.x);
+    run_network(feed, sm, image, a);
+}
+
+template <int NV>
+__global__ void __launch_bounds__(128) k_mlp_tc_units(const LearnArgs a,
+                                                      const unsigned char* image, int kstep) {
+    extern __shared__ __align__(1024) unsigned char sm[];
+    UnitFeed<NV> feed(a, state_in(a, kstep), threadIdx.x);
+    run_network(feed, sm, image, a);
 }
 
 // Parameter image: the BF16 B operands of the three layers, biases folded in (b1 into row 15 of
@@ -890,13 +1035,14 @@ cudaError_t launch_mlp_bwd_tc(int nv, const LearnBwdArgs& b, const void* wtc, in
     }
 }
 
-cudaError_t launch_mlp_tc(int nv, const LearnArgs& a, const void* wtc, int sm_count, int k,
-                          cudaStream_t s) {
+cudaError_t launch_mlp_tc(int nv, const LearnArgs& a, const void* wtc, int sm_count, bool units,
+                          int k, cudaStream_t s) {
     const long long n = (long long)a.nx * a.ny * nv * nv;
+    const bool by_units = units && a.nx % 128 == 0;
+    const long long work = by_units ? (long long)a.ny * (a.nx / 128) : (n + 127) / 128;
     // five resident CTAs per SM: 5 x 64 TMEM columns and 5 x 40 KB of shared memory
-    const int grid = (int)std::max<long long>(1, std::min<long long>((n + 127) / 128, 5LL * sm_count));
+    const int grid = (int)std::max<long long>(1, std::min<long long>(work, 5LL * sm_count));
     const unsigned char* img = static_cast<const unsigned char*>(wtc);
-    const FastDiv nbx = fast_div((unsigned)std::max(1, a.nx / 128));
     switch (nv) {
 #define X(nn)                                                                                   \
     case nn: {                                                                                  \
@@ -905,10 +1051,14 @@ cudaError_t launch_mlp_tc(int nv, const LearnArgs& a, const void* wtc, int sm_co
             cudaError_t e = cudaFuncSetAttribute(k_mlp_tc<nn>,                                  \
                                                  cudaFuncAttributeMaxDynamicSharedMemorySize,   \
                                                  kSmemReq);                                     \
+            if (e == cudaSuccess)                                                               \
+                e = cudaFuncSetAttribute(k_mlp_tc_units<nn>,                                    \
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemReq); \
             if (e != cudaSuccess) return e;                                                     \
             attr = true;                                                                        \
         }                                                                                       \
-        k_mlp_tc<nn><<<grid, 128, kSmemReq, s>>>(a, img, k, nbx);                               \
+        if (by_units) k_mlp_tc_units<nn><<<grid, 128, kSmemReq, s>>>(a, img, k);                \
+        else k_mlp_tc<nn><<<grid, 128, kSmemReq, s>>>(a, img, k);                               \
         return cudaGetLastError();                                                              \
     }
         LEARN_TC_NV_LIST(X)

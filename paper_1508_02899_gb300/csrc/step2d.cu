@@ -1439,7 +1439,7 @@ cudaError_t launch_corrected(const Ctx2D* c, const Step2DArgs& a, int k, cudaStr
 int enqueue_learned(Ctx2D* c, const Step2DArgs& a, int k, cudaStream_t s) {
     const LearnArgs la = learn_args(c, a.f[0], a.f[1], a.st);
     CK2(launch_rho_star(c->nv, la, k, s));
-    if (c->learn == 2) CK2(launch_mlp_tc(c->nv, la, c->d_wtc, c->sm_count, k, s));
+    if (c->learn == 2) CK2(launch_mlp_tc(c->nv, la, c->d_wtc, c->sm_count, c->ring, k, s));
     else CK2(launch_mlp_f32(c->nv, la, k, s));
     CK2(launch_corrected(c, a, k, s));
     return LAT_OK;
@@ -2012,7 +2012,7 @@ int ctx2d_learn_corr(Ctx2D* c, void* const f[2], int cur, float* G_out, int reus
     }
     const LearnArgs la = learn_args(c, f[cur], f[cur], c->d_st0);
     if (!reuse) CK2(launch_rho_star(c->nv, la, 0, s));
-    if (c->learn == 2) CK2(launch_mlp_tc(c->nv, la, c->d_wtc, c->sm_count, 0, s));
+    if (c->learn == 2) CK2(launch_mlp_tc(c->nv, la, c->d_wtc, c->sm_count, c->ring, 0, s));
     else CK2(launch_mlp_f32(c->nv, la, 0, s));
     if (G_out) {
         const size_t n = (size_t)2 * c->nv * c->nv * c->nx * c->ny;
@@ -2091,7 +2091,7 @@ int ctx2d_learn_grad(Ctx2D* c, void* const f[2], int cur, int n, const float* ta
             a.u = la.u;
             // the network of the context's mode: FP32 on CUDA cores, or BF16 on tensor cores
             if (launch_rho_star(c->nv, la, 0, s) != cudaSuccess ||
-                (c->learn == 2 ? launch_mlp_tc(c->nv, la, c->d_wtc, c->sm_count, 0, s)
+                (c->learn == 2 ? launch_mlp_tc(c->nv, la, c->d_wtc, c->sm_count, c->ring, 0, s)
                                : launch_mlp_f32(c->nv, la, 0, s)) != cudaSuccess ||
                 launch_corrected(c, a, 0, s) != cudaSuccess)
                 fail(LAT_ECUDA);

@@ -108,8 +108,9 @@ def test_fp32_network_matches_oracle(lat, nx, ny, nv):
 @pytest.mark.parametrize("nx,ny,nv", [(32, 20, 9), (150, 6, 5), (48, 16, 17), (256, 12, 9),
                                      (128, 7, 5)])
 def test_tensor_core_network_matches_oracle(lat, nx, ny, nv):
-    """Ragged 128-cell tiles in storage order, and (N_x a multiple of 128) row tiles taken planes
-    first."""
+    """Ragged 128-cell tiles in storage order (N_x = 128 is below the copy ring's window, so
+    its launch keeps plain loads and storage order too), and with N_x = 256 units of 128 x taken
+    plane by plane."""
     c = case(nx, ny, nv, 4, 11 + nx)
     W = quantised_weights(5, 0.4)
     want = Lr.rollout(c["f0"], W, 4, c["flows"], **c["kw"])
@@ -145,6 +146,32 @@ def test_corrected_step_on_the_ring_gives_the_plain_bits(lat, mode, nx, ny, nv):
         out.append(lt.state.cpu().numpy())
         lt.close()
     assert np.array_equal(out[0], out[1])
+
+
+@pytest.mark.parametrize("nx,ny,nv", [(256, 10, 9), (512, 7, 3), (384, 9, 5), (256, 12, 17)])
+def test_unit_order_network_gives_the_storage_order_bits(lat, nx, ny, nv):
+    """Tensor-core network with N_x a multiple of 128: units of 128 x taken plane by plane with
+    the velocity neighbourhood slid along each plane row (the default launch) against tiles in
+    storage order that gather all nine neighbours (launch kernel 1); the corrections must be the
+    same bits, and so must the state after three learned steps."""
+    c = case(nx, ny, nv, 3, 41 + nv)
+    W = quantised_weights(13, 0.5)
+    G, S = [], []
+    for plain in (True, False):
+        lt = lattice(lat, c)
+        if plain:
+            lt.set_launch(kernel=1)
+        lt.learn(pack(W), 2)
+        out = torch.empty((2, nv * nv * ny * nx), dtype=torch.float32, device="cuda")
+        lt.learn_corrections(out)
+        lt.step(3)
+        assert lt.status() == 0
+        G.append(out.cpu().numpy())
+        S.append(lt.state.cpu().numpy())
+        lt.close()
+    assert np.abs(G[1]).sum() > 0
+    assert np.array_equal(G[0], G[1])
+    assert np.array_equal(S[0], S[1])
 
 
 @pytest.mark.parametrize("mode", [1, 2])
